@@ -1,0 +1,148 @@
+"""Linear solvers for the oracle's Newton systems.
+
+DenseSolver     inertia by the signs of the eigenvalues of K (Sylvester's law
+                of inertia: the definition, via LAPACK's symmetric
+                eigensolver) and the solution by LAPACK's LU solve.  For the
+                tiny systems of the toys and the 30-bus case.
+SparseLDLSolver pivot-free LDL^T (D diagonal, "signed Cholesky", Section IV-B)
+                of P K P' under a given fill-reducing permutation, by the
+                plain left-looking column algorithm in ``ldlt.c``; inertia
+                from the signs of D.  Pinned against DenseSolver.
+dense_ldlt      pivot-free dense LDL^T written out in numpy (for the pins).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+import scipy.sparse as sp
+
+
+class DenseSolver:
+    def __init__(self, zero_tol: float = 0.0):
+        self.zero_tol = zero_tol
+        self.K = None
+
+    def factor(self, K):
+        Kd = K.toarray() if sp.issparse(K) else np.asarray(K)
+        self.K = Kd
+        ev = np.linalg.eigvalsh(Kd)
+        tol = self.zero_tol * max(1.0, np.abs(ev).max())
+        return int((ev > tol).sum()), int((ev < -tol).sum()), int((np.abs(ev) <= tol).sum())
+
+    def solve(self, b):
+        return np.linalg.solve(self.K, b)
+
+
+def dense_ldlt(K):
+    """K = L D L' with unit lower-triangular L and diagonal D, no pivoting.
+
+    Column j: d_j = K_jj - sum_k L_jk^2 d_k;  L_ij = (K_ij - sum_k L_ik d_k L_jk) / d_j.
+    """
+    K = np.asarray(K, dtype=float)
+    n = K.shape[0]
+    L = np.eye(n)
+    d = np.zeros(n)
+    for j in range(n):
+        d[j] = K[j, j] - np.sum(L[j, :j] ** 2 * d[:j])
+        if j + 1 < n:
+            L[j + 1:, j] = (K[j + 1:, j] - L[j + 1:, :j] @ (d[:j] * L[j, :j])) / d[j]
+    return L, d
+
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_LIB = None
+
+
+def build_c(force: bool = False) -> str:
+    """Compile ``ldlt.c`` into ``_oracle_ldlt.so`` (plain gcc, -O2)."""
+    src = os.path.join(_HERE, "ldlt.c")
+    out = os.path.join(_HERE, "_oracle_ldlt.so")
+    if force or not os.path.exists(out) or os.path.getmtime(out) < os.path.getmtime(src):
+        subprocess.check_call(["gcc", "-O2", "-fPIC", "-shared", "-o", out, src, "-lm"])
+    return out
+
+
+def _lib():
+    global _LIB
+    if _LIB is None:
+        lib = ctypes.CDLL(build_c())
+        i64p = ctypes.POINTER(ctypes.c_int64)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_ldlt_symbolic.argtypes = [ctypes.c_int64, i64p, i64p, i64p, i64p]
+        lib.oracle_ldlt_symbolic.restype = ctypes.c_int64
+        lib.oracle_ldlt_numeric.argtypes = [ctypes.c_int64, i64p, i64p, dp, i64p, i64p,
+                                            i64p, dp, dp, ctypes.c_double]
+        lib.oracle_ldlt_numeric.restype = ctypes.c_int64
+        lib.oracle_ldlt_solve.argtypes = [ctypes.c_int64, i64p, i64p, dp, dp, dp]
+        lib.oracle_ldlt_solve.restype = None
+        _LIB = lib
+    return _LIB
+
+
+def _p(a, t):
+    return a.ctypes.data_as(ctypes.POINTER(t))
+
+
+class SparseLDLSolver:
+    """Pivot-free sparse LDL^T of P K P' (P from ``perm``: new row i = old perm[i])."""
+
+    def __init__(self, perm_fn=None, pivot_tol: float = 0.0):
+        self.perm_fn = perm_fn
+        self.pivot_tol = pivot_tol
+        self.perm = None
+        self.pattern_key = None
+
+    def factor(self, K):
+        lib = _lib()
+        K = sp.csr_matrix(K)
+        n = K.shape[0]
+        if self.perm is None or self.perm.shape[0] != n:
+            self.perm = (np.asarray(self.perm_fn(K), dtype=np.int64) if self.perm_fn
+                         else np.arange(n, dtype=np.int64))
+        perm = self.perm
+        iperm = np.empty(n, dtype=np.int64)
+        iperm[perm] = np.arange(n)
+        # upper triangle of the permuted matrix, stored by columns (CSC)
+        Kp = K[perm][:, perm]
+        U = sp.triu(Kp, format="csc")
+        U.sum_duplicates()
+        U.sort_indices()
+        Ap = U.indptr.astype(np.int64)
+        Ai = U.indices.astype(np.int64)
+        Ax = U.data.astype(np.float64)
+        parent = np.zeros(n, dtype=np.int64)
+        Lnz = np.zeros(n, dtype=np.int64)
+        Lp = np.zeros(n + 1, dtype=np.int64)
+        lib.oracle_ldlt_symbolic(n, _p(Ap, ctypes.c_int64), _p(Ai, ctypes.c_int64),
+                                 _p(parent, ctypes.c_int64), _p(Lnz, ctypes.c_int64))
+        Lp[1:] = np.cumsum(Lnz)
+        Li = np.zeros(max(1, Lp[-1]), dtype=np.int64)
+        Lx = np.zeros(max(1, Lp[-1]))
+        D = np.zeros(n)
+        lib.oracle_ldlt_numeric(n, _p(Ap, ctypes.c_int64), _p(Ai, ctypes.c_int64),
+                                _p(Ax, ctypes.c_double), _p(parent, ctypes.c_int64),
+                                _p(Lp, ctypes.c_int64), _p(Li, ctypes.c_int64),
+                                _p(Lx, ctypes.c_double), _p(D, ctypes.c_double), self.pivot_tol)
+        self.n, self.iperm, self.Lp, self.Li, self.Lx, self.D = n, iperm, Lp, Li, Lx, D
+        self.nnzL = int(Lp[-1])
+        tol = self.pivot_tol
+        return int((D > tol).sum()), int((D < -tol).sum()), int((np.abs(D) <= tol).sum())
+
+    def solve(self, b):
+        lib = _lib()
+        x = np.ascontiguousarray(b[self.perm], dtype=np.float64)
+        out = np.zeros(self.n)
+        lib.oracle_ldlt_solve(self.n, _p(self.Lp, ctypes.c_int64), _p(self.Li, ctypes.c_int64),
+                              _p(self.Lx, ctypes.c_double), _p(self.D, ctypes.c_double),
+                              _p(x, ctypes.c_double))
+        out[self.perm] = x
+        return out
+
+    def factors(self):
+        """(L as CSC with unit diagonal, D) of the permuted matrix."""
+        n = self.n
+        L = sp.csc_matrix((self.Lx[:self.nnzL], self.Li[:self.nnzL], self.Lp), shape=(n, n))
+        return (L + sp.eye(n)).tocsc(), self.D.copy()

@@ -1,0 +1,291 @@
+"""Symbolic analysis of the block-arrow KKT matrix (oracle).
+
+The pivot-free factorisation of eq. (newtonsystem) (Section IV-B) allows the
+whole symbolic analysis to be done once per structure.  The paper leaves the
+ordering to cuDSS; this build fixes one deterministic algorithm, implemented
+twice (here and in the CUDA library) and compared bit for bit:
+
+1. Each scenario block is compressed to a *node graph* whose nodes keep the
+   primal and dual rows of one physical element together:
+     bus b      : theta_b (b != ref), v_b (if a variable of the block), Pbal_b, Qbal_b
+     branch l   : (limited branches only) sigma_f, sigma_t, therm_f, therm_t
+     generator g: base: q_g; contingency: p, q, pi_-, pi_+, sig_pmax, sig_pmin,
+                  [nu_-, nu_+, sig_qmax, sig_qmin], droop, sig_pmax-row,
+                  sig_pmin-row, [pvpq, sig_qmax-row, sig_qmin-row],
+                  comp(pi_-), comp(pi_+), [comp(nu_-), comp(nu_+)]
+                  (bracketed rows only for switch-set buses)
+     Delta      : Delta^k (contingencies)
+     border     : p_g^0 (every generator), v_b^0 (every PV bus) -- the
+                  first-stage variables u0 = (p_g^0, v_PV^0) of Section II-B.
+   Node ids: buses, then limited in-service branches, then in-service
+   generators, then Delta, then border nodes (p^0 by generator, v^0 by PV bus).
+   Two nodes are adjacent when a nonzero of the block's KKT matrix couples
+   one of their rows.
+2. Exact minimum degree on the elimination graph: repeatedly eliminate the
+   non-border node of smallest current degree (ties: smallest node id); its
+   neighbours become a clique.  Border nodes are never chosen: they come last.
+3. Node elimination tree: parent(p) = the neighbour of p at its elimination
+   with the earliest elimination position.  All border nodes form one final
+   "border" supernode whose front collects the Schur-complement contribution.
+4. Postorder of the tree (children visited in increasing node id).
+5. Fundamental supernodes, then relaxed amalgamation of only-child chains
+   while the merged supernode has at most ``relax_max_nodes`` nodes.
+6. Rows: nodes in postorder, each node's rows in the order of step 1, then
+   the border rows.
+
+Parity: integer, compared exactly with the CUDA implementation; pinned by
+brute-force dense boolean elimination (fill and tree) and hand-checked
+minimum-degree orders on path and grid graphs in the tests.
+"""
+from __future__ import annotations
+
+import heapq
+
+import numpy as np
+
+
+class BlockGraph:
+    """Node graph of one scenario block with the generic KKT rows of each node."""
+
+    def __init__(self, node_rows, adj, n_block_nodes):
+        self.node_rows = node_rows          # list of arrays (generic KKT indices)
+        self.adj = adj                      # list of sets of node ids
+        self.n_block = n_block_nodes        # nodes [0, n_block) are eliminable
+        self.n_nodes = len(node_rows)
+
+
+def block_graphs(model):
+    """Build the node graph of every block of a ``SCOPFModel``."""
+    M = model
+    n, m = M.n, M.m
+    out = []
+    for blk in M.blocks:
+        rows = []
+        # ---- bus nodes
+        for b in range(M.nb):
+            r = []
+            if blk.th[b] >= 0:
+                r.append(blk.gth[b])
+            if blk.v[b] >= 0:
+                r.append(blk.gv[b])
+            r += [n + blk.grP[b], n + blk.grQ[b]]
+            rows.append(r)
+        # ---- limited branch nodes
+        for j, l in enumerate(blk.thermal):
+            rows.append([blk.gsth[j, 0], blk.gsth[j, 1], n + blk.grth[j, 0], n + blk.grth[j, 1]])
+        # ---- generator nodes
+        ngk = len(blk.gens) if blk.k > 0 else 0
+        nsw = len(blk.switch) if blk.k > 0 else 0
+        sw_of_gen = {int(g): si for si, g in enumerate(blk.sw_gen)} if blk.k > 0 else {}
+        for gi, g in enumerate(blk.gens):
+            if blk.k == 0:
+                rows.append([blk.gq[g]])
+                continue
+            r = [blk.gp[g], blk.gq[g], blk.gpim[gi], blk.gpip[gi], blk.gspu[gi], blk.gspl[gi]]
+            si = sw_of_gen.get(int(g), -1)
+            if si >= 0:
+                r += [blk.gnum[si], blk.gnup[si], blk.gsqu[si], blk.gsql[si]]
+            r += [n + blk.grdroop[gi], n + blk.grspu[gi], n + blk.grspl[gi]]
+            if si >= 0:
+                r += [n + blk.grpvpq[si], n + blk.grsqu[si], n + blk.grsql[si]]
+            base = n + m + blk.p0
+            r += [base + gi, base + ngk + gi]
+            if si >= 0:
+                r += [base + 2 * ngk + si, base + 2 * ngk + nsw + si]
+            rows.append(r)
+        if blk.k > 0:
+            rows.append([blk.gdelta])
+        n_block = len(rows)
+        for g in range(M.ng):
+            rows.append([M.border0 + g])
+        for q in range(M.npv):
+            rows.append([M.border0 + M.ng + q])
+        out.append(BlockGraph([np.asarray(r, dtype=np.int64) for r in rows], None, n_block))
+    return out
+
+
+def attach_adjacency(graphs, K):
+    """Node adjacency from the pattern of the reduced KKT matrix ``K`` (generic order)."""
+    import scipy.sparse as sp
+    Kc = sp.csr_matrix(K)
+    owner_blk = np.full(Kc.shape[0], -1, dtype=np.int64)
+    for gi, G in enumerate(graphs):
+        node_of = {}
+        for nid, r in enumerate(G.node_rows):
+            for x in r.tolist():
+                node_of[x] = nid
+        G.node_of = node_of
+    for gi, G in enumerate(graphs):
+        adj = [set() for _ in range(G.n_nodes)]
+        for nid in range(G.n_block):
+            for x in G.node_rows[nid].tolist():
+                for y in Kc.indices[Kc.indptr[x]:Kc.indptr[x + 1]].tolist():
+                    other = G.node_of.get(y, -1)
+                    if other >= 0 and other != nid:
+                        adj[nid].add(other)
+                        adj[other].add(nid)
+        G.adj = adj
+    return graphs
+
+
+def min_degree(adj, n_block):
+    """Exact minimum degree with smallest-id tie-break; nodes >= n_block are
+    never eliminated.  Returns (order, struct) where struct[p] is the set of
+    neighbours of p when it was eliminated."""
+    n = len(adj)
+    A = [set(a) for a in adj]
+    heap = [(len(A[v]), v) for v in range(n_block)]
+    heapq.heapify(heap)
+    alive = [True] * n
+    order = []
+    struct = [None] * n
+    while heap:
+        d, v = heapq.heappop(heap)
+        if not alive[v] or d != len(A[v]):
+            continue
+        alive[v] = False
+        order.append(v)
+        nb = A[v]
+        struct[v] = set(nb)
+        for u in nb:
+            A[u] |= nb
+            A[u].discard(u)
+            A[u].discard(v)
+            if u < n_block:
+                heapq.heappush(heap, (len(A[u]), u))
+        A[v] = set()
+    return order, struct
+
+
+class Symbolic:
+    """Symbolic analysis of one block (see the module docstring)."""
+
+    def __init__(self, G: BlockGraph, relax_max_nodes: int = 8):
+        order, struct = min_degree(G.adj, G.n_block)
+        nb_nodes = G.n_block
+        self.elim_order = order
+        pos = np.full(G.n_nodes, -1, dtype=np.int64)
+        pos[order] = np.arange(len(order))
+        BORDER = -2
+        parent = np.full(nb_nodes, -1, dtype=np.int64)
+        for v in order:
+            st = [u for u in struct[v]]
+            inblk = [u for u in st if u < nb_nodes]
+            if inblk:
+                parent[v] = min(inblk, key=lambda u: pos[u])
+            elif st:
+                parent[v] = BORDER
+            else:
+                parent[v] = -1       # isolated from the border (not expected)
+        # postorder, children in increasing node id; roots (border children
+        # and isolated nodes) also in increasing id
+        children = [[] for _ in range(nb_nodes)]
+        roots = []
+        for v in range(nb_nodes):
+            if parent[v] >= 0:
+                children[parent[v]].append(v)
+            else:
+                roots.append(v)
+        post = []
+        for r0 in roots:
+            stack = [(r0, 0)]
+            while stack:
+                v, i = stack.pop()
+                if i < len(children[v]):
+                    stack.append((v, i + 1))
+                    stack.append((children[v][i], 0))
+                else:
+                    post.append(v)
+        self.post = np.array(post, dtype=np.int64)           # node ids in postorder
+        ppos = np.full(G.n_nodes, -1, dtype=np.int64)
+        ppos[self.post] = np.arange(nb_nodes)
+        n_border = G.n_nodes - nb_nodes
+        ppos[nb_nodes:] = nb_nodes + np.arange(n_border)
+        self.ppos = ppos
+        self.parent = parent
+        self.struct = struct
+        # ---- supernodes over the postorder
+        cnt = np.array([len(struct[v]) for v in range(nb_nodes)], dtype=np.int64)
+        nchild = np.array([len(c) for c in children], dtype=np.int64)
+        starts = [0]
+        size = 1
+        for i in range(1, nb_nodes):
+            v, u = self.post[i], self.post[i - 1]
+            # an only child directly below its parent in the postorder joins the
+            # parent's supernode (fundamental when cnt[u] == cnt[v] + 1, relaxed
+            # otherwise) while the supernode stays within relax_max_nodes nodes
+            chain = parent[u] == v and nchild[v] == 1
+            if chain and size < relax_max_nodes:
+                size += 1
+            else:
+                starts.append(i)
+                size = 1
+        starts.append(nb_nodes)
+        self.sn_start = np.array(starts, dtype=np.int64)      # in postorder positions
+        nsn = len(starts) - 1
+        sn_of = np.zeros(nb_nodes, dtype=np.int64)
+        for s in range(nsn):
+            sn_of[self.sn_start[s]:self.sn_start[s + 1]] = s
+        self.sn_of_pos = sn_of
+        # update nodes of each supernode: union of member structs minus members,
+        # sorted by postorder position (border nodes last, in id order)
+        upd = []
+        sn_parent = np.full(nsn, -1, dtype=np.int64)      # -2 = border supernode
+        for s in range(nsn):
+            members = self.post[self.sn_start[s]:self.sn_start[s + 1]]
+            mset = set(members.tolist())
+            u = set()
+            for v in members.tolist():
+                u |= struct[v]
+            u -= mset
+            ul = sorted(u, key=lambda x: ppos[x])
+            upd.append(np.array(ul, dtype=np.int64))
+            inb = [x for x in ul if x < nb_nodes]
+            if inb:
+                sn_parent[s] = sn_of[ppos[inb[0]]]
+            elif ul:
+                sn_parent[s] = -2
+        self.sn_update_nodes = upd
+        self.sn_parent = sn_parent
+        self.n_sn = nsn
+        # ---- row permutation (generic KKT indices in elimination order)
+        rows = [G.node_rows[v] for v in self.post.tolist()] + \
+               [G.node_rows[v] for v in range(nb_nodes, G.n_nodes)]
+        self.rows = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+        self.n_block_rows = int(sum(len(G.node_rows[v]) for v in range(nb_nodes)))
+
+
+def structural_kkt(model, seed: int = 12345):
+    """Reduced KKT matrix at a random interior point: every structurally
+    nonzero entry is numerically nonzero (with probability one)."""
+    from .ncl import NCLSolver, Params, State
+    from .linsolve import DenseSolver
+    rng = np.random.default_rng(seed)
+    S = NCLSolver(model, DenseSolver())
+    st = S.initial_state()
+    n, m, p = model.n, model.m, model.p
+    st.w = st.w + 1e-3 * rng.random(n)
+    st.lam = rng.standard_normal(m)
+    st.yc = rng.random(p) + 0.5
+    st.s = rng.random(p) + 0.5
+    st.zs = rng.random(p) + 0.5
+    st.zl = rng.random(len(S.il)) + 0.5
+    st.zu = rng.random(len(S.iu)) + 0.5
+    prm = Params(rho=10.0, lam_n=np.zeros(m), nu0_n=np.zeros(p))
+    H = model.hessian(st.w, st.lam)
+    J = model.jacobian(st.w)
+    return S.kkt_matrix(st, prm, H, J, 0.5)
+
+
+def kkt_permutation(model, K=None, relax_max_nodes: int = 8):
+    """Global fill-reducing order of the reduced KKT matrix: each block's rows
+    in its symbolic order, blocks 0..K in turn, then the border rows.  The
+    node graphs come from the structural pattern (``structural_kkt``)."""
+    Ks = structural_kkt(model)
+    graphs = attach_adjacency(block_graphs(model), Ks)
+    syms = [Symbolic(G, relax_max_nodes) for G in graphs]
+    parts = [S.rows[:S.n_block_rows] for S in syms]
+    border = np.arange(model.border0, model.border0 + model.nborder, dtype=np.int64)
+    perm = np.concatenate(parts + [border])
+    assert len(perm) == Ks.shape[0] and len(np.unique(perm)) == Ks.shape[0]
+    return perm, syms
