@@ -1,0 +1,223 @@
+/*
+ * scopf.h -- C ABI of the B300 library for the Newton step of the NCL
+ * augmented-Lagrangian / interior-point method on polar AC-SCOPF with
+ * complementarity-modelled recourse (Pacaud, Nurkanovic, Pozharskiy,
+ * Montoison, Shin: "An Augmented Lagrangian Method on GPU for
+ * Security-Constrained AC Optimal Power Flow").
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns an int status: SCOPF_OK (0) or a negative
+ *    SCOPF_ERR_* code; scopf_strerror() names it.  No C++ exception crosses
+ *    this boundary.
+ *  - "host" pointers are read during the call only and copied; the caller
+ *    keeps ownership.  "device" pointers are CUDA global-memory pointers that
+ *    the caller owns and keeps alive until the call has returned (all calls
+ *    synchronise the handle's stream before returning, except where noted).
+ *  - A handle is not thread-safe; use one handle per host thread / stream.
+ *  - Floating point is IEEE FP64 unless stated otherwise.
+ *
+ * Vector layouts ("natural order")
+ *  Variables w = [block 0 | block 1 | ... | block K | border u0], where the
+ *  border u0 = (p_g^0 for every generator, v_b^0 for every PV bus in
+ *  increasing bus id) holds the first-stage controls of Section II-B.
+ *  Block 0 (base case): theta_b (b != ref), v_b (buses without generator),
+ *  q_g^0, thermal slacks (per limited branch: from end, to end).
+ *  Block k >= 1: theta_b (b != ref), v_b, p_g^k, q_g^k (generators in
+ *  service), Delta^k, thermal slacks, pi_-, pi_+, sig_pmax, sig_pmin (per
+ *  generator in service), nu_-, nu_+, sig_qmax, sig_qmin (per switch bus).
+ *  Equality rows c = [block 0 | ... | block K]; per block: Pbal_b, Qbal_b
+ *  (all buses), thermal rows (f, t per limited branch); k >= 1 adds droop,
+ *  sig_pmax-def, sig_pmin-def (per generator), pvpq, sig_qmax-def,
+ *  sig_qmin-def (per switch bus).  Complementarity pairs (p of them) are
+ *  [block 1 | ... | block K]; per block (pi_-, sig_pmax), (pi_+, sig_pmin)
+ *  per generator, then (nu_-, sig_qmax), (nu_+, sig_qmin) per switch bus.
+ *  KKT vectors of eq. (newtonsystem) are ordered per block
+ *  [dw_k ; dlam_k ; dyc_k] for k = 0..K, then du0.
+ */
+#ifndef SCOPF_H
+#define SCOPF_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes -------------------------------------------------- */
+#define SCOPF_OK 0
+#define SCOPF_ERR_INVALID_ARG -1
+#define SCOPF_ERR_CUDA -2
+#define SCOPF_ERR_NOT_FACTORED -3
+#define SCOPF_ERR_WRONG_INERTIA -4
+#define SCOPF_ERR_REFINE_STALL -5
+#define SCOPF_ERR_INFEASIBLE -6
+#define SCOPF_ERR_MAX_ITER -7
+#define SCOPF_ERR_TIMEOUT -8
+#define SCOPF_ERR_OOM -9
+#define SCOPF_ERR_NUMERICAL -10
+
+#define SCOPF_CTG_LINE 0
+#define SCOPF_CTG_GEN 1
+
+#define SCOPF_PREC_FP64 0   /* block factors and solves in FP64 */
+#define SCOPF_PREC_MIXED 1  /* FP32 block factors and solves, FP64 Schur factor,
+                               FP64 residual and refinement */
+
+typedef struct scopf_handle scopf_handle;
+
+/* Network (host arrays, copied by scopf_create).  Per unit on 100 MVA.
+ * Buses: Pd, Qd (load), Gs, Bs (shunt), vmin, vmax.
+ * Branches (pi-model, tap 1): from, to, r, x, b (total charging), rate
+ *   (apparent-power limit; 0 = unlimited).
+ * Generators: bus (at most one generator per bus), pmin, pmax, qmin, qmax,
+ *   cost c2 ($/MW^2h), c1 ($/MWh), c0 ($/h).  ref_bus: angle reference. */
+typedef struct {
+    int32_t n_bus, n_branch, n_gen, ref_bus;
+    const double *Pd, *Qd, *Gs, *Bs, *vmin, *vmax;
+    const int32_t *br_from, *br_to;
+    const double *br_r, *br_x, *br_b, *br_rate;
+    const int32_t *gen_bus;
+    const double *pmin, *pmax, *qmin, *qmax, *c2, *c1, *c0;
+} scopf_network;
+
+/* One contingency: loss of a line or a generator (Section II), with the set
+ * of PV buses whose voltage control follows eq. (pvpq) (host array). */
+typedef struct {
+    int32_t kind;      /* SCOPF_CTG_LINE or SCOPF_CTG_GEN */
+    int32_t element;   /* branch or generator index */
+    int32_t n_switch;
+    const int32_t *switch_buses;  /* sorted, each with an in-service generator */
+} scopf_contingency;
+
+/* Algorithm constants.  tol and mu_min follow Section V-A; the others are
+ * the published defaults of the NCL and interior-point methods the paper
+ * builds on.  scopf_default_options fills every field. */
+typedef struct {
+    double tol, mu_min, mu_init, kappa_eps, kappa_mu, theta_mu, tau_min, s_max;
+    double kappa_sigma, bound_relax, bound_push, bound_frac, slack_init, comp_init;
+    double delta_w0, delta_w_min, delta_w_max, kappa_w_minus, kappa_w_plus, kappa_w_plus_bar;
+    double gamma_theta, gamma_phi, delta_sw, s_theta, s_phi, eta_phi, gamma_alpha;
+    double rho_init, rho_max, eta_init, omega_init;
+    double refine_tol;        /* target |K dx - b|_inf / |b|_inf of kkt_solve */
+    double pivot_tol;         /* |d| below this counts as a zero pivot */
+    int32_t max_backtrack, max_outer, max_inner, max_refine;
+    int32_t precision;        /* SCOPF_PREC_FP64 or SCOPF_PREC_MIXED */
+    int32_t relax_max_nodes;  /* supernode amalgamation limit (nodes) */
+    int32_t verbose;
+    int32_t spin_limit;       /* bound on device-side dependency waits (polls) */
+    int32_t host_only;        /* 1: scopf_create builds the model and the symbolic
+                                 analysis only (no device memory is touched); the
+                                 device entry points then return
+                                 SCOPF_ERR_INVALID_ARG */
+} scopf_options;
+
+/* Sizes of the handle's problem. */
+typedef struct {
+    int64_t n, m, p;          /* variables, equality rows, complementarity pairs */
+    int64_t n_kkt;            /* rows of eq. (newtonsystem) = n + m + p */
+    int64_t n_border;         /* first-stage variables u0 */
+    int32_t n_blocks;         /* K + 1 */
+    int64_t nnz_kkt;          /* stored nonzeros of the full symmetric KKT */
+    int64_t nnz_L;            /* factor entries (supernodal, incl. explicit zeros) */
+    int64_t n_supernodes;
+    double factor_flops;      /* flops of one block factorisation (all blocks) */
+    int64_t front_bytes;      /* device bytes of the frontal storage */
+} scopf_sizes;
+
+/* Primal-dual iterate (device pointers, FP64).  zl and zu have length n and
+ * are read only where the bound is finite. */
+typedef struct {
+    double *w, *r, *t, *s, *lam, *yc, *zl, *zu, *zs;
+} scopf_state;
+
+/* Outcome of ncl_solve. */
+typedef struct {
+    int32_t status;           /* SCOPF_OK, SCOPF_ERR_INFEASIBLE, SCOPF_ERR_MAX_ITER, ... */
+    int32_t outer_iters, inner_iters, factorizations, refine_steps;
+    int32_t fp64_fallbacks;   /* mixed mode: Newton steps redone in FP64 */
+    double objective, kkt_error, feas_rt, max_violation, rho, mu;
+    double time_total_s, time_newton_s;
+} scopf_result;
+
+void scopf_default_options(scopf_options *opt);
+
+/* Build the model of eq. (scopf) for the network and K contingencies, its
+ * layouts, the KKT pattern and the symbolic analysis of every block, and
+ * allocate device memory.  opt may be NULL (defaults). */
+int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t K,
+                 const scopf_options *opt, scopf_handle **out);
+void scopf_destroy(scopf_handle *h);
+const char *scopf_strerror(int status);
+
+int scopf_get_sizes(scopf_handle *h, scopf_sizes *out);
+/* Run the handle's kernels on this CUDA stream (cudaStream_t); NULL = legacy default. */
+int scopf_set_stream(scopf_handle *h, void *stream);
+int scopf_set_precision(scopf_handle *h, int32_t precision);
+
+/* Symbolic analysis of block k (Section IV-B: static structure of the
+ * pivot-free factorisation).  Host output arrays sized by the call with
+ * NULL pointers first: *n_nodes, *n_block_nodes, *n_sn, *n_rows are always
+ * written.  post[n_block_nodes]: node ids in elimination (post)order;
+ * node_parent[n_block_nodes]: parent node id (-2 = border, -1 = none);
+ * sn_start[n_sn+1]: supernode boundaries in postorder positions;
+ * rows[n_rows]: KKT indices (global natural order) in elimination order,
+ * block rows then border rows. */
+int scopf_symbolic_block(scopf_handle *h, int32_t k, int32_t *n_nodes, int32_t *n_block_nodes,
+                         int32_t *n_sn, int32_t *n_rows, int32_t *post, int32_t *node_parent,
+                         int32_t *sn_start, int64_t *rows);
+
+/* Model evaluation (Section II / eq. mpcc) at device w, lam: the objective
+ * (host out), its gradient g[n], the constraint values c[m] (device).  Any
+ * output pointer may be NULL. */
+int scopf_eval(scopf_handle *h, const double *w, double *obj, double *g, double *c);
+
+/* KKT assembly (eq. newtonsystem) at the iterate: A = H + barrier diagonal
+ * + V0 coupling + delta_w I, B = [J; (0 W2 W1)], C = diag(1/rho, 1/rho +
+ * s/zs).  lam_n, nu0_n: NCL multiplier estimates (device, m and p).  Also
+ * forms the right-hand side for barrier parameter mu into rhs (device,
+ * n_kkt; may be NULL).  The values are kept on the device for kkt_factor. */
+int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n,
+                 const double *nu0_n, double rho, double mu, double delta_w, double *rhs);
+/* Copy the assembled KKT matrix out (device, CSR in natural KKT order):
+ * row_ptr[n_kkt+1], col[nnz] (int64) and val[nnz]; any may be NULL. */
+int kkt_export(scopf_handle *h, int64_t *row_ptr, int64_t *col, double *val);
+
+/* Pivot-free LDL^T of every block (one persistent launch), Schur complement
+ * onto u0 and its dense LDL^T.  inertia[0..2] = (#positive, #negative,
+ * #zero-or-tiny pivots) over the whole KKT (host out).  precision overrides
+ * the handle's setting for this factorisation (-1 = handle's). */
+int kkt_factor(scopf_handle *h, int32_t precision, int32_t inertia[3]);
+
+/* Solve K x = b with the last factorisation and FP64 iterative refinement
+ * against the assembled (unregularised delta_w = 0 part excluded only when
+ * delta_w was 0) matrix until |b - Kx|_inf <= refine_tol |b|_inf or
+ * max_refine steps (-1 = options).  b, x: device, n_kkt, natural KKT order
+ * (x may alias b).  rel_residual and steps (host out, may be NULL). */
+int kkt_solve(scopf_handle *h, const double *b, double *x, int32_t max_refine,
+              double *rel_residual, int32_t *steps);
+
+/* Full NCL solve (Section IV-A) from the flat start, or from warm (device
+ * state, may be NULL).  The final iterate stays in the handle. */
+int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);
+/* Device views of the handle's current iterate (owned by the handle). */
+int scopf_get_state(scopf_handle *h, scopf_state *out);
+/* Copy the handle's iterate into caller-owned device buffers (dst fields
+ * may be NULL to skip), or load it from src into the handle (src fields
+ * must all be set).  Stream-ordered; synchronised before return. */
+int scopf_copy_state(scopf_handle *h, const scopf_state *dst);
+int scopf_load_state(scopf_handle *h, const scopf_state *src);
+/* NCL multiplier estimates of the last solve (device views, m and p), rho. */
+int scopf_get_ncl_params(scopf_handle *h, double **lam_n, double **nu0_n, double *rho);
+
+/* Adjoint of the converged solution: gradients of
+ * J = seed_pg0' p_g^0 + seed_cost * objective with respect to the bus loads
+ * Pd, Qd (n_bus each) and the linear cost coefficients c1 (n_gen), by one
+ * transposed solve with the final factorisation (K is symmetric).
+ * seed_pg0: device, n_gen (may be NULL = zero); outputs device. */
+int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
+                  double *grad_Pd, double *grad_Qd, double *grad_c1);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SCOPF_H */

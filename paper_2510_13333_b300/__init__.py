@@ -1,0 +1,336 @@
+"""Python binding of the B300 SCOPF / NCL Newton-step library (ctypes).
+
+Argument marshalling only: every step of the method runs in the CUDA
+library ``libscopf_b300.so`` built from ``csrc/`` (see ``build.py``).  If the
+library cannot be loaded, importing the entry points raises -- there is no
+fallback.  PyTorch supplies device memory and the CUDA stream.
+
+The function names follow the C ABI of ``include/scopf.h``:
+``scopf_create``, ``kkt_assemble``, ``kkt_factor``, ``kkt_solve``,
+``ncl_solve``, ``scopf_adjoint`` ...; ``SCOPF`` bundles them around a handle.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libscopf_b300.so")
+
+c_i32, c_i64, c_dbl = ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+P_i32 = ctypes.POINTER(c_i32)
+P_i64 = ctypes.POINTER(c_i64)
+P_dbl = ctypes.POINTER(c_dbl)
+
+PREC_FP64 = 0
+PREC_MIXED = 1
+
+STATUS = {0: "ok", -1: "invalid argument", -2: "CUDA error", -3: "not factored",
+          -4: "wrong inertia", -5: "refinement stalled", -6: "infeasible", -7: "max iter",
+          -8: "timeout", -9: "out of memory", -10: "numerical failure"}
+
+
+class ScopfError(RuntimeError):
+    def __init__(self, fn, status):
+        super().__init__(f"{fn} failed: {STATUS.get(status, status)} ({status})")
+        self.status = status
+
+
+class Network(ctypes.Structure):
+    _fields_ = [("n_bus", c_i32), ("n_branch", c_i32), ("n_gen", c_i32), ("ref_bus", c_i32),
+                ("Pd", P_dbl), ("Qd", P_dbl), ("Gs", P_dbl), ("Bs", P_dbl), ("vmin", P_dbl),
+                ("vmax", P_dbl), ("br_from", P_i32), ("br_to", P_i32), ("br_r", P_dbl),
+                ("br_x", P_dbl), ("br_b", P_dbl), ("br_rate", P_dbl), ("gen_bus", P_i32),
+                ("pmin", P_dbl), ("pmax", P_dbl), ("qmin", P_dbl), ("qmax", P_dbl), ("c2", P_dbl),
+                ("c1", P_dbl), ("c0", P_dbl)]
+
+
+class Contingency(ctypes.Structure):
+    _fields_ = [("kind", c_i32), ("element", c_i32), ("n_switch", c_i32),
+                ("switch_buses", P_i32)]
+
+
+_OPT_DOUBLES = ["tol", "mu_min", "mu_init", "kappa_eps", "kappa_mu", "theta_mu", "tau_min",
+                "s_max", "kappa_sigma", "bound_relax", "bound_push", "bound_frac", "slack_init",
+                "comp_init", "delta_w0", "delta_w_min", "delta_w_max", "kappa_w_minus",
+                "kappa_w_plus", "kappa_w_plus_bar", "gamma_theta", "gamma_phi", "delta_sw",
+                "s_theta", "s_phi", "eta_phi", "gamma_alpha", "rho_init", "rho_max", "eta_init",
+                "omega_init", "refine_tol", "pivot_tol"]
+_OPT_INTS = ["max_backtrack", "max_outer", "max_inner", "max_refine", "precision",
+             "relax_max_nodes", "verbose", "spin_limit", "host_only"]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [(n, c_dbl) for n in _OPT_DOUBLES] + [(n, c_i32) for n in _OPT_INTS]
+
+
+class Sizes(ctypes.Structure):
+    _fields_ = [("n", c_i64), ("m", c_i64), ("p", c_i64), ("n_kkt", c_i64), ("n_border", c_i64),
+                ("n_blocks", c_i32), ("nnz_kkt", c_i64), ("nnz_L", c_i64),
+                ("n_supernodes", c_i64), ("factor_flops", c_dbl), ("front_bytes", c_i64)]
+
+
+_STATE_FIELDS = ["w", "r", "t", "s", "lam", "yc", "zl", "zu", "zs"]
+
+
+class State(ctypes.Structure):
+    _fields_ = [(n, P_dbl) for n in _STATE_FIELDS]
+
+
+class Result(ctypes.Structure):
+    _fields_ = [("status", c_i32), ("outer_iters", c_i32), ("inner_iters", c_i32),
+                ("factorizations", c_i32), ("refine_steps", c_i32), ("fp64_fallbacks", c_i32),
+                ("objective", c_dbl), ("kkt_error", c_dbl), ("feas_rt", c_dbl),
+                ("max_violation", c_dbl), ("rho", c_dbl), ("mu", c_dbl),
+                ("time_total_s", c_dbl), ("time_newton_s", c_dbl)]
+
+
+_LIB = None
+
+
+def lib():
+    """Load the CUDA library (raises if it was not built)."""
+    global _LIB
+    if _LIB is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError(f"{LIB_PATH} is missing; build it with "
+                              "`python -m paper_2510_13333_b300.build`")
+        L = ctypes.CDLL(LIB_PATH)
+        H = ctypes.c_void_p
+        sig = {
+            "scopf_default_options": (None, [ctypes.POINTER(Options)]),
+            "scopf_create": (c_i32, [ctypes.POINTER(Network), ctypes.POINTER(Contingency), c_i32,
+                                     ctypes.POINTER(Options), ctypes.POINTER(H)]),
+            "scopf_destroy": (None, [H]),
+            "scopf_strerror": (ctypes.c_char_p, [c_i32]),
+            "scopf_get_sizes": (c_i32, [H, ctypes.POINTER(Sizes)]),
+            "scopf_set_stream": (c_i32, [H, ctypes.c_void_p]),
+            "scopf_set_precision": (c_i32, [H, c_i32]),
+            "scopf_symbolic_block": (c_i32, [H, c_i32, P_i32, P_i32, P_i32, P_i32, P_i32, P_i32,
+                                             P_i32, P_i64]),
+            "scopf_eval": (c_i32, [H, P_dbl, P_dbl, P_dbl, P_dbl]),
+            "kkt_assemble": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl, c_dbl,
+                                     P_dbl]),
+            "kkt_export": (c_i32, [H, P_i64, P_i64, P_dbl]),
+            "kkt_factor": (c_i32, [H, c_i32, P_i32]),
+            "kkt_solve": (c_i32, [H, P_dbl, P_dbl, c_i32, P_dbl, P_i32]),
+            "ncl_solve": (c_i32, [H, ctypes.POINTER(State), ctypes.POINTER(Result)]),
+            "scopf_get_state": (c_i32, [H, ctypes.POINTER(State)]),
+            "scopf_copy_state": (c_i32, [H, ctypes.POINTER(State)]),
+            "scopf_load_state": (c_i32, [H, ctypes.POINTER(State)]),
+            "scopf_get_ncl_params": (c_i32, [H, ctypes.POINTER(P_dbl), ctypes.POINTER(P_dbl),
+                                             P_dbl]),
+            "scopf_adjoint": (c_i32, [H, P_dbl, c_dbl, P_dbl, P_dbl, P_dbl]),
+        }
+        for name, (res, args) in sig.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = L
+    return _LIB
+
+
+def exported_symbols():
+    """Names declared by include/scopf.h that the library must export."""
+    import re
+    hdr = open(os.path.join(_HERE, "..", "include", "scopf.h")).read()
+    return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?(\w+)\(", hdr, re.M)))
+
+
+def default_options(**kw) -> Options:
+    o = Options()
+    lib().scopf_default_options(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise KeyError(k)
+        setattr(o, k, v)
+    return o
+
+
+def _dp(t):
+    """Device pointer of a torch tensor (float64), or NULL."""
+    if t is None:
+        return None
+    import torch
+    assert t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()
+    return ctypes.cast(ctypes.c_void_p(t.data_ptr()), P_dbl)
+
+
+def _hp(a, ctype):
+    return a.ctypes.data_as(ctypes.POINTER(ctype))
+
+
+def _check(fn, status):
+    if status != 0:
+        raise ScopfError(fn, status)
+
+
+class SCOPF:
+    """A handle around one SCOPF instance (network + contingencies)."""
+
+    def __init__(self, inst, options: Options | None = None, **opt_kw):
+        L = lib()
+        net = inst.net
+        self._keep = []
+
+        def d(a):
+            a = np.ascontiguousarray(a, dtype=np.float64)
+            self._keep.append(a)
+            return _hp(a, c_dbl)
+
+        def i(a):
+            a = np.ascontiguousarray(a, dtype=np.int32)
+            self._keep.append(a)
+            return _hp(a, c_i32)
+
+        N = Network(net.n_bus, net.n_branch, net.n_gen, int(net.ref_bus), d(net.Pd), d(net.Qd),
+                    d(net.Gs), d(net.Bs), d(net.vmin), d(net.vmax), i(net.f), i(net.t), d(net.r),
+                    d(net.x), d(net.b), d(net.rate), i(net.gbus), d(net.pmin), d(net.pmax),
+                    d(net.qmin), d(net.qmax), d(net.c2), d(net.c1), d(net.c0))
+        K = len(inst.ctgs)
+        C = (Contingency * max(1, K))()
+        for k, c in enumerate(inst.ctgs):
+            C[k] = Contingency(int(c.kind), int(c.element), len(c.switch_buses), i(c.switch_buses))
+        o = options or default_options()
+        for k, v in opt_kw.items():
+            setattr(o, k, v)
+        self.options = o
+        self.host_only = bool(o.host_only)
+        self.n_bus, self.n_gen = net.n_bus, net.n_gen
+        h = ctypes.c_void_p()
+        _check("scopf_create", L.scopf_create(ctypes.byref(N), C, K, ctypes.byref(o),
+                                              ctypes.byref(h)))
+        self.h = h
+        s = Sizes()
+        _check("scopf_get_sizes", L.scopf_get_sizes(h, ctypes.byref(s)))
+        self.sizes = s
+        self._keep = []
+        if not self.host_only:
+            import torch
+            self.set_stream(torch.cuda.current_stream())
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h is not None and h.value:
+            try:
+                lib().scopf_destroy(h)
+            except Exception:
+                pass
+            self.h = None
+
+    # ------------------------------------------------------------ basics
+    def set_stream(self, stream):
+        _check("scopf_set_stream", lib().scopf_set_stream(self.h, ctypes.c_void_p(stream.cuda_stream)))
+
+    def set_precision(self, prec: int):
+        _check("scopf_set_precision", lib().scopf_set_precision(self.h, prec))
+
+    def scopf_symbolic_block(self, k: int):
+        L = lib()
+        nn, nbn, nsn, nr = c_i32(), c_i32(), c_i32(), c_i32()
+        _check("scopf_symbolic_block", L.scopf_symbolic_block(
+            self.h, k, ctypes.byref(nn), ctypes.byref(nbn), ctypes.byref(nsn), ctypes.byref(nr),
+            None, None, None, None))
+        post = np.zeros(nbn.value, dtype=np.int32)
+        par = np.zeros(nbn.value, dtype=np.int32)
+        sns = np.zeros(nsn.value + 1, dtype=np.int32)
+        rows = np.zeros(nr.value, dtype=np.int64)
+        _check("scopf_symbolic_block", L.scopf_symbolic_block(
+            self.h, k, ctypes.byref(nn), ctypes.byref(nbn), ctypes.byref(nsn), ctypes.byref(nr),
+            _hp(post, c_i32), _hp(par, c_i32), _hp(sns, c_i32), _hp(rows, c_i64)))
+        return dict(n_nodes=nn.value, n_block_nodes=nbn.value, post=post, node_parent=par,
+                    sn_start=sns, rows=rows)
+
+    def kkt_pattern(self):
+        s = self.sizes
+        ptr = np.zeros(s.n_kkt + 1, dtype=np.int64)
+        col = np.zeros(s.nnz_kkt, dtype=np.int64)
+        _check("kkt_export", lib().kkt_export(self.h, _hp(ptr, c_i64), _hp(col, c_i64), None))
+        return ptr, col
+
+    # ------------------------------------------------------- device calls
+    def new_state(self):
+        import torch
+        s = self.sizes
+        n, m, p = s.n, s.m, s.p
+        z = lambda k: torch.zeros(k, dtype=torch.float64, device="cuda")
+        return dict(w=z(n), r=z(m), t=z(p), s=z(p), lam=z(m), yc=z(p), zl=z(n), zu=z(n), zs=z(p))
+
+    @staticmethod
+    def _state(st):
+        return State(*(_dp(st[f]) for f in _STATE_FIELDS))
+
+    def scopf_eval(self, w, want_c=True, want_g=True):
+        import torch
+        s = self.sizes
+        c = torch.empty(s.m, dtype=torch.float64, device="cuda") if want_c else None
+        g = torch.empty(s.n, dtype=torch.float64, device="cuda") if want_g else None
+        obj = c_dbl()
+        _check("scopf_eval", lib().scopf_eval(self.h, _dp(w), ctypes.byref(obj), _dp(g), _dp(c)))
+        return obj.value, g, c
+
+    def kkt_assemble(self, st, lam_n, nu0_n, rho, mu, delta_w, want_rhs=True):
+        import torch
+        rhs = torch.empty(self.sizes.n_kkt, dtype=torch.float64, device="cuda") if want_rhs else None
+        S = self._state(st)
+        _check("kkt_assemble", lib().kkt_assemble(self.h, ctypes.byref(S), _dp(lam_n), _dp(nu0_n),
+                                                  rho, mu, delta_w, _dp(rhs)))
+        return rhs
+
+    def kkt_values(self):
+        v = np.zeros(self.sizes.nnz_kkt)
+        _check("kkt_export", lib().kkt_export(self.h, None, None, _hp(v, c_dbl)))
+        return v
+
+    def kkt_factor(self, precision: int = -1):
+        inertia = np.zeros(3, dtype=np.int32)
+        _check("kkt_factor", lib().kkt_factor(self.h, precision, _hp(inertia, c_i32)))
+        return tuple(int(x) for x in inertia)
+
+    def kkt_solve(self, b, max_refine: int = -1, check: bool = True):
+        import torch
+        x = torch.empty_like(b)
+        rel, steps = c_dbl(), c_i32()
+        st = lib().kkt_solve(self.h, _dp(b), _dp(x), max_refine, ctypes.byref(rel), ctypes.byref(steps))
+        if check and st not in (0, -5):
+            raise ScopfError("kkt_solve", st)
+        return x, rel.value, steps.value, st
+
+    def ncl_solve(self, warm=None):
+        R = Result()
+        S = self._state(warm) if warm is not None else None
+        st = lib().ncl_solve(self.h, ctypes.byref(S) if S is not None else None, ctypes.byref(R))
+        out = {f: getattr(R, f) for f, _ in Result._fields_}
+        out["call_status"] = st
+        return out
+
+    def get_state(self):
+        st = self.new_state()
+        S = self._state(st)
+        _check("scopf_copy_state", lib().scopf_copy_state(self.h, ctypes.byref(S)))
+        return st
+
+    def load_state(self, st):
+        S = self._state(st)
+        _check("scopf_load_state", lib().scopf_load_state(self.h, ctypes.byref(S)))
+
+    def ncl_params(self):
+        import torch
+        s = self.sizes
+        pl, pn, rho = P_dbl(), P_dbl(), c_dbl()
+        _check("scopf_get_ncl_params", lib().scopf_get_ncl_params(self.h, ctypes.byref(pl),
+                                                                  ctypes.byref(pn), ctypes.byref(rho)))
+        return pl, pn, rho.value
+
+    def scopf_adjoint(self, seed_pg0=None, seed_cost=0.0):
+        import torch
+        net_nb, ng = self.n_bus, self.n_gen
+        gP = torch.zeros(net_nb, dtype=torch.float64, device="cuda")
+        gQ = torch.zeros(net_nb, dtype=torch.float64, device="cuda")
+        gc = torch.zeros(ng, dtype=torch.float64, device="cuda")
+        _check("scopf_adjoint", lib().scopf_adjoint(self.h, _dp(seed_pg0), float(seed_cost),
+                                                    _dp(gP), _dp(gQ), _dp(gc)))
+        return gP, gQ, gc

@@ -1,0 +1,620 @@
+// C ABI of the library (include/scopf.h): handle management, device
+// uploads, and the assemble / factor / solve entry points of the Newton step
+// of eq. (newtonsystem).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+using namespace scopf;
+
+#define CK(call)                                                                                   \
+    do {                                                                                           \
+        cudaError_t e_ = (call);                                                                   \
+        if (e_ != cudaSuccess) {                                                                   \
+            h->last_error = cudaGetErrorString(e_);                                                \
+            return SCOPF_ERR_CUDA;                                                                 \
+        }                                                                                          \
+    } while (0)
+
+namespace {
+
+template <typename T>
+int upload(scopf_handle *h, const std::vector<T> &v, const T **out) {
+    T *p = nullptr;
+    size_t bytes = sizeof(T) * (v.empty() ? 1 : v.size());
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SCOPF_ERR_OOM : SCOPF_ERR_CUDA;
+    }
+    h->allocations.push_back(p);
+    if (!v.empty()) {
+        e = cudaMemcpy(p, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) {
+            h->last_error = cudaGetErrorString(e);
+            return SCOPF_ERR_CUDA;
+        }
+    }
+    *out = p;
+    return SCOPF_OK;
+}
+
+template <typename T>
+int alloc(scopf_handle *h, size_t n, T **out) {
+    T *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SCOPF_ERR_OOM : SCOPF_ERR_CUDA;
+    }
+    cudaMemset(p, 0, sizeof(T) * (n ? n : 1));
+    h->allocations.push_back(p);
+    *out = p;
+    return SCOPF_OK;
+}
+
+#define TRY(x)                                                                                     \
+    do {                                                                                           \
+        int r_ = (x);                                                                              \
+        if (r_ != SCOPF_OK) return r_;                                                             \
+    } while (0)
+
+int setup_device(scopf_handle *h) {
+    Model &M = h->M;
+    HostFronts &HF = h->HF;
+    DevModel &d = h->dm;
+    d.n = M.n;
+    d.m = M.m;
+    d.p = M.p;
+    d.n_kkt = M.n_kkt;
+    d.nnz = (int64_t)M.kkt_col.size();
+    d.n_be = M.n_be;
+    d.n_se = M.n_se;
+    d.ev_branch0 = M.ev_branch0;
+    d.ev_shunt0 = M.ev_shunt0;
+    d.ev_comp0 = M.ev_comp0;
+    d.n_ev = M.n_ev;
+    d.border0 = M.border0;
+    d.ng = M.ng;
+    TRY(upload(h, M.be_x, &d.be_x));
+    TRY(upload(h, M.be_lam, &d.be_lam));
+    TRY(upload(h, M.be_th, &d.be_th));
+    TRY(upload(h, M.be_par, &d.be_par));
+    TRY(upload(h, M.se_v, &d.se_v));
+    TRY(upload(h, M.se_P, &d.se_P));
+    TRY(upload(h, M.se_Q, &d.se_Q));
+    TRY(upload(h, M.se_G, &d.se_G));
+    TRY(upload(h, M.se_B, &d.se_B));
+    TRY(upload(h, M.comp1, &d.comp1));
+    TRY(upload(h, M.comp2, &d.comp2));
+    TRY(upload(h, M.c_const, &d.c_const));
+    TRY(upload(h, M.cf_ptr, &d.cf_ptr));
+    TRY(upload(h, M.cf_idx, &d.cf_idx));
+    TRY(upload(h, M.cf_coef, &d.cf_coef));
+    TRY(upload(h, M.kkt_ptr, &d.kkt_ptr));
+    TRY(upload(h, M.kkt_col, &d.kkt_col));
+    TRY(upload(h, M.ctr_ptr, &d.ctr_ptr));
+    {
+        std::vector<int64_t> src(M.ctr.size());
+        std::vector<double> coef(M.ctr.size());
+        for (size_t i = 0; i < M.ctr.size(); i++) {
+            src[i] = M.ctr[i].src;
+            coef[i] = M.ctr[i].coef;
+        }
+        TRY(upload(h, src, &d.ctr_src));
+        TRY(upload(h, coef, &d.ctr_coef));
+        std::vector<int32_t> krow(M.kkt_col.size());
+        for (int64_t r = 0; r < M.n_kkt; r++)
+            for (int64_t q = M.kkt_ptr[r]; q < M.kkt_ptr[r + 1]; q++) krow[q] = (int32_t)r;
+        TRY(upload(h, krow, &d.kkt_row));
+    }
+    TRY(upload(h, M.row_kind, &d.row_kind));
+    TRY(upload(h, M.row_index, &d.row_index));
+    {
+        const double rf = h->opt.bound_relax;
+        std::vector<double> wl(M.n), wu(M.n);
+        for (int64_t i = 0; i < M.n; i++) {
+            wl[i] = std::isfinite(M.wl[i]) ? M.wl[i] - rf * std::fmax(1.0, std::fabs(M.wl[i])) : -INFINITY;
+            wu[i] = std::isfinite(M.wu[i]) ? M.wu[i] + rf * std::fmax(1.0, std::fabs(M.wu[i])) : INFINITY;
+        }
+        const double *pl, *pu;
+        TRY(upload(h, wl, &pl));
+        TRY(upload(h, wu, &pu));
+        d.wl = pl;
+        d.wu = pu;
+        h->wl = const_cast<double *>(pl);
+        h->wu = const_cast<double *>(pu);
+    }
+    TRY(upload(h, M.c2, &d.c2));
+    TRY(upload(h, M.c1, &d.c1));
+    // fronts
+    DevFront &F = h->df;
+    F.n_tasks = HF.n_tasks;
+    F.n_blocks = HF.n_blocks;
+    F.n_border = HF.n_border;
+    TRY(upload(h, HF.front_off, &F.front_off));
+    TRY(upload(h, HF.f, &F.f));
+    TRY(upload(h, HF.npiv, &F.npiv));
+    TRY(upload(h, HF.child_ptr, &F.child_ptr));
+    TRY(upload(h, HF.child, &F.child));
+    TRY(upload(h, HF.rel_off, &F.rel_off));
+    TRY(upload(h, HF.rel, &F.rel));
+    TRY(upload(h, HF.parent, &F.parent));
+    TRY(upload(h, HF.rows_off, &F.rows_off));
+    TRY(upload(h, HF.rows, &F.rows));
+    TRY(upload(h, HF.is_border, &F.is_border));
+    TRY(upload(h, HF.border_off, &F.border_off));
+    TRY(upload(h, HF.border_rows, &F.border_rows));
+    TRY(upload(h, HF.scatter, &F.scatter));
+    TRY(upload(h, HF.vec_off, &F.vec_off));
+    F.nnz = (int64_t)HF.scatter.size();
+    F.front_elems = HF.front_elems;
+    F.vec_elems = HF.vec_elems;
+    // work buffers
+    TRY(alloc(h, M.n_ev, &h->ev));
+    TRY(alloc(h, M.kkt_col.size(), &h->kval));
+    TRY(alloc(h, M.n_kkt, &h->diag));
+    TRY(alloc(h, M.n, &h->g));
+    TRY(alloc(h, M.n, &h->gw));
+    TRY(alloc(h, M.m, &h->c));
+    TRY(alloc(h, M.n_kkt, &h->rhs));
+    TRY(alloc(h, M.n_kkt, &h->sol));
+    TRY(alloc(h, M.n_kkt, &h->res));
+    TRY(alloc(h, M.n_kkt, &h->dx));
+    double *fr = nullptr, *vv = nullptr;
+    TRY(alloc(h, (size_t)HF.front_elems, &fr));
+    TRY(alloc(h, (size_t)HF.vec_elems, &vv));
+    h->fronts = fr;
+    h->vec = vv;
+    TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->S));
+    TRY(alloc(h, (size_t)M.nborder + 1, &h->border_work));
+    TRY(alloc(h, 1, &h->queue));
+    TRY(alloc(h, (size_t)HF.n_tasks, &h->done));
+    TRY(alloc(h, 1, &h->fstat));
+    TRY(alloc(h, 1024, &h->red_scratch));
+    TRY(alloc(h, 16, &h->red_out));
+    // iterate, NCL parameters, IPM scratch
+    for (scopf_state *s : {&h->st, &h->dir, &h->trial}) {
+        TRY(alloc(h, M.n, &s->w));
+        TRY(alloc(h, M.m, &s->r));
+        TRY(alloc(h, M.p, &s->t));
+        TRY(alloc(h, M.p, &s->s));
+        TRY(alloc(h, M.m, &s->lam));
+        TRY(alloc(h, M.p, &s->yc));
+        TRY(alloc(h, M.n, &s->zl));
+        TRY(alloc(h, M.n, &s->zu));
+        TRY(alloc(h, M.p, &s->zs));
+    }
+    TRY(alloc(h, M.m, &h->lam_n));
+    TRY(alloc(h, M.p, &h->nu0_n));
+    TRY(alloc(h, M.n, &h->tmp_n));
+    TRY(alloc(h, M.m, &h->tmp_m));
+    TRY(alloc(h, M.p, &h->tmp_p));
+    TRY(alloc(h, M.n_kkt, &h->tmp_kkt));
+    CK(cudaDeviceSynchronize());
+    return SCOPF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+void scopf_default_options(scopf_options *o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->tol = 1e-6;
+    o->mu_min = 1e-7;
+    o->mu_init = 1e-1;
+    o->kappa_eps = 10.0;
+    o->kappa_mu = 0.2;
+    o->theta_mu = 1.5;
+    o->tau_min = 0.99;
+    o->s_max = 100.0;
+    o->kappa_sigma = 1e10;
+    o->bound_relax = 1e-8;
+    o->bound_push = 1e-2;
+    o->bound_frac = 1e-2;
+    o->slack_init = 1e-1;
+    o->comp_init = 1e-1;
+    o->delta_w0 = 1e-4;
+    o->delta_w_min = 1e-20;
+    o->delta_w_max = 1e40;
+    o->kappa_w_minus = 1.0 / 3.0;
+    o->kappa_w_plus = 8.0;
+    o->kappa_w_plus_bar = 100.0;
+    o->gamma_theta = 1e-5;
+    o->gamma_phi = 1e-8;
+    o->delta_sw = 1.0;
+    o->s_theta = 1.1;
+    o->s_phi = 2.3;
+    o->eta_phi = 1e-8;
+    o->gamma_alpha = 0.05;
+    o->rho_init = 1e2;
+    o->rho_max = 1e12;
+    o->eta_init = 1e-2;
+    o->omega_init = 1e-2;
+    o->refine_tol = 1e-10;
+    o->pivot_tol = 0.0;
+    o->max_backtrack = 40;
+    o->max_outer = 40;
+    o->max_inner = 3000;
+    o->max_refine = 10;
+    o->precision = SCOPF_PREC_FP64;
+    o->relax_max_nodes = 8;
+    o->verbose = 0;
+    o->spin_limit = 1 << 24;
+    o->host_only = 0;
+}
+
+const char *scopf_strerror(int s) {
+    switch (s) {
+        case SCOPF_OK: return "ok";
+        case SCOPF_ERR_INVALID_ARG: return "invalid argument";
+        case SCOPF_ERR_CUDA: return "CUDA error";
+        case SCOPF_ERR_NOT_FACTORED: return "no valid factorization";
+        case SCOPF_ERR_WRONG_INERTIA: return "wrong inertia after maximal correction";
+        case SCOPF_ERR_REFINE_STALL: return "iterative refinement stalled";
+        case SCOPF_ERR_INFEASIBLE: return "locally infeasible (penalty diverged)";
+        case SCOPF_ERR_MAX_ITER: return "iteration limit";
+        case SCOPF_ERR_TIMEOUT: return "device dependency wait timed out";
+        case SCOPF_ERR_OOM: return "out of device memory";
+        case SCOPF_ERR_NUMERICAL: return "numerical failure";
+        default: return "unknown status";
+    }
+}
+
+int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t K,
+                 const scopf_options *opt, scopf_handle **out) {
+    if (!out) return SCOPF_ERR_INVALID_ARG;
+    *out = nullptr;
+    scopf_handle *h = new (std::nothrow) scopf_handle();
+    if (!h) return SCOPF_ERR_OOM;
+    if (opt)
+        h->opt = *opt;
+    else
+        scopf_default_options(&h->opt);
+    h->precision = h->opt.precision;
+    h->host_only = h->opt.host_only != 0;
+    std::string err = build_model(net, ctg, K, h->M);
+    if (!err.empty()) {
+        if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
+        delete h;
+        return SCOPF_ERR_INVALID_ARG;
+    }
+    h->syms.resize(h->M.blocks.size());
+    for (size_t k = 0; k < h->M.blocks.size(); k++) {
+        err = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes, h->syms[k]);
+        if (!err.empty()) {
+            if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
+            delete h;
+            return SCOPF_ERR_INVALID_ARG;
+        }
+    }
+    err = build_fronts(h->M, h->syms, h->HF);
+    if (!err.empty()) {
+        if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
+        delete h;
+        return SCOPF_ERR_INVALID_ARG;
+    }
+    if (!h->host_only) {
+        int r = setup_device(h);
+        if (r != SCOPF_OK) {
+            if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", h->last_error.c_str());
+            scopf_destroy(h);
+            return r;
+        }
+    }
+    *out = h;
+    return SCOPF_OK;
+}
+
+void scopf_destroy(scopf_handle *h) {
+    if (!h) return;
+    for (void *p : h->allocations) cudaFree(p);
+    delete h;
+}
+
+int scopf_get_sizes(scopf_handle *h, scopf_sizes *o) {
+    if (!h || !o) return SCOPF_ERR_INVALID_ARG;
+    o->n = h->M.n;
+    o->m = h->M.m;
+    o->p = h->M.p;
+    o->n_kkt = h->M.n_kkt;
+    o->n_border = h->M.nborder;
+    o->n_blocks = (int32_t)h->M.blocks.size();
+    o->nnz_kkt = (int64_t)h->M.kkt_col.size();
+    o->nnz_L = h->HF.nnz_L;
+    o->n_supernodes = h->HF.n_tasks - h->HF.n_blocks;
+    o->factor_flops = h->HF.flops;
+    o->front_bytes = h->HF.front_elems * 8;
+    return SCOPF_OK;
+}
+
+int scopf_set_stream(scopf_handle *h, void *stream) {
+    if (!h) return SCOPF_ERR_INVALID_ARG;
+    h->stream = (cudaStream_t)stream;
+    return SCOPF_OK;
+}
+
+int scopf_set_precision(scopf_handle *h, int32_t precision) {
+    if (!h || (precision != SCOPF_PREC_FP64 && precision != SCOPF_PREC_MIXED))
+        return SCOPF_ERR_INVALID_ARG;
+    h->precision = precision;
+    return SCOPF_OK;
+}
+
+int scopf_symbolic_block(scopf_handle *h, int32_t k, int32_t *n_nodes, int32_t *n_block_nodes,
+                         int32_t *n_sn, int32_t *n_rows, int32_t *post, int32_t *node_parent,
+                         int32_t *sn_start, int64_t *rows) {
+    if (!h || k < 0 || k >= (int32_t)h->syms.size()) return SCOPF_ERR_INVALID_ARG;
+    const BlockSymbolic &S = h->syms[k];
+    if (n_nodes) *n_nodes = S.n_nodes;
+    if (n_block_nodes) *n_block_nodes = S.n_block_nodes;
+    if (n_sn) *n_sn = (int32_t)S.sn_start.size() - 1;
+    if (n_rows) *n_rows = (int32_t)S.rows.size();
+    if (post)
+        for (int i = 0; i < S.n_block_nodes; i++) post[i] = S.post[i];
+    if (node_parent)
+        for (int i = 0; i < S.n_block_nodes; i++) node_parent[i] = S.node_parent[i];
+    if (sn_start)
+        for (size_t i = 0; i < S.sn_start.size(); i++) sn_start[i] = S.sn_start[i];
+    if (rows)
+        for (size_t i = 0; i < S.rows.size(); i++) rows[i] = S.rows[i];
+    return SCOPF_OK;
+}
+
+int scopf_eval(scopf_handle *h, const double *w, double *obj, double *g, double *c) {
+    if (!h || h->host_only || !w) return SCOPF_ERR_INVALID_ARG;
+    cudaStream_t s = h->stream;
+    const Model &M = h->M;
+    if (c) {
+        launch_eval_elements(h->dm, w, h->st.lam, h->st.yc, h->ev, 0, s);
+        launch_constraints(h->dm, w, h->ev, c, s);
+    }
+    if (g) launch_gradient(h->dm, w, g, s);
+    if (obj) {
+        std::vector<double> p0(M.ng);
+        CK(cudaMemcpyAsync(p0.data(), w + M.border0, sizeof(double) * M.ng, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        double f = 0;
+        for (int i = 0; i < M.ng; i++) {
+            const double p = 100.0 * p0[i];
+            f += M.c2[i] * p * p + M.c1[i] * p + M.c0[i];
+        }
+        *obj = f / 1.0e4;
+    }
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    return SCOPF_OK;
+}
+
+int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n, const double *nu0_n,
+                 double rho, double mu, double delta_w, double *rhs) {
+    if (!h || h->host_only || !it || !lam_n || (h->M.p && !nu0_n) || !(rho > 0))
+        return SCOPF_ERR_INVALID_ARG;
+    int r = assemble_impl(h, it, lam_n, nu0_n, rho, mu, delta_w, rhs);
+    if (r != SCOPF_OK) return r;
+    CK(cudaStreamSynchronize(h->stream));
+    return SCOPF_OK;
+}
+
+int kkt_export(scopf_handle *h, int64_t *row_ptr, int64_t *col, double *val) {
+    if (!h) return SCOPF_ERR_INVALID_ARG;
+    const Model &M = h->M;
+    if (row_ptr) std::memcpy(row_ptr, M.kkt_ptr.data(), sizeof(int64_t) * M.kkt_ptr.size());
+    if (col) std::memcpy(col, M.kkt_col.data(), sizeof(int64_t) * M.kkt_col.size());
+    if (val) {
+        if (h->host_only || !h->assembled) return SCOPF_ERR_NOT_FACTORED;
+        CK(cudaMemcpy(val, h->kval, sizeof(double) * M.kkt_col.size(), cudaMemcpyDeviceToHost));
+    }
+    return SCOPF_OK;
+}
+
+int kkt_factor(scopf_handle *h, int32_t precision, int32_t inertia[3]) {
+    if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
+    if (!h->assembled) return SCOPF_ERR_NOT_FACTORED;
+    int in[3] = {0, 0, 0};
+    int r = factor_impl(h, precision < 0 ? h->precision : precision, in);
+    if (inertia)
+        for (int i = 0; i < 3; i++) inertia[i] = in[i];
+    return r;
+}
+
+int kkt_solve(scopf_handle *h, const double *b, double *x, int32_t max_refine,
+              double *rel_residual, int32_t *steps) {
+    if (!h || h->host_only || !b || !x) return SCOPF_ERR_INVALID_ARG;
+    if (!h->factored) return SCOPF_ERR_NOT_FACTORED;
+    double rel = 0;
+    int st = 0;
+    int r = solve_impl(h, b, x, max_refine < 0 ? h->opt.max_refine : max_refine, &rel, &st);
+    if (rel_residual) *rel_residual = rel;
+    if (steps) *steps = st;
+    return r;
+}
+
+int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res) {
+    if (!h || h->host_only || !res) return SCOPF_ERR_INVALID_ARG;
+    return ncl_solve_impl(h, warm, res);
+}
+
+int scopf_get_state(scopf_handle *h, scopf_state *out) {
+    if (!h || h->host_only || !out) return SCOPF_ERR_INVALID_ARG;
+    *out = h->st;
+    return SCOPF_OK;
+}
+
+static int copy_state(scopf_handle *h, const scopf_state *a, const scopf_state *b, bool skip_null) {
+    const Model &M = h->M;
+    double *const *pa[9] = {&a->w, &a->r, &a->t, &a->s, &a->lam, &a->yc, &a->zl, &a->zu, &a->zs};
+    double *const *pb[9] = {&b->w, &b->r, &b->t, &b->s, &b->lam, &b->yc, &b->zl, &b->zu, &b->zs};
+    const int64_t len[9] = {M.n, M.m, M.p, M.p, M.m, M.p, M.n, M.n, M.p};
+    for (int i = 0; i < 9; i++) {
+        if (!*pa[i] || !*pb[i]) {
+            if (skip_null || len[i] == 0) continue;
+            return SCOPF_ERR_INVALID_ARG;
+        }
+        if (len[i])
+            CK(cudaMemcpyAsync(*pa[i], *pb[i], sizeof(double) * len[i], cudaMemcpyDeviceToDevice,
+                               h->stream));
+    }
+    CK(cudaStreamSynchronize(h->stream));
+    return SCOPF_OK;
+}
+
+int scopf_copy_state(scopf_handle *h, const scopf_state *dst) {
+    if (!h || h->host_only || !dst) return SCOPF_ERR_INVALID_ARG;
+    return copy_state(h, dst, &h->st, true);
+}
+
+int scopf_load_state(scopf_handle *h, const scopf_state *src) {
+    if (!h || h->host_only || !src) return SCOPF_ERR_INVALID_ARG;
+    return copy_state(h, &h->st, src, false);
+}
+
+int scopf_get_ncl_params(scopf_handle *h, double **lam_n, double **nu0_n, double *rho) {
+    if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
+    if (lam_n) *lam_n = h->lam_n;
+    if (nu0_n) *nu0_n = h->nu0_n;
+    if (rho) *rho = h->rho;
+    return SCOPF_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------- implementations
+namespace scopf {
+
+double device_maxabs(scopf_handle *h, const double *x, int64_t n) {
+    if (n <= 0) return 0.0;
+    reduce_maxabs(x, n, h->red_out, h->red_scratch, h->stream);
+    double v = 0;
+    cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    return v;
+}
+
+double device_sumabs(scopf_handle *h, const double *x, int64_t n) {
+    if (n <= 0) return 0.0;
+    reduce_sumabs(x, n, h->red_out, h->red_scratch, h->stream);
+    double v = 0;
+    cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    return v;
+}
+
+int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, const double *nu0_n,
+                  double rho, double mu, double delta_w, double *rhs) {
+    cudaStream_t s = h->stream;
+    const DevModel &d = h->dm;
+    launch_eval_elements(d, it->w, it->lam, it->yc, h->ev, 1, s);
+    launch_constraints(d, it->w, h->ev, h->c, s);
+    launch_gradient(d, it->w, h->g, s);
+    launch_diag_terms(d, it->w, it->zl, it->zu, it->s, it->zs, rho, delta_w, h->diag, s);
+    launch_assemble(d, h->ev, h->diag, h->kval, s);
+    launch_dual_product(d, h->kval, h->g, it->lam, it->yc, h->gw, s);
+    if (rhs) {
+        RhsArgs a{it->w, it->r, it->t, it->s, it->lam, it->yc, it->zs, h->gw, h->c, lam_n, nu0_n,
+                  rho, mu};
+        launch_rhs(d, a, rhs, s);
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return SCOPF_ERR_CUDA;
+    }
+    h->assembled = true;
+    h->factored = false;
+    h->last_delta_w = delta_w;
+    h->last_rho = rho;
+    return SCOPF_OK;
+}
+
+template <typename T>
+static int factor_t(scopf_handle *h, int inertia[3]) {
+    cudaStream_t s = h->stream;
+    T *fr = reinterpret_cast<T *>(h->fronts);
+    CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
+    launch_front_init<T>(h->df, h->kval, fr, s);
+    h->epoch++;
+    launch_factor<T>(h->df, fr, h->fstat, h->queue, h->done, h->epoch, h->opt.pivot_tol,
+                     h->opt.spin_limit, s);
+    launch_schur_sum<T>(h->df, fr, h->S, s);
+    launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s);
+    FactorStatus fs;
+    CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    inertia[0] = fs.n_pos;
+    inertia[1] = fs.n_neg;
+    inertia[2] = fs.n_zero;
+    h->n_factor++;
+    if (fs.error) {
+        h->last_error = "dependency wait timed out in the factorization";
+        return SCOPF_ERR_TIMEOUT;
+    }
+    h->factored = true;
+    return SCOPF_OK;
+}
+
+int factor_impl(scopf_handle *h, int precision, int inertia[3]) {
+    h->factored_precision = precision;
+    if (precision == SCOPF_PREC_MIXED) return factor_t<float>(h, inertia);
+    return factor_t<double>(h, inertia);
+}
+
+template <typename T>
+static int solve_once(scopf_handle *h, const double *b, double *x) {
+    h->epoch += 2;
+    launch_solve<T>(h->df, reinterpret_cast<T *>(h->fronts), reinterpret_cast<T *>(h->vec), h->S,
+                    (int)h->M.nborder, b, x, h->border_work, h->queue, h->done, h->epoch - 1,
+                    h->fstat, h->opt.spin_limit, h->stream);
+    h->epoch++;
+    return SCOPF_OK;
+}
+
+int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel, int *steps) {
+    cudaStream_t s = h->stream;
+    const int64_t n = h->M.n_kkt;
+    const bool mixed = h->factored_precision == SCOPF_PREC_MIXED;
+    auto once = [&](const double *rhs, double *out) {
+        return mixed ? solve_once<float>(h, rhs, out) : solve_once<double>(h, rhs, out);
+    };
+    // x0 = K^-1 b, then x += K^-1 (b - K x) until the residual is small enough
+    CK(cudaMemcpyAsync(h->res, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    once(h->res, h->dx);
+    CK(cudaMemcpyAsync(x, h->dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    const double bnorm = device_maxabs(h, h->res, n);
+    int it = 0;
+    double r = 0;
+    while (true) {
+        launch_residual(h->dm, h->kval, x, h->res, h->tmp_kkt, s);
+        r = device_maxabs(h, h->tmp_kkt, n) / (bnorm > 0 ? bnorm : 1.0);
+        if (!(r > h->opt.refine_tol) || it >= max_refine) break;
+        once(h->tmp_kkt, h->dx);
+        launch_axpy(n, 1.0, h->dx, x, s);
+        it++;
+    }
+    h->n_refine += it;
+    FactorStatus fs;
+    CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    CK(cudaGetLastError());
+    *rel = r;
+    *steps = it;
+    if (fs.error) return SCOPF_ERR_TIMEOUT;
+    if (!std::isfinite(r)) return SCOPF_ERR_NUMERICAL;
+    if (r > h->opt.refine_tol) return SCOPF_ERR_REFINE_STALL;
+    return SCOPF_OK;
+}
+
+}  // namespace scopf
+
+extern "C" int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
+                             double *grad_Pd, double *grad_Qd, double *grad_c1) {
+    (void)seed_pg0; (void)seed_cost; (void)grad_Pd; (void)grad_Qd; (void)grad_c1;
+    if (!h) return SCOPF_ERR_INVALID_ARG;
+    return SCOPF_ERR_INVALID_ARG;
+}

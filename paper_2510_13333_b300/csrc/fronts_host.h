@@ -1,0 +1,19 @@
+#pragma once
+
+#include "internal.h"
+
+namespace scopf {
+
+// Host copy of the frontal structure (see kernels.h: DevFront).
+struct HostFronts {
+    int n_tasks = 0, n_blocks = 0, n_border = 0, max_level = 0;
+    std::vector<int64_t> front_off, vec_off, rows_off, rel_off, border_off, scatter;
+    std::vector<int32_t> f, npiv, parent, is_border, child_ptr, child, rel, level, block;
+    std::vector<int64_t> rows, border_rows;
+    int64_t front_elems = 0, vec_elems = 0, nnz_L = 0;
+    double flops = 0;
+};
+
+std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms, HostFronts &H);
+
+}  // namespace scopf

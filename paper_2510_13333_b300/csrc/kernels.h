@@ -1,0 +1,104 @@
+// Device kernels of the NCL / interior-point Newton step (launch wrappers).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace scopf {
+
+// ---------------------------------------------------------------- model
+struct DevModel {
+    int64_t n, m, p, n_kkt, nnz;
+    int64_t n_be, n_se, ev_branch0, ev_shunt0, ev_comp0, n_ev;
+    const int32_t *be_x, *be_lam, *be_th;
+    const double *be_par;
+    const int32_t *se_v, *se_P, *se_Q;
+    const double *se_G, *se_B;
+    const int64_t *comp1, *comp2;
+    const double *c_const;
+    const int64_t *cf_ptr, *cf_idx;
+    const double *cf_coef;
+    const int64_t *kkt_ptr, *kkt_col, *ctr_ptr;
+    const int32_t *kkt_row;       // row of every stored entry
+    const int64_t *ctr_src;
+    const double *ctr_coef;
+    const int8_t *row_kind;
+    const int64_t *row_index;
+    const double *wl, *wu;        // relaxed bounds (+-inf where absent)
+    const double *grad_scale;     // per border p_g^0: c1 part etc. (see objective)
+    const double *c2, *c1;        // per generator
+    int64_t border0;
+    int ng;
+};
+
+// mode: 0 = values only (flows, thermal values), 1 = values + derivatives
+void launch_eval_elements(const DevModel &M, const double *w, const double *lam,
+                          const double *yc, double *ev, int mode, cudaStream_t s);
+void launch_constraints(const DevModel &M, const double *w, const double *ev, double *c,
+                        cudaStream_t s);
+void launch_gradient(const DevModel &M, const double *w, double *g, cudaStream_t s);
+void launch_diag_terms(const DevModel &M, const double *w, const double *zl, const double *zu,
+                       const double *sv, const double *zs, double rho, double delta_w,
+                       double *diag, cudaStream_t s);
+void launch_assemble(const DevModel &M, const double *ev, const double *diag, double *kval,
+                     cudaStream_t s);
+// gw[i] = g[i] + sum over dual columns of K(row of w_i, col) * (lam | yc)
+void launch_dual_product(const DevModel &M, const double *kval, const double *g,
+                         const double *lam, const double *yc, double *gw, cudaStream_t s);
+struct RhsArgs {
+    const double *w, *r, *t, *sv, *lam, *yc, *zs, *gw, *c, *lam_n, *nu0_n;
+    double rho, mu;
+};
+void launch_rhs(const DevModel &M, const RhsArgs &a, double *rhs, cudaStream_t s);
+// y = b - K x  (FP64); K from kval
+void launch_residual(const DevModel &M, const double *kval, const double *x, const double *b,
+                     double *y, cudaStream_t s);
+
+// ------------------------------------------------------------ reductions
+// out[0] = max |x|, computed deterministically in two passes into scratch
+void reduce_maxabs(const double *x, int64_t n, double *d_out, double *scratch, cudaStream_t s);
+void reduce_sumabs(const double *x, int64_t n, double *d_out, double *scratch, cudaStream_t s);
+// y += a * x
+void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
+
+// ----------------------------------------------------------- factorisation
+struct DevFront {
+    int n_tasks, n_blocks, n_border;
+    const int64_t *front_off;     // per task, element offset into fronts
+    const int32_t *f, *npiv;      // per task
+    const int32_t *child_ptr, *child; // per task: children task ids
+    const int64_t *rel_off;       // per task (as a child): offset into rel
+    const int32_t *rel;           // positions of a child's update rows in its parent front
+    const int32_t *parent;        // per task (-1 for border tasks)
+    const int64_t *rows_off;      // per task: offset into rows
+    const int64_t *rows;          // KKT indices of every front row
+    const int32_t *is_border;     // per task
+    const int64_t *border_off;    // per block: element offset of the border front
+    const int64_t *border_rows;   // n_border KKT indices (natural order)
+    const int64_t *scatter;       // per stored KKT entry: front element offset or -1
+    int64_t nnz;
+    int64_t front_elems;          // size of the front buffer (elements)
+    int64_t vec_elems;            // size of the per-front vector buffer
+    const int64_t *vec_off;       // per task offset into the vector buffer
+};
+
+struct FactorStatus {             // device-side counters
+    int n_pos, n_neg, n_zero, error, timeout_task, pad[3];
+};
+
+template <typename T>
+void launch_front_init(const DevFront &F, const double *kval, T *fronts, cudaStream_t s);
+template <typename T>
+void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, int *queue, int *done,
+                   int epoch, double pivot_tol, int spin_limit, cudaStream_t s);
+template <typename T>
+void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s);
+void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s);
+
+// Forward solve uses dependency epoch `epoch`, backward `epoch + 1`.
+template <typename T>
+void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
+                  const double *b, double *x, double *border_work, int *queue, int *done,
+                  int epoch, FactorStatus *st, int spin_limit, cudaStream_t s);
+
+}  // namespace scopf
