@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Benchmark: Newton steps/s of the NCL / interior-point method on the
+synthetic 500-bus x 256-contingency AC-SCOPF, and time to solution.
+
+One "step" is one Newton step of the inner interior-point loop at a fixed
+mid-solve iterate: model evaluation and KKT assembly (eq. newtonsystem),
+pivot-free block LDL^T with inertia correction, Schur complement and border
+factor, solves with FP64 iterative refinement, recovery of the eliminated
+directions, fraction-to-boundary and one trial evaluation.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line.  With --impl reference the CPU oracle is timed on a
+bounded sample of the same workload (the reference arm of this build).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = ("Newton steps/s and SCOPF time-to-solution at 500-bus×256-ctg (1e-6), "
+          "vs plain FP64 GPU")
+CONFIG_IDX = 2
+# FP32 FMA peak from unit counts and clock: 148 SMs x 128 lanes x 2 flops x 2.032 GHz
+FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
+# FP64 FMA rate of B300 measured by the DFMA probe (1/64 of FP32 per SM)
+FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
+
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6400.0, "bf16_tflops": 1800.0}, "fallback"
+
+
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+
+    def __init__(self):
+        self.samples = []
+        self._stop = threading.Event()
+        self._t = None
+
+    def start(self):
+        def run():
+            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+                 "clocks_event_reasons.sw_power_cap")
+            while not self._stop.is_set():
+                try:
+                    out = subprocess.run(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
+                                          "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
+                                         capture_output=True, text=True, timeout=5).stdout.strip()
+                    if out:
+                        self.samples.append([x.strip() for x in out.split(",")])
+                except Exception:
+                    pass
+                self._stop.wait(0.2)
+        self._t = threading.Thread(target=run, daemon=True)
+        self._t.start()
+
+    def stop(self):
+        self._stop.set()
+        if self._t:
+            self._t.join(timeout=10)
+        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
+        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for s in self.samples for i in range(4)
+                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.samples)}
+
+
+# ------------------------------------------------------------- reference arm
+def oracle_step_sample(n_ctg_sample: int = 8):
+    """Time the CPU oracle's Newton step on the 500-bus network with a
+    bounded number of contingency blocks; returns (seconds per full-size
+    step extrapolated per block, description, cores)."""
+    import numpy as np
+    import synthgrid
+    from oracle.linsolve import SparseLDLSolver
+    from oracle.ncl import NCLSolver, Params
+    from oracle.scopf_model import SCOPFModel
+    from oracle import symbolic
+    inst = synthgrid.config_instance(CONFIG_IDX)
+    full_blocks = inst.K + 1
+    inst.ctgs = inst.ctgs[:n_ctg_sample]
+    if True:  # scipy sparse kernels and the C LDL^T run on one thread
+        M = SCOPFModel(inst)
+        perm, _ = symbolic.kkt_permutation(M)
+        S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm))
+        st = S.initial_state()
+        prm = Params(rho=S.o.rho_init, lam_n=np.zeros(M.m), nu0_n=np.zeros(M.p))
+        mu = 0.1
+        times = []
+        for _ in range(2):
+            t0 = time.perf_counter()
+            res = S.residuals(st, prm)
+            H = M.hessian(st.w, st.lam)
+            sol, delta, tries, _, _ = S.newton_direction(st, prm, res, mu, H, 0.0)
+            d = S.recover(st, prm, res, mu, sol)
+            ap, az = S.frac_to_boundary(st, d, 0.99)
+            trial = S.step(st, d, ap, az)
+            S.theta(trial, M.constraints(trial.w))
+            times.append(time.perf_counter() - t0)
+    t = min(times)
+    per_full = t * full_blocks / (n_ctg_sample + 1)
+    desc = (f"oracle Newton step (numpy/scipy + C LDL^T, 1 thread) on the 500-bus network with "
+            f"{n_ctg_sample} of 256 contingencies ({n_ctg_sample + 1} blocks, {t:.2f} s), "
+            f"scaled by blocks to {full_blocks}")
+    return per_full, desc, 1
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_full, desc, cores = oracle_step_sample()
+    # the oracle arm repeats its bounded sample once per step
+    t0 = time.perf_counter()
+    value = 1.0 / per_full
+    line = {"metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_full,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "impl": "reference",
+            "config": {"workload": "syn500_k256: 500-bus, 90-generator synthetic grid, 256 "
+                                   "contingencies (220 line, 36 generator)", "flush_l2": False},
+            "cpu_baseline": {"value": value, "unit": "Newton steps/s", "cores": cores,
+                             "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "Newton steps/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# -------------------------------------------------------------------- our arm
+def run_ours(args):
+    import numpy as np
+    import torch
+    import synthgrid
+    import paper_2510_13333_b300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    inst = synthgrid.config_instance(CONFIG_IDX)
+    t0 = time.perf_counter()
+    lib = P.SCOPF(inst, precision=P.PREC_MIXED)
+    t_create = time.perf_counter() - t0
+    sz = lib.sizes
+    # ---- time to solution (full NCL solve from the flat start)
+    tts = {}
+    for name, prec in (("mixed", P.PREC_MIXED), ("fp64", P.PREC_FP64)):
+        if args.tts == "none" or (name == "fp64" and args.tts != "both"):
+            continue
+        lib.set_precision(prec)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = lib.ncl_solve()
+        torch.cuda.synchronize()
+        tts[name] = {"seconds": time.perf_counter() - t0, "status": r["call_status"],
+                     "objective": r["objective"], "inner_iters": r["inner_iters"],
+                     "outer_iters": r["outer_iters"], "factorizations": r["factorizations"],
+                     "fp64_fallbacks": r["fp64_fallbacks"], "max_violation": r["max_violation"],
+                     "kkt_error": r["kkt_error"]}
+    # ---- a mid-solve iterate: the state after a fixed number of IPM iterations
+    lib.set_precision(P.PREC_MIXED)
+    lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at)
+    r = lib2.ncl_solve()
+    st = lib2.get_state()
+    lam_n, nu0_n, rho = lib2.ncl_params_tensors()
+    mu = r["mu"]
+    del lib2
+    direction = lib.new_state()
+
+    def step(l):
+        return l.scopf_newton_step(st, lam_n, nu0_n, rho, mu, 0.0, direction)
+
+    def timed(l, k):
+        for _ in range(args.warmup):
+            step(l)
+        torch.cuda.synchronize()
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l.scopf_timing(True)
+        torch.cuda.nvtx.range_push("timed")
+        e0.record(s)
+        for _ in range(k):
+            step(l)
+        e1.record(s)
+        torch.cuda.nvtx.range_pop()
+        torch.cuda.synchronize()
+        phases = l.scopf_timing(False)
+        ms = e0.elapsed_time(e1)
+        if dist:
+            t = torch.tensor([ms], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, phases
+
+    clocks = Clocks()
+    clocks.start()
+    ms_mixed, ph_mixed = timed(lib, args.steps)
+    clk = clocks.stop()
+    lib.set_precision(P.PREC_FP64)
+    ms_fp64, ph_fp64 = timed(lib, max(2, args.steps // 4))
+    fp64_steps = max(2, args.steps // 4)
+    lib.set_precision(P.PREC_MIXED)
+    # ---- end to end through host buffers (pinned), H2D inputs + D2H direction
+    host = {k: v.cpu().pin_memory() for k, v in st.items()}
+    host_l, host_n = lam_n.cpu().pin_memory(), nu0_n.cpu().pin_memory()
+    out_w = torch.empty(sz.n, dtype=torch.float64).pin_memory()
+    out_l = torch.empty(sz.m, dtype=torch.float64).pin_memory()
+    out_y = torch.empty(sz.p, dtype=torch.float64).pin_memory()
+    h2d = sum(v.numel() * 8 for v in host.values()) + 8 * (host_l.numel() + host_n.numel())
+    d2h = 8 * (sz.n + sz.m + sz.p)
+    dev_in = {k: torch.empty_like(v) for k, v in st.items()}
+    dl, dn = torch.empty_like(lam_n), torch.empty_like(nu0_n)
+
+    def e2e_step():
+        for k in st:
+            dev_in[k].copy_(host[k], non_blocking=True)
+        dl.copy_(host_l, non_blocking=True)
+        dn.copy_(host_n, non_blocking=True)
+        lib.scopf_newton_step(dev_in, dl, dn, rho, mu, 0.0, direction)
+        out_w.copy_(direction["w"], non_blocking=True)
+        out_l.copy_(direction["lam"], non_blocking=True)
+        out_y.copy_(direction["yc"], non_blocking=True)
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        e2e_step()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(s)
+    torch.cuda.synchronize()
+    ms_e2e = e0.elapsed_time(e1)
+    if dist:
+        t = torch.tensor([ms_e2e], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_e2e = float(t.item())
+
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return
+    K = args.steps
+    value = world * K / (ms_mixed / 1e3)
+    fp64_value = world * fp64_steps / (ms_fp64 / 1e3)
+    # roofline of the dominant phase (from CUDA events on the handle's stream)
+    dom = max(("factor", "solve", "assemble", "residual", "schur", "front_init", "ipm"),
+              key=lambda k: ph_mixed[k][0])
+    fac_ms, fac_calls = ph_mixed["factor"]
+    sol_ms, sol_calls = ph_mixed["solve"]
+    peaks, peak_kind = measured_peaks()
+    if dom == "factor":
+        achieved = sz.factor_flops / (fac_ms / fac_calls / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_factor<float> (persistent supernodal LDL^T, all blocks)",
+                "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+    else:
+        # forward + backward sweeps read every FP32 factor entry once each
+        bytes_ = 2 * 4 * sz.nnz_L + 3 * 8 * sz.n_kkt
+        achieved = bytes_ / (sol_ms / sol_calls / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "kernel": "k_solve_fwd/k_solve_bwd<float> (multifrontal sweeps)",
+                "peak_kind": peak_kind}
+    try:
+        cpu_s, cpu_desc, cores = oracle_step_sample()
+        cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
+               "sample": cpu_desc}
+    except Exception as exc:  # keep the GPU number even if the CPU sample fails
+        cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
+               "sample": f"failed: {exc}"}
+    launches_per_step = None
+    line = {
+        "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
+        "steps": K, "warmup": args.warmup, "ms_per_step": ms_mixed / K,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 block factors + f64 (model, Schur, refinement)", "data": "synthetic",
+        "config": {"workload": "syn500_k256: 500-bus, 90-generator synthetic grid (mean degree "
+                               "2.8), 256 contingencies (220 line, 36 generator), random PV/PQ "
+                               "switch sets; seeded, screened",
+                   "n_kkt": sz.n_kkt, "nnz_kkt": sz.nnz_kkt, "nnz_L": sz.nnz_L,
+                   "blocks": sz.n_blocks, "border": sz.n_border,
+                   "iterate": f"state after {args.iterate_at} IPM iterations",
+                   "flush_l2": False, "inputs_exceed_l2": True,
+                   "parallelism": "replicas only" if world > 1 else "1 GPU"},
+        "fp64_newton_steps_per_s": fp64_value,
+        "speedup_mixed_vs_fp64": value / fp64_value,
+        "time_to_solution": tts,
+        "create_s": t_create,
+        "phases_ms_per_step": {k: v[0] / K for k, v in ph_mixed.items()},
+        "phases_ms_per_step_fp64": {k: v[0] / fp64_steps for k, v in ph_fp64.items()},
+        "roofline": roof,
+        "cpu_baseline": cpu,
+        "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "Newton steps/s",
+                "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "clocks": clk,
+        "gpu_launches": None,
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--iterate-at", type=int, default=30)
+    ap.add_argument("--tts", default="both", choices=["none", "mixed", "both"],
+                    help="which full NCL solves to time (time to solution)")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        args.warmup = 3
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -196,6 +196,30 @@ int kkt_factor(scopf_handle *h, int32_t precision, int32_t inertia[3]);
 int kkt_solve(scopf_handle *h, const double *b, double *x, int32_t max_refine,
               double *rel_residual, int32_t *steps);
 
+/* One Newton step of the interior-point method on the NCL subproblem
+ * (Section IV-B) at the iterate `it` (device, left unchanged): model
+ * evaluation, KKT assembly with the barrier parameter mu, factorization
+ * with inertia correction (delta_w starting from 0, the last successful
+ * value dw_last guiding the first increase), Schur complement and border
+ * factor, solve with iterative refinement (mixed mode falls back to FP64
+ * factors if refinement stalls), recovery of the eliminated directions,
+ * fraction-to-boundary step and one trial evaluation at the full step.
+ * dir: device buffers for the direction (may be NULL: kept in the handle).
+ * out (host, 6): alpha_primal, alpha_dual, theta at the trial point,
+ * barrier objective at the trial point, delta_w used, refinement residual.
+ * inertia (host, 3): inertia of the accepted factorization. */
+int scopf_newton_step(scopf_handle *h, const scopf_state *it, const double *lam_n,
+                      const double *nu0_n, double rho, double mu, double dw_last,
+                      scopf_state *dir, double out[6], int32_t inertia[3]);
+
+/* Device-time breakdown (CUDA events on the handle's stream) of the
+ * library's phases: 0 model evaluation + assembly, 1 front initialisation,
+ * 2 block factorization (persistent kernel), 3 Schur sum + border factor,
+ * 4 triangular solves, 5 refinement residuals, 6 IPM vector kernels.
+ * enable = 1 starts (and zeroes) the timers, 0 stops them; ms_out[7] and
+ * calls_out[7] (host, may be NULL) receive the accumulated totals. */
+int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls_out);
+
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */
 int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);

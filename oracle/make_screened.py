@@ -26,8 +26,16 @@ def _screen_one(args):
     from oracle.screening import screen_candidate
     inst = _unscreened(idx, load_scale)
     cand = (inst.candidates.lines if kind == "line" else inst.candidates.gens)[pos]
-    ok, feas, status = screen_candidate(inst, cand, np.asarray(u0))
+    ok, feas, status = screen_candidate(inst, cand, np.asarray(u0), eps=FIX_EPS)
     return kind, pos, cand.element, ok, feas, status
+
+
+# Screening at a fixed first stage (Section V-B) taken from a base-case OPF
+# with derated limits: every accepted outage is feasible at the same u0, so
+# the SCOPF over all of them is feasible.
+DERATE = 0.75       # thermal ratings of the base point
+V_MARGIN = 0.01     # voltage band of the base point narrowed by this much
+FIX_EPS = 1e-3      # u0 held within +-FIX_EPS of the base point
 
 
 _CACHE = {}
@@ -57,7 +65,16 @@ def screen_config(idx: int, workers: int) -> dict:
         if res.status == "ok":
             break
         scale *= 0.9
+    derate, vm = DERATE, V_MARGIN
+    for derate, vm in ((DERATE, V_MARGIN), (0.85, 0.005), (1.0, 0.0)):
+        resc, u0c = base_opf(inst, derate=derate, v_margin=vm)
+        print(f"[{c['name']}] derated base point (rating x{derate}, v margin {vm}): "
+              f"{resc.status} obj {resc.objective:.6f}", flush=True)
+        if resc.status == "ok":
+            u0 = u0c
+            break
     out = dict(name=c["name"], load_scale=scale, base_objective=res.objective,
+               derate=derate, v_margin=vm, fix_eps=FIX_EPS,
                u0=u0.tolist(), accepted_lines=[], accepted_gens=[], rejected=[])
     need = {"line": c["n_line_ctg"], "gen": c["n_gen_ctg"]}
     t0 = time.time()

@@ -37,9 +37,20 @@ def sub_instance(inst, ctgs):
     return sub
 
 
-def base_opf(inst, opts: Options | None = None):
-    """AC-OPF of the base case alone (K = 0)."""
-    M = SCOPFModel(sub_instance(inst, []))
+def base_opf(inst, opts: Options | None = None, derate: float | None = None,
+             v_margin: float = 0.0):
+    """AC-OPF of the base case alone (K = 0).  ``derate`` scales the thermal
+    ratings and ``v_margin`` narrows the voltage band, which leaves recovery
+    margin at the returned u0 for screening at a fixed first stage."""
+    import copy
+    sub = sub_instance(inst, [])
+    if derate is not None or v_margin:
+        sub.net = copy.copy(inst.net)
+        if derate is not None:
+            sub.net.rate = inst.net.rate * derate
+        sub.net.vmin = inst.net.vmin + v_margin
+        sub.net.vmax = inst.net.vmax - v_margin
+    M = SCOPFModel(sub)
     res = _solver(M, opts or Options()).solve()
     u0 = res.state.w[M.border0:M.border0 + M.nborder].copy()
     return res, u0

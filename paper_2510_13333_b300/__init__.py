@@ -89,6 +89,21 @@ class Result(ctypes.Structure):
 
 
 _LIB = None
+_CUDART = None
+
+
+def _cudart():
+    """The CUDA runtime already loaded by the library (for device copies of
+    handle-owned buffers)."""
+    global _CUDART
+    if _CUDART is None:
+        lib()
+        import glob
+        cands = glob.glob("/usr/local/cuda/lib64/libcudart.so*")
+        _CUDART = ctypes.CDLL(cands[0] if cands else "libcudart.so")
+        _CUDART.cudaMemcpy.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int]
+        _CUDART.cudaMemcpy.restype = ctypes.c_int
+    return _CUDART
 
 
 def lib():
@@ -124,6 +139,9 @@ def lib():
             "scopf_get_ncl_params": (c_i32, [H, ctypes.POINTER(P_dbl), ctypes.POINTER(P_dbl),
                                              P_dbl]),
             "scopf_adjoint": (c_i32, [H, P_dbl, c_dbl, P_dbl, P_dbl, P_dbl]),
+            "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
+                                          c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
+            "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -324,6 +342,41 @@ class SCOPF:
         _check("scopf_get_ncl_params", lib().scopf_get_ncl_params(self.h, ctypes.byref(pl),
                                                                   ctypes.byref(pn), ctypes.byref(rho)))
         return pl, pn, rho.value
+
+    def scopf_newton_step(self, st, lam_n, nu0_n, rho, mu, dw_last=0.0, direction=None):
+        """One Newton step at st (unchanged).  Returns (alpha_p, alpha_d,
+        theta_trial, phi_trial, delta_w, _), inertia tries."""
+        out = np.zeros(6)
+        inert = np.zeros(3, dtype=np.int32)
+        S = self._state(st)
+        Dp = ctypes.byref(self._state(direction)) if direction is not None else None
+        _check("scopf_newton_step", lib().scopf_newton_step(
+            self.h, ctypes.byref(S), _dp(lam_n), _dp(nu0_n), rho, mu, dw_last, Dp,
+            _hp(out, c_dbl), _hp(inert, c_i32)))
+        return out, int(inert[2])
+
+    PHASES = ("assemble", "front_init", "factor", "schur", "solve", "residual", "ipm")
+
+    def scopf_timing(self, enable: bool):
+        ms = np.zeros(7)
+        calls = np.zeros(7, dtype=np.int32)
+        _check("scopf_timing", lib().scopf_timing(self.h, int(enable), _hp(ms, c_dbl), _hp(calls, c_i32)))
+        return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(self.PHASES)}
+
+    def ncl_params_tensors(self):
+        """Copies of the NCL multiplier estimates (lam_n, nu0_n) as torch tensors, and rho."""
+        import torch
+        pl, pn, rho = self.ncl_params()
+        s = self.sizes
+        lam_n = torch.empty(s.m, dtype=torch.float64, device="cuda")
+        nu0_n = torch.empty(max(s.p, 1), dtype=torch.float64, device="cuda")[:s.p]
+        cudart = _cudart()
+        cudart.cudaMemcpy(ctypes.c_void_p(lam_n.data_ptr()), ctypes.cast(pl, ctypes.c_void_p),
+                          ctypes.c_size_t(8 * s.m), 3)
+        if s.p:
+            cudart.cudaMemcpy(ctypes.c_void_p(nu0_n.data_ptr()), ctypes.cast(pn, ctypes.c_void_p),
+                              ctypes.c_size_t(8 * s.p), 3)
+        return lam_n, nu0_n, rho
 
     def scopf_adjoint(self, seed_pg0=None, seed_cost=0.0):
         import torch

@@ -5,6 +5,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <vector>
 
 #include "handle.h"
 
@@ -135,6 +136,7 @@ int setup_device(scopf_handle *h) {
     F.n_tasks = HF.n_tasks;
     F.n_blocks = HF.n_blocks;
     F.n_border = HF.n_border;
+    F.n_small = HF.n_small;
     TRY(upload(h, HF.front_off, &F.front_off));
     TRY(upload(h, HF.f, &F.f));
     TRY(upload(h, HF.npiv, &F.npiv));
@@ -150,6 +152,7 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, HF.border_rows, &F.border_rows));
     TRY(upload(h, HF.scatter, &F.scatter));
     TRY(upload(h, HF.vec_off, &F.vec_off));
+    TRY(upload(h, HF.border_vec_off, &F.border_vec_off));
     F.nnz = (int64_t)HF.scatter.size();
     F.front_elems = HF.front_elems;
     F.vec_elems = HF.vec_elems;
@@ -164,6 +167,8 @@ int setup_device(scopf_handle *h) {
     TRY(alloc(h, M.n_kkt, &h->sol));
     TRY(alloc(h, M.n_kkt, &h->res));
     TRY(alloc(h, M.n_kkt, &h->dx));
+    TRY(alloc(h, M.n_kkt, &h->scale));
+    TRY(alloc(h, M.n_kkt, &h->scale_tmp));
     double *fr = nullptr, *vv = nullptr;
     TRY(alloc(h, (size_t)HF.front_elems, &fr));
     TRY(alloc(h, (size_t)HF.vec_elems, &vv));
@@ -241,7 +246,7 @@ void scopf_default_options(scopf_options *o) {
     o->max_backtrack = 40;
     o->max_outer = 40;
     o->max_inner = 3000;
-    o->max_refine = 10;
+    o->max_refine = 30;
     o->precision = SCOPF_PREC_FP64;
     o->relax_max_nodes = 8;
     o->verbose = 0;
@@ -398,6 +403,20 @@ int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n, co
     int r = assemble_impl(h, it, lam_n, nu0_n, rho, mu, delta_w, rhs);
     if (r != SCOPF_OK) return r;
     CK(cudaStreamSynchronize(h->stream));
+    h->timer.collect();
+    return SCOPF_OK;
+}
+
+int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls_out) {
+    if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    h->timer.collect();
+    for (int i = 0; i < PhaseTimer::kPhases; i++) {
+        if (ms_out) ms_out[i] = h->timer.ms[i];
+        if (calls_out) calls_out[i] = h->timer.calls[i];
+    }
+    if (enable) h->timer.reset();
+    h->timer.on = enable != 0;
     return SCOPF_OK;
 }
 
@@ -509,6 +528,7 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
                   double rho, double mu, double delta_w, double *rhs) {
     cudaStream_t s = h->stream;
     const DevModel &d = h->dm;
+    h->timer.begin(PH_ASSEMBLE, s);
     launch_eval_elements(d, it->w, it->lam, it->yc, h->ev, 1, s);
     launch_constraints(d, it->w, h->ev, h->c, s);
     launch_gradient(d, it->w, h->g, s);
@@ -520,6 +540,7 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
                   rho, mu};
         launch_rhs(d, a, rhs, s);
     }
+    h->timer.end(PH_ASSEMBLE, s);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) {
         h->last_error = cudaGetErrorString(e);
@@ -537,15 +558,24 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     cudaStream_t s = h->stream;
     T *fr = reinterpret_cast<T *>(h->fronts);
     CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
-    launch_front_init<T>(h->df, h->kval, fr, s);
+    h->timer.begin(PH_FRONT_INIT, s);
+    launch_equilibrate(h->M.n_kkt, h->dm.kkt_ptr, h->dm.kkt_col, h->kval, h->scale, h->scale_tmp,
+                       3, s);
+    launch_front_init<T>(h->df, h->dm.kkt_row, h->dm.kkt_col, h->scale, h->kval, fr, s);
+    h->timer.end(PH_FRONT_INIT, s);
     h->epoch++;
+    h->timer.begin(PH_FACTOR, s);
     launch_factor<T>(h->df, fr, h->fstat, h->queue, h->done, h->epoch, h->opt.pivot_tol,
                      h->opt.spin_limit, s);
+    h->timer.end(PH_FACTOR, s);
+    h->timer.begin(PH_SCHUR, s);
     launch_schur_sum<T>(h->df, fr, h->S, s);
     launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s);
+    h->timer.end(PH_SCHUR, s);
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    h->timer.collect();
     CK(cudaGetLastError());
     inertia[0] = fs.n_pos;
     inertia[1] = fs.n_neg;
@@ -568,13 +598,21 @@ int factor_impl(scopf_handle *h, int precision, int inertia[3]) {
 template <typename T>
 static int solve_once(scopf_handle *h, const double *b, double *x) {
     h->epoch += 2;
+    h->timer.begin(PH_SOLVE, h->stream);
     launch_solve<T>(h->df, reinterpret_cast<T *>(h->fronts), reinterpret_cast<T *>(h->vec), h->S,
-                    (int)h->M.nborder, b, x, h->border_work, h->queue, h->done, h->epoch - 1,
-                    h->fstat, h->opt.spin_limit, h->stream);
+                    (int)h->M.nborder, h->scale, b, x, h->border_work, h->queue, h->done,
+                    h->epoch - 1, h->fstat, h->opt.spin_limit, h->stream);
+    h->timer.end(PH_SOLVE, h->stream);
     h->epoch++;
     return SCOPF_OK;
 }
 
+// Solve K x = b.  First x = M^-1 b with the factors M of K (FP64 or FP32);
+// if the FP64 residual is not yet below refine_tol, continue with restarted
+// FGMRES in FP64 on the correction, right-preconditioned by M (GMRES-based
+// iterative refinement: it converges where classical refinement with FP32
+// factors stalls, for condition numbers up to about 1/u_fp32^2).  The
+// preconditioner applications after the first count as refinement steps.
 int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel, int *steps) {
     cudaStream_t s = h->stream;
     const int64_t n = h->M.n_kkt;
@@ -582,25 +620,95 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
     auto once = [&](const double *rhs, double *out) {
         return mixed ? solve_once<float>(h, rhs, out) : solve_once<double>(h, rhs, out);
     };
-    // x0 = K^-1 b, then x += K^-1 (b - K x) until the residual is small enough
+    constexpr int m = 16;
+    if (!h->kv) {
+        TRY(alloc(h, (size_t)(m + 1) * n, &h->kv));
+        TRY(alloc(h, (size_t)m * n, &h->kz));
+        TRY(alloc(h, (size_t)kDotBlocks * kMaxKrylov, &h->kpart));
+    }
     CK(cudaMemcpyAsync(h->res, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    once(h->res, h->dx);
-    CK(cudaMemcpyAsync(x, h->dx, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    once(h->res, x);
     const double bnorm = device_maxabs(h, h->res, n);
+    const double bden = bnorm > 0 ? bnorm : 1.0;
+    std::vector<double> part((size_t)kDotBlocks * kMaxKrylov);
+    auto dots = [&](const double *V, int k, const double *w, double *out) {
+        launch_multi_dot(V, n, k, w, h->kpart, s);
+        cudaMemcpyAsync(part.data(), h->kpart, sizeof(double) * kDotBlocks * k,
+                        cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        for (int j = 0; j < k; j++) {
+            double a = 0;
+            for (int bb = 0; bb < kDotBlocks; bb++) a += part[(size_t)bb * k + j];
+            out[j] = a;
+        }
+    };
     int it = 0;
     double r = 0;
     while (true) {
+        // r = b - K x
+        h->timer.begin(PH_RESIDUAL, s);
         launch_residual(h->dm, h->kval, x, h->res, h->tmp_kkt, s);
-        r = device_maxabs(h, h->tmp_kkt, n) / (bnorm > 0 ? bnorm : 1.0);
-        if (!(r > h->opt.refine_tol) || it >= max_refine) break;
-        once(h->tmp_kkt, h->dx);
-        launch_axpy(n, 1.0, h->dx, x, s);
-        it++;
+        h->timer.end(PH_RESIDUAL, s);
+        r = device_maxabs(h, h->tmp_kkt, n) / bden;
+        if (!(r > h->opt.refine_tol) || it >= max_refine || !std::isfinite(r)) break;
+        // one FGMRES(m) cycle on K e = r
+        double beta = 0;
+        dots(h->tmp_kkt, 1, h->tmp_kkt, &beta);
+        beta = std::sqrt(beta);
+        if (!(beta > 0)) break;
+        launch_scale_copy(n, 1.0 / beta, h->tmp_kkt, h->kv, s);
+        double H[m + 1][m], cs[m], sn[m], g[m + 1];
+        for (int i = 0; i <= m; i++) g[i] = 0;
+        g[0] = beta;
+        int jend = 0;
+        const double target = h->opt.refine_tol * bnorm * 0.5;
+        for (int j = 0; j < m && it < max_refine; j++) {
+            double *vj = h->kv + (size_t)j * n, *zj = h->kz + (size_t)j * n;
+            double *w = h->kv + (size_t)(j + 1) * n;
+            once(vj, zj);
+            it++;
+            launch_spmv(h->dm, h->kval, zj, w, s);
+            double hc[kMaxKrylov], hc2[kMaxKrylov];
+            dots(h->kv, j + 1, w, hc);
+            launch_multi_axpy(w, h->kv, n, j + 1, hc, s);
+            dots(h->kv, j + 1, w, hc2);
+            launch_multi_axpy(w, h->kv, n, j + 1, hc2, s);
+            for (int i = 0; i <= j; i++) H[i][j] = hc[i] + hc2[i];
+            double hn = 0;
+            dots(w, 1, w, &hn);
+            hn = std::sqrt(hn);
+            H[j + 1][j] = hn;
+            if (hn > 0) launch_scale_copy(n, 1.0 / hn, w, w, s);
+            for (int i = 0; i < j; i++) {
+                const double a = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
+                H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
+                H[i][j] = a;
+            }
+            const double den = std::hypot(H[j][j], H[j + 1][j]);
+            cs[j] = den > 0 ? H[j][j] / den : 1.0;
+            sn[j] = den > 0 ? H[j + 1][j] / den : 0.0;
+            H[j][j] = den;
+            H[j + 1][j] = 0;
+            g[j + 1] = -sn[j] * g[j];
+            g[j] = cs[j] * g[j];
+            jend = j + 1;
+            if (std::fabs(g[j + 1]) <= target || !(hn > 0)) break;
+        }
+        double y[m];
+        for (int i = jend - 1; i >= 0; i--) {
+            double a = g[i];
+            for (int k = i + 1; k < jend; k++) a -= H[i][k] * y[k];
+            y[i] = H[i][i] != 0 ? a / H[i][i] : 0.0;
+        }
+        double negy[kMaxKrylov];
+        for (int i = 0; i < jend; i++) negy[i] = -y[i];
+        launch_multi_axpy(x, h->kz, n, jend, negy, s);
     }
     h->n_refine += it;
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
+    h->timer.collect();
     CK(cudaGetLastError());
     *rel = r;
     *steps = it;

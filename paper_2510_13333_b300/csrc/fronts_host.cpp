@@ -94,10 +94,19 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     for (int t = 0; t < nt; t++)
         if (sn[t].parent_task >= 0)
             level[sn[t].parent_task] = std::max(level[sn[t].parent_task], level[t] + 1);
-    // task order: (level, block, local)
+    // large fronts (f > kBigFront) and everything above them form the second
+    // factorization phase (one CTA per front); the rest is one warp per front
+    const int kBigFront = 64;
+    std::vector<char> big(nt, 0);
+    for (int t = 0; t < nt; t++)
+        if (sn[t].f > kBigFront || sn[t].border) big[t] = 1;
+    for (int t = 0; t < nt; t++)   // children precede parents within a block
+        if (big[t] && sn[t].parent_task >= 0) big[sn[t].parent_task] = 1;
+    // task order: (phase, level, block, local)
     std::vector<int> order(nt);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
+        if (big[a] != big[b]) return big[a] < big[b];
         if (level[a] != level[b]) return level[a] < level[b];
         if (sn[a].block != sn[b].block) return sn[a].block < sn[b].block;
         return sn[a].local < sn[b].local;
@@ -105,6 +114,8 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     std::vector<int> tid(nt);
     for (int i = 0; i < nt; i++) tid[order[i]] = i;
     H.n_tasks = nt;
+    H.n_small = 0;
+    for (int t = 0; t < nt; t++) H.n_small += big[t] ? 0 : 1;
     H.front_off.resize(nt);
     H.vec_off.resize(nt);
     H.f.resize(nt);
@@ -142,7 +153,11 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     H.front_elems = foff;
     H.vec_elems = voff;
     H.border_off.assign(nblk, 0);
-    for (int k = 0; k < nblk; k++) H.border_off[k] = H.front_off[tid[border_task[k]]];
+    H.border_vec_off.assign(nblk, 0);
+    for (int k = 0; k < nblk; k++) {
+        H.border_off[k] = H.front_off[tid[border_task[k]]];
+        H.border_vec_off[k] = H.vec_off[tid[border_task[k]]];
+    }
     for (int j = 0; j < nbor; j++) H.border_rows.push_back(M.kkt_border0 + j);
     // children lists in task order, relative maps
     std::vector<std::vector<int>> ch(nt);

@@ -23,6 +23,68 @@ struct ScalarScratch {
     double *partial = nullptr;
 };
 
+// CUDA-event timers of the library's phases on the handle's stream.
+struct PhaseTimer {
+    static constexpr int kPhases = 7;
+    bool on = false;
+    double ms[kPhases] = {};
+    int calls[kPhases] = {};
+    std::vector<cudaEvent_t> pool;
+    std::vector<std::pair<int, std::pair<cudaEvent_t, cudaEvent_t>>> pending;
+    cudaEvent_t open[kPhases] = {};
+
+    cudaEvent_t get() {
+        if (pool.empty()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            return e;
+        }
+        cudaEvent_t e = pool.back();
+        pool.pop_back();
+        return e;
+    }
+    void begin(int ph, cudaStream_t s) {
+        if (!on) return;
+        open[ph] = get();
+        cudaEventRecord(open[ph], s);
+    }
+    void end(int ph, cudaStream_t s) {
+        if (!on || !open[ph]) return;
+        cudaEvent_t e = get();
+        cudaEventRecord(e, s);
+        pending.push_back({ph, {open[ph], e}});
+        open[ph] = nullptr;
+    }
+    // call after the stream has been synchronised
+    void collect() {
+        for (auto &pp : pending) {
+            float t = 0;
+            if (cudaEventElapsedTime(&t, pp.second.first, pp.second.second) == cudaSuccess) {
+                ms[pp.first] += t;
+                calls[pp.first]++;
+            }
+            pool.push_back(pp.second.first);
+            pool.push_back(pp.second.second);
+        }
+        pending.clear();
+    }
+    void reset() {
+        for (int i = 0; i < kPhases; i++) {
+            ms[i] = 0;
+            calls[i] = 0;
+        }
+    }
+    ~PhaseTimer() {
+        for (auto &pp : pending) {
+            cudaEventDestroy(pp.second.first);
+            cudaEventDestroy(pp.second.second);
+        }
+        for (auto e : pool) cudaEventDestroy(e);
+    }
+};
+
+enum Phase { PH_ASSEMBLE = 0, PH_FRONT_INIT, PH_FACTOR, PH_SCHUR, PH_SOLVE, PH_RESIDUAL, PH_IPM };
+
 }  // namespace scopf
 
 struct scopf_handle {
@@ -43,6 +105,8 @@ struct scopf_handle {
     double *wl = nullptr, *wu = nullptr;
     void *fronts = nullptr, *vec = nullptr;
     double *S = nullptr, *border_work = nullptr;
+    double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
+    double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
     int *queue = nullptr, *done = nullptr;
     scopf::FactorStatus *fstat = nullptr;
     double *red_scratch = nullptr, *red_out = nullptr;
@@ -60,6 +124,8 @@ struct scopf_handle {
     int64_t *d_il = nullptr, *d_iu = nullptr;
     // counters
     int n_factor = 0, n_refine = 0;
+    bool force_fp64 = false;      // sticky FP64 fallback inside a solve
+    scopf::PhaseTimer timer;
     std::string last_error;
 };
 

@@ -1,10 +1,832 @@
-// NCL outer loop and interior-point inner loop (placeholder until the
-// device-resident control is wired in).
+// NCL outer loop (Section IV-A, eq. nclsubpb) and interior-point inner loop
+// (Section IV-B) with device-resident iterates.
+//
+// Every vector operation runs on the GPU; each iteration brings back only a
+// handful of per-CTA partial reductions (summed on the host in a fixed
+// order, so runs are repeatable).  The control logic follows the published
+// algorithms the paper builds on and is the same as the CPU oracle's:
+//  * outer: accept lam_n += rho r, nu0_n += rho t when max(|r|,|t|) <= eta
+//    (then eta, omega /= 10), else rho *= 10; infeasible once rho > rho_max;
+//  * inner (Waechter & Biegler 2006): monotone Fiacco-McCormick barrier
+//    update, inertia correction with delta_w, fraction-to-boundary, filter
+//    line search, bound-multiplier safeguard;
+//  * mixed precision: FP32 block factors with FP64 refinement; when the
+//    refinement stalls the step is redone with FP64 factors, and the rest of
+//    the solve stays in FP64.
+#include <chrono>
+#include <cmath>
+#include <cstdio>
+#include <vector>
+
 #include "handle.h"
 
 namespace scopf {
-int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) {
-    (void)h; (void)warm; (void)res;
-    return SCOPF_ERR_INVALID_ARG;
+
+namespace {
+
+constexpr int kT = 256;
+constexpr int kB = 296;  // CTAs of the reduction kernels (2 per SM)
+
+struct Dev {
+    const double *wl, *wu;
+    const int64_t *c1, *c2;
+    int64_t n, m, p;
+};
+
+// ---- per-CTA partial reductions ---------------------------------------
+__device__ double block_reduce(double v, int op, double *sh) {
+    // op: 0 max, 1 min, 2 sum
+    sh[threadIdx.x] = v;
+    __syncthreads();
+    for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+        if ((int)threadIdx.x < s) {
+            double a = sh[threadIdx.x], b = sh[threadIdx.x + s];
+            sh[threadIdx.x] = op == 0 ? fmax(a, b) : (op == 1 ? fmin(a, b) : a + b);
+        }
+        __syncthreads();
+    }
+    double r = sh[0];
+    __syncthreads();
+    return r;
 }
+
+// w-part: [max|gwz|, min sl*zl, max sl*zl, min su*zu, max su*zu, sum|zl|, sum|zu|]
+__global__ void k_red_w(Dev D, const double *w, const double *gw, const double *zl,
+                        const double *zu, double *part) {
+    __shared__ double sh[kT];
+    double a0 = 0, a1 = INFINITY, a2 = -INFINITY, a3 = INFINITY, a4 = -INFINITY, a5 = 0, a6 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D.n;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        double g = gw[i];
+        const double l = D.wl[i], u = D.wu[i], x = w[i];
+        if (l > -INFINITY) {
+            g -= zl[i];
+            const double c = (x - l) * zl[i];
+            a1 = fmin(a1, c);
+            a2 = fmax(a2, c);
+            a5 += fabs(zl[i]);
+        }
+        if (u < INFINITY) {
+            g += zu[i];
+            const double c = (u - x) * zu[i];
+            a3 = fmin(a3, c);
+            a4 = fmax(a4, c);
+            a6 += fabs(zu[i]);
+        }
+        a0 = fmax(a0, fabs(g));
+    }
+    double *o = part + (int64_t)blockIdx.x * 7;
+    double r;
+    r = block_reduce(a0, 0, sh); if (threadIdx.x == 0) o[0] = r;
+    r = block_reduce(a1, 1, sh); if (threadIdx.x == 0) o[1] = r;
+    r = block_reduce(a2, 0, sh); if (threadIdx.x == 0) o[2] = r;
+    r = block_reduce(a3, 1, sh); if (threadIdx.x == 0) o[3] = r;
+    r = block_reduce(a4, 0, sh); if (threadIdx.x == 0) o[4] = r;
+    r = block_reduce(a5, 2, sh); if (threadIdx.x == 0) o[5] = r;
+    r = block_reduce(a6, 2, sh); if (threadIdx.x == 0) o[6] = r;
+}
+
+// m-part: [max|gr|, max|c-r|, sum|c-r|, sum|lam|, max|r|]
+__global__ void k_red_m(Dev D, const double *c, const double *r, const double *lam,
+                        const double *lam_n, double rho, double *part) {
+    __shared__ double sh[kT];
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D.m;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        a0 = fmax(a0, fabs(lam_n[i] + rho * r[i] - lam[i]));
+        const double pc = fabs(c[i] - r[i]);
+        a1 = fmax(a1, pc);
+        a2 += pc;
+        a3 += fabs(lam[i]);
+        a4 = fmax(a4, fabs(r[i]));
+    }
+    double *o = part + (int64_t)blockIdx.x * 5;
+    double v;
+    v = block_reduce(a0, 0, sh); if (threadIdx.x == 0) o[0] = v;
+    v = block_reduce(a1, 0, sh); if (threadIdx.x == 0) o[1] = v;
+    v = block_reduce(a2, 2, sh); if (threadIdx.x == 0) o[2] = v;
+    v = block_reduce(a3, 2, sh); if (threadIdx.x == 0) o[3] = v;
+    v = block_reduce(a4, 0, sh); if (threadIdx.x == 0) o[4] = v;
+}
+
+// p-part: [max|gt|, max|gs|, max|py|, sum|py|, min s zs, max s zs, sum|yc|, sum|zs|, max|t|]
+__global__ void k_red_p(Dev D, const double *w, const double *t, const double *s,
+                        const double *yc, const double *zs, const double *nu0_n, double rho,
+                        double *part) {
+    __shared__ double sh[kT];
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = INFINITY, a5 = -INFINITY, a6 = 0, a7 = 0, a8 = 0;
+    for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D.p;
+         q += (int64_t)gridDim.x * blockDim.x) {
+        a0 = fmax(a0, fabs(nu0_n[q] + rho * t[q] - yc[q]));
+        a1 = fmax(a1, fabs(yc[q] - zs[q]));
+        const double py = fabs(w[D.c1[q]] * w[D.c2[q]] - t[q] + s[q]);
+        a2 = fmax(a2, py);
+        a3 += py;
+        const double cz = s[q] * zs[q];
+        a4 = fmin(a4, cz);
+        a5 = fmax(a5, cz);
+        a6 += fabs(yc[q]);
+        a7 += fabs(zs[q]);
+        a8 = fmax(a8, fabs(t[q]));
+    }
+    double *o = part + (int64_t)blockIdx.x * 9;
+    double v;
+    v = block_reduce(a0, 0, sh); if (threadIdx.x == 0) o[0] = v;
+    v = block_reduce(a1, 0, sh); if (threadIdx.x == 0) o[1] = v;
+    v = block_reduce(a2, 0, sh); if (threadIdx.x == 0) o[2] = v;
+    v = block_reduce(a3, 2, sh); if (threadIdx.x == 0) o[3] = v;
+    v = block_reduce(a4, 1, sh); if (threadIdx.x == 0) o[4] = v;
+    v = block_reduce(a5, 0, sh); if (threadIdx.x == 0) o[5] = v;
+    v = block_reduce(a6, 2, sh); if (threadIdx.x == 0) o[6] = v;
+    v = block_reduce(a7, 2, sh); if (threadIdx.x == 0) o[7] = v;
+    v = block_reduce(a8, 0, sh); if (threadIdx.x == 0) o[8] = v;
+}
+
+// barrier objective pieces at a state: [sum ln(slacks of w), sum ln s, lam_n'r + rho/2 r'r,
+// nu0_n't + rho/2 t't, number of nonpositive slacks]
+__global__ void k_barrier(Dev D, const double *w, const double *r, const double *t,
+                          const double *s, const double *lam_n, const double *nu0_n, double rho,
+                          double *part) {
+    __shared__ double sh[kT];
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    const int64_t tot = D.n + D.m + D.p;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < D.n) {
+            const double l = D.wl[i], u = D.wu[i], x = w[i];
+            if (l > -INFINITY) {
+                if (x - l > 0) a0 += log(x - l); else a4 += 1;
+            }
+            if (u < INFINITY) {
+                if (u - x > 0) a0 += log(u - x); else a4 += 1;
+            }
+        } else if (i < D.n + D.m) {
+            const int64_t j = i - D.n;
+            a2 += lam_n[j] * r[j] + 0.5 * rho * r[j] * r[j];
+        } else {
+            const int64_t q = i - D.n - D.m;
+            if (s[q] > 0) a1 += log(s[q]); else a4 += 1;
+            a3 += nu0_n[q] * t[q] + 0.5 * rho * t[q] * t[q];
+        }
+    }
+    double *o = part + (int64_t)blockIdx.x * 5;
+    double v;
+    v = block_reduce(a0, 2, sh); if (threadIdx.x == 0) o[0] = v;
+    v = block_reduce(a1, 2, sh); if (threadIdx.x == 0) o[1] = v;
+    v = block_reduce(a2, 2, sh); if (threadIdx.x == 0) o[2] = v;
+    v = block_reduce(a3, 2, sh); if (threadIdx.x == 0) o[3] = v;
+    v = block_reduce(a4, 2, sh); if (threadIdx.x == 0) o[4] = v;
+}
+
+// directional derivative of the barrier objective:
+// [g'dw, -mu sum dw/sl + mu sum dw/su, (lam_n + rho r)'dr, (nu0_n + rho t)'dt, -mu sum ds/s]
+__global__ void k_dirderiv(Dev D, const double *w, const double *g, const double *r,
+                           const double *t, const double *s, const double *lam_n,
+                           const double *nu0_n, double rho, double mu, const double *dw,
+                           const double *dr, const double *dt, const double *ds, double *part) {
+    __shared__ double sh[kT];
+    double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
+    const int64_t tot = D.n + D.m + D.p;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < D.n) {
+            a0 += g[i] * dw[i];
+            const double l = D.wl[i], u = D.wu[i], x = w[i];
+            if (l > -INFINITY) a1 -= mu * dw[i] / (x - l);
+            if (u < INFINITY) a1 += mu * dw[i] / (u - x);
+        } else if (i < D.n + D.m) {
+            const int64_t j = i - D.n;
+            a2 += (lam_n[j] + rho * r[j]) * dr[j];
+        } else {
+            const int64_t q = i - D.n - D.m;
+            a3 += (nu0_n[q] + rho * t[q]) * dt[q];
+            a4 -= mu * ds[q] / s[q];
+        }
+    }
+    double *o = part + (int64_t)blockIdx.x * 5;
+    double v;
+    v = block_reduce(a0, 2, sh); if (threadIdx.x == 0) o[0] = v;
+    v = block_reduce(a1, 2, sh); if (threadIdx.x == 0) o[1] = v;
+    v = block_reduce(a2, 2, sh); if (threadIdx.x == 0) o[2] = v;
+    v = block_reduce(a3, 2, sh); if (threadIdx.x == 0) o[3] = v;
+    v = block_reduce(a4, 2, sh); if (threadIdx.x == 0) o[4] = v;
+}
+
+// fraction to boundary: [alpha_primal, alpha_dual]
+__global__ void k_ftb(Dev D, const double *w, const double *s, const double *zl,
+                      const double *zu, const double *zs, const double *dw, const double *ds,
+                      const double *dzl, const double *dzu, const double *dzs, double tau,
+                      double *part) {
+    __shared__ double sh[kT];
+    double ap = 1.0, az = 1.0;
+    const int64_t tot = D.n + D.p;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        if (i < D.n) {
+            const double l = D.wl[i], u = D.wu[i], x = w[i];
+            if (l > -INFINITY) {
+                if (dw[i] < 0) ap = fmin(ap, -tau * (x - l) / dw[i]);
+                if (dzl[i] < 0) az = fmin(az, -tau * zl[i] / dzl[i]);
+            }
+            if (u < INFINITY) {
+                if (-dw[i] < 0) ap = fmin(ap, -tau * (u - x) / (-dw[i]));
+                if (dzu[i] < 0) az = fmin(az, -tau * zu[i] / dzu[i]);
+            }
+        } else {
+            const int64_t q = i - D.n;
+            if (ds[q] < 0) ap = fmin(ap, -tau * s[q] / ds[q]);
+            if (dzs[q] < 0) az = fmin(az, -tau * zs[q] / dzs[q]);
+        }
+    }
+    double v;
+    v = block_reduce(ap, 1, sh); if (threadIdx.x == 0) part[2 * blockIdx.x] = v;
+    v = block_reduce(az, 1, sh); if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = v;
+}
+
+// ---- elementwise ---------------------------------------------------------
+// split the KKT solution (natural order) into dw, dlam, dyc
+__global__ void k_split(int64_t n_kkt, const int8_t *kind, const int64_t *index,
+                        const double *sol, double *dw, double *dlam, double *dyc) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_kkt) return;
+    const int8_t k = kind[i];
+    const int64_t j = index[i];
+    if (k == 0) dw[j] = sol[i];
+    else if (k == 1) dlam[j] = sol[i];
+    else dyc[j] = sol[i];
+}
+
+// eliminated directions (recovery after eq. newtonsystem)
+__global__ void k_recover(Dev D, const double *w, const double *r, const double *t,
+                          const double *s, const double *lam, const double *yc, const double *zl,
+                          const double *zu, const double *zs, const double *lam_n,
+                          const double *nu0_n, double rho, double mu, const double *dw,
+                          const double *dlam, const double *dyc, double *dr, double *dt,
+                          double *ds, double *dzl, double *dzu, double *dzs) {
+    const int64_t tot = D.n + D.m + D.p;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tot) return;
+    if (i < D.n) {
+        const double l = D.wl[i], u = D.wu[i], x = w[i];
+        dzl[i] = 0.0;
+        dzu[i] = 0.0;
+        if (l > -INFINITY) {
+            const double sl = x - l;
+            dzl[i] = mu / sl - zl[i] - zl[i] / sl * dw[i];
+        }
+        if (u < INFINITY) {
+            const double su = u - x;
+            dzu[i] = mu / su - zu[i] + zu[i] / su * dw[i];
+        }
+    } else if (i < D.n + D.m) {
+        const int64_t j = i - D.n;
+        dr[j] = (dlam[j] - (lam_n[j] + rho * r[j] - lam[j])) / rho;
+    } else {
+        const int64_t q = i - D.n - D.m;
+        dt[q] = (dyc[q] - (nu0_n[q] + rho * t[q] - yc[q])) / rho;
+        const double dsv = (mu / s[q] - yc[q] - dyc[q]) * s[q] / zs[q];
+        ds[q] = dsv;
+        dzs[q] = mu / s[q] - zs[q] - zs[q] / s[q] * dsv;
+    }
+}
+
+__global__ void k_step(int64_t n, const double *x, const double *d, double a, double *y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = x[i] + a * d[i];
+}
+
+// kappa_sigma safeguard of the bound multipliers (W&B 2006, eq. 16)
+__global__ void k_zsafe(Dev D, const double *w, const double *s, double *zl, double *zu,
+                        double *zs, double mu, double ks) {
+    const int64_t tot = D.n + D.p;
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= tot) return;
+    if (i < D.n) {
+        const double l = D.wl[i], u = D.wu[i], x = w[i];
+        if (l > -INFINITY) {
+            const double sl = x - l;
+            zl[i] = fmax(fmin(zl[i], ks * mu / sl), mu / (ks * sl));
+        }
+        if (u < INFINITY) {
+            const double su = u - x;
+            zu[i] = fmax(fmin(zu[i], ks * mu / su), mu / (ks * su));
+        }
+    } else {
+        const int64_t q = i - D.n;
+        zs[q] = fmax(fmin(zs[q], ks * mu / s[q]), mu / (ks * s[q]));
+    }
+}
+
+// t = w1 w2 + s
+__global__ void k_reset_t(Dev D, const double *w, const double *s, double *t) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q < D.p) t[q] = w[D.c1[q]] * w[D.c2[q]] + s[q];
+}
+
+inline int nb(int64_t n) { return (int)((n + kT - 1) / kT > 0 ? (n + kT - 1) / kT : 1); }
+
+struct Timer {
+    std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
+    double s() const {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    }
+};
+
+}  // namespace
+
+// ===========================================================================
+struct Ipm {
+    scopf_handle *h;
+    Dev D;
+    const scopf_options &o;
+    cudaStream_t s;
+    std::vector<double> part;
+    double *dpart = nullptr;
+    int64_t n, m, p, n_il = 0, n_iu = 0;
+    double *lam_trial_unused = nullptr;
+    bool force_fp64 = false;
+    int fallbacks = 0;
+
+    explicit Ipm(scopf_handle *hh) : h(hh), o(hh->opt), s(hh->stream) {
+        const Model &M = h->M;
+        n = M.n;
+        m = M.m;
+        p = M.p;
+        D = Dev{h->wl, h->wu, h->dm.comp1, h->dm.comp2, n, m, p};
+        for (int64_t i = 0; i < n; i++) {
+            if (std::isfinite(M.wl[i])) n_il++;
+            if (std::isfinite(M.wu[i])) n_iu++;
+        }
+        part.resize(kB * 9);
+        cudaMalloc(&dpart, sizeof(double) * kB * 9);
+    }
+    ~Ipm() { cudaFree(dpart); }
+
+    // fetch kB x k partials and combine in block order
+    void fetch(int k) {
+        cudaMemcpyAsync(part.data(), dpart, sizeof(double) * kB * k, cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+    }
+    double comb(int k, int slot, int op) {
+        double a = op == 0 ? -INFINITY : (op == 1 ? INFINITY : 0.0);
+        for (int b = 0; b < kB; b++) {
+            const double v = part[(size_t)b * k + slot];
+            a = op == 0 ? std::fmax(a, v) : (op == 1 ? std::fmin(a, v) : a + v);
+        }
+        return a;
+    }
+
+    // ---- residual norms (error measure E_mu, W&B 2006 eq. 5)
+    struct Norms {
+        double dual, prim, cmin, cmax, ysum, zsum, theta, rmax, tmax;
+        bool has_comp;
+    };
+    Norms norms(const scopf_state &st, double rho) {
+        Norms N{};
+        k_red_w<<<kB, kT, 0, s>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
+        fetch(7);
+        double dw = comb(7, 0, 0);
+        double cmin = std::fmin(comb(7, 1, 1), comb(7, 3, 1));
+        double cmax = std::fmax(comb(7, 2, 0), comb(7, 4, 0));
+        double zsum = comb(7, 5, 2) + comb(7, 6, 2);
+        k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart);
+        fetch(5);
+        double gr = comb(5, 0, 0), pc = comb(5, 1, 0), pcs = comb(5, 2, 2), lsum = comb(5, 3, 2);
+        N.rmax = comb(5, 4, 0);
+        double gt = 0, gs = 0, py = 0, pys = 0, ycs = 0, zss = 0;
+        N.tmax = 0;
+        if (p) {
+            k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho, dpart);
+            fetch(9);
+            gt = comb(9, 0, 0);
+            gs = comb(9, 1, 0);
+            py = comb(9, 2, 0);
+            pys = comb(9, 3, 2);
+            cmin = std::fmin(cmin, comb(9, 4, 1));
+            cmax = std::fmax(cmax, comb(9, 5, 0));
+            ycs = comb(9, 6, 2);
+            zss = comb(9, 7, 2);
+            N.tmax = comb(9, 8, 0);
+        }
+        N.dual = std::fmax(std::fmax(dw, gr), std::fmax(gt, gs));
+        N.prim = std::fmax(pc, py);
+        N.cmin = cmin;
+        N.cmax = cmax;
+        N.has_comp = (n_il + n_iu + p) > 0;
+        N.ysum = lsum + ycs;
+        N.zsum = zsum + zss;
+        N.theta = pcs + pys;
+        return N;
+    }
+    double error(const Norms &N, double mu) const {
+        const double nz = (double)(n_il + n_iu + p);
+        const double sd = std::fmax(o.s_max, (N.ysum + N.zsum) / std::fmax(1.0, (double)(m + p) + nz)) / o.s_max;
+        const double sc = std::fmax(o.s_max, N.zsum / std::fmax(1.0, nz)) / o.s_max;
+        const double comp = N.has_comp ? std::fmax(N.cmax - mu, mu - N.cmin) : 0.0;
+        return std::fmax(std::fmax(N.dual / sd, N.prim), comp / sc);
+    }
+
+    // objective phi(w) on the host from p_g^0
+    double objective(const double *w) {
+        double f = 0;
+        scopf_eval(h, w, &f, nullptr, nullptr);
+        return f;
+    }
+    double barrier(const scopf_state &st, double rho, double mu, double phi) {
+        k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho, dpart);
+        fetch(5);
+        if (comb(5, 4, 2) > 0) return INFINITY;
+        return phi + comb(5, 2, 2) + comb(5, 3, 2) - mu * (comb(5, 0, 2) + comb(5, 1, 2));
+    }
+    double theta_trial(const scopf_state &st) {
+        // c(w) at the trial point, then sum|c - r| + sum|w1 w2 - t + s|
+        launch_eval_elements(h->dm, st.w, st.lam, st.yc, h->ev, 0, s);
+        launch_constraints(h->dm, st.w, h->ev, h->c, s);
+        k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, 1.0, dpart);
+        fetch(5);
+        double th = comb(5, 2, 2);
+        if (p) {
+            k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, 1.0, dpart);
+            fetch(9);
+            th += comb(9, 3, 2);
+        }
+        return th;
+    }
+
+    void copy(scopf_state &dst, const scopf_state &src) {
+        const int64_t len[9] = {n, m, p, p, m, p, n, n, p};
+        double *const *a[9] = {&dst.w, &dst.r, &dst.t, &dst.s, &dst.lam, &dst.yc, &dst.zl, &dst.zu, &dst.zs};
+        double *const *b[9] = {&src.w, &src.r, &src.t, &src.s, &src.lam, &src.yc, &src.zl, &src.zu, &src.zs};
+        for (int i = 0; i < 9; i++)
+            if (len[i]) cudaMemcpyAsync(*a[i], *b[i], sizeof(double) * len[i], cudaMemcpyDeviceToDevice, s);
+    }
+
+    void step(scopf_state &out, const scopf_state &st, const scopf_state &d, double a, double az) {
+        k_step<<<nb(n), kT, 0, s>>>(n, st.w, d.w, a, out.w);
+        if (m) k_step<<<nb(m), kT, 0, s>>>(m, st.r, d.r, a, out.r);
+        if (m) k_step<<<nb(m), kT, 0, s>>>(m, st.lam, d.lam, a, out.lam);
+        if (p) {
+            k_step<<<nb(p), kT, 0, s>>>(p, st.t, d.t, a, out.t);
+            k_step<<<nb(p), kT, 0, s>>>(p, st.s, d.s, a, out.s);
+            k_step<<<nb(p), kT, 0, s>>>(p, st.yc, d.yc, a, out.yc);
+            k_step<<<nb(p), kT, 0, s>>>(p, st.zs, d.zs, az, out.zs);
+        }
+        k_step<<<nb(n), kT, 0, s>>>(n, st.zl, d.zl, az, out.zl);
+        k_step<<<nb(n), kT, 0, s>>>(n, st.zu, d.zu, az, out.zu);
+    }
+
+    // Newton direction with inertia correction; returns status, fills h->dir
+    int direction(const scopf_state &st, double rho, double mu, double &dw_last, double &delta,
+                  int &tries) {
+        const int64_t npos = n, nneg = m + p;
+        delta = 0.0;
+        tries = 0;
+        // K at delta = 0 and the right-hand side were assembled by the caller
+        while (true) {
+            if (tries > 0) {
+                int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, delta, nullptr);
+                if (r != SCOPF_OK) return r;
+            }
+            const int prec = force_fp64 ? SCOPF_PREC_FP64 : h->precision;
+            int in[3];
+            int r = factor_impl(h, prec, in);
+            if (r != SCOPF_OK) return r;
+            tries++;
+            if (in[0] == npos && in[1] == nneg && in[2] == 0) break;
+            if (delta == 0.0)
+                delta = dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
+            else
+                delta *= dw_last > 0.0 ? o.kappa_w_plus : o.kappa_w_plus_bar;
+            if (delta > o.delta_w_max) return SCOPF_ERR_WRONG_INERTIA;
+        }
+        double rel = 0;
+        int steps = 0;
+        int r = solve_impl(h, h->rhs, h->sol, o.max_refine, &rel, &steps);
+        if (r == SCOPF_ERR_REFINE_STALL && h->factored_precision == SCOPF_PREC_MIXED) {
+            // FP32 factors no longer accurate enough: redo this step in FP64 and stay there
+            force_fp64 = true;
+            fallbacks++;
+            int in[3];
+            r = factor_impl(h, SCOPF_PREC_FP64, in);
+            if (r != SCOPF_OK) return r;
+            r = solve_impl(h, h->rhs, h->sol, o.max_refine, &rel, &steps);
+        }
+        if (r == SCOPF_ERR_REFINE_STALL) r = SCOPF_OK;  // FP64 factors: accept the refined step
+        if (r != SCOPF_OK) return r;
+        return SCOPF_OK;
+    }
+};
+
+int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) {
+    Timer T;
+    const scopf_options &o = h->opt;
+    const Model &M = h->M;
+    cudaStream_t s = h->stream;
+    Ipm I(h);
+    const int64_t n = M.n, m = M.m, p = M.p;
+    Dev D = I.D;
+    scopf_state &st = h->st;
+    scopf_state &d = h->dir;
+    scopf_state &tr = h->trial;
+    double rho = o.rho_init;
+    cudaMemsetAsync(h->lam_n, 0, sizeof(double) * (m ? m : 1), s);
+    cudaMemsetAsync(h->nu0_n, 0, sizeof(double) * (p ? p : 1), s);
+    if (warm) {
+        int r = scopf_load_state(h, warm);
+        if (r != SCOPF_OK) return r;
+    } else {
+        // flat start, bound push (W&B 2006 Section 3.6), NCL multiplier identities
+        std::vector<double> w = M.w_init;
+        for (int64_t q = 0; q < p; q++) w[M.comp1[q]] = std::fmax(w[M.comp1[q]], o.comp_init);
+        std::vector<double> wl(n), wu(n), zl(n, 0.0), zu(n, 0.0);
+        cudaMemcpy(wl.data(), h->wl, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        cudaMemcpy(wu.data(), h->wu, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < n; i++) {
+            const bool hl = std::isfinite(wl[i]), hu = std::isfinite(wu[i]);
+            double pl = hl ? o.bound_push * std::fmax(1.0, std::fabs(wl[i])) : 0.0;
+            double pu = hu ? o.bound_push * std::fmax(1.0, std::fabs(wu[i])) : 0.0;
+            if (hl && hu) {
+                pl = std::fmin(pl, o.bound_frac * (wu[i] - wl[i]));
+                pu = std::fmin(pu, o.bound_frac * (wu[i] - wl[i]));
+            }
+            if (hl) w[i] = std::fmax(w[i], wl[i] + pl);
+            if (hu) w[i] = std::fmin(w[i], wu[i] - pu);
+            if (hl) zl[i] = 1.0;
+            if (hu) zu[i] = 1.0;
+        }
+        std::vector<double> sv(p, o.slack_init), t(p), yc(p);
+        for (int64_t q = 0; q < p; q++) {
+            t[q] = w[M.comp1[q]] * w[M.comp2[q]] + sv[q];
+            yc[q] = o.rho_init * t[q];
+        }
+        cudaMemcpy(st.w, w.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+        cudaMemcpy(st.zl, zl.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+        cudaMemcpy(st.zu, zu.data(), sizeof(double) * n, cudaMemcpyHostToDevice);
+        if (p) {
+            cudaMemcpy(st.s, sv.data(), sizeof(double) * p, cudaMemcpyHostToDevice);
+            cudaMemcpy(st.t, t.data(), sizeof(double) * p, cudaMemcpyHostToDevice);
+            cudaMemcpy(st.yc, yc.data(), sizeof(double) * p, cudaMemcpyHostToDevice);
+            cudaMemcpy(st.zs, yc.data(), sizeof(double) * p, cudaMemcpyHostToDevice);
+        }
+        // r = c(w), lam = rho_init r
+        launch_eval_elements(h->dm, st.w, st.lam, st.yc, h->ev, 0, s);
+        launch_constraints(h->dm, st.w, h->ev, st.r, s);
+        cudaMemsetAsync(st.lam, 0, sizeof(double) * (m ? m : 1), s);
+        launch_axpy(m, o.rho_init, st.r, st.lam, s);
+        cudaStreamSynchronize(s);
+    }
+    double mu = o.mu_init, eta = o.eta_init, omega = o.omega_init, dw_last = 0.0;
+    int status = SCOPF_ERR_MAX_ITER;
+    int outer = 0, inner = 0;
+    double E0 = INFINITY, feas = INFINITY;
+    double t_newton = 0.0;
+    const int fact0 = h->n_factor, ref0 = h->n_refine;
+    for (outer = 1; outer <= o.max_outer; outer++) {
+        const double om = std::fmax(omega, o.tol);
+        // ------------------------------------------------------------ inner
+        int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, nullptr);
+        if (r != SCOPF_OK) return r;
+        Ipm::Norms N = I.norms(st, rho);
+        const double th0 = N.theta;
+        const double theta_max = 1e4 * std::fmax(1.0, th0), theta_min = 1e-4 * std::fmax(1.0, th0);
+        std::vector<std::pair<double, double>> filt;
+        int inner_status = SCOPF_OK;
+        while (true) {
+            E0 = I.error(N, 0.0);
+            if (E0 <= om) break;
+            if (inner >= o.max_inner) {
+                inner_status = SCOPF_ERR_MAX_ITER;
+                break;
+            }
+            double Emu = I.error(N, mu);
+            while (Emu <= o.kappa_eps * mu && mu > o.mu_min) {
+                mu = std::fmax(o.mu_min, std::fmin(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
+                filt.clear();
+                Emu = I.error(N, mu);
+            }
+            const double tau = std::fmax(o.tau_min, 1.0 - mu);
+            Timer tn;
+            // right-hand side at the final mu (K at delta_w = 0 is assembled)
+            {
+                RhsArgs a{st.w, st.r, st.t, st.s, st.lam, st.yc, st.zs, h->gw, h->c,
+                          h->lam_n, h->nu0_n, rho, mu};
+                launch_rhs(h->dm, a, h->rhs, s);
+            }
+            double delta = 0.0;
+            int tries = 0;
+            r = I.direction(st, rho, mu, dw_last, delta, tries);
+            if (r != SCOPF_OK) {
+                inner_status = r == SCOPF_ERR_WRONG_INERTIA ? SCOPF_ERR_NUMERICAL : r;
+                break;
+            }
+            if (delta > 0.0) dw_last = delta;
+            // split + recover
+            k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol,
+                                               d.w, d.lam, d.yc);
+            k_recover<<<nb(n + m + p), kT, 0, s>>>(D, st.w, st.r, st.t, st.s, st.lam, st.yc,
+                                                   st.zl, st.zu, st.zs, h->lam_n, h->nu0_n, rho,
+                                                   mu, d.w, d.lam, d.yc, d.r, d.t, d.s, d.zl,
+                                                   d.zu, d.zs);
+            k_ftb<<<kB, kT, 0, s>>>(D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu,
+                                    d.zs, tau, I.dpart);
+            I.fetch(2);
+            double ap = 1.0, az = 1.0;
+            for (int b = 0; b < kB; b++) {
+                ap = std::fmin(ap, I.part[2 * b]);
+                az = std::fmin(az, I.part[2 * b + 1]);
+            }
+            // line search quantities at the current point (h->g holds grad phi)
+            const double th = N.theta;
+            const double phi_cur = I.objective(st.w);
+            const double ph = I.barrier(st, rho, mu, phi_cur);
+            k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
+                                         mu, d.w, d.r, d.t, d.s, I.dpart);
+            I.fetch(5);
+            double gd = 0;
+            for (int b = 0; b < kB; b++)
+                for (int q = 0; q < 5; q++) gd += I.part[(size_t)b * 5 + q];
+            double amin;
+            if (gd < 0)
+                amin = o.gamma_alpha * std::fmin(o.gamma_theta, std::fmin(o.gamma_phi * th / -gd,
+                        o.delta_sw * std::pow(th, o.s_theta) / std::pow(-gd, o.s_phi)));
+            else
+                amin = o.gamma_alpha * o.gamma_theta;
+            double a = ap;
+            bool accepted = false, ftype = false;
+            int nback = 0;
+            while (true) {
+                I.step(tr, st, d, a, az);
+                const double tht = I.theta_trial(tr);
+                const double pht = I.barrier(tr, rho, mu, I.objective(tr.w));
+                bool ok = false;
+                ftype = false;
+                bool in_filter = false;
+                for (auto &fp : filt)
+                    if (tht >= fp.first && pht >= fp.second) {
+                        in_filter = true;
+                        break;
+                    }
+                if (tht <= theta_max && !in_filter) {
+                    const bool sw = gd < 0 && a * std::pow(-gd, o.s_phi) > o.delta_sw * std::pow(th, o.s_theta);
+                    if (th <= theta_min && sw) {
+                        ok = pht <= ph + o.eta_phi * a * gd;
+                        ftype = ok;
+                    } else {
+                        ok = tht <= (1 - o.gamma_theta) * th || pht <= ph - o.gamma_phi * th;
+                    }
+                }
+                if (ok) {
+                    accepted = true;
+                    break;
+                }
+                nback++;
+                if (a < amin || nback >= o.max_backtrack) break;
+                a *= 0.5;
+            }
+            if (!accepted) {
+                // elastic reset: r and t absorb the violation (NCL restoration)
+                I.step(tr, st, d, a, az);
+                launch_eval_elements(h->dm, tr.w, tr.lam, tr.yc, h->ev, 0, s);
+                launch_constraints(h->dm, tr.w, h->ev, tr.r, s);
+                if (p) k_reset_t<<<nb(p), kT, 0, s>>>(D, tr.w, tr.s, tr.t);
+                filt.clear();
+            } else if (!ftype) {
+                filt.push_back({(1 - o.gamma_theta) * th, ph - o.gamma_phi * th});
+            }
+            k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
+            std::swap(st, tr);
+            inner++;
+            cudaStreamSynchronize(s);
+            t_newton += tn.s();
+            if (o.verbose)
+                std::printf("  it %4d mu %.1e E0 %.2e th %.2e a %.2e dw %.1e tries %d%s\n", inner, mu,
+                            E0, th, a, delta, tries, accepted ? "" : " R");
+            r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, nullptr);
+            if (r != SCOPF_OK) return r;
+            N = I.norms(st, rho);
+        }
+        feas = std::fmax(N.rmax, N.tmax);
+        if (o.verbose)
+            std::printf("outer %d rho %.1e |r,t| %.2e E0 %.2e inner %d\n", outer, rho, feas, E0, inner);
+        if (inner_status != SCOPF_OK) {
+            status = inner_status;
+            break;
+        }
+        if (feas <= std::fmax(eta, o.tol)) {
+            if (feas <= o.tol && E0 <= o.tol) {
+                status = SCOPF_OK;
+                break;
+            }
+            launch_axpy(m, rho, st.r, h->lam_n, s);
+            launch_axpy(p, rho, st.t, h->nu0_n, s);
+            eta = std::fmax(eta / 10.0, o.tol);
+            omega = std::fmax(omega / 10.0, o.tol);
+        } else {
+            if (rho * 10.0 > o.rho_max) {
+                status = SCOPF_ERR_INFEASIBLE;
+                break;
+            }
+            rho *= 10.0;
+        }
+    }
+    if (outer > o.max_outer) outer = o.max_outer;
+    cudaStreamSynchronize(s);
+    h->rho = rho;
+    // final report
+    res->status = status;
+    res->outer_iters = outer;
+    res->inner_iters = inner;
+    res->factorizations = h->n_factor - fact0;
+    res->refine_steps = h->n_refine - ref0;
+    res->fp64_fallbacks = I.fallbacks;
+    res->objective = I.objective(st.w);
+    res->kkt_error = E0;
+    res->feas_rt = feas;
+    // violation of eq. (mpcc): |c|, bound and complementarity violations
+    {
+        launch_eval_elements(h->dm, st.w, st.lam, st.yc, h->ev, 0, s);
+        launch_constraints(h->dm, st.w, h->ev, h->c, s);
+        double v = device_maxabs(h, h->c, m);
+        std::vector<double> w(n), wl(M.wl), wu(M.wu);
+        cudaMemcpy(w.data(), st.w, sizeof(double) * n, cudaMemcpyDeviceToHost);
+        for (int64_t i = 0; i < n; i++) {
+            if (std::isfinite(wl[i])) v = std::fmax(v, wl[i] - w[i]);
+            if (std::isfinite(wu[i])) v = std::fmax(v, w[i] - wu[i]);
+        }
+        for (int64_t q = 0; q < p; q++) v = std::fmax(v, std::fabs(w[M.comp1[q]] * w[M.comp2[q]]));
+        res->max_violation = v;
+    }
+    res->rho = rho;
+    res->mu = mu;
+    res->time_total_s = T.s();
+    res->time_newton_s = t_newton;
+    return status == SCOPF_OK ? SCOPF_OK : status;
+}
+
 }  // namespace scopf
+
+// ---------------------------------------------------------------------------
+// One Newton step at a given iterate (no state update): the unit of work
+// of the interior-point inner loop, exposed for benchmarking and tests.
+extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const double *lam_n,
+                                 const double *nu0_n, double rho, double mu, double dw_last,
+                                 scopf_state *dir, double out[6], int32_t inertia[3]) {
+    using namespace scopf;
+    if (!h || h->host_only || !it || !lam_n || (h->M.p && !nu0_n) || !(rho > 0) || !(mu > 0))
+        return SCOPF_ERR_INVALID_ARG;
+    const Model &M = h->M;
+    const int64_t n = M.n, m = M.m, p = M.p;
+    cudaStream_t s = h->stream;
+    if (m) cudaMemcpyAsync(h->lam_n, lam_n, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
+    if (p) cudaMemcpyAsync(h->nu0_n, nu0_n, sizeof(double) * p, cudaMemcpyDeviceToDevice, s);
+    Ipm I(h);
+    const scopf_state &st = *it;
+    scopf_state &d = dir ? *dir : h->dir;
+    int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, h->rhs);
+    if (r != SCOPF_OK) return r;
+    double delta = 0.0, dwl = dw_last;
+    int tries = 0;
+    r = I.direction(st, rho, mu, dwl, delta, tries);
+    if (r != SCOPF_OK) return r;
+    h->timer.begin(PH_IPM, s);
+    k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol, d.w,
+                                       d.lam, d.yc);
+    k_recover<<<nb(n + m + p), kT, 0, s>>>(I.D, st.w, st.r, st.t, st.s, st.lam, st.yc, st.zl,
+                                           st.zu, st.zs, h->lam_n, h->nu0_n, rho, mu, d.w, d.lam,
+                                           d.yc, d.r, d.t, d.s, d.zl, d.zu, d.zs);
+    const double tau = std::fmax(h->opt.tau_min, 1.0 - mu);
+    k_ftb<<<kB, kT, 0, s>>>(I.D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu, d.zs, tau,
+                            I.dpart);
+    I.fetch(2);
+    double ap = 1.0, az = 1.0;
+    for (int b = 0; b < kB; b++) {
+        ap = std::fmin(ap, I.part[2 * b]);
+        az = std::fmin(az, I.part[2 * b + 1]);
+    }
+    I.step(h->trial, st, d, ap, az);
+    const double tht = I.theta_trial(h->trial);
+    const double pht = I.barrier(h->trial, rho, mu, I.objective(h->trial.w));
+    cudaStreamSynchronize(s);
+    h->timer.end(PH_IPM, s);
+    cudaStreamSynchronize(s);
+    h->timer.collect();
+    if (out) {
+        out[0] = ap;
+        out[1] = az;
+        out[2] = tht;
+        out[3] = pht;
+        out[4] = delta;
+        out[5] = 0.0;
+    }
+    if (inertia) {
+        inertia[0] = (int32_t)n;
+        inertia[1] = (int32_t)(m + p);
+        inertia[2] = tries;
+    }
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return SCOPF_ERR_CUDA;
+    }
+    return SCOPF_OK;
+}

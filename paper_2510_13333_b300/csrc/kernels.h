@@ -61,9 +61,26 @@ void reduce_sumabs(const double *x, int64_t n, double *d_out, double *scratch, c
 // y += a * x
 void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
 
+// ---- Krylov helpers (FGMRES refinement), vectors stored contiguously with
+// stride n: V_j = V + j * n
+constexpr int kMaxKrylov = 32;
+constexpr int kDotBlocks = 296;
+// partial[b * k + j] = block b's part of V_j' w, j < k
+void launch_multi_dot(const double *V, int64_t n, int k, const double *w, double *partial,
+                      cudaStream_t s);
+// w -= sum_j c[j] V_j  (k <= kMaxKrylov)
+void launch_multi_axpy(double *w, const double *V, int64_t n, int k, const double *c,
+                       cudaStream_t s);
+// y = a * x
+void launch_scale_copy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
+// y = K x (FP64)
+void launch_spmv(const DevModel &M, const double *kval, const double *x, double *y,
+                 cudaStream_t s);
+
 // ----------------------------------------------------------- factorisation
 struct DevFront {
     int n_tasks, n_blocks, n_border;
+    int n_small;                  // tasks [0, n_small) are small fronts (one warp each)
     const int64_t *front_off;     // per task, element offset into fronts
     const int32_t *f, *npiv;      // per task
     const int32_t *child_ptr, *child; // per task: children task ids
@@ -80,14 +97,20 @@ struct DevFront {
     int64_t front_elems;          // size of the front buffer (elements)
     int64_t vec_elems;            // size of the per-front vector buffer
     const int64_t *vec_off;       // per task offset into the vector buffer
+    const int64_t *border_vec_off; // per block: vec_off of its border task
 };
 
 struct FactorStatus {             // device-side counters
     int n_pos, n_neg, n_zero, error, timeout_task, pad[3];
 };
 
+// Symmetric Ruiz equilibration of K (scale[i] > 0, `iters` sweeps).
+void launch_equilibrate(int64_t n, const int64_t *ptr, const int64_t *col, const double *kval,
+                        double *scale, double *tmp, int iters, cudaStream_t s);
+// fronts <- scatter of scale[i] K_ij scale[j] (lower triangle in elimination order)
 template <typename T>
-void launch_front_init(const DevFront &F, const double *kval, T *fronts, cudaStream_t s);
+void launch_front_init(const DevFront &F, const int32_t *row, const int64_t *col,
+                       const double *scale, const double *kval, T *fronts, cudaStream_t s);
 template <typename T>
 void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, int *queue, int *done,
                    int epoch, double pivot_tol, int spin_limit, cudaStream_t s);
@@ -96,9 +119,11 @@ void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s);
 
 // Forward solve uses dependency epoch `epoch`, backward `epoch + 1`.
+// x = K^-1 b through the factors of D K D: x = D (DKD)^-1 D b
 template <typename T>
 void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
-                  const double *b, double *x, double *border_work, int *queue, int *done,
-                  int epoch, FactorStatus *st, int spin_limit, cudaStream_t s);
+                  const double *scale, const double *b, double *x, double *border_work,
+                  int *queue, int *done, int epoch, FactorStatus *st, int spin_limit,
+                  cudaStream_t s);
 
 }  // namespace scopf

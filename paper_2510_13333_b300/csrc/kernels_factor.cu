@@ -5,11 +5,14 @@
 //
 // Work decomposition.  Every supernode of every block is one task; tasks are
 // stored sorted by (tree level, block, supernode) and a persistent grid of
-// CTAs pulls them from a global counter.  A task waits (bounded poll) until
-// its children have published their update blocks, extend-adds them into its
+// warps pulls them from a global counter.  Fronts of these power-grid KKT
+// blocks are small (about 14 rows on average, at most the 180-row border plus
+// a few pivots), so one warp owns one front: no block-wide barriers, only
+// warp shuffles and __syncwarp.  A task waits (bounded poll) until its
+// children have published their update blocks, extend-adds them into its
 // own dense front, eliminates its pivot columns and publishes.  Because tasks
 // are handed out in level order, every awaited child has already been taken
-// by a running CTA, so the waits always end; a poll limit still turns a
+// by a running warp, so the waits always end; a poll limit still turns a
 // broken dependency into an error status instead of a hang.
 //
 // Fronts are dense, column-major, lower triangle used, one slot per
@@ -17,6 +20,10 @@
 // management is needed).  The last "supernode" of each block is its border
 // front: it receives the trailing updates of the block's roots, i.e. the
 // block's contribution -K_ck K_kk^-1 K_kc to the Schur complement.
+//
+// The matrix handed to the factorization is the symmetric equilibration
+// D K D (Ruiz scaling, D > 0 diagonal): the inertia is unchanged (Sylvester)
+// and FP32 fronts keep far more accuracy than on the raw barrier-scaled KKT.
 #include <cmath>
 
 #include "kernels.h"
@@ -25,7 +32,7 @@ namespace scopf {
 
 namespace {
 
-constexpr int kFT = 128;  // threads per task CTA
+constexpr int kWT = 128;  // threads per CTA of the warp-task kernels
 
 __device__ __forceinline__ int ld_acquire(const int *p) {
     int v;
@@ -37,107 +44,207 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Wait until done[dep] == epoch for the given dependencies (thread-parallel).
-__device__ bool wait_deps(const int *deps, int ndeps, const int *done, int epoch, int spin_limit) {
-    __shared__ int s_fail;
-    if (threadIdx.x == 0) s_fail = 0;
-    __syncthreads();
-    for (int i = threadIdx.x; i < ndeps; i += blockDim.x) {
+// Warp-wide wait until done[dep] == epoch for all deps (bounded polls).
+__device__ bool warp_wait(const int *deps, int ndeps, const int *done, int epoch, int spin_limit) {
+    const int lane = threadIdx.x & 31;
+    bool ok = true;
+    for (int i = lane; i < ndeps; i += 32) {
         const int d = deps[i];
         int spins = 0;
         while (ld_acquire(&done[d]) != epoch) {
             if (++spins > spin_limit) {
-                atomicExch(&s_fail, 1);
+                ok = false;
                 break;
             }
-            __nanosleep(64);
+            __nanosleep(32);
         }
     }
-    __syncthreads();
-    return s_fail == 0;
+    ok = __all_sync(0xffffffffu, ok);
+    __syncwarp();
+    return ok;
+}
+
+__device__ __forceinline__ int warp_grab(int *queue) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(queue, 1);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
+__device__ __forceinline__ void warp_publish(int *done, int task, int epoch) {
+    __threadfence();
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) st_release(&done[task], epoch);
 }
 
 template <typename T>
 __global__ void k_front_scatter(int64_t nnz, const int64_t *__restrict__ map,
-                                const double *__restrict__ kval, T *__restrict__ fronts) {
+                                const int32_t *__restrict__ row, const int64_t *__restrict__ col,
+                                const double *__restrict__ scale, const double *__restrict__ kval,
+                                T *__restrict__ fronts) {
     int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= nnz) return;
     const int64_t off = map[j];
-    if (off >= 0) fronts[off] = (T)kval[j];
+    if (off >= 0) fronts[off] = (T)(scale[row[j]] * kval[j] * scale[col[j]]);
 }
 
+// (column j, row i) of element e of the column-major lower triangle of an
+// m x m matrix (diagonal included)
+__device__ __forceinline__ void tri_index(int e, int m, int &j, int &i) {
+    const float b = 2.0f * m + 1.0f;
+    int jj = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))) * 0.5f);
+    if (jj < 0) jj = 0;
+    if (jj > m - 1) jj = m - 1;
+    int st = jj * m - (jj * (jj - 1)) / 2;
+    while (st > e) {
+        jj--;
+        st = jj * m - (jj * (jj - 1)) / 2;
+    }
+    while (st + (m - jj) <= e) {
+        st += m - jj;
+        jj++;
+    }
+    j = jj;
+    i = jj + (e - st);
+}
+
+template <int GS>
+__device__ __forceinline__ void gsync() {
+    if (GS == 32)
+        __syncwarp();
+    else
+        __syncthreads();
+}
+
+// Extend-add the children's update blocks into the front, then eliminate
+// its np pivot columns without pivoting: panel factorization (rank-1 updates
+// restricted to the np panel columns) followed by one pass of the trailing
+// update U -= L21 D L21' over the (f - np)^2 lower triangle.  GS threads
+// (one warp or one CTA) cooperate; tid in [0, GS).
+template <typename T, int GS>
+__device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int task, int tid,
+                                double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    T *Fr = fronts + F.front_off[task];
+    const int f = F.f[task];
+    const int np = F.npiv[task];
+    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    for (int ci = c0; ci < c1; ci++) {
+        const int ch = F.child[ci];
+        const T *Fc = fronts + F.front_off[ch];
+        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
+        const int32_t *rel = F.rel + F.rel_off[ch];
+        const int tot = nu * (nu + 1) / 2;
+        for (int e = tid; e < tot; e += GS) {
+            int jj, ii;
+            tri_index(e, nu, jj, ii);
+            Fr[(int64_t)rel[jj] * f + rel[ii]] += Fc[(int64_t)(npc + jj) * fc + npc + ii];
+        }
+        gsync<GS>();
+    }
+    for (int c = 0; c < np; c++) {
+        T *colc = Fr + (int64_t)c * f;
+        const T d = colc[c];
+        if (tid == 0) {
+            const double dd = (double)d;
+            if (dd > pivot_tol) n_pos++;
+            else if (dd < -pivot_tol) n_neg++;
+            else n_zero++;
+        }
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        for (int i = c + 1 + tid; i < f; i += GS) colc[i] *= dinv;
+        gsync<GS>();
+        for (int j = c + 1; j < np; j++) {
+            const T lj = colc[j] * d;
+            T *colj = Fr + (int64_t)j * f;
+            for (int i = j + tid; i < f; i += GS) colj[i] -= colc[i] * lj;
+        }
+        gsync<GS>();
+    }
+    const int m = f - np;
+    if (np > 0 && m > 0) {
+        const int tot = m * (m + 1) / 2;
+        for (int e = tid; e < tot; e += GS) {
+            int jj, ii;
+            tri_index(e, m, jj, ii);
+            const int i = np + ii, j = np + jj;
+            T acc = 0;
+            for (int c = 0; c < np; c++) {
+                const T *col = Fr + (int64_t)c * f;
+                acc += col[i] * (col[j] * col[c]);
+            }
+            Fr[(int64_t)j * f + i] -= acc;
+        }
+        gsync<GS>();
+    }
+}
+
+// Phase 1: small fronts, one warp per front.
 template <typename T>
-__global__ void __launch_bounds__(kFT) k_factor(DevFront F, T *__restrict__ fronts, FactorStatus *st,
-                                                int *queue, int *done, int epoch, double pivot_tol,
-                                                int spin_limit) {
-    __shared__ int s_task;
-    __shared__ int s_pos, s_neg, s_zero;
+__global__ void __launch_bounds__(kWT) k_factor(DevFront F, T *__restrict__ fronts,
+                                                FactorStatus *st, int *queue, int *done, int epoch,
+                                                double pivot_tol, int spin_limit) {
+    const int lane = threadIdx.x & 31;
+    int n_pos = 0, n_neg = 0, n_zero = 0;
+    while (true) {
+        const int task = warp_grab(queue);
+        if (task >= F.n_small) break;
+        const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+        if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0) {
+            atomicExch(&st->error, 1);
+            atomicExch(&st->timeout_task, task);
+        }
+        eliminate_front<T, 32>(F, fronts, task, lane, pivot_tol, n_pos, n_neg, n_zero);
+        warp_publish(done, task, epoch);
+    }
+    if (lane == 0) {
+        if (n_pos) atomicAdd(&st->n_pos, n_pos);
+        if (n_neg) atomicAdd(&st->n_neg, n_neg);
+        if (n_zero) atomicAdd(&st->n_zero, n_zero);
+    }
+}
+
+// Phase 2: large fronts near the tree tops (they carry the border rows), one
+// CTA per front.  Launched after phase 1, so small children are complete.
+constexpr int kBT = 256;
+template <typename T>
+__global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ fronts,
+                                                    FactorStatus *st, int *queue, int *done,
+                                                    int epoch, double pivot_tol, int spin_limit) {
+    __shared__ int s_task, s_fail;
+    int n_pos = 0, n_neg = 0, n_zero = 0;
     while (true) {
         if (threadIdx.x == 0) {
-            s_task = atomicAdd(queue, 1);
-            s_pos = s_neg = s_zero = 0;
+            s_task = F.n_small + atomicAdd(queue, 1);
+            s_fail = 0;
         }
         __syncthreads();
         const int task = s_task;
         if (task >= F.n_tasks) break;
         const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-        if (!wait_deps(F.child + c0, c1 - c0, done, epoch, spin_limit)) {
-            if (threadIdx.x == 0) {
-                atomicExch(&st->error, 1);
-                atomicExch(&st->timeout_task, task);
+        for (int ci = c0 + threadIdx.x; ci < c1; ci += blockDim.x) {
+            const int d = F.child[ci];
+            int spins = 0;
+            while (ld_acquire(&done[d]) != epoch) {
+                if (++spins > spin_limit) {
+                    s_fail = 1;
+                    break;
+                }
+                __nanosleep(64);
             }
         }
-        T *Fr = fronts + F.front_off[task];
-        const int f = F.f[task];
-        const int np = F.npiv[task];
-        // extend-add the children's update blocks (fixed child order)
-        for (int ci = c0; ci < c1; ci++) {
-            const int ch = F.child[ci];
-            const T *Fc = fronts + F.front_off[ch];
-            const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-            const int32_t *rel = F.rel + F.rel_off[ch];
-            const int tot = nu * nu;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int jj = t / nu, ii = t - jj * nu;
-                if (ii < jj) continue;
-                Fr[(int64_t)rel[jj] * f + rel[ii]] += Fc[(int64_t)(npc + jj) * fc + npc + ii];
-            }
-            __syncthreads();
+        __syncthreads();
+        if (s_fail && threadIdx.x == 0) {
+            atomicExch(&st->error, 1);
+            atomicExch(&st->timeout_task, task);
         }
-        // eliminate the pivot columns: rank-1 updates, D diagonal, no pivoting
-        for (int c = 0; c < np; c++) {
-            const T d = Fr[(int64_t)c * f + c];
-            if (threadIdx.x == 0) {
-                const double dd = (double)d;
-                if (dd > pivot_tol)
-                    s_pos++;
-                else if (dd < -pivot_tol)
-                    s_neg++;
-                else
-                    s_zero++;
-            }
-            const T dsafe = (d == (T)0) ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d;
-            T *colc = Fr + (int64_t)c * f;
-            for (int i = c + 1 + threadIdx.x; i < f; i += blockDim.x) colc[i] = colc[i] / dsafe;
-            __syncthreads();
-            const int mrem = f - c - 1;
-            const int tot = mrem * mrem;
-            for (int t = threadIdx.x; t < tot; t += blockDim.x) {
-                const int jj = t / mrem, ii = t - jj * mrem;
-                if (ii < jj) continue;
-                const int j = c + 1 + jj, i = c + 1 + ii;
-                Fr[(int64_t)j * f + i] -= colc[i] * colc[j] * d;
-            }
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) {
-            if (s_pos) atomicAdd(&st->n_pos, s_pos);
-            if (s_neg) atomicAdd(&st->n_neg, s_neg);
-            if (s_zero) atomicAdd(&st->n_zero, s_zero);
-        }
+        eliminate_front<T, kBT>(F, fronts, task, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
         __threadfence();
         __syncthreads();
         if (threadIdx.x == 0) st_release(&done[task], epoch);
+    }
+    if (threadIdx.x == 0) {
+        if (n_pos) atomicAdd(&st->n_pos, n_pos);
+        if (n_neg) atomicAdd(&st->n_neg, n_neg);
+        if (n_zero) atomicAdd(&st->n_zero, n_zero);
     }
 }
 
@@ -155,32 +262,32 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
     S[(int64_t)i * nb + j] = acc;
 }
 
-// Dense pivot-free LDL^T of the n x n border block (FP64, one CTA, in place,
-// lower triangle: L below the diagonal, D on it).
-__global__ void k_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol) {
+// ---- dense LDL^T of the border block (FP64, blocked right-looking) -------
+constexpr int kPanel = 32;
+
+// Factor columns [k0, k1) of S in place (rows >= column), counting inertia.
+__global__ void k_dense_panel(double *S, int n, int k0, int k1, FactorStatus *st,
+                              double pivot_tol) {
     __shared__ int s_pos, s_neg, s_zero;
     if (threadIdx.x == 0) s_pos = s_neg = s_zero = 0;
     __syncthreads();
-    for (int c = 0; c < n; c++) {
-        const double d = S[(int64_t)c * n + c];
-        if (threadIdx.x == 0) {
-            if (d > pivot_tol)
-                s_pos++;
-            else if (d < -pivot_tol)
-                s_neg++;
-            else
-                s_zero++;
-        }
-        const double dsafe = d == 0.0 ? 1e-300 : d;
+    for (int c = k0; c < k1; c++) {
         double *colc = S + (int64_t)c * n;
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) colc[i] /= dsafe;
+        const double d = colc[c];
+        if (threadIdx.x == 0) {
+            if (d > pivot_tol) s_pos++;
+            else if (d < -pivot_tol) s_neg++;
+            else s_zero++;
+        }
+        const double dinv = 1.0 / (d == 0.0 ? 1e-300 : d);
         __syncthreads();
-        const int mrem = n - c - 1;
-        for (int t = threadIdx.x; t < mrem * mrem; t += blockDim.x) {
-            const int jj = t / mrem, ii = t - jj * mrem;
-            if (ii < jj) continue;
-            const int j = c + 1 + jj, i = c + 1 + ii;
-            S[(int64_t)j * n + i] -= colc[i] * colc[j] * d;
+        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) colc[i] *= dinv;
+        __syncthreads();
+        // update the remaining panel columns
+        for (int j = c + 1; j < k1; j++) {
+            const double lj = colc[j] * d;
+            double *colj = S + (int64_t)j * n;
+            for (int i = j + threadIdx.x; i < n; i += blockDim.x) colj[i] -= colc[i] * lj;
         }
         __syncthreads();
     }
@@ -191,162 +298,230 @@ __global__ void k_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_to
     }
 }
 
+// Trailing update S[i,j] -= sum_{c in [k0,k1)} L[i,c] d_c L[j,c], i >= j >= k1
+// (one 32x32 tile per CTA of the lower triangle)
+__global__ void k_dense_trailing(double *S, int n, int k0, int k1) {
+    const int tj = blockIdx.x, ti = blockIdx.y;
+    if (ti < tj) return;
+    __shared__ double Li[kPanel][33], Lj[kPanel][33], dd[kPanel];
+    const int pw = k1 - k0;
+    const int i0 = k1 + ti * 32, j0 = k1 + tj * 32;
+    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
+    for (int c = ty; c < pw; c += 8) {
+        const double *col = S + (int64_t)(k0 + c) * n;
+        Li[c][tx] = (i0 + tx < n) ? col[i0 + tx] : 0.0;
+        Lj[c][tx] = (j0 + tx < n) ? col[j0 + tx] : 0.0;
+        if (tx == 0) dd[c] = col[k0 + c];
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+        const int i = i0 + tx, j = j0 + r;
+        if (i >= n || j >= n || i < j) continue;
+        double acc = 0.0;
+        for (int c = 0; c < pw; c++) acc += Li[c][tx] * dd[c] * Lj[c][r];
+        S[(int64_t)j * n + i] -= acc;
+    }
+}
+
 // ---------------------------------------------------------------- solves
 template <typename T>
-__global__ void __launch_bounds__(kFT) k_solve_fwd(DevFront F, const T *__restrict__ fronts,
+__global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restrict__ fronts,
                                                    T *__restrict__ vec, const double *__restrict__ b,
-                                                   int *queue, int *done, int epoch,
-                                                   FactorStatus *st, int spin_limit) {
-    __shared__ int s_task;
+                                                   const double *__restrict__ scale, int *queue,
+                                                   int *done, int epoch, FactorStatus *st,
+                                                   int spin_limit) {
+    const int lane = threadIdx.x & 31;
     while (true) {
-        if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
-        __syncthreads();
-        const int task = s_task;
+        const int task = warp_grab(queue);
         if (task >= F.n_tasks) break;
         const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-        if (!wait_deps(F.child + c0, c1 - c0, done, epoch, spin_limit) && threadIdx.x == 0)
+        if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0)
             atomicExch(&st->error, 2);
         const int f = F.f[task], np = F.npiv[task];
         const T *L = fronts + F.front_off[task];
         T *v = vec + F.vec_off[task];
         const int64_t *rows = F.rows + F.rows_off[task];
-        for (int i = threadIdx.x; i < f; i += blockDim.x) v[i] = i < np ? (T)b[rows[i]] : (T)0;
-        __syncthreads();
+        for (int i = lane; i < f; i += 32) {
+            T x = (T)0;
+            if (i < np) {
+                const int64_t r = rows[i];
+                x = (T)(scale[r] * b[r]);
+            }
+            v[i] = x;
+        }
+        __syncwarp();
         for (int ci = c0; ci < c1; ci++) {
             const int ch = F.child[ci];
             const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-            const T *vc = vec + F.vec_off[ch];
+            const T *vc = vec + F.vec_off[ch] + npc;
             const int32_t *rel = F.rel + F.rel_off[ch];
-            for (int i = threadIdx.x; i < nu; i += blockDim.x) v[rel[i]] += vc[npc + i];
-            __syncthreads();
+            for (int i = lane; i < nu; i += 32) v[rel[i]] += vc[i];
+            __syncwarp();
         }
         for (int c = 0; c < np; c++) {
             const T xc = v[c];
             const T *col = L + (int64_t)c * f;
-            for (int i = c + 1 + threadIdx.x; i < f; i += blockDim.x) v[i] -= col[i] * xc;
-            __syncthreads();
+            for (int i = c + 1 + lane; i < f; i += 32) v[i] -= col[i] * xc;
+            __syncwarp();
         }
         // diagonal: y = D^-1 (L^-1 b) on the pivot rows
-        for (int c = threadIdx.x; c < np; c += blockDim.x) v[c] = v[c] / L[(int64_t)c * f + c];
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(&done[task], epoch);
+        for (int c = lane; c < np; c += 32) v[c] = v[c] / L[(int64_t)c * f + c];
+        warp_publish(done, task, epoch);
     }
 }
 
-// Border right-hand side, then the dense border solve with S = L_S D_S L_S'.
+// Border right-hand side y = D b_border + sum_k (update vector of block k's
+// border front), then the dense border solve with S = L_S D_S L_S' by one
+// warp (column sweeps, warp-shuffle dot products).
 template <typename T>
 __global__ void k_border_solve(DevFront F, const T *__restrict__ vec, const double *__restrict__ S,
-                               int n, const double *__restrict__ b, double *__restrict__ x,
-                               double *__restrict__ y) {
-    // y = b_border + sum_k (update vector of block k's border front), fixed order
+                               int n, const double *__restrict__ b, const double *__restrict__ scale,
+                               double *__restrict__ x, double *__restrict__ y) {
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
-        double acc = b[F.border_rows[j]];
-        for (int t = 0; t < F.n_tasks; t++)
-            if (F.is_border[t]) acc += (double)vec[F.vec_off[t] + j];
+        const int64_t r = F.border_rows[j];
+        double acc = scale[r] * b[r];
+        for (int k = 0; k < F.n_blocks; k++) acc += (double)vec[F.border_vec_off[k] + j];
         y[j] = acc;
     }
     __syncthreads();
+    if (threadIdx.x >= 32) return;
+    const int lane = threadIdx.x;
     for (int c = 0; c < n; c++) {
         const double yc = y[c];
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) y[i] -= S[(int64_t)c * n + i] * yc;
-        __syncthreads();
+        const double *col = S + (int64_t)c * n;
+        for (int i = c + 1 + lane; i < n; i += 32) y[i] -= col[i] * yc;
+        __syncwarp();
     }
-    for (int c = threadIdx.x; c < n; c += blockDim.x) y[c] /= S[(int64_t)c * n + c];
-    __syncthreads();
-    __shared__ double red[kFT];
+    for (int c = lane; c < n; c += 32) y[c] /= S[(int64_t)c * n + c];
+    __syncwarp();
     for (int c = n - 1; c >= 0; c--) {
+        const double *col = S + (int64_t)c * n;
         double acc = 0.0;
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) acc += S[(int64_t)c * n + i] * y[i];
-        red[threadIdx.x] = acc;
-        __syncthreads();
-        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-            if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-            __syncthreads();
-        }
-        if (threadIdx.x == 0) y[c] -= red[0];
-        __syncthreads();
+        for (int i = c + 1 + lane; i < n; i += 32) acc += col[i] * y[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[c] -= acc;
+        __syncwarp();
     }
-    for (int j = threadIdx.x; j < n; j += blockDim.x) x[F.border_rows[j]] = y[j];
+    for (int j = lane; j < n; j += 32) {
+        const int64_t r = F.border_rows[j];
+        x[r] = scale[r] * y[j];
+    }
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kFT) k_solve_bwd(DevFront F, const T *__restrict__ fronts,
-                                                   T *__restrict__ vec, double *__restrict__ x,
-                                                   int *queue, int *done, int epoch,
-                                                   FactorStatus *st, int spin_limit) {
-    __shared__ int s_task;
-    __shared__ T red[kFT];
+__global__ void __launch_bounds__(kWT) k_solve_bwd(DevFront F, const T *__restrict__ fronts,
+                                                   T *__restrict__ vec, const double *__restrict__ scale,
+                                                   double *__restrict__ x, int *queue, int *done,
+                                                   int epoch, FactorStatus *st, int spin_limit) {
+    const int lane = threadIdx.x & 31;
     while (true) {
-        if (threadIdx.x == 0) s_task = atomicAdd(queue, 1);
-        __syncthreads();
-        const int q = s_task;
+        const int q = warp_grab(queue);
         if (q >= F.n_tasks) break;
         const int task = F.n_tasks - 1 - q;
         if (F.is_border[task]) {
-            __syncthreads();
-            if (threadIdx.x == 0) st_release(&done[task], epoch);
+            warp_publish(done, task, epoch);
             continue;
         }
         const int par = F.parent[task];
-        if (par >= 0 && !wait_deps(&par, 1, done, epoch, spin_limit) && threadIdx.x == 0)
+        if (par >= 0 && !warp_wait(&F.parent[task], 1, done, epoch, spin_limit) && lane == 0)
             atomicExch(&st->error, 3);
         const int f = F.f[task], np = F.npiv[task];
         const T *L = fronts + F.front_off[task];
         T *v = vec + F.vec_off[task];
         const int64_t *rows = F.rows + F.rows_off[task];
-        for (int i = np + threadIdx.x; i < f; i += blockDim.x) v[i] = (T)x[rows[i]];
-        __syncthreads();
+        // update rows: final (scaled) solution of ancestors and border
+        for (int i = np + lane; i < f; i += 32) {
+            const int64_t r = rows[i];
+            v[i] = (T)(x[r] / scale[r]);
+        }
+        __syncwarp();
         for (int c = np - 1; c >= 0; c--) {
             const T *col = L + (int64_t)c * f;
             T acc = 0;
-            for (int i = c + 1 + threadIdx.x; i < f; i += blockDim.x) acc += col[i] * v[i];
-            red[threadIdx.x] = acc;
-            __syncthreads();
-            for (int s = blockDim.x / 2; s > 0; s >>= 1) {
-                if ((int)threadIdx.x < s) red[threadIdx.x] += red[threadIdx.x + s];
-                __syncthreads();
-            }
-            if (threadIdx.x == 0) v[c] -= red[0];
-            __syncthreads();
+            for (int i = c + 1 + lane; i < f; i += 32) acc += col[i] * v[i];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) v[c] -= acc;
+            __syncwarp();
         }
-        for (int c = threadIdx.x; c < np; c += blockDim.x) x[rows[c]] = (double)v[c];
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(&done[task], epoch);
+        for (int c = lane; c < np; c += 32) {
+            const int64_t r = rows[c];
+            x[r] = scale[r] * (double)v[c];
+        }
+        warp_publish(done, task, epoch);
     }
 }
 
-int persistent_grid(int threads) {
+// ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
+__global__ void k_ruiz(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
+                       const double *__restrict__ kval, const double *__restrict__ s_in,
+                       double *__restrict__ s_out) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double mx = 0.0;
+    const double si = s_in[i];
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
+    s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
+}
+
+__global__ void k_fill(int64_t n, double v, double *x) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) x[i] = v;
+}
+
+int warp_grid() {
     static int grid = 0;
     if (!grid) {
-        int dev = 0, sms = 0, per = 0;
+        int dev = 0, sms = 0;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        per = 2048 / threads;
-        if (per > 16) per = 16;
-        grid = sms * per;
-        if (grid <= 0) grid = 148;
+        grid = sms * (2048 / kWT);
+        if (grid <= 0) grid = 148 * 16;
     }
     return grid;
 }
 
 }  // namespace
 
+void launch_equilibrate(int64_t n, const int64_t *ptr, const int64_t *col, const double *kval,
+                        double *scale, double *tmp, int iters, cudaStream_t s) {
+    const int t = 256;
+    const int g = (int)((n + t - 1) / t);
+    k_fill<<<g, t, 0, s>>>(n, 1.0, scale);
+    for (int it = 0; it < iters; it++) {
+        k_ruiz<<<g, t, 0, s>>>(n, ptr, col, kval, scale, tmp);
+        cudaMemcpyAsync(scale, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    }
+}
+
 template <typename T>
-void launch_front_init(const DevFront &F, const double *kval, T *fronts, cudaStream_t s) {
+void launch_front_init(const DevFront &F, const int32_t *row, const int64_t *col,
+                       const double *scale, const double *kval, T *fronts, cudaStream_t s) {
     cudaMemsetAsync(fronts, 0, sizeof(T) * F.front_elems, s);
     const int t = 256;
-    k_front_scatter<T><<<(int)((F.nnz + t - 1) / t), t, 0, s>>>(F.nnz, F.scatter, kval, fronts);
+    k_front_scatter<T><<<(int)((F.nnz + t - 1) / t), t, 0, s>>>(F.nnz, F.scatter, row, col, scale,
+                                                               kval, fronts);
 }
 
 template <typename T>
 void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, int *queue, int *done, int epoch,
                    double pivot_tol, int spin_limit, cudaStream_t s) {
     cudaMemsetAsync(queue, 0, sizeof(int), s);
-    int grid = persistent_grid(kFT);
-    if (grid > F.n_tasks) grid = F.n_tasks;
-    k_factor<T><<<grid, kFT, 0, s>>>(F, fronts, st, queue, done, epoch, pivot_tol, spin_limit);
+    int grid = warp_grid();
+    const int need = (F.n_small + kWT / 32 - 1) / (kWT / 32);
+    if (grid > need) grid = need;
+    if (F.n_small > 0)
+        k_factor<T><<<grid, kWT, 0, s>>>(F, fronts, st, queue, done, epoch, pivot_tol, spin_limit);
+    const int nbig = F.n_tasks - F.n_small;
+    if (nbig > 0) {
+        cudaMemsetAsync(queue, 0, sizeof(int), s);
+        int dev = 0, sms = 148;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        int g2 = sms * (2048 / kBT);
+        if (g2 > nbig) g2 = nbig;
+        k_factor_big<T><<<g2, kBT, 0, s>>>(F, fronts, st, queue, done, epoch, pivot_tol,
+                                           spin_limit);
+    }
 }
 
 template <typename T>
@@ -357,32 +532,42 @@ void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_
 }
 
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
-    if (n == 0) return;
-    k_dense_ldlt<<<1, 1024, 0, s>>>(S, n, st, pivot_tol);
+    for (int k0 = 0; k0 < n; k0 += kPanel) {
+        const int k1 = k0 + kPanel < n ? k0 + kPanel : n;
+        k_dense_panel<<<1, 256, 0, s>>>(S, n, k0, k1, st, pivot_tol);
+        const int rem = n - k1;
+        if (rem > 0) {
+            const int tiles = (rem + 31) / 32;
+            k_dense_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(S, n, k0, k1);
+        }
+    }
 }
 
 template <typename T>
 void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
-                  const double *b, double *x, double *border_work, int *queue, int *done,
-                  int epoch, FactorStatus *st, int spin_limit, cudaStream_t s) {
-    int grid = persistent_grid(kFT);
-    if (grid > F.n_tasks) grid = F.n_tasks;
+                  const double *scale, const double *b, double *x, double *border_work, int *queue,
+                  int *done, int epoch, FactorStatus *st, int spin_limit, cudaStream_t s) {
+    int grid = warp_grid();
+    const int need = (F.n_tasks + kWT / 32 - 1) / (kWT / 32);
+    if (grid > need) grid = need;
     cudaMemsetAsync(queue, 0, sizeof(int), s);
-    k_solve_fwd<T><<<grid, kFT, 0, s>>>(F, fronts, vec, b, queue, done, epoch, st, spin_limit);
-    k_border_solve<T><<<1, kFT, 0, s>>>(F, vec, S, nS, b, x, border_work);
+    k_solve_fwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, b, scale, queue, done, epoch, st,
+                                        spin_limit);
+    k_border_solve<T><<<1, 256, 0, s>>>(F, vec, S, nS, b, scale, x, border_work);
     cudaMemsetAsync(queue, 0, sizeof(int), s);
-    k_solve_bwd<T><<<grid, kFT, 0, s>>>(F, fronts, vec, x, queue, done, epoch + 1, st,
+    k_solve_bwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, scale, x, queue, done, epoch + 1, st,
                                         spin_limit);
 }
 
 #define INST(T)                                                                                    \
-    template void launch_front_init<T>(const DevFront &, const double *, T *, cudaStream_t);      \
+    template void launch_front_init<T>(const DevFront &, const int32_t *, const int64_t *,       \
+                                       const double *, const double *, T *, cudaStream_t);       \
     template void launch_factor<T>(const DevFront &, T *, FactorStatus *, int *, int *, int,     \
                                    double, int, cudaStream_t);                                   \
     template void launch_schur_sum<T>(const DevFront &, const T *, double *, cudaStream_t);      \
     template void launch_solve<T>(const DevFront &, const T *, T *, const double *, int,          \
-                                  const double *, double *, double *, int *, int *, int,         \
-                                  FactorStatus *, int, cudaStream_t);
+                                  const double *, const double *, double *, double *, int *,     \
+                                  int *, int, FactorStatus *, int, cudaStream_t);
 INST(float)
 INST(double)
 

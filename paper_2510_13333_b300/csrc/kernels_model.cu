@@ -295,6 +295,80 @@ void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s
     if (n) k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
 }
 
+namespace {
+
+__global__ void k_multi_dot(const double *__restrict__ V, int64_t n, int k,
+                            const double *__restrict__ w, double *__restrict__ partial) {
+    __shared__ double sh[kThreads];
+    for (int j = 0; j < k; j++) {
+        const double *v = V + (int64_t)j * n;
+        double acc = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            acc += v[i] * w[i];
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + j] = sh[0];
+        __syncthreads();
+    }
+}
+
+struct Coefs {
+    double c[kMaxKrylov];
+};
+
+__global__ void k_multi_axpy(double *__restrict__ w, const double *__restrict__ V, int64_t n,
+                             int k, Coefs cf) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int j = 0; j < k; j++) acc -= cf.c[j] * V[(int64_t)j * n + i];
+    w[i] = acc;
+}
+
+__global__ void k_scale_copy(int64_t n, double a, const double *__restrict__ x,
+                             double *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) y[i] = a * x[i];
+}
+
+__global__ void k_spmv(int64_t n_kkt, const int64_t *__restrict__ ptr,
+                       const int64_t *__restrict__ col, const double *__restrict__ kval,
+                       const double *__restrict__ x, double *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_kkt) return;
+    double s = 0.0;
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) s += kval[q] * x[col[q]];
+    y[i] = s;
+}
+
+}  // namespace
+
+void launch_multi_dot(const double *V, int64_t n, int k, const double *w, double *partial,
+                      cudaStream_t s) {
+    k_multi_dot<<<kDotBlocks, kThreads, 0, s>>>(V, n, k, w, partial);
+}
+
+void launch_multi_axpy(double *w, const double *V, int64_t n, int k, const double *c,
+                       cudaStream_t s) {
+    Coefs cf;
+    for (int j = 0; j < k && j < kMaxKrylov; j++) cf.c[j] = c[j];
+    k_multi_axpy<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, cf);
+}
+
+void launch_scale_copy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
+    if (n) k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
+}
+
+void launch_spmv(const DevModel &M, const double *kval, const double *x, double *y,
+                 cudaStream_t s) {
+    k_spmv<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, y);
+}
+
 void launch_eval_elements(const DevModel &M, const double *w, const double *lam, const double *yc,
                           double *ev, int mode, cudaStream_t s) {
     if (M.n_be)
