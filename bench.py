@@ -186,11 +186,12 @@ def run_ours(args):
     st = lib2.get_state()
     lam_n, nu0_n, rho = lib2.ncl_params_tensors()
     mu = r["mu"]
+    dw_last = r["delta_w_last"]
     del lib2
     direction = lib.new_state()
 
     def step(l):
-        return l.scopf_newton_step(st, lam_n, nu0_n, rho, mu, 0.0, direction)
+        return l.scopf_newton_step(st, lam_n, nu0_n, rho, mu, dw_last, direction)
 
     def timed(l, k):
         for _ in range(args.warmup):
@@ -241,7 +242,7 @@ def run_ours(args):
             dev_in[k].copy_(host[k], non_blocking=True)
         dl.copy_(host_l, non_blocking=True)
         dn.copy_(host_n, non_blocking=True)
-        lib.scopf_newton_step(dev_in, dl, dn, rho, mu, 0.0, direction)
+        lib.scopf_newton_step(dev_in, dl, dn, rho, mu, dw_last, direction)
         out_w.copy_(direction["w"], non_blocking=True)
         out_l.copy_(direction["lam"], non_blocking=True)
         out_y.copy_(direction["yc"], non_blocking=True)
@@ -308,7 +309,8 @@ def run_ours(args):
                                "switch sets; seeded, screened",
                    "n_kkt": sz.n_kkt, "nnz_kkt": sz.nnz_kkt, "nnz_L": sz.nnz_L,
                    "blocks": sz.n_blocks, "border": sz.n_border,
-                   "iterate": f"state after {args.iterate_at} IPM iterations",
+                   "iterate": f"state after {args.iterate_at} IPM iterations (mu {mu:.1e}, "
+                              f"rho {rho:.0e}, last delta_w {dw_last:.1e})",
                    "flush_l2": False, "inputs_exceed_l2": True,
                    "parallelism": "replicas only" if world > 1 else "1 GPU"},
         "fp64_newton_steps_per_s": fp64_value,

@@ -137,6 +137,7 @@ typedef struct {
     int32_t fp64_fallbacks;   /* mixed mode: Newton steps redone in FP64 */
     double objective, kkt_error, feas_rt, max_violation, rho, mu;
     double time_total_s, time_newton_s;
+    double delta_w_last;      /* last nonzero inertia-correction delta_w */
 } scopf_result;
 
 void scopf_default_options(scopf_options *opt);

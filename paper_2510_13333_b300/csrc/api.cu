@@ -115,6 +115,18 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, M.row_kind, &d.row_kind));
     TRY(upload(h, M.row_index, &d.row_index));
     {
+        std::vector<int8_t> is_long(M.n_kkt, 0);
+        std::vector<int64_t> long_rows;
+        for (int64_t r = 0; r < M.n_kkt; r++)
+            if (M.kkt_ptr[r + 1] - M.kkt_ptr[r] > kLongRow) {
+                is_long[r] = 1;
+                long_rows.push_back(r);
+            }
+        TRY(upload(h, is_long, &d.is_long));
+        TRY(upload(h, long_rows, &d.long_rows));
+        d.n_long = (int64_t)long_rows.size();
+    }
+    {
         const double rf = h->opt.bound_relax;
         std::vector<double> wl(M.n), wu(M.n);
         for (int64_t i = 0; i < M.n; i++) {
@@ -153,6 +165,11 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, HF.scatter, &F.scatter));
     TRY(upload(h, HF.vec_off, &F.vec_off));
     TRY(upload(h, HF.border_vec_off, &F.border_vec_off));
+    TRY(upload(h, HF.orig_ptr, &F.orig_ptr));
+    TRY(upload(h, HF.orig_nz, &F.orig_nz));
+    TRY(upload(h, HF.orig_off, &F.orig_off));
+    F.kkt_row = d.kkt_row;
+    F.kkt_col = d.kkt_col;
     F.nnz = (int64_t)HF.scatter.size();
     F.front_elems = HF.front_elems;
     F.vec_elems = HF.vec_elems;
@@ -169,6 +186,8 @@ int setup_device(scopf_handle *h) {
     TRY(alloc(h, M.n_kkt, &h->dx));
     TRY(alloc(h, M.n_kkt, &h->scale));
     TRY(alloc(h, M.n_kkt, &h->scale_tmp));
+    F.kval = h->kval;
+    F.scale = h->scale;
     double *fr = nullptr, *vv = nullptr;
     TRY(alloc(h, (size_t)HF.front_elems, &fr));
     TRY(alloc(h, (size_t)HF.vec_elems, &vv));
@@ -559,9 +578,7 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     T *fr = reinterpret_cast<T *>(h->fronts);
     CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
     h->timer.begin(PH_FRONT_INIT, s);
-    launch_equilibrate(h->M.n_kkt, h->dm.kkt_ptr, h->dm.kkt_col, h->kval, h->scale, h->scale_tmp,
-                       3, s);
-    launch_front_init<T>(h->df, h->dm.kkt_row, h->dm.kkt_col, h->scale, h->kval, fr, s);
+    launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, 3, s);
     h->timer.end(PH_FRONT_INIT, s);
     h->epoch++;
     h->timer.begin(PH_FACTOR, s);
@@ -650,6 +667,9 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         launch_residual(h->dm, h->kval, x, h->res, h->tmp_kkt, s);
         h->timer.end(PH_RESIDUAL, s);
         r = device_maxabs(h, h->tmp_kkt, n) / bden;
+        if (h->opt.verbose >= 2)
+            std::printf("    refine: %d preconditioner applications, |b-Kx|/|b| = %.3e (%s)\n", it,
+                        r, mixed ? "fp32 factors" : "fp64 factors");
         if (!(r > h->opt.refine_tol) || it >= max_refine || !std::isfinite(r)) break;
         // one FGMRES(m) cycle on K e = r
         double beta = 0;

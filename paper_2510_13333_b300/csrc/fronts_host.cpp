@@ -216,6 +216,27 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
             H.scatter[q] = H.front_off[t] + lc * x.f + lr;
         }
     }
+    // per-task lists of original entries (offset inside the task's front)
+    {
+        std::vector<int> task_of_front_start(0);
+        std::vector<std::vector<std::pair<int64_t, int32_t>>> per(nt);
+        for (size_t q = 0; q < H.scatter.size(); q++) {
+            const int64_t off = H.scatter[q];
+            if (off < 0) continue;
+            // the front containing off: last task whose front_off <= off
+            const int t = (int)(std::upper_bound(H.front_off.begin(), H.front_off.end(), off) -
+                                H.front_off.begin()) - 1;
+            per[t].push_back({(int64_t)q, (int32_t)(off - H.front_off[t])});
+        }
+        H.orig_ptr.assign(nt + 1, 0);
+        for (int t = 0; t < nt; t++) {
+            H.orig_ptr[t + 1] = H.orig_ptr[t] + (int64_t)per[t].size();
+            for (auto &pr : per[t]) {
+                H.orig_nz.push_back(pr.first);
+                H.orig_off.push_back(pr.second);
+            }
+        }
+    }
     H.max_level = 0;
     for (int i = 0; i < nt; i++) H.max_level = std::max(H.max_level, H.level[i]);
     return "";

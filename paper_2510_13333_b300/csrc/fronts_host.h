@@ -9,7 +9,8 @@ struct HostFronts {
     int n_tasks = 0, n_blocks = 0, n_border = 0, max_level = 0, n_small = 0;
     std::vector<int64_t> front_off, vec_off, rows_off, rel_off, border_off, border_vec_off, scatter;
     std::vector<int32_t> f, npiv, parent, is_border, child_ptr, child, rel, level, block;
-    std::vector<int64_t> rows, border_rows;
+    std::vector<int64_t> rows, border_rows, orig_ptr, orig_nz;
+    std::vector<int32_t> orig_off;
     int64_t front_elems = 0, vec_elems = 0, nnz_L = 0;
     double flops = 0;
 };

@@ -492,6 +492,10 @@ struct Ipm {
             int r = factor_impl(h, prec, in);
             if (r != SCOPF_OK) return r;
             tries++;
+            if (o.verbose >= 2)
+                std::printf("    factor (%s) delta_w %.2e inertia (%d, %d, %d), want (%lld, %lld, 0)\n",
+                            prec == SCOPF_PREC_MIXED ? "fp32" : "fp64", delta, in[0], in[1], in[2],
+                            (long long)npos, (long long)nneg);
             if (in[0] == npos && in[1] == nneg && in[2] == 0) break;
             if (delta == 0.0)
                 delta = dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
@@ -760,6 +764,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     res->mu = mu;
     res->time_total_s = T.s();
     res->time_newton_s = t_newton;
+    res->delta_w_last = dw_last;
     return status == SCOPF_OK ? SCOPF_OK : status;
 }
 

@@ -29,7 +29,13 @@ struct DevModel {
     const double *c2, *c1;        // per generator
     int64_t border0;
     int ng;
+    // KKT rows with more than kLongRow stored entries (the border rows, which
+    // couple to every contingency block) are handled one warp per row
+    const int8_t *is_long;
+    const int64_t *long_rows;
+    int64_t n_long;
 };
+constexpr int kLongRow = 48;
 
 // mode: 0 = values only (flows, thermal values), 1 = values + derivatives
 void launch_eval_elements(const DevModel &M, const double *w, const double *lam,
@@ -98,6 +104,16 @@ struct DevFront {
     int64_t vec_elems;            // size of the per-front vector buffer
     const int64_t *vec_off;       // per task offset into the vector buffer
     const int64_t *border_vec_off; // per block: vec_off of its border task
+    // original KKT entries of each front (lower triangle in elimination
+    // order): entries [orig_ptr[t], orig_ptr[t+1]) with the stored-entry index
+    // and the offset inside the front; each task loads its own before use
+    const int64_t *orig_ptr;
+    const int64_t *orig_nz;
+    const int32_t *orig_off;
+    const int32_t *kkt_row;       // row of every stored KKT entry
+    const int64_t *kkt_col;
+    const double *kval;           // assembled K (set before each factorization)
+    const double *scale;          // Ruiz scaling
 };
 
 struct FactorStatus {             // device-side counters
@@ -105,8 +121,8 @@ struct FactorStatus {             // device-side counters
 };
 
 // Symmetric Ruiz equilibration of K (scale[i] > 0, `iters` sweeps).
-void launch_equilibrate(int64_t n, const int64_t *ptr, const int64_t *col, const double *kval,
-                        double *scale, double *tmp, int iters, cudaStream_t s);
+void launch_equilibrate(const DevModel &M, const double *kval, double *scale, double *tmp,
+                        int iters, cudaStream_t s);
 // fronts <- scatter of scale[i] K_ij scale[j] (lower triangle in elimination order)
 template <typename T>
 void launch_front_init(const DevFront &F, const int32_t *row, const int64_t *col,

@@ -70,6 +70,15 @@ __device__ __forceinline__ int warp_grab(int *queue) {
     return __shfl_sync(0xffffffffu, t, 0);
 }
 
+// A warp takes kChunk consecutive tasks per atomic (processed in order:
+// tasks of a chunk only wait on earlier tasks, all already taken).
+constexpr int kChunk = 4;
+__device__ __forceinline__ int warp_grab_chunk(int *queue) {
+    int t = 0;
+    if ((threadIdx.x & 31) == 0) t = atomicAdd(queue, kChunk);
+    return __shfl_sync(0xffffffffu, t, 0);
+}
+
 __device__ __forceinline__ void warp_publish(int *done, int task, int epoch) {
     __threadfence();
     __syncwarp();
@@ -127,16 +136,24 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int t
     const int f = F.f[task];
     const int np = F.npiv[task];
     const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    // the front's own original entries (scaled), zeros elsewhere
+    for (int e = tid; e < f * f; e += GS) Fr[e] = (T)0;
+    gsync<GS>();
+    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += GS) {
+        const int64_t nz = F.orig_nz[q];
+        Fr[F.orig_off[q]] = (T)(F.scale[F.kkt_row[nz]] * F.kval[nz] * F.scale[F.kkt_col[nz]]);
+    }
+    gsync<GS>();
     for (int ci = c0; ci < c1; ci++) {
         const int ch = F.child[ci];
         const T *Fc = fronts + F.front_off[ch];
         const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
         const int32_t *rel = F.rel + F.rel_off[ch];
-        const int tot = nu * (nu + 1) / 2;
+        const int tot = nu * nu;
         for (int e = tid; e < tot; e += GS) {
-            int jj, ii;
-            tri_index(e, nu, jj, ii);
-            Fr[(int64_t)rel[jj] * f + rel[ii]] += Fc[(int64_t)(npc + jj) * fc + npc + ii];
+            const int jj = e / nu, ii = e - jj * nu;
+            if (ii >= jj)
+                Fr[(int64_t)rel[jj] * f + rel[ii]] += Fc[(int64_t)(npc + jj) * fc + npc + ii];
         }
         gsync<GS>();
     }
@@ -161,10 +178,10 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int t
     }
     const int m = f - np;
     if (np > 0 && m > 0) {
-        const int tot = m * (m + 1) / 2;
+        const int tot = m * m;
         for (int e = tid; e < tot; e += GS) {
-            int jj, ii;
-            tri_index(e, m, jj, ii);
+            const int jj = e / m, ii = e - jj * m;
+            if (ii < jj) continue;
             const int i = np + ii, j = np + jj;
             T acc = 0;
             for (int c = 0; c < np; c++) {
@@ -185,15 +202,18 @@ __global__ void __launch_bounds__(kWT) k_factor(DevFront F, T *__restrict__ fron
     const int lane = threadIdx.x & 31;
     int n_pos = 0, n_neg = 0, n_zero = 0;
     while (true) {
-        const int task = warp_grab(queue);
-        if (task >= F.n_small) break;
-        const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-        if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0) {
-            atomicExch(&st->error, 1);
-            atomicExch(&st->timeout_task, task);
+        const int base = warp_grab_chunk(queue);
+        if (base >= F.n_small) break;
+        const int end = min(base + kChunk, F.n_small);
+        for (int task = base; task < end; task++) {
+            const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+            if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0) {
+                atomicExch(&st->error, 1);
+                atomicExch(&st->timeout_task, task);
+            }
+            eliminate_front<T, 32>(F, fronts, task, lane, pivot_tol, n_pos, n_neg, n_zero);
+            warp_publish(done, task, epoch);
         }
-        eliminate_front<T, 32>(F, fronts, task, lane, pivot_tol, n_pos, n_neg, n_zero);
-        warp_publish(done, task, epoch);
     }
     if (lane == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -256,8 +276,16 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
     if (idx >= nb * nb) return;
     const int j = idx / nb, i = idx - j * nb;
     if (i < j) return;
-    double acc = 0.0;
-    for (int k = 0; k < n_blocks; k++) acc += (double)fronts[boff[k] + (int64_t)j * nb + i];
+    // eight independent partial sums (fixed assignment k mod 8), combined in order
+    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    const int64_t off = (int64_t)j * nb + i;
+    int k = 0;
+    for (; k + 8 <= n_blocks; k += 8) {
+#pragma unroll
+        for (int u = 0; u < 8; u++) a[u] += (double)fronts[boff[k + u] + off];
+    }
+    for (int u = 0; k < n_blocks; k++, u++) a[u] += (double)fronts[boff[k] + off];
+    const double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
     S[(int64_t)j * nb + i] = acc;
     S[(int64_t)i * nb + j] = acc;
 }
@@ -265,14 +293,23 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
 // ---- dense LDL^T of the border block (FP64, blocked right-looking) -------
 constexpr int kPanel = 32;
 
-// Factor columns [k0, k1) of S in place (rows >= column), counting inertia.
+// Factor columns [k0, k1) of S in place (rows >= k0), counting inertia.  The
+// panel (n - k0 rows x pw columns) is staged in shared memory; panel columns
+// are updated by different warps in parallel.
 __global__ void k_dense_panel(double *S, int n, int k0, int k1, FactorStatus *st,
                               double pivot_tol) {
+    extern __shared__ double P[];   // P[cl * R + il], R = n - k0
     __shared__ int s_pos, s_neg, s_zero;
+    const int R = n - k0, pw = k1 - k0;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
     if (threadIdx.x == 0) s_pos = s_neg = s_zero = 0;
+    for (int t = threadIdx.x; t < pw * R; t += blockDim.x) {
+        const int cl = t / R, il = t - cl * R;
+        P[t] = S[(int64_t)(k0 + cl) * n + k0 + il];
+    }
     __syncthreads();
-    for (int c = k0; c < k1; c++) {
-        double *colc = S + (int64_t)c * n;
+    for (int c = 0; c < pw; c++) {
+        double *colc = P + c * R;
         const double d = colc[c];
         if (threadIdx.x == 0) {
             if (d > pivot_tol) s_pos++;
@@ -280,16 +317,18 @@ __global__ void k_dense_panel(double *S, int n, int k0, int k1, FactorStatus *st
             else s_zero++;
         }
         const double dinv = 1.0 / (d == 0.0 ? 1e-300 : d);
+        for (int i = c + 1 + threadIdx.x; i < R; i += blockDim.x) colc[i] *= dinv;
         __syncthreads();
-        for (int i = c + 1 + threadIdx.x; i < n; i += blockDim.x) colc[i] *= dinv;
-        __syncthreads();
-        // update the remaining panel columns
-        for (int j = c + 1; j < k1; j++) {
+        for (int j = c + 1 + warp; j < pw; j += nw) {
             const double lj = colc[j] * d;
-            double *colj = S + (int64_t)j * n;
-            for (int i = j + threadIdx.x; i < n; i += blockDim.x) colj[i] -= colc[i] * lj;
+            double *colj = P + j * R;
+            for (int i = j + lane; i < R; i += 32) colj[i] -= colc[i] * lj;
         }
         __syncthreads();
+    }
+    for (int t = threadIdx.x; t < pw * R; t += blockDim.x) {
+        const int cl = t / R, il = t - cl * R;
+        if (il >= cl) S[(int64_t)(k0 + cl) * n + k0 + il] = P[t];
     }
     if (threadIdx.x == 0) {
         atomicAdd(&st->n_pos, s_pos);
@@ -331,9 +370,8 @@ __global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restri
                                                    int *done, int epoch, FactorStatus *st,
                                                    int spin_limit) {
     const int lane = threadIdx.x & 31;
-    while (true) {
-        const int task = warp_grab(queue);
-        if (task >= F.n_tasks) break;
+    for (int base = warp_grab_chunk(queue); base < F.n_tasks; base = warp_grab_chunk(queue))
+    for (int task = base; task < min(base + kChunk, F.n_tasks); task++) {
         const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
         if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0)
             atomicExch(&st->error, 2);
@@ -373,36 +411,95 @@ __global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restri
 // Border right-hand side y = D b_border + sum_k (update vector of block k's
 // border front), then the dense border solve with S = L_S D_S L_S' by one
 // warp (column sweeps, warp-shuffle dot products).
+constexpr int kBS = 1024;   // threads of the border solve
 template <typename T>
-__global__ void k_border_solve(DevFront F, const T *__restrict__ vec, const double *__restrict__ S,
-                               int n, const double *__restrict__ b, const double *__restrict__ scale,
-                               double *__restrict__ x, double *__restrict__ y) {
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+__global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__restrict__ vec,
+                                                      const double *__restrict__ S, int n,
+                                                      const double *__restrict__ b,
+                                                      const double *__restrict__ scale,
+                                                      double *__restrict__ x,
+                                                      double *__restrict__ y) {
+    extern __shared__ double sm[];          // partial sums, then the 32x32 diagonal blocks
+    __shared__ double blk[32][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBS >> 5;
+    // y = D b_border + sum over blocks of the border update vectors:
+    // G groups of threads split the blocks, fixed combination order
+    const int G = kBS / n > 0 ? kBS / n : 1;
+    for (int t = tid; t < G * n; t += kBS) {
+        const int g = t / n, j = t - g * n;
+        double a0 = 0, a1 = 0;
+        int k = g;
+        for (; k + G < F.n_blocks; k += 2 * G) {
+            a0 += (double)vec[F.border_vec_off[k] + j];
+            a1 += (double)vec[F.border_vec_off[k + G] + j];
+        }
+        if (k < F.n_blocks) a0 += (double)vec[F.border_vec_off[k] + j];
+        sm[t] = a0 + a1;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
         double acc = scale[r] * b[r];
-        for (int k = 0; k < F.n_blocks; k++) acc += (double)vec[F.border_vec_off[k] + j];
+        for (int g = 0; g < G; g++) acc += sm[g * n + j];
         y[j] = acc;
     }
     __syncthreads();
-    if (threadIdx.x >= 32) return;
-    const int lane = threadIdx.x;
-    for (int c = 0; c < n; c++) {
-        const double yc = y[c];
-        const double *col = S + (int64_t)c * n;
-        for (int i = c + 1 + lane; i < n; i += 32) y[i] -= col[i] * yc;
-        __syncwarp();
+    // forward: L y = y, blocks of 32 rows (warp 0 solves the diagonal block,
+    // then every thread updates the rows below)
+    for (int b0 = 0; b0 < n; b0 += 32) {
+        const int bs = n - b0 < 32 ? n - b0 : 32;
+        for (int t = tid; t < 32 * 32; t += kBS) {
+            const int c = t >> 5, r = t & 31;
+            blk[r][c] = (r < bs && c < bs) ? S[(int64_t)(b0 + c) * n + b0 + r] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double yl = lane < bs ? y[b0 + lane] : 0.0;
+            for (int j = 0; j < bs; j++) {
+                const double yj = __shfl_sync(0xffffffffu, yl, j);
+                if (lane > j) yl -= blk[lane][j] * yj;
+            }
+            if (lane < bs) y[b0 + lane] = yl;
+        }
+        __syncthreads();
+        for (int i = b0 + bs + tid; i < n; i += kBS) {
+            double acc = 0.0;
+            for (int j = 0; j < bs; j++) acc += S[(int64_t)(b0 + j) * n + i] * y[b0 + j];
+            y[i] -= acc;
+        }
+        __syncthreads();
     }
-    for (int c = lane; c < n; c += 32) y[c] /= S[(int64_t)c * n + c];
-    __syncwarp();
-    for (int c = n - 1; c >= 0; c--) {
-        const double *col = S + (int64_t)c * n;
-        double acc = 0.0;
-        for (int i = c + 1 + lane; i < n; i += 32) acc += col[i] * y[i];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) y[c] -= acc;
-        __syncwarp();
+    for (int c = tid; c < n; c += kBS) y[c] /= S[(int64_t)c * n + c];
+    __syncthreads();
+    // backward: L' x = y, blocks from the bottom
+    const int nblk = (n + 31) / 32;
+    for (int bi = nblk - 1; bi >= 0; bi--) {
+        const int b0 = bi * 32, bs = n - b0 < 32 ? n - b0 : 32;
+        // rows below the block are final: y_i -= sum_{k >= b0+bs} L[k][i] x_k
+        for (int il = warp; il < bs; il += nw) {
+            const int i = b0 + il;
+            const double *col = S + (int64_t)i * n;
+            double acc = 0.0;
+            for (int k = b0 + bs + lane; k < n; k += 32) acc += col[k] * y[k];
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == 0) y[i] -= acc;
+        }
+        for (int t = tid; t < 32 * 32; t += kBS) {
+            const int c = t >> 5, r = t & 31;
+            blk[r][c] = (r < bs && c < bs) ? S[(int64_t)(b0 + c) * n + b0 + r] : 0.0;
+        }
+        __syncthreads();
+        if (warp == 0) {
+            double xl = lane < bs ? y[b0 + lane] : 0.0;
+            for (int k = bs - 1; k >= 0; k--) {
+                const double xk = __shfl_sync(0xffffffffu, xl, k);
+                if (lane < k) xl -= blk[k][lane] * xk;
+            }
+            if (lane < bs) y[b0 + lane] = xl;
+        }
+        __syncthreads();
     }
-    for (int j = lane; j < n; j += 32) {
+    for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
         x[r] = scale[r] * y[j];
     }
@@ -414,9 +511,8 @@ __global__ void __launch_bounds__(kWT) k_solve_bwd(DevFront F, const T *__restri
                                                    double *__restrict__ x, int *queue, int *done,
                                                    int epoch, FactorStatus *st, int spin_limit) {
     const int lane = threadIdx.x & 31;
-    while (true) {
-        const int q = warp_grab(queue);
-        if (q >= F.n_tasks) break;
+    for (int base = warp_grab_chunk(queue); base < F.n_tasks; base = warp_grab_chunk(queue))
+    for (int q = base; q < min(base + kChunk, F.n_tasks); q++) {
         const int task = F.n_tasks - 1 - q;
         if (F.is_border[task]) {
             warp_publish(done, task, epoch);
@@ -454,13 +550,29 @@ __global__ void __launch_bounds__(kWT) k_solve_bwd(DevFront F, const T *__restri
 // ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
 __global__ void k_ruiz(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
                        const double *__restrict__ kval, const double *__restrict__ s_in,
-                       double *__restrict__ s_out) {
+                       double *__restrict__ s_out, const int8_t *__restrict__ is_long) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    if (i >= n || is_long[i]) return;
     double mx = 0.0;
     const double si = s_in[i];
     for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
     s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
+}
+
+__global__ void k_ruiz_long(int64_t n_long, const int64_t *__restrict__ rows,
+                            const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
+                            const double *__restrict__ kval, const double *__restrict__ s_in,
+                            double *__restrict__ s_out) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_long) return;
+    const int64_t i = rows[w];
+    const double si = s_in[i];
+    double mx = 0.0;
+    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
+        mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
+    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if (lane == 0) s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
 }
 
 __global__ void k_fill(int64_t n, double v, double *x) {
@@ -482,15 +594,23 @@ int warp_grid() {
 
 }  // namespace
 
-void launch_equilibrate(int64_t n, const int64_t *ptr, const int64_t *col, const double *kval,
-                        double *scale, double *tmp, int iters, cudaStream_t s) {
+void launch_equilibrate(const DevModel &M, const double *kval, double *scale, double *tmp,
+                        int iters, cudaStream_t s) {
     const int t = 256;
+    const int64_t n = M.n_kkt;
     const int g = (int)((n + t - 1) / t);
+    const int gl = (int)((32 * M.n_long + t - 1) / t);
     k_fill<<<g, t, 0, s>>>(n, 1.0, scale);
+    double *a = scale, *b = tmp;
     for (int it = 0; it < iters; it++) {
-        k_ruiz<<<g, t, 0, s>>>(n, ptr, col, kval, scale, tmp);
-        cudaMemcpyAsync(scale, tmp, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+        k_ruiz<<<g, t, 0, s>>>(n, M.kkt_ptr, M.kkt_col, kval, a, b, M.is_long);
+        if (M.n_long)
+            k_ruiz_long<<<gl, t, 0, s>>>(M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, a, b);
+        double *c = a;
+        a = b;
+        b = c;
     }
+    if (a != scale) cudaMemcpyAsync(scale, a, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
 }
 
 template <typename T>
@@ -534,7 +654,12 @@ void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
     for (int k0 = 0; k0 < n; k0 += kPanel) {
         const int k1 = k0 + kPanel < n ? k0 + kPanel : n;
-        k_dense_panel<<<1, 256, 0, s>>>(S, n, k0, k1, st, pivot_tol);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+            attr = true;
+        }
+        k_dense_panel<<<1, 256, sizeof(double) * (size_t)(n - k0) * (k1 - k0), s>>>(S, n, k0, k1, st, pivot_tol);
         const int rem = n - k1;
         if (rem > 0) {
             const int tiles = (rem + 31) / 32;
@@ -553,7 +678,11 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
     cudaMemsetAsync(queue, 0, sizeof(int), s);
     k_solve_fwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, b, scale, queue, done, epoch, st,
                                         spin_limit);
-    k_border_solve<T><<<1, 256, 0, s>>>(F, vec, S, nS, b, scale, x, border_work);
+    {
+        const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
+        k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
+            F, vec, S, nS, b, scale, x, border_work);
+    }
     cudaMemsetAsync(queue, 0, sizeof(int), s);
     k_solve_bwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, scale, x, queue, done, epoch + 1, st,
                                         spin_limit);

@@ -205,24 +205,55 @@ __global__ void k_assemble(int64_t nnz, const int32_t *__restrict__ row,
     kval[j] = v;
 }
 
+__device__ __forceinline__ double dual_term(int64_t q, const int64_t *__restrict__ col,
+                                            const int8_t *__restrict__ kind,
+                                            const int64_t *__restrict__ index,
+                                            const double *__restrict__ kval,
+                                            const double *__restrict__ lam,
+                                            const double *__restrict__ yc) {
+    const int64_t c = col[q];
+    const int8_t k = kind[c];
+    if (k == 1) return kval[q] * lam[index[c]];
+    if (k == 2) return kval[q] * yc[index[c]];
+    return 0.0;
+}
+
 __global__ void k_dual_product(int64_t n_kkt, const int64_t *__restrict__ ptr,
                                const int64_t *__restrict__ col, const int8_t *__restrict__ kind,
                                const int64_t *__restrict__ index, const double *__restrict__ kval,
                                const double *__restrict__ g, const double *__restrict__ lam,
-                               const double *__restrict__ yc, double *__restrict__ gw) {
+                               const double *__restrict__ yc, double *__restrict__ gw,
+                               const int8_t *__restrict__ is_long) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_kkt || kind[i] != 0) return;
+    if (i >= n_kkt || kind[i] != 0 || is_long[i]) return;
     double s = 0.0;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) {
-        const int64_t c = col[q];
-        const int8_t k = kind[c];
-        if (k == 1)
-            s += kval[q] * lam[index[c]];
-        else if (k == 2)
-            s += kval[q] * yc[index[c]];
-    }
+    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) s += dual_term(q, col, kind, index, kval, lam, yc);
     const int64_t wi = index[i];
     gw[wi] = g[wi] + s;
+}
+
+// the same for the long rows, one warp per row
+__global__ void k_dual_product_long(int64_t n_long, const int64_t *__restrict__ rows,
+                                    const int64_t *__restrict__ ptr,
+                                    const int64_t *__restrict__ col,
+                                    const int8_t *__restrict__ kind,
+                                    const int64_t *__restrict__ index,
+                                    const double *__restrict__ kval, const double *__restrict__ g,
+                                    const double *__restrict__ lam, const double *__restrict__ yc,
+                                    double *__restrict__ gw) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_long) return;
+    const int64_t i = rows[w];
+    if (kind[i] != 0) return;
+    double s = 0.0;
+    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
+        s += dual_term(q, col, kind, index, kval, lam, yc);
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) {
+        const int64_t wi = index[i];
+        gw[wi] = g[wi] + s;
+    }
 }
 
 __global__ void k_rhs(int64_t n_kkt, const int8_t *__restrict__ kind,
@@ -251,15 +282,32 @@ __global__ void k_rhs(int64_t n_kkt, const int8_t *__restrict__ kind,
     rhs[i] = v;
 }
 
+// y = b - K x (b may be NULL: y = -K x ... used with sign = -1 for y = K x)
 __global__ void k_residual(int64_t n_kkt, const int64_t *__restrict__ ptr,
                            const int64_t *__restrict__ col, const double *__restrict__ kval,
                            const double *__restrict__ x, const double *__restrict__ b,
-                           double *__restrict__ y) {
+                           double *__restrict__ y, const int8_t *__restrict__ is_long,
+                           double sign) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_kkt) return;
+    if (i >= n_kkt || is_long[i]) return;
     double s = 0.0;
     for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) s += kval[q] * x[col[q]];
-    y[i] = b[i] - s;
+    y[i] = (b ? b[i] : 0.0) + sign * s;
+}
+
+__global__ void k_residual_long(int64_t n_long, const int64_t *__restrict__ rows,
+                                const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
+                                const double *__restrict__ kval, const double *__restrict__ x,
+                                const double *__restrict__ b, double *__restrict__ y,
+                                double sign) {
+    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (w >= n_long) return;
+    const int64_t i = rows[w];
+    double s = 0.0;
+    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32) s += kval[q] * x[col[q]];
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (lane == 0) y[i] = (b ? b[i] : 0.0) + sign * s;
 }
 
 template <int OP>
@@ -336,16 +384,6 @@ __global__ void k_scale_copy(int64_t n, double a, const double *__restrict__ x,
     if (i < n) y[i] = a * x[i];
 }
 
-__global__ void k_spmv(int64_t n_kkt, const int64_t *__restrict__ ptr,
-                       const int64_t *__restrict__ col, const double *__restrict__ kval,
-                       const double *__restrict__ x, double *__restrict__ y) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n_kkt) return;
-    double s = 0.0;
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) s += kval[q] * x[col[q]];
-    y[i] = s;
-}
-
 }  // namespace
 
 void launch_multi_dot(const double *V, int64_t n, int k, const double *w, double *partial,
@@ -366,7 +404,11 @@ void launch_scale_copy(int64_t n, double a, const double *x, double *y, cudaStre
 
 void launch_spmv(const DevModel &M, const double *kval, const double *x, double *y,
                  cudaStream_t s) {
-    k_spmv<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, y);
+    k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x,
+                                                     nullptr, y, M.is_long, 1.0);
+    if (M.n_long)
+        k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+            M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, x, nullptr, y, 1.0);
 }
 
 void launch_eval_elements(const DevModel &M, const double *w, const double *lam, const double *yc,
@@ -409,7 +451,12 @@ void launch_assemble(const DevModel &M, const double *ev, const double *diag, do
 void launch_dual_product(const DevModel &M, const double *kval, const double *g, const double *lam,
                          const double *yc, double *gw, cudaStream_t s) {
     k_dual_product<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, M.row_kind,
-                                                         M.row_index, kval, g, lam, yc, gw);
+                                                         M.row_index, kval, g, lam, yc, gw,
+                                                         M.is_long);
+    if (M.n_long)
+        k_dual_product_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+            M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, M.row_kind, M.row_index, kval, g, lam,
+            yc, gw);
 }
 
 void launch_rhs(const DevModel &M, const RhsArgs &a, double *rhs, cudaStream_t s) {
@@ -419,7 +466,11 @@ void launch_rhs(const DevModel &M, const RhsArgs &a, double *rhs, cudaStream_t s
 
 void launch_residual(const DevModel &M, const double *kval, const double *x, const double *b,
                      double *y, cudaStream_t s) {
-    k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, b, y);
+    k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, b, y,
+                                                     M.is_long, -1.0);
+    if (M.n_long)
+        k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+            M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, x, b, y, -1.0);
 }
 
 void reduce_maxabs(const double *x, int64_t n, double *d_out, double *scratch, cudaStream_t s) {
