@@ -221,6 +221,17 @@ int scopf_newton_step(scopf_handle *h, const scopf_state *it, const double *lam_
  * calls_out[7] (host, may be NULL) receive the accumulated totals. */
 int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls_out);
 
+/* Dense pivot-free LDL^T factorization and solve of a symmetric n x n
+ * matrix: the factor of the first-stage Schur complement (border block) of
+ * eq. (newtonsystem), available on its own.  S: device, column-major,
+ * n*n, read only (a private copy is factored); b, x: device, n (x may not
+ * alias S).  inertia (host, 3, may be NULL): signs of D.  stream: a
+ * cudaStream_t or NULL.  Allocates its scratch (n*n + n doubles) with
+ * cudaMalloc and frees it before returning. */
+int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *x,
+                           int32_t inertia[3], void *stream);
+
+
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */
 int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);

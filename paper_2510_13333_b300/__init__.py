@@ -142,6 +142,7 @@ def lib():
             "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
+            "scopf_dense_ldlt_solve": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32, ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -156,6 +157,20 @@ def exported_symbols():
     import re
     hdr = open(os.path.join(_HERE, "..", "include", "scopf.h")).read()
     return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?(\w+)\(", hdr, re.M)))
+
+
+def scopf_dense_ldlt_solve(S, b):
+    """Dense pivot-free LDL^T solve of S x = b (torch float64 CUDA tensors,
+    S column-major n x n, i.e. pass S.T.contiguous() for a row-major array).
+    Returns (x, inertia)."""
+    import torch
+    n = b.numel()
+    x = torch.empty_like(b)
+    inert = np.zeros(3, dtype=np.int32)
+    _check("scopf_dense_ldlt_solve", lib().scopf_dense_ldlt_solve(
+        _dp(S), n, _dp(b), _dp(x), _hp(inert, c_i32),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return x, tuple(int(v) for v in inert)
 
 
 def default_options(**kw) -> Options:

@@ -26,6 +26,7 @@
 // and FP32 fronts keep far more accuracy than on the raw barrier-scaled KKT.
 #include <cmath>
 
+#include "dense_ldlt.cuh"
 #include "kernels.h"
 
 namespace scopf {
@@ -420,8 +421,7 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
                                                       double *__restrict__ x,
                                                       double *__restrict__ y) {
     extern __shared__ double sm[];          // partial sums, then the 32x32 diagonal blocks
-    __shared__ double blk[32][33];
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBS >> 5;
+    const int tid = threadIdx.x;
     // y = D b_border + sum over blocks of the border update vectors:
     // G groups of threads split the blocks, fixed combination order
     const int G = kBS / n > 0 ? kBS / n : 1;
@@ -444,61 +444,7 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
         y[j] = acc;
     }
     __syncthreads();
-    // forward: L y = y, blocks of 32 rows (warp 0 solves the diagonal block,
-    // then every thread updates the rows below)
-    for (int b0 = 0; b0 < n; b0 += 32) {
-        const int bs = n - b0 < 32 ? n - b0 : 32;
-        for (int t = tid; t < 32 * 32; t += kBS) {
-            const int c = t >> 5, r = t & 31;
-            blk[r][c] = (r < bs && c < bs) ? S[(int64_t)(b0 + c) * n + b0 + r] : 0.0;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double yl = lane < bs ? y[b0 + lane] : 0.0;
-            for (int j = 0; j < bs; j++) {
-                const double yj = __shfl_sync(0xffffffffu, yl, j);
-                if (lane > j) yl -= blk[lane][j] * yj;
-            }
-            if (lane < bs) y[b0 + lane] = yl;
-        }
-        __syncthreads();
-        for (int i = b0 + bs + tid; i < n; i += kBS) {
-            double acc = 0.0;
-            for (int j = 0; j < bs; j++) acc += S[(int64_t)(b0 + j) * n + i] * y[b0 + j];
-            y[i] -= acc;
-        }
-        __syncthreads();
-    }
-    for (int c = tid; c < n; c += kBS) y[c] /= S[(int64_t)c * n + c];
-    __syncthreads();
-    // backward: L' x = y, blocks from the bottom
-    const int nblk = (n + 31) / 32;
-    for (int bi = nblk - 1; bi >= 0; bi--) {
-        const int b0 = bi * 32, bs = n - b0 < 32 ? n - b0 : 32;
-        // rows below the block are final: y_i -= sum_{k >= b0+bs} L[k][i] x_k
-        for (int il = warp; il < bs; il += nw) {
-            const int i = b0 + il;
-            const double *col = S + (int64_t)i * n;
-            double acc = 0.0;
-            for (int k = b0 + bs + lane; k < n; k += 32) acc += col[k] * y[k];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) y[i] -= acc;
-        }
-        for (int t = tid; t < 32 * 32; t += kBS) {
-            const int c = t >> 5, r = t & 31;
-            blk[r][c] = (r < bs && c < bs) ? S[(int64_t)(b0 + c) * n + b0 + r] : 0.0;
-        }
-        __syncthreads();
-        if (warp == 0) {
-            double xl = lane < bs ? y[b0 + lane] : 0.0;
-            for (int k = bs - 1; k >= 0; k--) {
-                const double xk = __shfl_sync(0xffffffffu, xl, k);
-                if (lane < k) xl -= blk[k][lane] * xk;
-            }
-            if (lane < bs) y[b0 + lane] = xl;
-        }
-        __syncthreads();
-    }
+    block_ldlt_solve<kBS>(S, n, y);
     for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
         x[r] = scale[r] * y[j];
