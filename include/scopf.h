@@ -231,6 +231,18 @@ int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls
 int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *x,
                            int32_t inertia[3], void *stream);
 
+/* The same factor + solve for callers that must not allocate device memory
+ * during the call (e.g. an application whose device memory is reserved by
+ * its own pool allocator, or a latency-critical loop that cannot take the
+ * device-wide synchronisation of cudaMalloc/cudaFree).  The paper has no
+ * counterpart: this is a deployment variant of scopf_dense_ldlt_solve.
+ * Scratch is a static per-device array sized for n <= 768 (about 4.7 MB,
+ * held by every GPU that loads the library until exit); n > 768 returns
+ * SCOPF_ERR_INVALID_ARG.  The first call on a device looks up the array's
+ * device address; make it before any stream capture.  All calls on a device
+ * share the array, so calls that overlap on the GPU race: order them. */
+int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, double *x,
+                                   int32_t inertia[3], void *stream);
 
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */

@@ -143,6 +143,8 @@ def lib():
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
             "scopf_dense_ldlt_solve": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32, ctypes.c_void_p]),
+            "scopf_dense_ldlt_solve_noalloc": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32,
+                                                       ctypes.c_void_p]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -171,6 +173,21 @@ def scopf_dense_ldlt_solve(S, b):
         _dp(S), n, _dp(b), _dp(x), _hp(inert, c_i32),
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
     return x, tuple(int(v) for v in inert)
+
+
+def scopf_dense_ldlt_solve_noalloc(S, b, x=None):
+    """As scopf_dense_ldlt_solve, through the entry point that allocates no
+    device memory (static per-device scratch, n <= 768).  The output x may be
+    passed in preallocated.  Returns (x, inertia, status)."""
+    import torch
+    n = b.numel()
+    if x is None:
+        x = torch.empty_like(b)
+    inert = np.zeros(3, dtype=np.int32)
+    st = lib().scopf_dense_ldlt_solve_noalloc(
+        _dp(S), n, _dp(b), _dp(x), _hp(inert, c_i32),
+        ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
+    return x, tuple(int(v) for v in inert), st
 
 
 def default_options(**kw) -> Options:
