@@ -151,6 +151,7 @@ class NCLSolver:
         self.n, self.m, self.p = P.n, P.m, P.p
         self.n_inner = 0
         self.history = []
+        self.skip_delta0 = False
 
     # ------------------------------------------------------------ helpers
     def project_start(self, w):
@@ -293,12 +294,21 @@ class NCLSolver:
         o = self.o
         n_pos, n_neg = self.n, self.m + self.p
         rhs = self.reduced_rhs(st, prm, res, mu)
-        delta = 0.0
+        # Once a delta_w = 0 factorization has shown zero pivots (variables
+        # that enter only linearly are eliminated before their rows, so the
+        # zeros recur at every iterate) the trial at 0 is skipped: it would
+        # fail again, and the delta_w sequence that follows is unchanged.
+        if self.skip_delta0:
+            delta = o.delta_w0 if dw_last == 0.0 else max(o.delta_w_min, o.kappa_w_minus * dw_last)
+        else:
+            delta = 0.0
         tries = 0
         while True:
             K = self.kkt_matrix(st, prm, H, res["J"], delta)
             ip, ineg, iz = self.lin.factor(K)
             tries += 1
+            if delta == 0.0 and iz > 0:
+                self.skip_delta0 = True
             if ip == n_pos and ineg == n_neg and iz == 0:
                 break
             if delta == 0.0:

@@ -162,7 +162,6 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, HF.is_border, &F.is_border));
     TRY(upload(h, HF.border_off, &F.border_off));
     TRY(upload(h, HF.border_rows, &F.border_rows));
-    TRY(upload(h, HF.scatter, &F.scatter));
     TRY(upload(h, HF.vec_off, &F.vec_off));
     TRY(upload(h, HF.border_vec_off, &F.border_vec_off));
     TRY(upload(h, HF.orig_ptr, &F.orig_ptr));
@@ -170,7 +169,6 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, HF.orig_off, &F.orig_off));
     F.kkt_row = d.kkt_row;
     F.kkt_col = d.kkt_col;
-    F.nnz = (int64_t)HF.scatter.size();
     F.front_elems = HF.front_elems;
     F.vec_elems = HF.vec_elems;
     // work buffers
@@ -188,6 +186,13 @@ int setup_device(scopf_handle *h) {
     TRY(alloc(h, M.n_kkt, &h->scale_tmp));
     F.kval = h->kval;
     F.scale = h->scale;
+    {
+        double *ov = nullptr;
+        TRY(alloc(h, HF.orig_nz.size(), &ov));
+        F.ovals = ov;
+        h->ovals = ov;
+        F.n_orig = (int64_t)HF.orig_nz.size();
+    }
     double *fr = nullptr, *vv = nullptr;
     TRY(alloc(h, (size_t)HF.front_elems, &fr));
     TRY(alloc(h, (size_t)HF.vec_elems, &vv));
@@ -195,8 +200,23 @@ int setup_device(scopf_handle *h) {
     h->vec = vv;
     TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->S));
     TRY(alloc(h, (size_t)M.nborder + 1, &h->border_work));
-    TRY(alloc(h, 1, &h->queue));
-    TRY(alloc(h, (size_t)HF.n_tasks, &h->done));
+    {
+        const size_t nt = HF.n_tasks > 0 ? (size_t)HF.n_tasks : 1;
+        TRY(alloc(h, nt, &F.q_slots_a));
+        TRY(alloc(h, nt, &F.q_slots_b));
+        TRY(alloc(h, nt, &F.q_pending));
+        TRY(alloc(h, 4, &F.q_ctr));
+        TRY(upload(h, HF.init_small, &F.init_small));
+        TRY(upload(h, HF.init_big, &F.init_big));
+        TRY(upload(h, HF.init_fwd, &F.init_fwd));
+        TRY(upload(h, HF.init_bwd, &F.init_bwd));
+        TRY(upload(h, HF.pend_factor, &F.pend_factor));
+        TRY(upload(h, HF.nchild, &F.nchild));
+        F.n_init_small = (int)HF.init_small.size();
+        F.n_init_big = (int)HF.init_big.size();
+        F.n_init_fwd = (int)HF.init_fwd.size();
+        F.n_init_bwd = (int)HF.init_bwd.size();
+    }
     TRY(alloc(h, 1, &h->fstat));
     TRY(alloc(h, 1024, &h->red_scratch));
     TRY(alloc(h, 16, &h->red_out));
@@ -579,11 +599,10 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
     h->timer.begin(PH_FRONT_INIT, s);
     launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, 3, s);
+    launch_orig_vals(h->df, h->ovals, s);
     h->timer.end(PH_FRONT_INIT, s);
-    h->epoch++;
     h->timer.begin(PH_FACTOR, s);
-    launch_factor<T>(h->df, fr, h->fstat, h->queue, h->done, h->epoch, h->opt.pivot_tol,
-                     h->opt.spin_limit, s);
+    launch_factor<T>(h->df, fr, h->fstat, h->opt.pivot_tol, h->opt.spin_limit, s);
     h->timer.end(PH_FACTOR, s);
     h->timer.begin(PH_SCHUR, s);
     launch_schur_sum<T>(h->df, fr, h->S, s);
@@ -614,13 +633,11 @@ int factor_impl(scopf_handle *h, int precision, int inertia[3]) {
 
 template <typename T>
 static int solve_once(scopf_handle *h, const double *b, double *x) {
-    h->epoch += 2;
     h->timer.begin(PH_SOLVE, h->stream);
     launch_solve<T>(h->df, reinterpret_cast<T *>(h->fronts), reinterpret_cast<T *>(h->vec), h->S,
-                    (int)h->M.nborder, h->scale, b, x, h->border_work, h->queue, h->done,
-                    h->epoch - 1, h->fstat, h->opt.spin_limit, h->stream);
+                    (int)h->M.nborder, h->scale, b, x, h->border_work, h->fstat,
+                    h->opt.spin_limit, h->stream);
     h->timer.end(PH_SOLVE, h->stream);
-    h->epoch++;
     return SCOPF_OK;
 }
 

@@ -168,6 +168,23 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         H.child_ptr[i + 1] = H.child_ptr[i] + (int)ch[i].size();
         for (int c : ch[i]) H.child.push_back(c);
     }
+    // ready-queue seeds.  Factorization: phase 1 (small fronts) starts from
+    // its leaves; phase 2 counts only its own children (the small ones are
+    // complete when it starts).  Forward solve: all leaves.  Backward solve:
+    // the non-border tasks whose parent is a border front (the block roots).
+    H.nchild.assign(nt, 0);
+    H.pend_factor.assign(nt, 0);
+    for (int i = 0; i < nt; i++) {
+        H.nchild[i] = (int)ch[i].size();
+        for (int c : ch[i])
+            if (!(i >= H.n_small && c < H.n_small)) H.pend_factor[i]++;
+    }
+    for (int i = 0; i < nt; i++) {
+        if (H.nchild[i] == 0) H.init_fwd.push_back(i);
+        if (i < H.n_small && H.pend_factor[i] == 0) H.init_small.push_back(i);
+        if (i >= H.n_small && H.pend_factor[i] == 0) H.init_big.push_back(i);
+        if (!H.is_border[i] && (H.parent[i] < 0 || H.is_border[H.parent[i]])) H.init_bwd.push_back(i);
+    }
     H.rel_off.assign(nt, 0);
     for (int i = 0; i < nt; i++) {
         H.rel_off[i] = (int64_t)H.rel.size();

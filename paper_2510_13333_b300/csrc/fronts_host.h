@@ -11,6 +11,9 @@ struct HostFronts {
     std::vector<int32_t> f, npiv, parent, is_border, child_ptr, child, rel, level, block;
     std::vector<int64_t> rows, border_rows, orig_ptr, orig_nz;
     std::vector<int32_t> orig_off;
+    // ready-queue seeds of the task DAG: tasks runnable at the start of each
+    // sweep, and the dependency counts the sweeps start from
+    std::vector<int32_t> init_small, init_big, init_fwd, init_bwd, pend_factor, nchild;
     int64_t front_elems = 0, vec_elems = 0, nnz_L = 0;
     double flops = 0;
 };

@@ -107,10 +107,9 @@ struct scopf_handle {
     double *S = nullptr, *border_work = nullptr;
     double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
-    int *queue = nullptr, *done = nullptr;
+    double *ovals = nullptr;                                // scaled front originals
     scopf::FactorStatus *fstat = nullptr;
     double *red_scratch = nullptr, *red_out = nullptr;
-    int epoch = 0;
     bool assembled = false, factored = false;
     int factored_precision = SCOPF_PREC_FP64;
     double last_delta_w = 0.0, last_rho = 0.0;
@@ -125,6 +124,7 @@ struct scopf_handle {
     // counters
     int n_factor = 0, n_refine = 0;
     bool force_fp64 = false;      // sticky FP64 fallback inside a solve
+    bool skip_delta0 = false;     // delta_w = 0 factorizations showed zero pivots
     scopf::PhaseTimer timer;
     std::string last_error;
 };

@@ -479,19 +479,28 @@ struct Ipm {
     int direction(const scopf_state &st, double rho, double mu, double &dw_last, double &delta,
                   int &tries) {
         const int64_t npos = n, nneg = m + p;
-        delta = 0.0;
+        // Inertia correction (W&B 2006, Alg. IC).  Once a delta_w = 0
+        // factorization has shown zero pivots -- variables entering only
+        // linearly (p^k, Delta^k, free q^k) are eliminated before their rows,
+        // so these zeros recur at every iterate -- the trial at 0 is skipped:
+        // it would fail again and the delta_w sequence is unchanged.
+        delta = h->skip_delta0
+                    ? (dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last))
+                    : 0.0;
         tries = 0;
-        // K at delta = 0 and the right-hand side were assembled by the caller
+        double assembled = 0.0;   // K at delta = 0 and the RHS were assembled by the caller
         while (true) {
-            if (tries > 0) {
+            if (delta != assembled) {
                 int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, delta, nullptr);
                 if (r != SCOPF_OK) return r;
+                assembled = delta;
             }
             const int prec = force_fp64 ? SCOPF_PREC_FP64 : h->precision;
             int in[3];
             int r = factor_impl(h, prec, in);
             if (r != SCOPF_OK) return r;
             tries++;
+            if (delta == 0.0 && in[2] > 0) h->skip_delta0 = true;
             if (o.verbose >= 2)
                 std::printf("    factor (%s) delta_w %.2e inertia (%d, %d, %d), want (%lld, %lld, 0)\n",
                             prec == SCOPF_PREC_MIXED ? "fp32" : "fp64", delta, in[0], in[1], in[2],
@@ -533,6 +542,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     scopf_state &d = h->dir;
     scopf_state &tr = h->trial;
     double rho = o.rho_init;
+    h->skip_delta0 = false;
     cudaMemsetAsync(h->lam_n, 0, sizeof(double) * (m ? m : 1), s);
     cudaMemsetAsync(h->nu0_n, 0, sizeof(double) * (p ? p : 1), s);
     if (warm) {

@@ -98,8 +98,6 @@ struct DevFront {
     const int32_t *is_border;     // per task
     const int64_t *border_off;    // per block: element offset of the border front
     const int64_t *border_rows;   // n_border KKT indices (natural order)
-    const int64_t *scatter;       // per stored KKT entry: front element offset or -1
-    int64_t nnz;
     int64_t front_elems;          // size of the front buffer (elements)
     int64_t vec_elems;            // size of the per-front vector buffer
     const int64_t *vec_off;       // per task offset into the vector buffer
@@ -114,7 +112,19 @@ struct DevFront {
     const int64_t *kkt_col;
     const double *kval;           // assembled K (set before each factorization)
     const double *scale;          // Ruiz scaling
+    const double *ovals;          // scaled original entries in task order (n_orig)
+    int64_t n_orig;
+    // ready queues (two per run: factor phases 1/2, or forward/backward solve)
+    int *q_slots_a, *q_slots_b;   // n_tasks each: task ids in the order they became ready
+    int *q_ctr;                   // [a.claim, a.fill, b.claim, b.fill]
+    int *q_pending;               // n_tasks: outstanding dependencies
+    const int32_t *init_small, *init_big, *init_fwd, *init_bwd;
+    int n_init_small, n_init_big, n_init_fwd, n_init_bwd;
+    const int32_t *pend_factor;   // dependencies counted by the factorization phases
+    const int32_t *nchild;        // children per task
 };
+// ovals[p] = scale[i] K_ij scale[j] for the p-th original front entry
+void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s);
 
 struct FactorStatus {             // device-side counters
     int n_pos, n_neg, n_zero, error, timeout_task, pad[3];
@@ -123,23 +133,17 @@ struct FactorStatus {             // device-side counters
 // Symmetric Ruiz equilibration of K (scale[i] > 0, `iters` sweeps).
 void launch_equilibrate(const DevModel &M, const double *kval, double *scale, double *tmp,
                         int iters, cudaStream_t s);
-// fronts <- scatter of scale[i] K_ij scale[j] (lower triangle in elimination order)
 template <typename T>
-void launch_front_init(const DevFront &F, const int32_t *row, const int64_t *col,
-                       const double *scale, const double *kval, T *fronts, cudaStream_t s);
-template <typename T>
-void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, int *queue, int *done,
-                   int epoch, double pivot_tol, int spin_limit, cudaStream_t s);
+void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_tol,
+                   int spin_limit, cudaStream_t s);
 template <typename T>
 void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s);
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s);
 
-// Forward solve uses dependency epoch `epoch`, backward `epoch + 1`.
 // x = K^-1 b through the factors of D K D: x = D (DKD)^-1 D b
 template <typename T>
 void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
                   const double *scale, const double *b, double *x, double *border_work,
-                  int *queue, int *done, int epoch, FactorStatus *st, int spin_limit,
-                  cudaStream_t s);
+                  FactorStatus *st, int spin_limit, cudaStream_t s);
 
 }  // namespace scopf

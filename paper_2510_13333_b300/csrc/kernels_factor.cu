@@ -45,56 +45,100 @@ __device__ __forceinline__ void st_release(int *p, int v) {
     asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
-// Warp-wide wait until done[dep] == epoch for all deps (bounded polls).
-__device__ bool warp_wait(const int *deps, int ndeps, const int *done, int epoch, int spin_limit) {
-    const int lane = threadIdx.x & 31;
-    bool ok = true;
-    for (int i = lane; i < ndeps; i += 32) {
-        const int d = deps[i];
-        int spins = 0;
-        while (ld_acquire(&done[d]) != epoch) {
-            if (++spins > spin_limit) {
-                ok = false;
-                break;
-            }
-            __nanosleep(32);
-        }
+// ---- ready queue ----------------------------------------------------------
+// Tasks become ready when their dependencies complete (bottom-up: the last
+// child pushes its parent; top-down: a parent pushes its children) and are
+// appended to a slot array; workers claim slots in order and wait (bounded)
+// for a claimed slot to be filled.  Every task is pushed exactly once, so
+// slot s is filled by the s-th push.  If every worker waits, all filled
+// slots have been claimed and finished, and in a tree that means every task
+// is done (an unfinished task has an unfinished descendant, down to a seeded
+// leaf); so a wait always ends while the run has work, and workers that have
+// not started hold no slot.
+struct QueueView {
+    int *slots;     // -1 = not yet filled
+    int *ctr;       // [0] next slot to claim, [1] next slot to fill
+    int *pending;   // outstanding dependencies per task
+    int n_items;    // tasks pushed in this run
+};
+
+// lane 0 claims a slot and waits for it; returns the task, -1 when the run
+// is finished, -2 when the wait ran out (error)
+__device__ __forceinline__ int claim_slot(const QueueView &Q, int spin_limit) {
+    const int s = atomicAdd(&Q.ctr[0], 1);
+    if (s >= Q.n_items) return -1;
+    int t, spins = 0;
+    while ((t = ld_acquire(&Q.slots[s])) < 0) {
+        if (++spins > spin_limit) return -2;
+        __nanosleep(32);
     }
-    ok = __all_sync(0xffffffffu, ok);
+    return t;
+}
+
+// warp-wide claim: the task id in every lane; the warp barrier orders lane
+// 0's acquire before the other lanes' reads of the task's inputs
+__device__ __forceinline__ int warp_claim(const QueueView &Q, int spin_limit, FactorStatus *st,
+                                          int err) {
+    int task = 0;
+    if ((threadIdx.x & 31) == 0) {
+        task = claim_slot(Q, spin_limit);
+        if (task == -2) atomicExch(&st->error, err);
+    }
+    task = __shfl_sync(0xffffffffu, task, 0);
     __syncwarp();
-    return ok;
+    return task;
 }
 
-__device__ __forceinline__ int warp_grab(int *queue) {
-    int t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(queue, 1);
-    return __shfl_sync(0xffffffffu, t, 0);
+__device__ __forceinline__ void push_task(const QueueView &Q, int task) {
+    const int s = atomicAdd(&Q.ctr[1], 1);
+    st_release(&Q.slots[s], task);
 }
 
-// A warp takes kChunk consecutive tasks per atomic (processed in order:
-// tasks of a chunk only wait on earlier tasks, all already taken).
-constexpr int kChunk = 4;
-__device__ __forceinline__ int warp_grab_chunk(int *queue) {
-    int t = 0;
-    if ((threadIdx.x & 31) == 0) t = atomicAdd(queue, kChunk);
-    return __shfl_sync(0xffffffffu, t, 0);
-}
-
-__device__ __forceinline__ void warp_publish(int *done, int task, int epoch) {
+// one thread, after a barrier that ordered its group's writes: count the task
+// off at its parent; the last child pushes the parent
+__device__ __forceinline__ void complete_child(const QueueView &Q, int parent) {
     __threadfence();
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) st_release(&done[task], epoch);
+    if (atomicSub(&Q.pending[parent], 1) == 1) {
+        __threadfence();
+        push_task(Q, parent);
+    }
 }
 
-template <typename T>
-__global__ void k_front_scatter(int64_t nnz, const int64_t *__restrict__ map,
-                                const int32_t *__restrict__ row, const int64_t *__restrict__ col,
-                                const double *__restrict__ scale, const double *__restrict__ kval,
-                                T *__restrict__ fronts) {
-    int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (j >= nnz) return;
-    const int64_t off = map[j];
-    if (off >= 0) fronts[off] = (T)(scale[row[j]] * kval[j] * scale[col[j]]);
+// whole warp, after __syncwarp: push every child of `task`
+__device__ __forceinline__ void push_children(const QueueView &Q, const DevFront &F, int task) {
+    const int lane = threadIdx.x & 31;
+    const int c0 = F.child_ptr[task], nc = F.child_ptr[task + 1] - c0;
+    if (nc == 0) return;
+    __threadfence();
+    int base = 0;
+    if (lane == 0) base = atomicAdd(&Q.ctr[1], nc);
+    base = __shfl_sync(0xffffffffu, base, 0);
+    for (int i = lane; i < nc; i += 32) st_release(&Q.slots[base + i], F.child[c0 + i]);
+}
+
+// both queues of a run: slots from their seed lists, counters, pending
+__global__ void k_queue_reset(int n, int *slots_a, const int32_t *init_a, int n_a, int *slots_b,
+                              const int32_t *init_b, int n_b, int *pending,
+                              const int32_t *pend, int *ctr) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) {
+        slots_a[i] = i < n_a ? init_a[i] : -1;
+        slots_b[i] = i < n_b ? init_b[i] : -1;
+        pending[i] = pend ? pend[i] : 0;
+    }
+    if (i == 0) {
+        ctr[0] = 0;
+        ctr[1] = n_a;
+        ctr[2] = 0;
+        ctr[3] = n_b;
+    }
+}
+
+QueueView queue_a(const DevFront &F, int n_items) {
+    return QueueView{F.q_slots_a, F.q_ctr, F.q_pending, n_items};
+}
+QueueView queue_b(const DevFront &F, int n_items) {
+    return QueueView{F.q_slots_b, F.q_ctr + 2, F.q_pending, n_items};
 }
 
 // (column j, row i) of element e of the column-major lower triangle of an
@@ -140,10 +184,8 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int t
     // the front's own original entries (scaled), zeros elsewhere
     for (int e = tid; e < f * f; e += GS) Fr[e] = (T)0;
     gsync<GS>();
-    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += GS) {
-        const int64_t nz = F.orig_nz[q];
-        Fr[F.orig_off[q]] = (T)(F.scale[F.kkt_row[nz]] * F.kval[nz] * F.scale[F.kkt_col[nz]]);
-    }
+    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += GS)
+        Fr[F.orig_off[q]] = (T)F.ovals[q];
     gsync<GS>();
     for (int ci = c0; ci < c1; ci++) {
         const int ch = F.child[ci];
@@ -195,26 +237,94 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int t
     }
 }
 
+// A front with f <= 32 rows held in one warp's shared-memory tile (lane i
+// owns row i): originals, extend-add, unblocked right-looking elimination,
+// then one coalesced write of the whole front (L panel, D, update block).
+template <typename T>
+__device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, int task,
+                                     int lane, T (*tile)[33], double pivot_tol, int &n_pos,
+                                     int &n_neg, int &n_zero) {
+    T *Fr = fronts + F.front_off[task];
+    const int f = F.f[task];
+    const int np = F.npiv[task];
+    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    for (int j = 0; j < 32; j++) tile[lane][j] = (T)0;
+    __syncwarp();
+    const int64_t o0 = F.orig_ptr[task], o1 = F.orig_ptr[task + 1];
+    for (int64_t q = o0 + lane; q < o1; q += 32) {
+        const int off = F.orig_off[q];
+        const int col = off / f, row = off - col * f;
+        tile[row][col] = (T)F.ovals[q];
+    }
+    __syncwarp();
+    for (int ci = c0; ci < c1; ci++) {
+        const int ch = F.child[ci];
+        const T *Fc = fronts + F.front_off[ch];
+        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
+        const int32_t *rel = F.rel + F.rel_off[ch];
+        const int myrel = lane < nu ? rel[lane] : 0;
+        // eight independent column loads in flight per step
+        for (int j0 = 0; j0 < nu; j0 += 8) {
+            T v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = j0 + k;
+                v[k] = (jj < nu && lane >= jj && lane < nu)
+                           ? Fc[(int64_t)(npc + jj) * fc + npc + lane] : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = j0 + k;
+                const int rj = __shfl_sync(0xffffffffu, myrel, jj & 31);
+                if (jj < nu && lane >= jj && lane < nu) tile[myrel][rj] += v[k];
+            }
+        }
+        __syncwarp();
+    }
+    for (int c = 0; c < np; c++) {
+        const T d = tile[c][c];
+        if (lane == 0) {
+            const double dd = (double)d;
+            if (dd > pivot_tol) n_pos++;
+            else if (dd < -pivot_tol) n_neg++;
+            else n_zero++;
+        }
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        T l = (T)0;
+        if (lane > c && lane < f) {
+            l = tile[lane][c] * dinv;
+            tile[lane][c] = l;
+        }
+        __syncwarp();
+        for (int j = c + 1; j < f; j++) {
+            const T lj = __shfl_sync(0xffffffffu, l, j) * d;
+            if (lane >= j && lane < f) tile[lane][j] -= l * lj;
+        }
+        __syncwarp();
+    }
+    for (int j = 0; j < f; j++)
+        if (lane < f) Fr[(int64_t)j * f + lane] = tile[lane][j];
+}
+
 // Phase 1: small fronts, one warp per front.
 template <typename T>
 __global__ void __launch_bounds__(kWT) k_factor(DevFront F, T *__restrict__ fronts,
-                                                FactorStatus *st, int *queue, int *done, int epoch,
-                                                double pivot_tol, int spin_limit) {
+                                                FactorStatus *st, QueueView Q, double pivot_tol,
+                                                int spin_limit) {
+    __shared__ T tiles[kWT / 32][32][33];
     const int lane = threadIdx.x & 31;
+    T (*tile)[33] = tiles[threadIdx.x >> 5];
     int n_pos = 0, n_neg = 0, n_zero = 0;
     while (true) {
-        const int base = warp_grab_chunk(queue);
-        if (base >= F.n_small) break;
-        const int end = min(base + kChunk, F.n_small);
-        for (int task = base; task < end; task++) {
-            const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-            if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0) {
-                atomicExch(&st->error, 1);
-                atomicExch(&st->timeout_task, task);
-            }
+        const int task = warp_claim(Q, spin_limit, st, 1);
+        if (task < 0) break;
+        if (F.f[task] <= 32)
+            eliminate_front_tile<T>(F, fronts, task, lane, tile, pivot_tol, n_pos, n_neg, n_zero);
+        else
             eliminate_front<T, 32>(F, fronts, task, lane, pivot_tol, n_pos, n_neg, n_zero);
-            warp_publish(done, task, epoch);
-        }
+        __syncwarp();
+        const int par = F.parent[task];
+        if (lane == 0 && par >= 0 && par < F.n_small) complete_child(Q, par);
     }
     if (lane == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -226,41 +336,98 @@ __global__ void __launch_bounds__(kWT) k_factor(DevFront F, T *__restrict__ fron
 // Phase 2: large fronts near the tree tops (they carry the border rows), one
 // CTA per front.  Launched after phase 1, so small children are complete.
 constexpr int kBT = 256;
+constexpr int kBigPanelBytes = 96 * 1024;
+constexpr int kBigPanel = kBigPanelBytes / 8;   // panel elements that fit (FP64 bound)
+
+// Large front: zero + originals and extend-add in global memory, then the
+// np x f panel is copied to shared memory and eliminated there (rank-1
+// updates restricted to the panel columns, columns spread over warps), and
+// the trailing update U -= L21 D L21' makes one pass over the update block
+// with L read from shared memory.
+template <typename T>
+__device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, int task,
+                                    double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    extern __shared__ unsigned char big_smem[];
+    T *P = reinterpret_cast<T *>(big_smem);   // P[c * f + i]
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBT >> 5;
+    T *Fr = fronts + F.front_off[task];
+    const int f = F.f[task];
+    const int np = F.npiv[task];
+    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    for (int e = tid; e < f * f; e += kBT) Fr[e] = (T)0;
+    __syncthreads();
+    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += kBT)
+        Fr[F.orig_off[q]] = (T)F.ovals[q];
+    __syncthreads();
+    for (int ci = c0; ci < c1; ci++) {
+        const int ch = F.child[ci];
+        const T *Fc = fronts + F.front_off[ch];
+        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
+        const int32_t *rel = F.rel + F.rel_off[ch];
+        for (int jj = warp; jj < nu; jj += nw) {
+            const int64_t dst = (int64_t)rel[jj] * f;
+            const T *src = Fc + (int64_t)(npc + jj) * fc + npc;
+            for (int ii = jj + lane; ii < nu; ii += 32) Fr[dst + rel[ii]] += src[ii];
+        }
+        __syncthreads();
+    }
+    if (np == 0) return;
+    for (int e = tid; e < np * f; e += kBT) P[e] = Fr[e];
+    __syncthreads();
+    for (int c = 0; c < np; c++) {
+        T *colc = P + c * f;
+        const T d = colc[c];
+        if (tid == 0) {
+            const double dd = (double)d;
+            if (dd > pivot_tol) n_pos++;
+            else if (dd < -pivot_tol) n_neg++;
+            else n_zero++;
+        }
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        for (int i = c + 1 + tid; i < f; i += kBT) colc[i] *= dinv;
+        __syncthreads();
+        for (int j = c + 1 + warp; j < np; j += nw) {
+            const T lj = colc[j] * d;
+            T *colj = P + j * f;
+            for (int i = j + lane; i < f; i += 32) colj[i] -= colc[i] * lj;
+        }
+        __syncthreads();
+    }
+    for (int e = tid; e < np * f; e += kBT) Fr[e] = P[e];
+    const int m = f - np;
+    for (int jj = warp; jj < m; jj += nw) {
+        const int j = np + jj;
+        T *colj = Fr + (int64_t)j * f;
+        for (int i = j + lane; i < f; i += 32) {
+            T acc = 0;
+            for (int c = 0; c < np; c++) acc += P[c * f + i] * (P[c * f + j] * P[c * f + c]);
+            colj[i] -= acc;
+        }
+    }
+    __syncthreads();
+}
 template <typename T>
 __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ fronts,
-                                                    FactorStatus *st, int *queue, int *done,
-                                                    int epoch, double pivot_tol, int spin_limit) {
-    __shared__ int s_task, s_fail;
+                                                    FactorStatus *st, QueueView Q,
+                                                    double pivot_tol, int spin_limit) {
+    __shared__ int s_task;
     int n_pos = 0, n_neg = 0, n_zero = 0;
     while (true) {
         if (threadIdx.x == 0) {
-            s_task = F.n_small + atomicAdd(queue, 1);
-            s_fail = 0;
+            s_task = claim_slot(Q, spin_limit);
+            if (s_task == -2) atomicExch(&st->error, 1);
         }
         __syncthreads();
         const int task = s_task;
-        if (task >= F.n_tasks) break;
-        const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-        for (int ci = c0 + threadIdx.x; ci < c1; ci += blockDim.x) {
-            const int d = F.child[ci];
-            int spins = 0;
-            while (ld_acquire(&done[d]) != epoch) {
-                if (++spins > spin_limit) {
-                    s_fail = 1;
-                    break;
-                }
-                __nanosleep(64);
-            }
-        }
         __syncthreads();
-        if (s_fail && threadIdx.x == 0) {
-            atomicExch(&st->error, 1);
-            atomicExch(&st->timeout_task, task);
-        }
-        eliminate_front<T, kBT>(F, fronts, task, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
-        __threadfence();
-        __syncthreads();
-        if (threadIdx.x == 0) st_release(&done[task], epoch);
+        if (task < 0) break;
+        if ((int64_t)F.f[task] * F.npiv[task] <= kBigPanel)
+            eliminate_front_big<T>(F, fronts, task, pivot_tol, n_pos, n_neg, n_zero);
+        else
+            eliminate_front<T, kBT>(F, fronts, task, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
+        __syncthreads();   // orders every thread's writes before the release below
+        const int par = F.parent[task];
+        if (threadIdx.x == 0 && par >= 0) complete_child(Q, par);
     }
     if (threadIdx.x == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -364,48 +531,94 @@ __global__ void k_dense_trailing(double *S, int n, int k0, int k1) {
 }
 
 // ---------------------------------------------------------------- solves
+// Forward sweep of one front: gather D b on its pivot rows plus the
+// children's update vectors, then y = D^-1 L^-1 (.) on the pivot rows and
+// the update vector -L21 y for the parent on the others.
 template <typename T>
-__global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restrict__ fronts,
-                                                   T *__restrict__ vec, const double *__restrict__ b,
-                                                   const double *__restrict__ scale, int *queue,
-                                                   int *done, int epoch, FactorStatus *st,
-                                                   int spin_limit) {
-    const int lane = threadIdx.x & 31;
-    for (int base = warp_grab_chunk(queue); base < F.n_tasks; base = warp_grab_chunk(queue))
-    for (int task = base; task < min(base + kChunk, F.n_tasks); task++) {
-        const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-        if (!warp_wait(F.child + c0, c1 - c0, done, epoch, spin_limit) && lane == 0)
-            atomicExch(&st->error, 2);
-        const int f = F.f[task], np = F.npiv[task];
-        const T *L = fronts + F.front_off[task];
-        T *v = vec + F.vec_off[task];
-        const int64_t *rows = F.rows + F.rows_off[task];
-        for (int i = lane; i < f; i += 32) {
-            T x = (T)0;
-            if (i < np) {
-                const int64_t r = rows[i];
-                x = (T)(scale[r] * b[r]);
-            }
-            v[i] = x;
+__device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict__ fronts,
+                                          T *__restrict__ vec, const double *__restrict__ b,
+                                          const double *__restrict__ scale, int task, int lane,
+                                          T *sv) {
+    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    const int f = F.f[task], np = F.npiv[task];
+    const T *L = fronts + F.front_off[task];
+    T *v = vec + F.vec_off[task];
+    const int64_t *rows = F.rows + F.rows_off[task];
+    if (f <= 32) {
+        // lane i owns row i; its row of the L panel is prefetched into registers
+        T Lr[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) Lr[c] = (c < np && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
+        const T dl = lane < np ? L[(int64_t)lane * f + lane] : (T)1;
+        T vi = (T)0;
+        if (lane < np) {
+            const int64_t r = rows[lane];
+            vi = (T)(scale[r] * b[r]);
         }
+        sv[lane] = vi;
         __syncwarp();
         for (int ci = c0; ci < c1; ci++) {
             const int ch = F.child[ci];
-            const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-            const T *vc = vec + F.vec_off[ch] + npc;
-            const int32_t *rel = F.rel + F.rel_off[ch];
-            for (int i = lane; i < nu; i += 32) v[rel[i]] += vc[i];
+            const int nu = F.f[ch] - F.npiv[ch];
+            if (lane < nu) sv[F.rel[F.rel_off[ch] + lane]] += vec[F.vec_off[ch] + F.npiv[ch] + lane];
             __syncwarp();
         }
-        for (int c = 0; c < np; c++) {
-            const T xc = v[c];
-            const T *col = L + (int64_t)c * f;
-            for (int i = c + 1 + lane; i < f; i += 32) v[i] -= col[i] * xc;
-            __syncwarp();
+        vi = sv[lane];
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+            if (c < np) {
+                const T xc = __shfl_sync(0xffffffffu, vi, c);
+                if (lane > c) vi -= Lr[c] * xc;
+            }
         }
-        // diagonal: y = D^-1 (L^-1 b) on the pivot rows
-        for (int c = lane; c < np; c += 32) v[c] = v[c] / L[(int64_t)c * f + c];
-        warp_publish(done, task, epoch);
+        if (lane < np) vi /= dl;
+        if (lane < f) v[lane] = vi;
+        return;
+    }
+    for (int i = lane; i < f; i += 32) {
+        T x = (T)0;
+        if (i < np) {
+            const int64_t r = rows[i];
+            x = (T)(scale[r] * b[r]);
+        }
+        v[i] = x;
+    }
+    __syncwarp();
+    for (int ci = c0; ci < c1; ci++) {
+        const int ch = F.child[ci];
+        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
+        const T *vc = vec + F.vec_off[ch] + npc;
+        const int32_t *rel = F.rel + F.rel_off[ch];
+        for (int i = lane; i < nu; i += 32) v[rel[i]] += vc[i];
+        __syncwarp();
+    }
+    for (int c = 0; c < np; c++) {
+        const T xc = v[c];
+        const T *col = L + (int64_t)c * f;
+        for (int i = c + 1 + lane; i < f; i += 32) v[i] -= col[i] * xc;
+        __syncwarp();
+    }
+    // diagonal: y = D^-1 (L^-1 b) on the pivot rows
+    for (int c = lane; c < np; c += 32) v[c] = v[c] / L[(int64_t)c * f + c];
+}
+
+// bottom-up over every task (border fronts included: they collect the
+// block's contribution to the border right-hand side)
+template <typename T>
+__global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restrict__ fronts,
+                                                   T *__restrict__ vec, const double *__restrict__ b,
+                                                   const double *__restrict__ scale, QueueView Q,
+                                                   FactorStatus *st, int spin_limit) {
+    __shared__ T sv_all[kWT / 32][32];
+    const int lane = threadIdx.x & 31;
+    T *sv = sv_all[threadIdx.x >> 5];
+    while (true) {
+        const int task = warp_claim(Q, spin_limit, st, 2);
+        if (task < 0) break;
+        fwd_front<T>(F, fronts, vec, b, scale, task, lane, sv);
+        __syncwarp();
+        const int par = F.parent[task];
+        if (lane == 0 && par >= 0) complete_child(Q, par);
     }
 }
 
@@ -451,45 +664,71 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
     }
 }
 
+// Backward sweep of one (non-border) front: its update rows hold the final
+// solution of ancestors and border, the pivot rows solve L11' x = y - L21' x2.
+template <typename T>
+__device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict__ fronts,
+                                          T *__restrict__ vec, const double *__restrict__ scale,
+                                          double *__restrict__ x, int task, int lane) {
+    const int f = F.f[task], np = F.npiv[task];
+    const T *L = fronts + F.front_off[task];
+    T *v = vec + F.vec_off[task];
+    const int64_t *rows = F.rows + F.rows_off[task];
+    if (f <= 32) {
+        T Lr[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++) Lr[c] = (c < np && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
+        T vi = (T)0;
+        int64_t r = 0;
+        if (lane < f) r = rows[lane];
+        if (lane < np)
+            vi = v[lane];
+        else if (lane < f)
+            vi = (T)(x[r] / scale[r]);
+#pragma unroll
+        for (int c = 31; c >= 0; c--) {
+            if (c < np) {
+                T p = (lane > c && lane < f) ? Lr[c] * vi : (T)0;
+                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                if (lane == c) vi -= p;
+            }
+        }
+        if (lane < np) x[r] = scale[r] * (double)vi;
+        return;
+    }
+    for (int i = np + lane; i < f; i += 32) {
+        const int64_t r = rows[i];
+        v[i] = (T)(x[r] / scale[r]);
+    }
+    __syncwarp();
+    for (int c = np - 1; c >= 0; c--) {
+        const T *col = L + (int64_t)c * f;
+        T acc = 0;
+        for (int i = c + 1 + lane; i < f; i += 32) acc += col[i] * v[i];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) v[c] -= acc;
+        __syncwarp();
+    }
+    for (int c = lane; c < np; c += 32) {
+        const int64_t r = rows[c];
+        x[r] = scale[r] * (double)v[c];
+    }
+}
+
+// top-down from the block roots (the border solution is already in x); a
+// finished front pushes its children
 template <typename T>
 __global__ void __launch_bounds__(kWT) k_solve_bwd(DevFront F, const T *__restrict__ fronts,
                                                    T *__restrict__ vec, const double *__restrict__ scale,
-                                                   double *__restrict__ x, int *queue, int *done,
-                                                   int epoch, FactorStatus *st, int spin_limit) {
+                                                   double *__restrict__ x, QueueView Q,
+                                                   FactorStatus *st, int spin_limit) {
     const int lane = threadIdx.x & 31;
-    for (int base = warp_grab_chunk(queue); base < F.n_tasks; base = warp_grab_chunk(queue))
-    for (int q = base; q < min(base + kChunk, F.n_tasks); q++) {
-        const int task = F.n_tasks - 1 - q;
-        if (F.is_border[task]) {
-            warp_publish(done, task, epoch);
-            continue;
-        }
-        const int par = F.parent[task];
-        if (par >= 0 && !warp_wait(&F.parent[task], 1, done, epoch, spin_limit) && lane == 0)
-            atomicExch(&st->error, 3);
-        const int f = F.f[task], np = F.npiv[task];
-        const T *L = fronts + F.front_off[task];
-        T *v = vec + F.vec_off[task];
-        const int64_t *rows = F.rows + F.rows_off[task];
-        // update rows: final (scaled) solution of ancestors and border
-        for (int i = np + lane; i < f; i += 32) {
-            const int64_t r = rows[i];
-            v[i] = (T)(x[r] / scale[r]);
-        }
+    while (true) {
+        const int task = warp_claim(Q, spin_limit, st, 3);
+        if (task < 0) break;
+        bwd_front<T>(F, fronts, vec, scale, x, task, lane);
         __syncwarp();
-        for (int c = np - 1; c >= 0; c--) {
-            const T *col = L + (int64_t)c * f;
-            T acc = 0;
-            for (int i = c + 1 + lane; i < f; i += 32) acc += col[i] * v[i];
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) v[c] -= acc;
-            __syncwarp();
-        }
-        for (int c = lane; c < np; c += 32) {
-            const int64_t r = rows[c];
-            x[r] = scale[r] * (double)v[c];
-        }
-        warp_publish(done, task, epoch);
+        push_children(Q, F, task);
     }
 }
 
@@ -519,6 +758,17 @@ __global__ void k_ruiz_long(int64_t n_long, const int64_t *__restrict__ rows,
         mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
     for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
     if (lane == 0) s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
+}
+
+// scaled original entries of every front, in task order
+__global__ void k_orig_vals(int64_t n_orig, const int64_t *__restrict__ nz,
+                            const int32_t *__restrict__ row, const int64_t *__restrict__ col,
+                            const double *__restrict__ scale, const double *__restrict__ kval,
+                            double *__restrict__ ovals) {
+    int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n_orig) return;
+    const int64_t q = nz[p];
+    ovals[p] = scale[row[q]] * kval[q] * scale[col[q]];
 }
 
 __global__ void k_fill(int64_t n, double v, double *x) {
@@ -559,34 +809,49 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     if (a != scale) cudaMemcpyAsync(scale, a, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
 }
 
-template <typename T>
-void launch_front_init(const DevFront &F, const int32_t *row, const int64_t *col,
-                       const double *scale, const double *kval, T *fronts, cudaStream_t s) {
-    cudaMemsetAsync(fronts, 0, sizeof(T) * F.front_elems, s);
+void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s) {
     const int t = 256;
-    k_front_scatter<T><<<(int)((F.nnz + t - 1) / t), t, 0, s>>>(F.nnz, F.scatter, row, col, scale,
-                                                               kval, fronts);
+    if (F.n_orig > 0)
+        k_orig_vals<<<(int)((F.n_orig + t - 1) / t), t, 0, s>>>(F.n_orig, F.orig_nz, F.kkt_row,
+                                                               F.kkt_col, F.scale, F.kval, ovals);
+}
+
+void launch_queue_reset(const DevFront &F, const int32_t *init_a, int n_a, const int32_t *init_b,
+                        int n_b, const int32_t *pend, cudaStream_t s) {
+    const int t = 256;
+    const int n = F.n_tasks > 0 ? F.n_tasks : 1;
+    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_tasks, F.q_slots_a, init_a, n_a, F.q_slots_b,
+                                                init_b, n_b, F.q_pending, pend, F.q_ctr);
 }
 
 template <typename T>
-void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, int *queue, int *done, int epoch,
-                   double pivot_tol, int spin_limit, cudaStream_t s) {
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
+void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_tol,
+                   int spin_limit, cudaStream_t s) {
+    // queue a: phase 1 (small fronts), queue b: phase 2 (large fronts)
+    launch_queue_reset(F, F.init_small, F.n_init_small, F.init_big, F.n_init_big, F.pend_factor, s);
     int grid = warp_grid();
     const int need = (F.n_small + kWT / 32 - 1) / (kWT / 32);
     if (grid > need) grid = need;
     if (F.n_small > 0)
-        k_factor<T><<<grid, kWT, 0, s>>>(F, fronts, st, queue, done, epoch, pivot_tol, spin_limit);
+        k_factor<T><<<grid, kWT, 0, s>>>(F, fronts, st, queue_a(F, F.n_small), pivot_tol,
+                                         spin_limit);
     const int nbig = F.n_tasks - F.n_small;
     if (nbig > 0) {
-        cudaMemsetAsync(queue, 0, sizeof(int), s);
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        int g2 = sms * (2048 / kBT);
+        static bool attr = false;
+        if (!attr) {
+            cudaFuncSetAttribute(k_factor_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kBigPanelBytes);
+            cudaFuncSetAttribute(k_factor_big<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 kBigPanelBytes);
+            attr = true;
+        }
+        int g2 = sms * 2;
         if (g2 > nbig) g2 = nbig;
-        k_factor_big<T><<<g2, kBT, 0, s>>>(F, fronts, st, queue, done, epoch, pivot_tol,
-                                           spin_limit);
+        k_factor_big<T><<<g2, kBT, kBigPanelBytes, s>>>(F, fronts, st, queue_b(F, nbig), pivot_tol,
+                                                        spin_limit);
     }
 }
 
@@ -616,33 +881,33 @@ void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cud
 
 template <typename T>
 void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
-                  const double *scale, const double *b, double *x, double *border_work, int *queue,
-                  int *done, int epoch, FactorStatus *st, int spin_limit, cudaStream_t s) {
+                  const double *scale, const double *b, double *x, double *border_work,
+                  FactorStatus *st, int spin_limit, cudaStream_t s) {
+    // queue a: forward sweep (all tasks), queue b: backward sweep (non-border)
+    launch_queue_reset(F, F.init_fwd, F.n_init_fwd, F.init_bwd, F.n_init_bwd, F.nchild, s);
     int grid = warp_grid();
     const int need = (F.n_tasks + kWT / 32 - 1) / (kWT / 32);
     if (grid > need) grid = need;
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
-    k_solve_fwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, b, scale, queue, done, epoch, st,
+    k_solve_fwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, b, scale, queue_a(F, F.n_tasks), st,
                                         spin_limit);
     {
         const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
         k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
             F, vec, S, nS, b, scale, x, border_work);
     }
-    cudaMemsetAsync(queue, 0, sizeof(int), s);
-    k_solve_bwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, scale, x, queue, done, epoch + 1, st,
-                                        spin_limit);
+    const int nb = F.n_tasks - F.n_blocks;
+    if (nb > 0)
+        k_solve_bwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, scale, x, queue_b(F, nb), st,
+                                            spin_limit);
 }
 
 #define INST(T)                                                                                    \
-    template void launch_front_init<T>(const DevFront &, const int32_t *, const int64_t *,       \
-                                       const double *, const double *, T *, cudaStream_t);       \
-    template void launch_factor<T>(const DevFront &, T *, FactorStatus *, int *, int *, int,     \
-                                   double, int, cudaStream_t);                                   \
+    template void launch_factor<T>(const DevFront &, T *, FactorStatus *, double, int,           \
+                                   cudaStream_t);                                                \
     template void launch_schur_sum<T>(const DevFront &, const T *, double *, cudaStream_t);      \
     template void launch_solve<T>(const DevFront &, const T *, T *, const double *, int,          \
-                                  const double *, const double *, double *, double *, int *,     \
-                                  int *, int, FactorStatus *, int, cudaStream_t);
+                                  const double *, const double *, double *, double *,             \
+                                  FactorStatus *, int, cudaStream_t);
 INST(float)
 INST(double)
 
