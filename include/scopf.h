@@ -109,6 +109,12 @@ typedef struct {
                                  analysis only (no device memory is touched); the
                                  device entry points then return
                                  SCOPF_ERR_INVALID_ARG */
+    int32_t cluster_max_tasks; /* a subtree of at most this many small fronts is
+                                 one work item of the factorization and solve
+                                 sweeps (run by one warp); >= 1 */
+    int32_t relax_max_front;  /* relaxed amalgamation: a supernode absorbs a child
+                                 while its front stays within this many rows
+                                 (0 = off) */
 } scopf_options;
 
 /* Sizes of the handle's problem. */
@@ -220,6 +226,23 @@ int scopf_newton_step(scopf_handle *h, const scopf_state *it, const double *lam_
  * enable = 1 starts (and zeroes) the timers, 0 stops them; ms_out[7] and
  * calls_out[7] (host, may be NULL) receive the accumulated totals. */
 int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls_out);
+
+/* Scheduler trace.  The factorization and the triangular sweeps run work
+ * items (a subtree of small fronts run by one warp, or one front) from ready
+ * queues.  enable = 1 allocates a device buffer and makes every later sweep
+ * record, per item, four uint64: the device clock (%globaltimer, ns) when
+ * its worker started to claim it, when it got it, when it finished, and the
+ * SM it ran on; 0 stops recording and frees the buffer.  Kinds: 0 forward
+ * sweep, 1 backward sweep, 2 factorization phase 1 (small fronts), 3 phase
+ * 2 (large fronts); each keeps the record of its last run (zeros for items
+ * that did not run).  scopf_trace_read copies kind `kind` to out (host,
+ * 4 * n_items uint64).  scopf_trace_items describes the items: out (host,
+ * 6 * n_items int32) = fronts in the item, parent item (-1 none), 1 if
+ * phase 1, largest front (rows), total pivots, block; returns n_items
+ * through *n_items. */
+int scopf_trace(scopf_handle *h, int32_t enable);
+int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out);
+int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out);
 
 /* Dense pivot-free LDL^T factorization and solve of a symmetric n x n
  * matrix: the factor of the first-stage Schur complement (border block) of

@@ -30,7 +30,20 @@ twice (here and in the CUDA library) and compared bit for bit:
 4. Postorder of the tree (children visited in increasing node id).
 5. Fundamental supernodes, then relaxed amalgamation of only-child chains
    while the merged supernode has at most ``relax_max_nodes`` nodes.
-6. Rows: nodes in postorder, each node's rows in the order of step 1, then
+6. Relaxed amalgamation bounded by front size: supernodes in postorder
+   (children first); each considers its children in increasing supernode
+   index and absorbs child c when its front (pivot rows plus update rows)
+   would stay within ``relax_max_front`` rows after adding c's pivot rows.
+   c's update rows lie inside the parent's front, so the merged front is the
+   parent's front plus c's pivot rows, and explicit zeros fill the rest of
+   c's columns.  Only direct children are candidates: a grandchild that did
+   not fit its own parent cannot fit the larger merged front.  The merged
+   supernode eliminates its absorbed children (in increasing index, each in
+   its own member order) and then its own nodes.
+7. Postorder of the final supernode tree (roots and children in increasing
+   supernode index); the node order is each supernode's member list in turn.
+   Reordering independent subtrees changes no fill.
+8. Rows: nodes in that order, each node's rows in the order of step 1, then
    the border rows.
 
 Parity: integer, compared exactly with the CUDA implementation; pinned by
@@ -160,7 +173,7 @@ def min_degree(adj, n_block):
 class Symbolic:
     """Symbolic analysis of one block (see the module docstring)."""
 
-    def __init__(self, G: BlockGraph, relax_max_nodes: int = 8):
+    def __init__(self, G: BlockGraph, relax_max_nodes: int = 8, relax_max_front: int = 32):
         order, struct = min_degree(G.adj, G.n_block)
         nb_nodes = G.n_block
         self.elim_order = order
@@ -221,22 +234,35 @@ class Symbolic:
                 starts.append(i)
                 size = 1
         starts.append(nb_nodes)
-        self.sn_start = np.array(starts, dtype=np.int64)      # in postorder positions
-        nsn = len(starts) - 1
+        self._supernode_links(np.array(starts, dtype=np.int64))
+        if relax_max_front > 0:
+            self._relax_by_front(G, relax_max_front)
+        # ---- row permutation (generic KKT indices in elimination order)
+        rows = [G.node_rows[v] for v in self.post.tolist()] + \
+               [G.node_rows[v] for v in range(nb_nodes, G.n_nodes)]
+        self.rows = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
+        self.n_block_rows = int(sum(len(G.node_rows[v]) for v in range(nb_nodes)))
+
+    def _supernode_links(self, sn_start):
+        """Update nodes (union of the members' structures minus the members,
+        sorted by position, border nodes last) and parent of every supernode
+        (the supernode of the first in-block update node; -2 = border)."""
+        nb_nodes = len(self.post)
+        self.sn_start = sn_start
+        nsn = len(sn_start) - 1
         sn_of = np.zeros(nb_nodes, dtype=np.int64)
         for s in range(nsn):
-            sn_of[self.sn_start[s]:self.sn_start[s + 1]] = s
+            sn_of[sn_start[s]:sn_start[s + 1]] = s
         self.sn_of_pos = sn_of
-        # update nodes of each supernode: union of member structs minus members,
-        # sorted by postorder position (border nodes last, in id order)
+        ppos = self.ppos
         upd = []
-        sn_parent = np.full(nsn, -1, dtype=np.int64)      # -2 = border supernode
+        sn_parent = np.full(nsn, -1, dtype=np.int64)
         for s in range(nsn):
-            members = self.post[self.sn_start[s]:self.sn_start[s + 1]]
+            members = self.post[sn_start[s]:sn_start[s + 1]]
             mset = set(members.tolist())
             u = set()
             for v in members.tolist():
-                u |= struct[v]
+                u |= self.struct[v]
             u -= mset
             ul = sorted(u, key=lambda x: ppos[x])
             upd.append(np.array(ul, dtype=np.int64))
@@ -248,11 +274,66 @@ class Symbolic:
         self.sn_update_nodes = upd
         self.sn_parent = sn_parent
         self.n_sn = nsn
-        # ---- row permutation (generic KKT indices in elimination order)
-        rows = [G.node_rows[v] for v in self.post.tolist()] + \
-               [G.node_rows[v] for v in range(nb_nodes, G.n_nodes)]
-        self.rows = np.concatenate(rows) if rows else np.zeros(0, dtype=np.int64)
-        self.n_block_rows = int(sum(len(G.node_rows[v]) for v in range(nb_nodes)))
+
+    def _relax_by_front(self, G, max_front):
+        """Step 6 and 7 of the module docstring."""
+        nsn = self.n_sn
+        nrow = [len(r) for r in G.node_rows]
+        members = [self.post[self.sn_start[s]:self.sn_start[s + 1]].tolist() for s in range(nsn)]
+        npiv = [sum(nrow[v] for v in members[s]) for s in range(nsn)]
+        front = [npiv[s] + sum(nrow[u] for u in self.sn_update_nodes[s].tolist()) for s in range(nsn)]
+        kids = [[] for _ in range(nsn)]
+        for s in range(nsn):
+            if self.sn_parent[s] >= 0:
+                kids[self.sn_parent[s]].append(s)
+        absorbed = [[] for _ in range(nsn)]
+        into = [-1] * nsn
+        for s in range(nsn):                       # children before parents
+            for c in kids[s]:                      # increasing index
+                if front[s] + npiv[c] <= max_front:
+                    absorbed[s].append(c)
+                    into[c] = s
+                    front[s] += npiv[c]
+                    npiv[s] += npiv[c]
+
+        def expand(s):
+            out = []
+            for c in absorbed[s]:
+                out += expand(c)
+            return out + members[s]
+
+        rep_ = list(range(nsn))
+        for s in range(nsn - 1, -1, -1):
+            if into[s] >= 0:
+                rep_[s] = rep_[into[s]]
+        tree_kids = [[] for _ in range(nsn)]
+        roots = []
+        for s in range(nsn):
+            if into[s] >= 0:
+                continue
+            if self.sn_parent[s] >= 0:
+                tree_kids[rep_[self.sn_parent[s]]].append(s)
+            else:
+                roots.append(s)
+        order = []
+        for r0 in roots:
+            stack = [(r0, 0)]
+            while stack:
+                v, i = stack.pop()
+                if i < len(tree_kids[v]):
+                    stack.append((v, i + 1))
+                    stack.append((tree_kids[v][i], 0))
+                else:
+                    order.append(v)
+        post, starts = [], [0]
+        for s in order:
+            post += expand(s)
+            starts.append(len(post))
+        nb_nodes = len(self.post)
+        assert len(post) == nb_nodes
+        self.post = np.array(post, dtype=np.int64)
+        self.ppos[self.post] = np.arange(nb_nodes)
+        self._supernode_links(np.array(starts, dtype=np.int64))
 
 
 def structural_kkt(model, seed: int = 12345):
@@ -277,13 +358,13 @@ def structural_kkt(model, seed: int = 12345):
     return S.kkt_matrix(st, prm, H, J, 0.5)
 
 
-def kkt_permutation(model, K=None, relax_max_nodes: int = 8):
+def kkt_permutation(model, K=None, relax_max_nodes: int = 8, relax_max_front: int = 32):
     """Global fill-reducing order of the reduced KKT matrix: each block's rows
     in its symbolic order, blocks 0..K in turn, then the border rows.  The
     node graphs come from the structural pattern (``structural_kkt``)."""
     Ks = structural_kkt(model)
     graphs = attach_adjacency(block_graphs(model), Ks)
-    syms = [Symbolic(G, relax_max_nodes) for G in graphs]
+    syms = [Symbolic(G, relax_max_nodes, relax_max_front) for G in graphs]
     parts = [S.rows[:S.n_block_rows] for S in syms]
     border = np.arange(model.border0, model.border0 + model.nborder, dtype=np.int64)
     perm = np.concatenate(parts + [border])

@@ -60,7 +60,8 @@ _OPT_DOUBLES = ["tol", "mu_min", "mu_init", "kappa_eps", "kappa_mu", "theta_mu",
                 "s_theta", "s_phi", "eta_phi", "gamma_alpha", "rho_init", "rho_max", "eta_init",
                 "omega_init", "refine_tol", "pivot_tol"]
 _OPT_INTS = ["max_backtrack", "max_outer", "max_inner", "max_refine", "precision",
-             "relax_max_nodes", "verbose", "spin_limit", "host_only"]
+             "relax_max_nodes", "verbose", "spin_limit", "host_only", "cluster_max_tasks",
+             "relax_max_front"]
 
 
 class Options(ctypes.Structure):
@@ -142,6 +143,9 @@ def lib():
             "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
+            "scopf_trace": (c_i32, [H, c_i32]),
+            "scopf_trace_read": (c_i32, [H, c_i32, ctypes.POINTER(ctypes.c_uint64)]),
+            "scopf_trace_items": (c_i32, [H, P_i32, P_i32]),
             "scopf_dense_ldlt_solve": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32, ctypes.c_void_p]),
             "scopf_dense_ldlt_solve_noalloc": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32,
                                                        ctypes.c_void_p]),
@@ -394,6 +398,28 @@ class SCOPF:
         calls = np.zeros(7, dtype=np.int32)
         _check("scopf_timing", lib().scopf_timing(self.h, int(enable), _hp(ms, c_dbl), _hp(calls, c_i32)))
         return {k: (float(ms[i]), int(calls[i])) for i, k in enumerate(self.PHASES)}
+
+    def scopf_trace(self, enable: bool):
+        """Start (True) or stop the scheduler trace (see scopf.h)."""
+        _check("scopf_trace", lib().scopf_trace(self.h, 1 if enable else 0))
+
+    def scopf_trace_read(self, kind: int):
+        """(n_items, 4) uint64: claim start, claim end, finish (ns), SM."""
+        n = c_i32()
+        _check("scopf_trace_items", lib().scopf_trace_items(self.h, ctypes.byref(n), None))
+        out = np.zeros((n.value, 4), dtype=np.uint64)
+        _check("scopf_trace_read", lib().scopf_trace_read(
+            self.h, kind, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))))
+        return out
+
+    def scopf_trace_items(self):
+        """(n_items, 6) int32: fronts, parent item, phase-1 flag, largest
+        front, pivots, block."""
+        n = c_i32()
+        _check("scopf_trace_items", lib().scopf_trace_items(self.h, ctypes.byref(n), None))
+        out = np.zeros((n.value, 6), dtype=np.int32)
+        _check("scopf_trace_items", lib().scopf_trace_items(self.h, ctypes.byref(n), _hp(out, c_i32)))
+        return out
 
     def ncl_params_tensors(self):
         """Copies of the NCL multiplier estimates (lam_n, nu0_n) as torch tensors, and rho."""

@@ -201,7 +201,25 @@ int setup_device(scopf_handle *h) {
     TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->S));
     TRY(alloc(h, (size_t)M.nborder + 1, &h->border_work));
     {
-        const size_t nt = HF.n_tasks > 0 ? (size_t)HF.n_tasks : 1;
+        const size_t nt = HF.n_items > 0 ? (size_t)HF.n_items : 1;
+        F.n_items = HF.n_items;
+        F.max_f = 32;
+        for (int t = 0; t < HF.n_tasks; t++) F.max_f = std::max(F.max_f, (int)HF.f[t]);
+        F.n_items_small = HF.n_items_small;
+        TRY(upload(h, HF.item_ptr, &F.item_ptr));
+        {
+            const int32_t *tr = nullptr, *cr = nullptr;
+            TRY(upload(h, HF.task_rec, &tr));
+            F.task_rec = reinterpret_cast<const int4 *>(tr);
+            std::vector<int32_t> crv = HF.child_rec;
+            if (crv.empty()) crv.assign(8, 0);
+            TRY(upload(h, crv, &cr));
+            F.child_rec = reinterpret_cast<const int4 *>(cr);
+        }
+        TRY(upload(h, HF.item_parent, &F.item_parent));
+        TRY(upload(h, HF.item_child_ptr, &F.item_child_ptr));
+        TRY(upload(h, HF.item_child, &F.item_child));
+        TRY(upload(h, HF.item_cont, &F.item_cont));
         TRY(alloc(h, nt, &F.q_slots_a));
         TRY(alloc(h, nt, &F.q_slots_b));
         TRY(alloc(h, nt, &F.q_pending));
@@ -291,6 +309,8 @@ void scopf_default_options(scopf_options *o) {
     o->verbose = 0;
     o->spin_limit = 1 << 24;
     o->host_only = 0;
+    o->cluster_max_tasks = 8;
+    o->relax_max_front = 32;
 }
 
 const char *scopf_strerror(int s) {
@@ -330,14 +350,19 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
     }
     h->syms.resize(h->M.blocks.size());
     for (size_t k = 0; k < h->M.blocks.size(); k++) {
-        err = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes, h->syms[k]);
+        err = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes, h->opt.relax_max_front,
+                             h->syms[k]);
         if (!err.empty()) {
             if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
             delete h;
             return SCOPF_ERR_INVALID_ARG;
         }
     }
-    err = build_fronts(h->M, h->syms, h->HF);
+    if (h->opt.cluster_max_tasks < 1) {
+        delete h;
+        return SCOPF_ERR_INVALID_ARG;
+    }
+    err = build_fronts(h->M, h->syms, h->opt.cluster_max_tasks, h->HF);
     if (!err.empty()) {
         if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
         delete h;
@@ -358,6 +383,7 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
 void scopf_destroy(scopf_handle *h) {
     if (!h) return;
     for (void *p : h->allocations) cudaFree(p);
+    if (h->trace) cudaFree(h->trace);
     delete h;
 }
 
@@ -443,6 +469,59 @@ int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n, co
     if (r != SCOPF_OK) return r;
     CK(cudaStreamSynchronize(h->stream));
     h->timer.collect();
+    return SCOPF_OK;
+}
+
+int scopf_trace(scopf_handle *h, int32_t enable) {
+    if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
+    CK(cudaStreamSynchronize(h->stream));
+    if (h->trace) {
+        cudaFree(h->trace);
+        h->trace = nullptr;
+    }
+    if (enable) {
+        const size_t bytes = sizeof(unsigned long long) * 16 * (size_t)std::max(1, h->HF.n_items);
+        cudaError_t e = cudaMalloc(&h->trace, bytes);
+        if (e != cudaSuccess) {
+            h->trace = nullptr;
+            h->last_error = cudaGetErrorString(e);
+            return e == cudaErrorMemoryAllocation ? SCOPF_ERR_OOM : SCOPF_ERR_CUDA;
+        }
+        CK(cudaMemset(h->trace, 0, bytes));
+    }
+    h->df.trace = h->trace;
+    return SCOPF_OK;
+}
+
+int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out) {
+    if (!h || h->host_only || !h->trace || kind < 0 || kind > 3 || !out)
+        return SCOPF_ERR_INVALID_ARG;
+    const size_t n = 4 * (size_t)h->HF.n_items;
+    CK(cudaStreamSynchronize(h->stream));
+    CK(cudaMemcpy(out, h->trace + (size_t)kind * n, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
+    return SCOPF_OK;
+}
+
+int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out) {
+    if (!h || !n_items) return SCOPF_ERR_INVALID_ARG;
+    const HostFronts &HF = h->HF;
+    *n_items = HF.n_items;
+    if (!out) return SCOPF_OK;
+    for (int i = 0; i < HF.n_items; i++) {
+        const int t0 = HF.item_ptr[i], t1 = HF.item_ptr[i + 1];
+        int npv = 0, fmax = 0;
+        for (int t = t0; t < t1; t++) {
+            npv += HF.npiv[t];
+            fmax = std::max(fmax, (int)HF.f[t]);
+        }
+        int32_t *o = out + 6 * (size_t)i;
+        o[0] = t1 - t0;
+        o[1] = HF.item_parent[i];
+        o[2] = i < HF.n_items_small ? 1 : 0;
+        o[3] = fmax;
+        o[4] = npv;
+        o[5] = HF.block[t0];
+    }
     return SCOPF_OK;
 }
 

@@ -3,13 +3,15 @@
 // child-to-parent index maps of the extend-add, the scatter map of the
 // original KKT entries into the fronts, tree levels and the task order.
 #include <algorithm>
+#include <climits>
 #include <numeric>
 
 #include "fronts_host.h"
 
 namespace scopf {
 
-std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms, HostFronts &H) {
+std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms, int cluster_cap,
+                         HostFronts &H) {
     const int nblk = (int)M.blocks.size();
     const int nbor = (int)M.nborder;
     H = HostFronts();
@@ -89,11 +91,6 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         }
     }
     const int nt = (int)sn.size();
-    // levels (children have smaller task ids within a block: postorder)
-    std::vector<int> level(nt, 0);
-    for (int t = 0; t < nt; t++)
-        if (sn[t].parent_task >= 0)
-            level[sn[t].parent_task] = std::max(level[sn[t].parent_task], level[t] + 1);
     // large fronts (f > kBigFront) and everything above them form the second
     // factorization phase (one CTA per front); the rest is one warp per front
     const int kBigFront = 64;
@@ -102,20 +99,67 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         if (sn[t].f > kBigFront || sn[t].border) big[t] = 1;
     for (int t = 0; t < nt; t++)   // children precede parents within a block
         if (big[t] && sn[t].parent_task >= 0) big[sn[t].parent_task] = 1;
-    // task order: (phase, level, block, local)
+    // Work items.  A maximal subtree of at most `cluster_cap` small fronts is
+    // one item (a warp runs it in postorder with no scheduling in between);
+    // the small fronts above such subtrees and every large front are items of
+    // their own.  Small fronts have only small descendants, and a subtree
+    // occupies the contiguous postorder range that ends at its root.
+    // Only fronts of at most 32 rows (one warp tile) join subtrees: a larger
+    // front costs as much as a whole small subtree, and a subtree runs
+    // sequentially.
+    std::vector<int> sz(nt, 1);
+    std::vector<char> clus(nt, 0);   // the whole subtree is tile-sized
+    for (int t = 0; t < nt; t++) clus[t] = !big[t] && sn[t].f <= 32;
+    for (int t = 0; t < nt; t++) {
+        const int p = sn[t].parent_task;
+        if (p < 0) continue;
+        if (!clus[t]) clus[p] = 0;
+        if (!big[t] && !big[p]) sz[p] += sz[t];
+    }
+    std::vector<int> item_root(nt, -1);   // root task of each task's item
+    for (int t = nt - 1; t >= 0; t--) {
+        const int p = sn[t].parent_task;
+        if (!clus[t] || sz[t] > cluster_cap)
+            item_root[t] = t;
+        else if (p >= 0 && clus[p] && sz[p] <= cluster_cap)
+            item_root[t] = item_root[p];
+        else
+            item_root[t] = t;
+    }
+    // item heights (clusters and leaves 0) order the items: (phase, height,
+    // block, root); tasks of an item follow in postorder
+    std::vector<int> level(nt, 0);
+    for (int t = 0; t < nt; t++) {
+        const int p = sn[t].parent_task;
+        if (item_root[t] == t && p >= 0)
+            level[item_root[p]] = std::max(level[item_root[p]], level[t] + 1);
+    }
     std::vector<int> order(nt);
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
-        if (big[a] != big[b]) return big[a] < big[b];
-        if (level[a] != level[b]) return level[a] < level[b];
-        if (sn[a].block != sn[b].block) return sn[a].block < sn[b].block;
-        return sn[a].local < sn[b].local;
+        const int ra = item_root[a], rb = item_root[b];
+        if (big[ra] != big[rb]) return big[ra] < big[rb];
+        if (level[ra] != level[rb]) return level[ra] < level[rb];
+        if (sn[ra].block != sn[rb].block) return sn[ra].block < sn[rb].block;
+        if (ra != rb) return ra < rb;
+        return a < b;
     });
+    for (int t = 0; t < nt; t++) level[t] = level[item_root[t]];
     std::vector<int> tid(nt);
     for (int i = 0; i < nt; i++) tid[order[i]] = i;
     H.n_tasks = nt;
     H.n_small = 0;
     for (int t = 0; t < nt; t++) H.n_small += big[t] ? 0 : 1;
+    // items as contiguous task ranges
+    H.item_ptr.clear();
+    H.item_of_task.assign(nt, 0);
+    for (int i = 0; i < nt; i++) {
+        if (i == 0 || item_root[order[i]] != item_root[order[i - 1]]) H.item_ptr.push_back(i);
+        H.item_of_task[i] = (int32_t)H.item_ptr.size() - 1;
+    }
+    H.item_ptr.push_back(nt);
+    H.n_items = (int)H.item_ptr.size() - 1;
+    H.n_items_small = H.n_small > 0 ? H.item_of_task[H.n_small - 1] + 1 : 0;
     H.front_off.resize(nt);
     H.vec_off.resize(nt);
     H.f.resize(nt);
@@ -168,23 +212,74 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         H.child_ptr[i + 1] = H.child_ptr[i] + (int)ch[i].size();
         for (int c : ch[i]) H.child.push_back(c);
     }
-    // ready-queue seeds.  Factorization: phase 1 (small fronts) starts from
-    // its leaves; phase 2 counts only its own children (the small ones are
-    // complete when it starts).  Forward solve: all leaves.  Backward solve:
-    // the non-border tasks whose parent is a border front (the block roots).
-    H.nchild.assign(nt, 0);
-    H.pend_factor.assign(nt, 0);
-    for (int i = 0; i < nt; i++) {
-        H.nchild[i] = (int)ch[i].size();
-        for (int c : ch[i])
-            if (!(i >= H.n_small && c < H.n_small)) H.pend_factor[i]++;
+    // Ready-queue seeds, on items.  Factorization: phase 1 (small items)
+    // starts from its leaves; phase 2 (large fronts, one item each) counts
+    // only its own children (the small ones are complete when it starts).
+    // Forward solve: all leaf items.  Backward solve: the items whose parent
+    // is a border front (block roots); a finished item pushes its child items.
+    const int ni = H.n_items;
+    H.item_parent.assign(ni, -1);
+    H.item_is_border.assign(ni, 0);
+    std::vector<std::vector<int>> ich(ni);
+    for (int i = 0; i < ni; i++) {
+        const int root = H.item_ptr[i + 1] - 1;
+        const int pt = H.parent[root];
+        H.item_is_border[i] = H.is_border[root];
+        if (pt >= 0) {
+            H.item_parent[i] = H.item_of_task[pt];
+            ich[H.item_parent[i]].push_back(i);
+        }
     }
-    for (int i = 0; i < nt; i++) {
+    H.item_child_ptr.assign(ni + 1, 0);
+    H.item_child.clear();
+    H.nchild.assign(ni, 0);
+    H.pend_factor.assign(ni, 0);
+    for (int i = 0; i < ni; i++) {
+        H.item_child_ptr[i + 1] = H.item_child_ptr[i] + (int)ich[i].size();
+        for (int c : ich[i]) H.item_child.push_back(c);
+        H.nchild[i] = (int)ich[i].size();
+        for (int c : ich[i])
+            if (!(i >= H.n_items_small && c < H.n_items_small)) H.pend_factor[i]++;
+    }
+    for (int i = 0; i < ni; i++) {
         if (H.nchild[i] == 0) H.init_fwd.push_back(i);
-        if (i < H.n_small && H.pend_factor[i] == 0) H.init_small.push_back(i);
-        if (i >= H.n_small && H.pend_factor[i] == 0) H.init_big.push_back(i);
-        if (!H.is_border[i] && (H.parent[i] < 0 || H.is_border[H.parent[i]])) H.init_bwd.push_back(i);
+        if (i < H.n_items_small && H.pend_factor[i] == 0) H.init_small.push_back(i);
+        if (i >= H.n_items_small && H.pend_factor[i] == 0) H.init_big.push_back(i);
+        const int pi = H.item_parent[i];
+        if (!H.item_is_border[i] && (pi < 0 || H.item_is_border[pi])) H.init_bwd.push_back(i);
     }
+    // Critical path first.  Estimated item cost (a few microseconds per
+    // front, more for wide ones); rank_up = cost of the path from the item
+    // to its root (bottom-up sweeps seed the longest paths first), rank_dn
+    // = the longest path below it (the backward sweep continues with the
+    // child that has the longest one).
+    std::vector<double> cost(ni, 0.0), rank_up(ni, 0.0), rank_dn(ni, 0.0);
+    for (int i = 0; i < ni; i++)
+        for (int t = H.item_ptr[i]; t < H.item_ptr[i + 1]; t++)
+            cost[i] += 4.0 + H.f[t] / 16.0 + (double)H.npiv[t] * H.f[t] / 256.0;
+    for (int i = ni - 1; i >= 0; i--)   // parents have larger ids
+        rank_up[i] = cost[i] + (H.item_parent[i] >= 0 ? rank_up[H.item_parent[i]] : 0.0);
+    for (int i = 0; i < ni; i++) {
+        double best = 0.0;
+        for (int c : ich[i]) best = std::max(best, rank_dn[c]);
+        rank_dn[i] = cost[i] + best;
+    }
+    H.item_cont.assign(ni, -1);
+    for (int i = 0; i < ni; i++) {
+        double best = -1.0;
+        for (int c : ich[i])
+            if (rank_dn[c] > best) {
+                best = rank_dn[c];
+                H.item_cont[i] = c;
+            }
+    }
+    auto by = [](const std::vector<double> &r) {
+        return [&r](int a, int b) { return r[a] != r[b] ? r[a] > r[b] : a < b; };
+    };
+    std::stable_sort(H.init_small.begin(), H.init_small.end(), by(rank_up));
+    std::stable_sort(H.init_big.begin(), H.init_big.end(), by(rank_up));
+    std::stable_sort(H.init_fwd.begin(), H.init_fwd.end(), by(rank_up));
+    std::stable_sort(H.init_bwd.begin(), H.init_bwd.end(), by(rank_dn));
     H.rel_off.assign(nt, 0);
     for (int i = 0; i < nt; i++) {
         H.rel_off[i] = (int64_t)H.rel.size();
@@ -256,6 +351,40 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     }
     H.max_level = 0;
     for (int i = 0; i < nt; i++) H.max_level = std::max(H.max_level, H.level[i]);
+    // packed per-task and per-child records: one or two 16-byte loads give
+    // everything a front needs to start
+    if (H.orig_ptr[nt] >= (int64_t)INT32_MAX || (int64_t)H.rel.size() >= (int64_t)INT32_MAX)
+        return "frontal structure too large for 32-bit record fields";
+    auto lo = [](int64_t v) { return (int32_t)(uint32_t)(uint64_t)v; };
+    auto hi = [](int64_t v) { return (int32_t)(uint32_t)((uint64_t)v >> 32); };
+    H.task_rec.assign(8 * (size_t)(nt + 1), 0);
+    for (int t = 0; t <= nt; t++) {
+        int32_t *r = &H.task_rec[8 * (size_t)t];
+        if (t < nt) {
+            r[0] = lo(H.front_off[t]);
+            r[1] = hi(H.front_off[t]);
+            r[2] = lo(H.vec_off[t]);
+            r[3] = hi(H.vec_off[t]);
+            r[4] = H.f[t] | (H.npiv[t] << 16);
+            r[7] = H.parent[t];
+        } else {
+            r[7] = -1;
+        }
+        r[5] = H.child_ptr[t];
+        r[6] = (int32_t)H.orig_ptr[t];
+    }
+    H.child_rec.assign(8 * H.child.size(), 0);
+    for (size_t q = 0; q < H.child.size(); q++) {
+        const int c = H.child[q];
+        int32_t *r = &H.child_rec[8 * q];
+        r[0] = lo(H.front_off[c]);
+        r[1] = hi(H.front_off[c]);
+        r[2] = lo(H.vec_off[c]);
+        r[3] = hi(H.vec_off[c]);
+        r[4] = (int32_t)H.rel_off[c];
+        r[5] = H.f[c] | (H.npiv[c] << 16);
+        r[6] = c;
+    }
     return "";
 }
 

@@ -125,6 +125,7 @@ struct scopf_handle {
     int n_factor = 0, n_refine = 0;
     bool force_fp64 = false;      // sticky FP64 fallback inside a solve
     bool skip_delta0 = false;     // delta_w = 0 factorizations showed zero pivots
+    unsigned long long *trace = nullptr;   // scheduler trace buffer (cudaMalloc'd)
     scopf::PhaseTimer timer;
     std::string last_error;
 };

@@ -114,6 +114,7 @@ struct BlockSymbolic {
     int64_t n_block_rows = 0;
 };
 
-std::string symbolic_block(const Model &M, int k, int relax_max_nodes, BlockSymbolic &S);
+std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax_max_front,
+                           BlockSymbolic &S);
 
 }  // namespace scopf

@@ -114,14 +114,30 @@ struct DevFront {
     const double *scale;          // Ruiz scaling
     const double *ovals;          // scaled original entries in task order (n_orig)
     int64_t n_orig;
-    // ready queues (two per run: factor phases 1/2, or forward/backward solve)
-    int *q_slots_a, *q_slots_b;   // n_tasks each: task ids in the order they became ready
+    // work items: item i is tasks [item_ptr[i], item_ptr[i+1]) in postorder
+    // (a subtree of small fronts, or one front); items [0, n_items_small)
+    // hold the small fronts
+    int n_items, n_items_small;
+    int max_f;                    // largest front (rows), at least 32
+    // packed records, 8 int32 each.  task_rec[t] (t <= n_tasks, the last a
+    // sentinel): front_off (2 words), vec_off (2), f | npiv << 16,
+    // first child slot, first original entry, parent.  child_rec[q] for
+    // child slot q: front_off (2), vec_off (2), rel_off, f | npiv << 16,
+    // task id, 0
+    const int4 *task_rec, *child_rec;
+    // scheduler trace (NULL = off): 4 kinds x n_items x 4 uint64
+    unsigned long long *trace;
+    const int32_t *item_ptr, *item_parent, *item_child_ptr, *item_child;
+    const int32_t *item_cont;     // backward sweep: child item run next by the same warp (-1 none)
+    // ready queues of items (two per run: factor phases 1/2, or forward and
+    // backward solve)
+    int *q_slots_a, *q_slots_b;   // n_items each: item ids in the order they became ready
     int *q_ctr;                   // [a.claim, a.fill, b.claim, b.fill]
-    int *q_pending;               // n_tasks: outstanding dependencies
+    int *q_pending;               // n_items: outstanding dependencies
     const int32_t *init_small, *init_big, *init_fwd, *init_bwd;
     int n_init_small, n_init_big, n_init_fwd, n_init_bwd;
     const int32_t *pend_factor;   // dependencies counted by the factorization phases
-    const int32_t *nchild;        // children per task
+    const int32_t *nchild;        // child items per item
 };
 // ovals[p] = scale[i] K_ij scale[j] for the p-th original front entry
 void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s);

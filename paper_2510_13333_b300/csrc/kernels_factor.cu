@@ -3,17 +3,18 @@
 // triangular solves (Section IV-B: the NCL term makes eq. (newtonsystem)
 // factorizable without numerical pivoting).
 //
-// Work decomposition.  Every supernode of every block is one task; tasks are
-// stored sorted by (tree level, block, supernode) and a persistent grid of
-// warps pulls them from a global counter.  Fronts of these power-grid KKT
-// blocks are small (about 14 rows on average, at most the 180-row border plus
-// a few pivots), so one warp owns one front: no block-wide barriers, only
-// warp shuffles and __syncwarp.  A task waits (bounded poll) until its
-// children have published their update blocks, extend-adds them into its
-// own dense front, eliminates its pivot columns and publishes.  Because tasks
-// are handed out in level order, every awaited child has already been taken
-// by a running warp, so the waits always end; a poll limit still turns a
-// broken dependency into an error status instead of a hang.
+// Work decomposition.  Every supernode of every block is one task (one dense
+// front).  Fronts of these power-grid KKT blocks are small (about 14 rows on
+// average, at most the 180-row border plus a few pivots), so one warp owns one
+// front: no block-wide barriers, only warp shuffles and __syncwarp.  Tasks are
+// grouped into work items -- a subtree of up to a few dozen small fronts,
+// which one warp runs in postorder with nothing but __syncwarp in between, or
+// a single front near the tree tops -- and items are scheduled by ready
+// queues: the last child item to finish pushes its parent (factorization,
+// forward sweep), a finished item pushes its children (backward sweep).  A
+// persistent grid of warps claims items in the order they became ready, so
+// no warp ever waits on a dependency; waits on a claimed, not yet filled
+// slot are bounded and turn into an error status instead of a hang.
 //
 // Fronts are dense, column-major, lower triangle used, one slot per
 // supernode (HBM is large enough to keep every front resident, so no stack
@@ -46,74 +47,107 @@ __device__ __forceinline__ void st_release(int *p, int v) {
 }
 
 // ---- ready queue ----------------------------------------------------------
-// Tasks become ready when their dependencies complete (bottom-up: the last
-// child pushes its parent; top-down: a parent pushes its children) and are
-// appended to a slot array; workers claim slots in order and wait (bounded)
-// for a claimed slot to be filled.  Every task is pushed exactly once, so
-// slot s is filled by the s-th push.  If every worker waits, all filled
-// slots have been claimed and finished, and in a tree that means every task
-// is done (an unfinished task has an unfinished descendant, down to a seeded
-// leaf); so a wait always ends while the run has work, and workers that have
-// not started hold no slot.
+// Items become ready when their dependencies complete (bottom-up: the last
+// child's worker; top-down: the parent's worker) and are appended to a slot
+// array; workers claim slots in order and wait (bounded) for a claimed slot
+// to be filled.  The worker that makes an item ready usually runs it itself
+// next (the parent after its last child; one child after its parent), so
+// dependency chains skip the queue; it then pushes a skip marker in the
+// item's place, so every run still fills exactly n_items slots and slot s
+// is filled by the s-th push.  If every worker waits, all filled slots have
+// been claimed and finished, and in a tree that means every item is done
+// (an unfinished item has an unfinished descendant, down to a seeded leaf);
+// so a wait always ends while the run has work, and workers that have not
+// started hold no slot.
+constexpr int kSkip = 0x7fffffff;   // slot value of an item run by continuation
 struct QueueView {
     int *slots;     // -1 = not yet filled
     int *ctr;       // [0] next slot to claim, [1] next slot to fill
-    int *pending;   // outstanding dependencies per task
-    int n_items;    // tasks pushed in this run
+    int *pending;   // outstanding dependencies per item
+    int n_items;    // slots filled in this run
 };
 
-// lane 0 claims a slot and waits for it; returns the task, -1 when the run
-// is finished, -2 when the wait ran out (error)
+// lane 0 claims a slot and waits for it; returns the item, kSkip, -1 when
+// the run is finished, -2 when the wait ran out (error)
 __device__ __forceinline__ int claim_slot(const QueueView &Q, int spin_limit) {
     const int s = atomicAdd(&Q.ctr[0], 1);
     if (s >= Q.n_items) return -1;
+    // exponential backoff (32 ns .. 1 us): idle workers leave the issue
+    // slots to the ones that have work
     int t, spins = 0;
+    unsigned ns = 32;
     while ((t = ld_acquire(&Q.slots[s])) < 0) {
         if (++spins > spin_limit) return -2;
-        __nanosleep(32);
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
     }
     return t;
 }
 
-// warp-wide claim: the task id in every lane; the warp barrier orders lane
-// 0's acquire before the other lanes' reads of the task's inputs
+// warp-wide claim of the next item to run (skip markers are passed over):
+// the item in every lane, -1 when the run is finished; the warp barrier
+// orders lane 0's acquire before the other lanes' reads of the item's inputs
 __device__ __forceinline__ int warp_claim(const QueueView &Q, int spin_limit, FactorStatus *st,
                                           int err) {
-    int task = 0;
+    int item = 0;
     if ((threadIdx.x & 31) == 0) {
-        task = claim_slot(Q, spin_limit);
-        if (task == -2) atomicExch(&st->error, err);
+        do {
+            item = claim_slot(Q, spin_limit);
+        } while (item == kSkip);
+        if (item == -2) {
+            atomicExch(&st->error, err);
+            item = -1;
+        }
     }
-    task = __shfl_sync(0xffffffffu, task, 0);
+    item = __shfl_sync(0xffffffffu, item, 0);
     __syncwarp();
-    return task;
+    return item;
 }
 
-__device__ __forceinline__ void push_task(const QueueView &Q, int task) {
+__device__ __forceinline__ void push_task(const QueueView &Q, int item) {
     const int s = atomicAdd(&Q.ctr[1], 1);
-    st_release(&Q.slots[s], task);
+    st_release(&Q.slots[s], item);
 }
 
-// one thread, after a barrier that ordered its group's writes: count the task
-// off at its parent; the last child pushes the parent
-__device__ __forceinline__ void complete_child(const QueueView &Q, int parent) {
+// one thread, after a barrier that ordered its group's writes: count the
+// item off at its parent.  Returns true if it was the last child: the
+// caller then runs the parent itself (a skip marker takes its slot; the
+// fence after the count orders the other children's writes before the
+// caller's reads).
+__device__ __forceinline__ bool complete_child(const QueueView &Q, int parent) {
     __threadfence();
     if (atomicSub(&Q.pending[parent], 1) == 1) {
         __threadfence();
-        push_task(Q, parent);
+        push_task(Q, kSkip);
+        return true;
     }
+    return false;
 }
 
-// whole warp, after __syncwarp: push every child of `task`
-__device__ __forceinline__ void push_children(const QueueView &Q, const DevFront &F, int task) {
+// warp-wide version: lane 0 counts, every lane learns the outcome
+__device__ __forceinline__ bool warp_complete_child(const QueueView &Q, int parent) {
+    int last = 0;
+    if ((threadIdx.x & 31) == 0) last = complete_child(Q, parent) ? 1 : 0;
+    last = __shfl_sync(0xffffffffu, last, 0);
+    __syncwarp();
+    return last != 0;
+}
+
+// whole warp, after __syncwarp: push every child item of `item` except
+// `keep` (run next by this warp; a skip marker takes its slot)
+__device__ __forceinline__ void push_children(const QueueView &Q, const DevFront &F, int item,
+                                              int keep) {
     const int lane = threadIdx.x & 31;
-    const int c0 = F.child_ptr[task], nc = F.child_ptr[task + 1] - c0;
+    const int c0 = F.item_child_ptr[item], nc = F.item_child_ptr[item + 1] - c0;
     if (nc == 0) return;
     __threadfence();
     int base = 0;
     if (lane == 0) base = atomicAdd(&Q.ctr[1], nc);
     base = __shfl_sync(0xffffffffu, base, 0);
-    for (int i = lane; i < nc; i += 32) st_release(&Q.slots[base + i], F.child[c0 + i]);
+    for (int i = lane; i < nc; i += 32) {
+        const int c = F.item_child[c0 + i];
+        st_release(&Q.slots[base + i], c == keep ? kSkip : c);
+    }
 }
 
 // both queues of a run: slots from their seed lists, counters, pending
@@ -134,31 +168,29 @@ __global__ void k_queue_reset(int n, int *slots_a, const int32_t *init_a, int n_
     }
 }
 
+// ---- scheduler trace (see scopf_trace): per item, claim start, claim end,
+// finish (device clock, ns) and SM
+__device__ __forceinline__ unsigned long long dev_clock_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+__device__ __forceinline__ void trace_item(const DevFront &F, int kind, int item,
+                                           unsigned long long tc, unsigned long long ts) {
+    unsigned sm;
+    asm("mov.u32 %0, %%smid;" : "=r"(sm));
+    unsigned long long *r = F.trace + ((size_t)kind * F.n_items + item) * 4;
+    r[0] = tc;
+    r[1] = ts;
+    r[2] = dev_clock_ns();
+    r[3] = sm;
+}
+
 QueueView queue_a(const DevFront &F, int n_items) {
     return QueueView{F.q_slots_a, F.q_ctr, F.q_pending, n_items};
 }
 QueueView queue_b(const DevFront &F, int n_items) {
     return QueueView{F.q_slots_b, F.q_ctr + 2, F.q_pending, n_items};
-}
-
-// (column j, row i) of element e of the column-major lower triangle of an
-// m x m matrix (diagonal included)
-__device__ __forceinline__ void tri_index(int e, int m, int &j, int &i) {
-    const float b = 2.0f * m + 1.0f;
-    int jj = (int)((b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))) * 0.5f);
-    if (jj < 0) jj = 0;
-    if (jj > m - 1) jj = m - 1;
-    int st = jj * m - (jj * (jj - 1)) / 2;
-    while (st > e) {
-        jj--;
-        st = jj * m - (jj * (jj - 1)) / 2;
-    }
-    while (st + (m - jj) <= e) {
-        st += m - jj;
-        jj++;
-    }
-    j = jj;
-    i = jj + (e - st);
 }
 
 template <int GS>
@@ -169,29 +201,67 @@ __device__ __forceinline__ void gsync() {
         __syncthreads();
 }
 
+// ---- packed records: every thread loads the same words (broadcast loads),
+// so a front's whole description arrives in one round trip
+struct TaskInfo {
+    int64_t front_off, vo;   // vo: offset of the front's rows and vector
+    int f, np, c0, c1;       // rows, pivots, child slots [c0, c1)
+    int o0, o1, parent;      // original entries [o0, o1)
+};
+__device__ __forceinline__ int64_t join64(int lo, int hi) {
+    return (int64_t)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
+}
+__device__ __forceinline__ TaskInfo task_info(const DevFront &F, int t) {
+    const int4 a = F.task_rec[2 * t], b = F.task_rec[2 * t + 1], n = F.task_rec[2 * t + 3];
+    TaskInfo ti;
+    ti.front_off = join64(a.x, a.y);
+    ti.vo = join64(a.z, a.w);
+    ti.f = b.x & 0xffff;
+    ti.np = b.x >> 16;
+    ti.c0 = b.y;
+    ti.o0 = b.z;
+    ti.parent = b.w;
+    ti.c1 = n.y;
+    ti.o1 = n.z;
+    return ti;
+}
+struct ChildInfo {
+    int64_t front_off, vo;
+    int rel_off, fc, npc, task;
+};
+__device__ __forceinline__ ChildInfo child_info(const DevFront &F, int q) {
+    const int4 a = F.child_rec[2 * q], b = F.child_rec[2 * q + 1];
+    ChildInfo c;
+    c.front_off = join64(a.x, a.y);
+    c.vo = join64(a.z, a.w);
+    c.rel_off = b.x;
+    c.fc = b.y & 0xffff;
+    c.npc = b.y >> 16;
+    c.task = b.z;
+    return c;
+}
+
 // Extend-add the children's update blocks into the front, then eliminate
 // its np pivot columns without pivoting: panel factorization (rank-1 updates
 // restricted to the np panel columns) followed by one pass of the trailing
 // update U -= L21 D L21' over the (f - np)^2 lower triangle.  GS threads
 // (one warp or one CTA) cooperate; tid in [0, GS).
 template <typename T, int GS>
-__device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int task, int tid,
-                                double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
-    T *Fr = fronts + F.front_off[task];
-    const int f = F.f[task];
-    const int np = F.npiv[task];
-    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+__device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
+                                int tid, double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    T *Fr = fronts + ti.front_off;
+    const int f = ti.f;
+    const int np = ti.np;
     // the front's own original entries (scaled), zeros elsewhere
     for (int e = tid; e < f * f; e += GS) Fr[e] = (T)0;
     gsync<GS>();
-    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += GS)
-        Fr[F.orig_off[q]] = (T)F.ovals[q];
+    for (int q = ti.o0 + tid; q < ti.o1; q += GS) Fr[F.orig_off[q]] = (T)F.ovals[q];
     gsync<GS>();
-    for (int ci = c0; ci < c1; ci++) {
-        const int ch = F.child[ci];
-        const T *Fc = fronts + F.front_off[ch];
-        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-        const int32_t *rel = F.rel + F.rel_off[ch];
+    for (int ci = ti.c0; ci < ti.c1; ci++) {
+        const ChildInfo c = child_info(F, ci);
+        const T *Fc = fronts + c.front_off;
+        const int fc = c.fc, npc = c.npc, nu = fc - npc;
+        const int32_t *rel = F.rel + c.rel_off;
         const int tot = nu * nu;
         for (int e = tid; e < tot; e += GS) {
             const int jj = e / nu, ii = e - jj * nu;
@@ -241,39 +311,35 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, int t
 // owns row i): originals, extend-add, unblocked right-looking elimination,
 // then one coalesced write of the whole front (L panel, D, update block).
 template <typename T>
-__device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, int task,
+__device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                      int lane, T (*tile)[33], double pivot_tol, int &n_pos,
                                      int &n_neg, int &n_zero) {
-    T *Fr = fronts + F.front_off[task];
-    const int f = F.f[task];
-    const int np = F.npiv[task];
-    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    T *Fr = fronts + ti.front_off;
+    const int f = ti.f;
+    const int np = ti.np;
     for (int j = 0; j < 32; j++) tile[lane][j] = (T)0;
     __syncwarp();
-    const int64_t o0 = F.orig_ptr[task], o1 = F.orig_ptr[task + 1];
-    for (int64_t q = o0 + lane; q < o1; q += 32) {
+    for (int q = ti.o0 + lane; q < ti.o1; q += 32) {
         const int off = F.orig_off[q];
         const int col = off / f, row = off - col * f;
         tile[row][col] = (T)F.ovals[q];
     }
     __syncwarp();
-    for (int ci = c0; ci < c1; ci++) {
-        const int ch = F.child[ci];
-        const T *Fc = fronts + F.front_off[ch];
-        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-        const int32_t *rel = F.rel + F.rel_off[ch];
-        const int myrel = lane < nu ? rel[lane] : 0;
-        // eight independent column loads in flight per step
-        for (int j0 = 0; j0 < nu; j0 += 8) {
-            T v[8];
+    for (int ci = ti.c0; ci < ti.c1; ci++) {
+        const ChildInfo c = child_info(F, ci);
+        const T *Fc = fronts + c.front_off + (int64_t)c.npc * c.fc + c.npc;
+        const int fc = c.fc, nu = fc - c.npc;
+        const int myrel = lane < nu ? F.rel[c.rel_off + lane] : 0;
+        // sixteen independent column loads in flight per step (lane = row)
+        for (int j0 = 0; j0 < nu; j0 += 16) {
+            T v[16];
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int k = 0; k < 16; k++) {
                 const int jj = j0 + k;
-                v[k] = (jj < nu && lane >= jj && lane < nu)
-                           ? Fc[(int64_t)(npc + jj) * fc + npc + lane] : (T)0;
+                v[k] = (jj < nu && lane >= jj && lane < nu) ? Fc[(int64_t)jj * fc + lane] : (T)0;
             }
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int k = 0; k < 16; k++) {
                 const int jj = j0 + k;
                 const int rj = __shfl_sync(0xffffffffu, myrel, jj & 31);
                 if (jj < nu && lane >= jj && lane < nu) tile[myrel][rj] += v[k];
@@ -306,25 +372,163 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         if (lane < f) Fr[(int64_t)j * f + lane] = tile[lane][j];
 }
 
-// Phase 1: small fronts, one warp per front.
+// A front with 32 < f <= 64 rows: the whole front in a 64 x 65 shared
+// buffer (lane owns rows lane and lane + 32), otherwise the same steps as
+// the 32-row tile: originals, extend-add, right-looking elimination of the
+// np pivots, one coalesced write of the front.
+constexpr int kMedF = 64;
 template <typename T>
-__global__ void __launch_bounds__(kWT) k_factor(DevFront F, T *__restrict__ fronts,
+__device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts,
+                                       const TaskInfo &ti, int lane, T (*M)[kMedF + 1],
+                                       double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    T *Fr = fronts + ti.front_off;
+    const int f = ti.f, np = ti.np;
+    const int i0 = lane, i1 = lane + 32;
+    for (int c = 0; c < kMedF; c++) {
+        M[i0][c] = (T)0;
+        M[i1][c] = (T)0;
+    }
+    __syncwarp();
+    for (int q = ti.o0 + lane; q < ti.o1; q += 32) {
+        const int off = F.orig_off[q];
+        const int col = off / f, row = off - col * f;
+        M[row][col] = (T)F.ovals[q];
+    }
+    __syncwarp();
+    for (int ci = ti.c0; ci < ti.c1; ci++) {
+        const ChildInfo c = child_info(F, ci);
+        const int fc = c.fc, nu = fc - c.npc;
+        const T *Fc = fronts + c.front_off + (int64_t)c.npc * fc + c.npc;
+        const int32_t *rel = F.rel + c.rel_off;
+        const int r0 = lane < nu ? rel[lane] : 0, r1 = lane + 32 < nu ? rel[lane + 32] : 0;
+        for (int j0 = 0; j0 < nu; j0 += 8) {
+            T v0[8], v1[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = j0 + k;
+                v0[k] = (jj < nu && lane < nu && lane >= jj) ? Fc[(int64_t)jj * fc + lane] : (T)0;
+                v1[k] = (jj < nu && lane + 32 < nu) ? Fc[(int64_t)jj * fc + lane + 32] : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = j0 + k;
+                if (jj < nu) {
+                    const int rj = F.rel[c.rel_off + jj];   // broadcast (same address)
+                    if (lane < nu && lane >= jj) M[r0][rj] += v0[k];
+                    if (lane + 32 < nu) M[r1][rj] += v1[k];
+                }
+            }
+        }
+        __syncwarp();
+    }
+    for (int c = 0; c < np; c++) {
+        const T d = M[c][c];
+        if (lane == 0) {
+            const double dd = (double)d;
+            if (dd > pivot_tol) n_pos++;
+            else if (dd < -pivot_tol) n_neg++;
+            else n_zero++;
+        }
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        T l0 = (T)0, l1 = (T)0;
+        if (i0 > c && i0 < f) {
+            l0 = M[i0][c] * dinv;
+            M[i0][c] = l0;
+        }
+        if (i1 > c && i1 < f) {
+            l1 = M[i1][c] * dinv;
+            M[i1][c] = l1;
+        }
+        __syncwarp();
+        for (int j = c + 1; j < f; j++) {
+            const T lj = M[j][c] * d;
+            if (i0 >= j && i0 < f) M[i0][j] -= l0 * lj;
+            if (i1 >= j && i1 < f) M[i1][j] -= l1 * lj;
+        }
+        __syncwarp();
+    }
+    for (int j = 0; j < f; j++) {
+        T *colj = Fr + (int64_t)j * f;
+        if (i0 < f) colj[i0] = M[i0][j];
+        if (i1 < f) colj[i1] = M[i1][j];
+    }
+}
+
+// one medium buffer per CTA, taken by a warp with a bounded shared lock
+__device__ __forceinline__ bool take_medium(int *lock, int spin_limit) {
+    int ok = 1;
+    if ((threadIdx.x & 31) == 0) {
+        int spins = 0;
+        unsigned ns = 64;
+        while (atomicCAS(lock, 0, 1) != 0) {
+            if (++spins > spin_limit) {
+                ok = 0;
+                break;
+            }
+            __nanosleep(ns);
+            if (ns < 1024) ns <<= 1;
+        }
+        __threadfence_block();
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    __syncwarp();
+    return ok != 0;
+}
+__device__ __forceinline__ void give_medium(int *lock) {
+    __syncwarp();
+    if ((threadIdx.x & 31) == 0) {
+        __threadfence_block();
+        atomicExch(lock, 0);
+    }
+}
+
+// Phase 1: small fronts, one warp per front.
+constexpr int kFT = 256;   // threads per CTA of the phase-1 kernel
+template <typename T>
+__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 2) k_factor(DevFront F, T *__restrict__ fronts,
                                                 FactorStatus *st, QueueView Q, double pivot_tol,
                                                 int spin_limit) {
-    __shared__ T tiles[kWT / 32][32][33];
+    // dynamic shared memory: one 32 x 33 tile per warp, then the CTA's
+    // 64 x 65 medium buffer, then its lock
+    extern __shared__ __align__(16) unsigned char factor_smem[];
+    T (*tiles)[33] = reinterpret_cast<T (*)[33]>(factor_smem);
     const int lane = threadIdx.x & 31;
-    T (*tile)[33] = tiles[threadIdx.x >> 5];
+    T (*tile)[33] = tiles + 32 * (threadIdx.x >> 5);
+    T (*medium)[kMedF + 1] = reinterpret_cast<T (*)[kMedF + 1]>(tiles + 32 * (kFT / 32));
+    int *lock = reinterpret_cast<int *>(medium + kMedF);
+    if (threadIdx.x == 0) *lock = 0;
+    __syncthreads();
     int n_pos = 0, n_neg = 0, n_zero = 0;
+    int item = -1;
     while (true) {
-        const int task = warp_claim(Q, spin_limit, st, 1);
-        if (task < 0) break;
-        if (F.f[task] <= 32)
-            eliminate_front_tile<T>(F, fronts, task, lane, tile, pivot_tol, n_pos, n_neg, n_zero);
-        else
-            eliminate_front<T, 32>(F, fronts, task, lane, pivot_tol, n_pos, n_neg, n_zero);
-        __syncwarp();
-        const int par = F.parent[task];
-        if (lane == 0 && par >= 0 && par < F.n_small) complete_child(Q, par);
+        const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
+        if (item < 0) item = warp_claim(Q, spin_limit, st, 1);
+        if (item < 0) break;
+        const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
+        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
+        TaskInfo ti = task_info(F, t0);
+        for (int task = t0; task < t1; task++) {
+            const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
+            if (ti.f <= 32) {
+                eliminate_front_tile<T>(F, fronts, ti, lane, tile, pivot_tol, n_pos, n_neg,
+                                        n_zero);
+            } else if (ti.f <= kMedF) {
+                if (take_medium(lock, spin_limit)) {
+                    eliminate_front_medium<T>(F, fronts, ti, lane, medium, pivot_tol, n_pos,
+                                              n_neg, n_zero);
+                    give_medium(lock);
+                } else {
+                    if (lane == 0) atomicExch(&st->error, 1);
+                }
+            } else {
+                eliminate_front<T, 32>(F, fronts, ti, lane, pivot_tol, n_pos, n_neg, n_zero);
+            }
+            __syncwarp();   // the next front of the item reads this one
+            ti = nx;
+        }
+        if (F.trace && lane == 0) trace_item(F, 2, item, tc, ts);
+        const int par = F.item_parent[item];
+        item = (par >= 0 && par < F.n_items_small && warp_complete_child(Q, par)) ? par : -1;
     }
     if (lane == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -345,25 +549,23 @@ constexpr int kBigPanel = kBigPanelBytes / 8;   // panel elements that fit (FP64
 // the trailing update U -= L21 D L21' makes one pass over the update block
 // with L read from shared memory.
 template <typename T>
-__device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, int task,
+__device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                     double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
     extern __shared__ unsigned char big_smem[];
     T *P = reinterpret_cast<T *>(big_smem);   // P[c * f + i]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBT >> 5;
-    T *Fr = fronts + F.front_off[task];
-    const int f = F.f[task];
-    const int np = F.npiv[task];
-    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
+    T *Fr = fronts + ti.front_off;
+    const int f = ti.f;
+    const int np = ti.np;
     for (int e = tid; e < f * f; e += kBT) Fr[e] = (T)0;
     __syncthreads();
-    for (int64_t q = F.orig_ptr[task] + tid; q < F.orig_ptr[task + 1]; q += kBT)
-        Fr[F.orig_off[q]] = (T)F.ovals[q];
+    for (int q = ti.o0 + tid; q < ti.o1; q += kBT) Fr[F.orig_off[q]] = (T)F.ovals[q];
     __syncthreads();
-    for (int ci = c0; ci < c1; ci++) {
-        const int ch = F.child[ci];
-        const T *Fc = fronts + F.front_off[ch];
-        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-        const int32_t *rel = F.rel + F.rel_off[ch];
+    for (int ci = ti.c0; ci < ti.c1; ci++) {
+        const ChildInfo c = child_info(F, ci);
+        const T *Fc = fronts + c.front_off;
+        const int fc = c.fc, npc = c.npc, nu = fc - npc;
+        const int32_t *rel = F.rel + c.rel_off;
         for (int jj = warp; jj < nu; jj += nw) {
             const int64_t dst = (int64_t)rel[jj] * f;
             const T *src = Fc + (int64_t)(npc + jj) * fc + npc;
@@ -412,22 +614,38 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
                                                     double pivot_tol, int spin_limit) {
     __shared__ int s_task;
     int n_pos = 0, n_neg = 0, n_zero = 0;
+    if (threadIdx.x == 0) s_task = -1;
+    __syncthreads();
     while (true) {
-        if (threadIdx.x == 0) {
-            s_task = claim_slot(Q, spin_limit);
-            if (s_task == -2) atomicExch(&st->error, 1);
+        const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
+        if (threadIdx.x == 0 && s_task < 0) {
+            int t;
+            do {
+                t = claim_slot(Q, spin_limit);
+            } while (t == kSkip);
+            if (t == -2) {
+                atomicExch(&st->error, 1);
+                t = -1;
+            }
+            s_task = t;
         }
         __syncthreads();
-        const int task = s_task;
+        const int item = s_task;
         __syncthreads();
-        if (task < 0) break;
-        if ((int64_t)F.f[task] * F.npiv[task] <= kBigPanel)
-            eliminate_front_big<T>(F, fronts, task, pivot_tol, n_pos, n_neg, n_zero);
+        if (item < 0) break;
+        const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
+        const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per large item
+        if ((int64_t)ti.f * ti.np <= kBigPanel)
+            eliminate_front_big<T>(F, fronts, ti, pivot_tol, n_pos, n_neg, n_zero);
         else
-            eliminate_front<T, kBT>(F, fronts, task, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
+            eliminate_front<T, kBT>(F, fronts, ti, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
         __syncthreads();   // orders every thread's writes before the release below
-        const int par = F.parent[task];
-        if (threadIdx.x == 0 && par >= 0) complete_child(Q, par);
+        if (threadIdx.x == 0) {
+            if (F.trace) trace_item(F, 3, item, tc, ts);
+            const int par = F.item_parent[item];
+            s_task = (par >= 0 && complete_child(Q, par)) ? par : -1;
+        }
+        __syncthreads();
     }
     if (threadIdx.x == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -531,94 +749,163 @@ __global__ void k_dense_trailing(double *S, int n, int k0, int k1) {
 }
 
 // ---------------------------------------------------------------- solves
+// f <= 32: lane i owns row i; its row of the L panel (np <= NP columns) is
+// prefetched into registers, the children's update vectors are gathered in
+// batches of four (all loads in flight, adds in child order), and the
+// triangular solve runs on shuffles
+template <typename T, int NP>
+__device__ __forceinline__ void fwd_small(const DevFront &F, const T *__restrict__ L,
+                                          T *__restrict__ v, const int64_t *__restrict__ rows,
+                                          const double *__restrict__ b,
+                                          const double *__restrict__ scale,
+                                          const T *__restrict__ vec, const TaskInfo &ti, int lane,
+                                          T *sv) {
+    const int f = ti.f, np = ti.np;
+    T Lr[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) Lr[c] = (c < np && lane > c && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
+    const T dl = lane < np ? L[(int64_t)lane * f + lane] : (T)1;
+    T vi = (T)0;
+    if (lane < np) {
+        const int64_t r = rows[lane];
+        vi = (T)(scale[r] * b[r]);
+    }
+    sv[lane] = vi;
+    __syncwarp();
+    for (int q0 = ti.c0; q0 < ti.c1; q0 += 4) {
+        int rr[4];
+        T vv[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            rr[k] = -1;
+            vv[k] = (T)0;
+            if (q0 + k < ti.c1) {
+                const ChildInfo c = child_info(F, q0 + k);
+                if (lane < c.fc - c.npc) {
+                    rr[k] = F.rel[c.rel_off + lane];
+                    vv[k] = vec[c.vo + c.npc + lane];
+                }
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            if (q0 + k < ti.c1) {
+                if (rr[k] >= 0) sv[rr[k]] += vv[k];
+                __syncwarp();
+            }
+        }
+    }
+    vi = sv[lane];
+#pragma unroll
+    for (int c = 0; c < NP; c++) {
+        if (c < np) {
+            const T xc = __shfl_sync(0xffffffffu, vi, c);
+            vi -= Lr[c] * xc;
+        }
+    }
+    if (lane < np) vi /= dl;
+    if (lane < f) v[lane] = vi;
+}
+
 // Forward sweep of one front: gather D b on its pivot rows plus the
 // children's update vectors, then y = D^-1 L^-1 (.) on the pivot rows and
 // the update vector -L21 y for the parent on the others.
 template <typename T>
 __device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict__ fronts,
                                           T *__restrict__ vec, const double *__restrict__ b,
-                                          const double *__restrict__ scale, int task, int lane,
-                                          T *sv) {
-    const int c0 = F.child_ptr[task], c1 = F.child_ptr[task + 1];
-    const int f = F.f[task], np = F.npiv[task];
-    const T *L = fronts + F.front_off[task];
-    T *v = vec + F.vec_off[task];
-    const int64_t *rows = F.rows + F.rows_off[task];
+                                          const double *__restrict__ scale, const TaskInfo &ti,
+                                          int lane, T *sv) {
+    const int f = ti.f, np = ti.np;
+    const T *L = fronts + ti.front_off;
+    T *v = vec + ti.vo;
+    const int64_t *rows = F.rows + ti.vo;
     if (f <= 32) {
-        // lane i owns row i; its row of the L panel is prefetched into registers
-        T Lr[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) Lr[c] = (c < np && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
-        const T dl = lane < np ? L[(int64_t)lane * f + lane] : (T)1;
-        T vi = (T)0;
-        if (lane < np) {
-            const int64_t r = rows[lane];
-            vi = (T)(scale[r] * b[r]);
-        }
-        sv[lane] = vi;
-        __syncwarp();
-        for (int ci = c0; ci < c1; ci++) {
-            const int ch = F.child[ci];
-            const int nu = F.f[ch] - F.npiv[ch];
-            if (lane < nu) sv[F.rel[F.rel_off[ch] + lane]] += vec[F.vec_off[ch] + F.npiv[ch] + lane];
-            __syncwarp();
-        }
-        vi = sv[lane];
-#pragma unroll
-        for (int c = 0; c < 32; c++) {
-            if (c < np) {
-                const T xc = __shfl_sync(0xffffffffu, vi, c);
-                if (lane > c) vi -= Lr[c] * xc;
-            }
-        }
-        if (lane < np) vi /= dl;
-        if (lane < f) v[lane] = vi;
+        if (np <= 8)
+            fwd_small<T, 8>(F, L, v, rows, b, scale, vec, ti, lane, sv);
+        else
+            fwd_small<T, 32>(F, L, v, rows, b, scale, vec, ti, lane, sv);
         return;
     }
+    // f > 32: the front's vector is staged in the warp's shared buffer; the
+    // pivot block is solved in 32-row tiles (rows in registers, shuffles),
+    // and the update rows take the mat-vec -L21 y with independent loads
     for (int i = lane; i < f; i += 32) {
         T x = (T)0;
         if (i < np) {
             const int64_t r = rows[i];
             x = (T)(scale[r] * b[r]);
         }
-        v[i] = x;
+        sv[i] = x;
     }
     __syncwarp();
-    for (int ci = c0; ci < c1; ci++) {
-        const int ch = F.child[ci];
-        const int fc = F.f[ch], npc = F.npiv[ch], nu = fc - npc;
-        const T *vc = vec + F.vec_off[ch] + npc;
-        const int32_t *rel = F.rel + F.rel_off[ch];
-        for (int i = lane; i < nu; i += 32) v[rel[i]] += vc[i];
+    for (int q = ti.c0; q < ti.c1; q++) {
+        const ChildInfo c = child_info(F, q);
+        const int nu = c.fc - c.npc;
+        const T *vc = vec + c.vo + c.npc;
+        const int32_t *rel = F.rel + c.rel_off;
+        for (int i = lane; i < nu; i += 32) sv[rel[i]] += vc[i];
         __syncwarp();
     }
-    for (int c = 0; c < np; c++) {
-        const T xc = v[c];
-        const T *col = L + (int64_t)c * f;
-        for (int i = c + 1 + lane; i < f; i += 32) v[i] -= col[i] * xc;
+    for (int k0 = 0; k0 < np; k0 += 32) {
+        const int kn = min(32, np - k0);
+        const int row = k0 + lane;
+        T acc = (T)0;
+        if (lane < kn) {
+            acc = sv[row];
+#pragma unroll 4
+            for (int c = 0; c < k0; c++) acc -= L[(int64_t)c * f + row] * sv[c];
+        }
+        T Lr[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+            Lr[c] = (c < lane && lane < kn) ? L[(int64_t)(k0 + c) * f + row] : (T)0;
+#pragma unroll
+        for (int c = 0; c < 32; c++) {
+            if (c < kn) {
+                const T xc = __shfl_sync(0xffffffffu, acc, c);
+                acc -= Lr[c] * xc;
+            }
+        }
+        if (lane < kn) sv[row] = acc;
         __syncwarp();
+    }
+    for (int i = np + lane; i < f; i += 32) {
+        T acc = sv[i];
+#pragma unroll 8
+        for (int c = 0; c < np; c++) acc -= L[(int64_t)c * f + i] * sv[c];
+        v[i] = acc;
     }
     // diagonal: y = D^-1 (L^-1 b) on the pivot rows
-    for (int c = lane; c < np; c += 32) v[c] = v[c] / L[(int64_t)c * f + c];
+    for (int c = lane; c < np; c += 32) v[c] = sv[c] / L[(int64_t)c * f + c];
 }
 
 // bottom-up over every task (border fronts included: they collect the
 // block's contribution to the border right-hand side)
 template <typename T>
-__global__ void __launch_bounds__(kWT) k_solve_fwd(DevFront F, const T *__restrict__ fronts,
-                                                   T *__restrict__ vec, const double *__restrict__ b,
-                                                   const double *__restrict__ scale, QueueView Q,
-                                                   FactorStatus *st, int spin_limit) {
-    __shared__ T sv_all[kWT / 32][32];
+__global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
+    k_solve_fwd(DevFront F, const T *__restrict__ fronts, T *__restrict__ vec,
+                const double *__restrict__ b, const double *__restrict__ scale, QueueView Q,
+                FactorStatus *st, int spin_limit) {
+    extern __shared__ unsigned char solve_smem[];
     const int lane = threadIdx.x & 31;
-    T *sv = sv_all[threadIdx.x >> 5];
+    T *sv = reinterpret_cast<T *>(solve_smem) + (threadIdx.x >> 5) * F.max_f;
+    int item = -1;
     while (true) {
-        const int task = warp_claim(Q, spin_limit, st, 2);
-        if (task < 0) break;
-        fwd_front<T>(F, fronts, vec, b, scale, task, lane, sv);
-        __syncwarp();
-        const int par = F.parent[task];
-        if (lane == 0 && par >= 0) complete_child(Q, par);
+        const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
+        if (item < 0) item = warp_claim(Q, spin_limit, st, 2);
+        if (item < 0) break;
+        const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
+        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
+        TaskInfo ti = task_info(F, t0);
+        for (int task = t0; task < t1; task++) {
+            const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
+            fwd_front<T>(F, fronts, vec, b, scale, ti, lane, sv);
+            __syncwarp();
+            ti = nx;
+        }
+        if (F.trace && lane == 0) trace_item(F, 0, item, tc, ts);
+        const int par = F.item_parent[item];
+        item = (par >= 0 && warp_complete_child(Q, par)) ? par : -1;
     }
 }
 
@@ -664,71 +951,125 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
     }
 }
 
+// f <= 32: lane i owns row i; L' z = y on the pivot rows with the update
+// rows' final values, column dot products by warp reductions
+template <typename T, int NP>
+__device__ __forceinline__ void bwd_small(const T *__restrict__ L, const T *__restrict__ v,
+                                          const int64_t *__restrict__ rows,
+                                          const double *__restrict__ scale,
+                                          double *__restrict__ x, int f, int np, int lane) {
+    T Lr[NP];
+#pragma unroll
+    for (int c = 0; c < NP; c++) Lr[c] = (c < np && lane > c && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
+    T vi = (T)0;
+    int64_t r = 0;
+    if (lane < f) r = rows[lane];
+    if (lane < np)
+        vi = v[lane];
+    else if (lane < f)
+        vi = (T)(x[r] / scale[r]);
+#pragma unroll
+    for (int c = NP - 1; c >= 0; c--) {
+        if (c < np) {
+            T p = Lr[c] * vi;
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == c) vi -= p;
+        }
+    }
+    if (lane < np) x[r] = scale[r] * (double)vi;
+}
+
 // Backward sweep of one (non-border) front: its update rows hold the final
 // solution of ancestors and border, the pivot rows solve L11' x = y - L21' x2.
 template <typename T>
 __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict__ fronts,
                                           T *__restrict__ vec, const double *__restrict__ scale,
-                                          double *__restrict__ x, int task, int lane) {
-    const int f = F.f[task], np = F.npiv[task];
-    const T *L = fronts + F.front_off[task];
-    T *v = vec + F.vec_off[task];
-    const int64_t *rows = F.rows + F.rows_off[task];
+                                          double *__restrict__ x, const TaskInfo &ti, int lane,
+                                          T *sv) {
+    const int f = ti.f, np = ti.np;
+    const T *L = fronts + ti.front_off;
+    T *v = vec + ti.vo;
+    const int64_t *rows = F.rows + ti.vo;
     if (f <= 32) {
-        T Lr[32];
-#pragma unroll
-        for (int c = 0; c < 32; c++) Lr[c] = (c < np && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
-        T vi = (T)0;
-        int64_t r = 0;
-        if (lane < f) r = rows[lane];
-        if (lane < np)
-            vi = v[lane];
-        else if (lane < f)
-            vi = (T)(x[r] / scale[r]);
-#pragma unroll
-        for (int c = 31; c >= 0; c--) {
-            if (c < np) {
-                T p = (lane > c && lane < f) ? Lr[c] * vi : (T)0;
-                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-                if (lane == c) vi -= p;
-            }
-        }
-        if (lane < np) x[r] = scale[r] * (double)vi;
+        if (np <= 8)
+            bwd_small<T, 8>(L, v, rows, scale, x, f, np, lane);
+        else
+            bwd_small<T, 32>(L, v, rows, scale, x, f, np, lane);
         return;
     }
-    for (int i = np + lane; i < f; i += 32) {
-        const int64_t r = rows[i];
-        v[i] = (T)(x[r] / scale[r]);
+    // f > 32: stage [y (pivots); x (update rows)] in the warp's shared
+    // buffer, then solve L' z = y in 32-row tiles from the last: the tile's
+    // coupling to everything below it is one dot product per column (warp
+    // reductions over independent loads), the tile itself a register solve
+    for (int i = lane; i < f; i += 32) {
+        if (i < np) {
+            sv[i] = v[i];
+        } else {
+            const int64_t r = rows[i];
+            sv[i] = (T)(x[r] / scale[r]);
+        }
     }
     __syncwarp();
-    for (int c = np - 1; c >= 0; c--) {
-        const T *col = L + (int64_t)c * f;
-        T acc = 0;
-        for (int i = c + 1 + lane; i < f; i += 32) acc += col[i] * v[i];
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-        if (lane == 0) v[c] -= acc;
+    for (int k0 = ((np - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
+        const int kn = min(32, np - k0);
+        T zi = lane < kn ? sv[k0 + lane] : (T)0;
+        for (int j = 0; j < kn; j++) {
+            const T *col = L + (int64_t)(k0 + j) * f;
+            T p = (T)0;
+#pragma unroll 4
+            for (int i = k0 + kn + lane; i < f; i += 32) p += col[i] * sv[i];
+            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+            if (lane == j) zi -= p;
+        }
+        T Lr[32];
+#pragma unroll
+        for (int c = 0; c < 32; c++)
+            Lr[c] = (c < lane && lane < kn) ? L[(int64_t)(k0 + c) * f + k0 + lane] : (T)0;
+#pragma unroll
+        for (int c = 31; c >= 0; c--) {
+            if (c < kn) {
+                T q = Lr[c] * zi;
+                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
+                if (lane == c) zi -= q;
+            }
+        }
+        if (lane < kn) sv[k0 + lane] = zi;
         __syncwarp();
     }
     for (int c = lane; c < np; c += 32) {
         const int64_t r = rows[c];
-        x[r] = scale[r] * (double)v[c];
+        x[r] = scale[r] * (double)sv[c];
     }
 }
 
 // top-down from the block roots (the border solution is already in x); a
 // finished front pushes its children
 template <typename T>
-__global__ void __launch_bounds__(kWT) k_solve_bwd(DevFront F, const T *__restrict__ fronts,
+__global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFront F, const T *__restrict__ fronts,
                                                    T *__restrict__ vec, const double *__restrict__ scale,
                                                    double *__restrict__ x, QueueView Q,
                                                    FactorStatus *st, int spin_limit) {
+    extern __shared__ unsigned char solve_smem[];
     const int lane = threadIdx.x & 31;
+    T *sv = reinterpret_cast<T *>(solve_smem) + (threadIdx.x >> 5) * F.max_f;
+    int item = -1;
     while (true) {
-        const int task = warp_claim(Q, spin_limit, st, 3);
-        if (task < 0) break;
-        bwd_front<T>(F, fronts, vec, scale, x, task, lane);
-        __syncwarp();
-        push_children(Q, F, task);
+        const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
+        if (item < 0) item = warp_claim(Q, spin_limit, st, 3);
+        if (item < 0) break;
+        const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
+        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
+        TaskInfo ti = task_info(F, t1 - 1);
+        for (int task = t1 - 1; task >= t0; task--) {
+            const TaskInfo nx = task_info(F, task > t0 ? task - 1 : task);   // prefetch
+            bwd_front<T>(F, fronts, vec, scale, x, ti, lane, sv);
+            __syncwarp();
+            ti = nx;
+        }
+        if (F.trace && lane == 0) trace_item(F, 1, item, tc, ts);
+        const int keep = F.item_cont[item];   // the child with the longest path below
+        push_children(Q, F, item, keep);
+        item = keep;
     }
 }
 
@@ -819,8 +1160,8 @@ void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s) {
 void launch_queue_reset(const DevFront &F, const int32_t *init_a, int n_a, const int32_t *init_b,
                         int n_b, const int32_t *pend, cudaStream_t s) {
     const int t = 256;
-    const int n = F.n_tasks > 0 ? F.n_tasks : 1;
-    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_tasks, F.q_slots_a, init_a, n_a, F.q_slots_b,
+    const int n = F.n_items > 0 ? F.n_items : 1;
+    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, init_a, n_a, F.q_slots_b,
                                                 init_b, n_b, F.q_pending, pend, F.q_ctr);
 }
 
@@ -829,13 +1170,27 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
                    int spin_limit, cudaStream_t s) {
     // queue a: phase 1 (small fronts), queue b: phase 2 (large fronts)
     launch_queue_reset(F, F.init_small, F.n_init_small, F.init_big, F.n_init_big, F.pend_factor, s);
-    int grid = warp_grid();
-    const int need = (F.n_small + kWT / 32 - 1) / (kWT / 32);
+    const size_t sm1 = sizeof(T) * (33 * 32 * (kFT / 32) + kMedF * (kMedF + 1)) + 16;
+    static int grid1[2] = {0, 0};   // resident CTAs (float, double)
+    int &g1 = grid1[sizeof(T) == 4 ? 0 : 1];
+    if (!g1) {
+        for (const void *k : {(const void *)k_factor<float>, (const void *)k_factor<double>}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
+        int dev = 0, sms = 148, occ = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor<T>, kFT, sm1);
+        g1 = sms * (occ > 0 ? occ : 1);
+    }
+    int grid = g1;
+    const int need = (F.n_items_small + kFT / 32 - 1) / (kFT / 32);
     if (grid > need) grid = need;
-    if (F.n_small > 0)
-        k_factor<T><<<grid, kWT, 0, s>>>(F, fronts, st, queue_a(F, F.n_small), pivot_tol,
-                                         spin_limit);
-    const int nbig = F.n_tasks - F.n_small;
+    if (F.n_items_small > 0)
+        k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, F.n_items_small), pivot_tol,
+                                           spin_limit);
+    const int nbig = F.n_items - F.n_items_small;
     if (nbig > 0) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -886,19 +1241,27 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
     // queue a: forward sweep (all tasks), queue b: backward sweep (non-border)
     launch_queue_reset(F, F.init_fwd, F.n_init_fwd, F.init_bwd, F.n_init_bwd, F.nchild, s);
     int grid = warp_grid();
-    const int need = (F.n_tasks + kWT / 32 - 1) / (kWT / 32);
+    const int need = (F.n_items + kWT / 32 - 1) / (kWT / 32);
     if (grid > need) grid = need;
-    k_solve_fwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, b, scale, queue_a(F, F.n_tasks), st,
-                                        spin_limit);
+    const size_t sm = sizeof(T) * (size_t)(kWT / 32) * F.max_f;
+    static bool attr = false;
+    if (!attr && sm > 48 * 1024) {
+        for (const void *k : {(const void *)k_solve_fwd<float>, (const void *)k_solve_fwd<double>,
+                              (const void *)k_solve_bwd<float>, (const void *)k_solve_bwd<double>})
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
+        attr = true;
+    }
+    k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, b, scale, queue_a(F, F.n_items), st,
+                                         spin_limit);
     {
         const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
         k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
             F, vec, S, nS, b, scale, x, border_work);
     }
-    const int nb = F.n_tasks - F.n_blocks;
+    const int nb = F.n_items - F.n_blocks;   // every item but the border fronts
     if (nb > 0)
-        k_solve_bwd<T><<<grid, kWT, 0, s>>>(F, fronts, vec, scale, x, queue_b(F, nb), st,
-                                            spin_limit);
+        k_solve_bwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, scale, x, queue_b(F, nb), st,
+                                             spin_limit);
 }
 
 #define INST(T)                                                                                    \

@@ -23,7 +23,8 @@
 
 namespace scopf {
 
-std::string symbolic_block(const Model &M, int k, int relax_max_nodes, BlockSymbolic &S) {
+std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax_max_front,
+                           BlockSymbolic &S) {
     const Block &B = M.blocks[k];
     const int nb = M.nb, ng = M.ng, npv = (int)M.pv.size();
     auto Kw = [&](int64_t local) { return B.kkt0 + local; };
@@ -177,31 +178,101 @@ std::string symbolic_block(const Model &M, int k, int relax_max_nodes, BlockSymb
         }
     }
     S.sn_start.push_back(n_block);
-    const int nsn = (int)S.sn_start.size() - 1;
-    std::vector<int> sn_of(n_block);
-    for (int s = 0; s < nsn; s++)
-        for (int i = S.sn_start[s]; i < S.sn_start[s + 1]; i++) sn_of[i] = s;
-    S.sn_update_nodes.assign(nsn, {});
-    S.sn_parent.assign(nsn, -1);
-    for (int s = 0; s < nsn; s++) {
-        std::set<int> mem, u;
-        for (int i = S.sn_start[s]; i < S.sn_start[s + 1]; i++) mem.insert(S.post[i]);
-        for (int v : mem)
-            for (int x : st[v])
-                if (!mem.count(x)) u.insert(x);
-        std::vector<int> ul(u.begin(), u.end());
-        std::sort(ul.begin(), ul.end(), [&](int a, int b) { return ppos[a] < ppos[b]; });
-        S.sn_update_nodes[s] = ul;
-        int first_block = -1;
-        for (int x : ul)
-            if (x < n_block) {
-                first_block = x;
-                break;
+    // update nodes (union of member structures minus members, by position,
+    // border nodes last) and parent supernode (-2 = border) of every supernode
+    auto link = [&]() {
+        const int nsn = (int)S.sn_start.size() - 1;
+        std::vector<int> sn_of(n_block);
+        for (int s = 0; s < nsn; s++)
+            for (int i = S.sn_start[s]; i < S.sn_start[s + 1]; i++) sn_of[i] = s;
+        S.sn_update_nodes.assign(nsn, {});
+        S.sn_parent.assign(nsn, -1);
+        for (int s = 0; s < nsn; s++) {
+            std::set<int> mem, u;
+            for (int i = S.sn_start[s]; i < S.sn_start[s + 1]; i++) mem.insert(S.post[i]);
+            for (int v : mem)
+                for (int x : st[v])
+                    if (!mem.count(x)) u.insert(x);
+            std::vector<int> ul(u.begin(), u.end());
+            std::sort(ul.begin(), ul.end(), [&](int a, int b) { return ppos[a] < ppos[b]; });
+            S.sn_update_nodes[s] = ul;
+            int first_block = -1;
+            for (int x : ul)
+                if (x < n_block) {
+                    first_block = x;
+                    break;
+                }
+            if (first_block >= 0)
+                S.sn_parent[s] = sn_of[ppos[first_block]];
+            else if (!ul.empty())
+                S.sn_parent[s] = -2;
+        }
+    };
+    link();
+    if (relax_max_front > 0) {
+        // relaxed amalgamation bounded by the front size: a supernode absorbs
+        // a direct child c (children in increasing index) while its front
+        // stays within relax_max_front rows after adding c's pivot rows; the
+        // final supernode tree is postordered (roots and children in
+        // increasing index), each supernode listing its absorbed children's
+        // nodes (recursively, in order) before its own
+        const int nsn = (int)S.sn_start.size() - 1;
+        std::vector<std::vector<int>> members(nsn), kids(nsn), absorbed(nsn), tree_kids(nsn);
+        std::vector<int> npiv(nsn, 0), front(nsn, 0), into(nsn, -1), rep(nsn);
+        for (int s = 0; s < nsn; s++) {
+            for (int i = S.sn_start[s]; i < S.sn_start[s + 1]; i++) {
+                members[s].push_back(S.post[i]);
+                npiv[s] += (int)rows[S.post[i]].size();
             }
-        if (first_block >= 0)
-            S.sn_parent[s] = sn_of[ppos[first_block]];
-        else if (!ul.empty())
-            S.sn_parent[s] = -2;
+            front[s] = npiv[s];
+            for (int u : S.sn_update_nodes[s]) front[s] += (int)rows[u].size();
+            if (S.sn_parent[s] >= 0) kids[S.sn_parent[s]].push_back(s);
+        }
+        for (int s = 0; s < nsn; s++)
+            for (int c : kids[s])
+                if (front[s] + npiv[c] <= relax_max_front) {
+                    absorbed[s].push_back(c);
+                    into[c] = s;
+                    front[s] += npiv[c];
+                    npiv[s] += npiv[c];
+                }
+        for (int s = nsn - 1; s >= 0; s--) rep[s] = into[s] >= 0 ? rep[into[s]] : s;
+        std::vector<int> sroots;
+        for (int s = 0; s < nsn; s++) {
+            if (into[s] >= 0) continue;
+            if (S.sn_parent[s] >= 0)
+                tree_kids[rep[S.sn_parent[s]]].push_back(s);
+            else
+                sroots.push_back(s);
+        }
+        std::vector<int> order;
+        for (int r0 : sroots) {
+            std::vector<std::pair<int, int>> stack = {{r0, 0}};
+            while (!stack.empty()) {
+                auto [v, i] = stack.back();
+                stack.pop_back();
+                if (i < (int)tree_kids[v].size()) {
+                    stack.push_back({v, i + 1});
+                    stack.push_back({tree_kids[v][i], 0});
+                } else {
+                    order.push_back(v);
+                }
+            }
+        }
+        std::function<void(int, std::vector<int> &)> expand = [&](int s, std::vector<int> &out) {
+            for (int c : absorbed[s]) expand(c, out);
+            out.insert(out.end(), members[s].begin(), members[s].end());
+        };
+        std::vector<int> post;
+        S.sn_start.assign(1, 0);
+        for (int s : order) {
+            expand(s, post);
+            S.sn_start.push_back((int)post.size());
+        }
+        if ((int)post.size() != n_block) return "internal: relaxed supernodes lost nodes";
+        S.post = post;
+        for (int i = 0; i < n_block; i++) ppos[S.post[i]] = i;
+        link();
     }
     S.rows.clear();
     for (int v : S.post) S.rows.insert(S.rows.end(), rows[v].begin(), rows[v].end());

@@ -198,6 +198,65 @@ def test_symbolic_structure_brute_force():
                 assert ppos[v] < ppos[Sy.parent[v]]
 
 
+def test_relaxed_amalgamation_star_by_hand():
+    """Star: four one-row leaves around a one-row centre, no border.  Leaves
+    (fronts of 2 rows: pivot + centre) are children of the centre (front 1).
+    With a 3-row bound the centre absorbs leaves 0 and 1 (front 1 -> 2 -> 3)
+    and rejects 2 and 3; the final tree {2}, {3} -> {0, 1, 4} is postordered
+    children first, each supernode listing absorbed nodes before its own."""
+    rows = [np.array([i]) for i in range(5)]
+    adj = [{4}, {4}, {4}, {4}, {0, 1, 2, 3}]
+    G = symbolic.BlockGraph(rows, adj, 5)
+    S = symbolic.Symbolic(G, relax_max_nodes=8, relax_max_front=3)
+    assert S.post.tolist() == [2, 3, 0, 1, 4]
+    assert S.sn_start.tolist() == [0, 1, 2, 5]
+    assert S.sn_parent.tolist() == [2, 2, -1]
+    assert [u.tolist() for u in S.sn_update_nodes] == [[4], [4], []]
+    S0 = symbolic.Symbolic(G, relax_max_nodes=8, relax_max_front=0)
+    assert S0.post.tolist() == [0, 1, 2, 3, 4] and S0.sn_start.tolist() == [0, 1, 2, 3, 4, 5]
+
+
+@pytest.mark.parametrize("max_front", [16, 32, 48])
+def test_relaxed_amalgamation_invariants(max_front):
+    """On every block of a small instance: the node order is a topological
+    order of the elimination tree; every front holds its members' fill
+    (brute-force elimination gives the structures); no final child fits its
+    parent's front (greedy absorption is maximal); a front above the bound is
+    an unmerged chain of only children."""
+    inst = H.small_instance()
+    M = SCOPFModel(inst)
+    K = symbolic.structural_kkt(M)
+    graphs = symbolic.attach_adjacency(symbolic.block_graphs(M), K)
+    for G in graphs:
+        S = symbolic.Symbolic(G, relax_max_nodes=8, relax_max_front=max_front)
+        nb = G.n_block
+        assert sorted(S.post.tolist()) == list(range(nb))
+        ppos = {v: i for i, v in enumerate(S.post.tolist())}
+        for v in range(nb):
+            if S.parent[v] >= 0:
+                assert ppos[v] < ppos[S.parent[v]]
+        nrow = [len(r) for r in G.node_rows]
+        nsn = S.n_sn
+        npiv, front, members = [], [], []
+        for s in range(nsn):
+            mem = S.post[S.sn_start[s]:S.sn_start[s + 1]].tolist()
+            members.append(mem)
+            fill = set().union(*[S.struct[v] for v in mem]) - set(mem)
+            assert fill == set(S.sn_update_nodes[s].tolist())
+            npiv.append(sum(nrow[v] for v in mem))
+            front.append(npiv[-1] + sum(nrow[u] for u in fill))
+        for s in range(nsn):
+            p = S.sn_parent[s]
+            if p >= 0:
+                assert p > s
+                assert front[p] + npiv[s] > max_front
+            if front[s] > max_front:
+                mem = members[s]
+                for a, b in zip(mem[:-1], mem[1:]):
+                    assert S.parent[a] == b
+                    assert sum(1 for v in range(nb) if S.parent[v] == b) == 1
+
+
 def test_global_permutation_fill_matches_etree_counts():
     """nnz(L) of the scalar factor under the oracle permutation equals the
     count from brute-force dense symbolic elimination."""
