@@ -173,7 +173,7 @@ def min_degree(adj, n_block):
 class Symbolic:
     """Symbolic analysis of one block (see the module docstring)."""
 
-    def __init__(self, G: BlockGraph, relax_max_nodes: int = 8, relax_max_front: int = 32):
+    def __init__(self, G: BlockGraph, relax_max_nodes: int = 8, relax_max_front: int = 0):
         order, struct = min_degree(G.adj, G.n_block)
         nb_nodes = G.n_block
         self.elim_order = order
@@ -358,7 +358,7 @@ def structural_kkt(model, seed: int = 12345):
     return S.kkt_matrix(st, prm, H, J, 0.5)
 
 
-def kkt_permutation(model, K=None, relax_max_nodes: int = 8, relax_max_front: int = 32):
+def kkt_permutation(model, K=None, relax_max_nodes: int = 8, relax_max_front: int = 0):
     """Global fill-reducing order of the reduced KKT matrix: each block's rows
     in its symbolic order, blocks 0..K in turn, then the border rows.  The
     node graphs come from the structural pattern (``structural_kkt``)."""

@@ -310,7 +310,7 @@ void scopf_default_options(scopf_options *o) {
     o->spin_limit = 1 << 24;
     o->host_only = 0;
     o->cluster_max_tasks = 8;
-    o->relax_max_front = 32;
+    o->relax_max_front = 0;
 }
 
 const char *scopf_strerror(int s) {
