@@ -231,15 +231,17 @@ int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls
  * items (a subtree of small fronts run by one warp, or one front) from ready
  * queues.  enable = 1 allocates a device buffer and makes every later sweep
  * record, per item, four uint64: the device clock (%globaltimer, ns) when
- * its worker started to claim it, when it got it, when it finished, and the
- * SM it ran on; 0 stops recording and frees the buffer.  Kinds: 0 forward
- * sweep, 1 backward sweep, 2 factorization phase 1 (small fronts), 3 phase
- * 2 (large fronts); each keeps the record of its last run (zeros for items
- * that did not run).  scopf_trace_read copies kind `kind` to out (host,
- * 4 * n_items uint64).  scopf_trace_items describes the items: out (host,
- * 6 * n_items int32) = fronts in the item, parent item (-1 none), 1 if
- * phase 1, largest front (rows), total pivots, block; returns n_items
- * through *n_items. */
+ * its worker started to look for it (or finished the item it continues
+ * from), when it started it, when it finished it, and the SM it ran on;
+ * 0 stops recording and frees the buffer.  Kinds: 0 forward sweep, 1
+ * backward sweep, 2-4 factorization phases 1-3 (tile-sized fronts, medium
+ * fronts and their ancestors, large fronts and theirs); each keeps the
+ * record of its last run (zeros for items that did not run).
+ * scopf_trace_read copies kind `kind` to out (host, 4 * n_items uint64).
+ * scopf_trace_items describes the items: out (host, 6 * n_items int32) =
+ * fronts in the item, parent item (-1 none), factorization phase (1-3),
+ * largest front (rows), total pivots, block; returns n_items through
+ * *n_items (out may be NULL). */
 int scopf_trace(scopf_handle *h, int32_t enable);
 int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out);
 int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out);

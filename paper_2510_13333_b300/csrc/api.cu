@@ -206,6 +206,7 @@ int setup_device(scopf_handle *h) {
         F.max_f = 32;
         for (int t = 0; t < HF.n_tasks; t++) F.max_f = std::max(F.max_f, (int)HF.f[t]);
         F.n_items_small = HF.n_items_small;
+        F.n_items_med = HF.n_items_med;
         TRY(upload(h, HF.item_ptr, &F.item_ptr));
         {
             const int32_t *tr = nullptr, *cr = nullptr;
@@ -222,15 +223,18 @@ int setup_device(scopf_handle *h) {
         TRY(upload(h, HF.item_cont, &F.item_cont));
         TRY(alloc(h, nt, &F.q_slots_a));
         TRY(alloc(h, nt, &F.q_slots_b));
+        TRY(alloc(h, nt, &F.q_slots_c));
         TRY(alloc(h, nt, &F.q_pending));
-        TRY(alloc(h, 4, &F.q_ctr));
+        TRY(alloc(h, 6, &F.q_ctr));
         TRY(upload(h, HF.init_small, &F.init_small));
+        TRY(upload(h, HF.init_med, &F.init_med));
         TRY(upload(h, HF.init_big, &F.init_big));
         TRY(upload(h, HF.init_fwd, &F.init_fwd));
         TRY(upload(h, HF.init_bwd, &F.init_bwd));
         TRY(upload(h, HF.pend_factor, &F.pend_factor));
         TRY(upload(h, HF.nchild, &F.nchild));
         F.n_init_small = (int)HF.init_small.size();
+        F.n_init_med = (int)HF.init_med.size();
         F.n_init_big = (int)HF.init_big.size();
         F.n_init_fwd = (int)HF.init_fwd.size();
         F.n_init_bwd = (int)HF.init_bwd.size();
@@ -480,7 +484,7 @@ int scopf_trace(scopf_handle *h, int32_t enable) {
         h->trace = nullptr;
     }
     if (enable) {
-        const size_t bytes = sizeof(unsigned long long) * 16 * (size_t)std::max(1, h->HF.n_items);
+        const size_t bytes = sizeof(unsigned long long) * 20 * (size_t)std::max(1, h->HF.n_items);
         cudaError_t e = cudaMalloc(&h->trace, bytes);
         if (e != cudaSuccess) {
             h->trace = nullptr;
@@ -494,7 +498,7 @@ int scopf_trace(scopf_handle *h, int32_t enable) {
 }
 
 int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out) {
-    if (!h || h->host_only || !h->trace || kind < 0 || kind > 3 || !out)
+    if (!h || h->host_only || !h->trace || kind < 0 || kind > 4 || !out)
         return SCOPF_ERR_INVALID_ARG;
     const size_t n = 4 * (size_t)h->HF.n_items;
     CK(cudaStreamSynchronize(h->stream));
@@ -517,7 +521,7 @@ int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out) {
         int32_t *o = out + 6 * (size_t)i;
         o[0] = t1 - t0;
         o[1] = HF.item_parent[i];
-        o[2] = i < HF.n_items_small ? 1 : 0;
+        o[2] = i < HF.n_items_small ? 1 : (i < HF.n_items_med ? 2 : 3);
         o[3] = fmax;
         o[4] = npv;
         o[5] = HF.block[t0];

@@ -91,14 +91,21 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         }
     }
     const int nt = (int)sn.size();
-    // large fronts (f > kBigFront) and everything above them form the second
-    // factorization phase (one CTA per front); the rest is one warp per front
-    const int kBigFront = 64;
-    std::vector<char> big(nt, 0);
+    // Factorization phases, each closed upwards (a front's ancestors are in
+    // its phase or a later one): 2 = large fronts (f > 64, and the border
+    // fronts) and their ancestors, one CTA per front; 1 = medium fronts
+    // (32 < f <= 64) and their ancestors, one warp with a 64-row shared
+    // front each; 0 = the rest (tile-sized fronts with tile-sized subtrees),
+    // one warp with a 32-row shared tile each.
+    std::vector<char> phase(nt, 0);
     for (int t = 0; t < nt; t++)
-        if (sn[t].f > kBigFront || sn[t].border) big[t] = 1;
-    for (int t = 0; t < nt; t++)   // children precede parents within a block
-        if (big[t] && sn[t].parent_task >= 0) big[sn[t].parent_task] = 1;
+        phase[t] = (sn[t].f > 64 || sn[t].border) ? 2 : (sn[t].f > 32 ? 1 : 0);
+    for (int t = 0; t < nt; t++) {   // children precede parents within a block
+        const int p = sn[t].parent_task;
+        if (p >= 0) phase[p] = std::max(phase[p], phase[t]);
+    }
+    std::vector<char> big(nt, 0);
+    for (int t = 0; t < nt; t++) big[t] = phase[t] != 0;
     // Work items.  A maximal subtree of at most `cluster_cap` small fronts is
     // one item (a warp runs it in postorder with no scheduling in between);
     // the small fronts above such subtrees and every large front are items of
@@ -138,7 +145,7 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     std::iota(order.begin(), order.end(), 0);
     std::sort(order.begin(), order.end(), [&](int a, int b) {
         const int ra = item_root[a], rb = item_root[b];
-        if (big[ra] != big[rb]) return big[ra] < big[rb];
+        if (phase[ra] != phase[rb]) return phase[ra] < phase[rb];
         if (level[ra] != level[rb]) return level[ra] < level[rb];
         if (sn[ra].block != sn[rb].block) return sn[ra].block < sn[rb].block;
         if (ra != rb) return ra < rb;
@@ -160,6 +167,11 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     H.item_ptr.push_back(nt);
     H.n_items = (int)H.item_ptr.size() - 1;
     H.n_items_small = H.n_small > 0 ? H.item_of_task[H.n_small - 1] + 1 : 0;
+    {
+        int n_med = 0;   // tasks of phases 0 and 1
+        for (int t = 0; t < nt; t++) n_med += phase[t] < 2 ? 1 : 0;
+        H.n_items_med = n_med > 0 ? H.item_of_task[n_med - 1] + 1 : 0;
+    }
     H.front_off.resize(nt);
     H.vec_off.resize(nt);
     H.f.resize(nt);
@@ -234,17 +246,23 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
     H.item_child.clear();
     H.nchild.assign(ni, 0);
     H.pend_factor.assign(ni, 0);
+    auto item_phase = [&](int i) {
+        return i < H.n_items_small ? 0 : (i < H.n_items_med ? 1 : 2);
+    };
     for (int i = 0; i < ni; i++) {
         H.item_child_ptr[i + 1] = H.item_child_ptr[i] + (int)ich[i].size();
         for (int c : ich[i]) H.item_child.push_back(c);
         H.nchild[i] = (int)ich[i].size();
         for (int c : ich[i])
-            if (!(i >= H.n_items_small && c < H.n_items_small)) H.pend_factor[i]++;
+            if (item_phase(i) == item_phase(c)) H.pend_factor[i]++;
     }
     for (int i = 0; i < ni; i++) {
         if (H.nchild[i] == 0) H.init_fwd.push_back(i);
-        if (i < H.n_items_small && H.pend_factor[i] == 0) H.init_small.push_back(i);
-        if (i >= H.n_items_small && H.pend_factor[i] == 0) H.init_big.push_back(i);
+        if (H.pend_factor[i] == 0) {
+            if (item_phase(i) == 0) H.init_small.push_back(i);
+            if (item_phase(i) == 1) H.init_med.push_back(i);
+            if (item_phase(i) == 2) H.init_big.push_back(i);
+        }
         const int pi = H.item_parent[i];
         if (!H.item_is_border[i] && (pi < 0 || H.item_is_border[pi])) H.init_bwd.push_back(i);
     }
@@ -277,6 +295,7 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         return [&r](int a, int b) { return r[a] != r[b] ? r[a] > r[b] : a < b; };
     };
     std::stable_sort(H.init_small.begin(), H.init_small.end(), by(rank_up));
+    std::stable_sort(H.init_med.begin(), H.init_med.end(), by(rank_up));
     std::stable_sort(H.init_big.begin(), H.init_big.end(), by(rank_up));
     std::stable_sort(H.init_fwd.begin(), H.init_fwd.end(), by(rank_up));
     std::stable_sort(H.init_bwd.begin(), H.init_bwd.end(), by(rank_dn));

@@ -13,12 +13,12 @@ struct HostFronts {
     std::vector<int32_t> orig_off;
     // work items: contiguous task ranges (a subtree of small fronts run by
     // one warp in postorder, or a single front) and their tree
-    int n_items = 0, n_items_small = 0;
+    int n_items = 0, n_items_small = 0, n_items_med = 0;
     std::vector<int32_t> item_ptr, item_of_task, item_parent, item_is_border, item_child_ptr,
         item_child, item_cont;
     // ready-queue seeds: items runnable at the start of each sweep, and the
     // dependency counts the sweeps start from
-    std::vector<int32_t> init_small, init_big, init_fwd, init_bwd, pend_factor, nchild;
+    std::vector<int32_t> init_small, init_med, init_big, init_fwd, init_bwd, pend_factor, nchild;
     // packed records (see kernels.h: DevFront::task_rec, child_rec)
     std::vector<int32_t> task_rec, child_rec;
     int64_t front_elems = 0, vec_elems = 0, nnz_L = 0;

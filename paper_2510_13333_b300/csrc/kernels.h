@@ -115,9 +115,11 @@ struct DevFront {
     const double *ovals;          // scaled original entries in task order (n_orig)
     int64_t n_orig;
     // work items: item i is tasks [item_ptr[i], item_ptr[i+1]) in postorder
-    // (a subtree of small fronts, or one front); items [0, n_items_small)
-    // hold the small fronts
-    int n_items, n_items_small;
+    // (a subtree of small fronts, or one front).  Factorization phases:
+    // items [0, n_items_small) tile-sized fronts, [n_items_small,
+    // n_items_med) medium fronts and their ancestors, the rest large fronts
+    // and theirs
+    int n_items, n_items_small, n_items_med;
     int max_f;                    // largest front (rows), at least 32
     // packed records, 8 int32 each.  task_rec[t] (t <= n_tasks, the last a
     // sentinel): front_off (2 words), vec_off (2), f | npiv << 16,
@@ -129,13 +131,13 @@ struct DevFront {
     unsigned long long *trace;
     const int32_t *item_ptr, *item_parent, *item_child_ptr, *item_child;
     const int32_t *item_cont;     // backward sweep: child item run next by the same warp (-1 none)
-    // ready queues of items (two per run: factor phases 1/2, or forward and
-    // backward solve)
-    int *q_slots_a, *q_slots_b;   // n_items each: item ids in the order they became ready
-    int *q_ctr;                   // [a.claim, a.fill, b.claim, b.fill]
+    // ready queues of items (three per run: the factorization phases, or
+    // the forward and backward sweeps)
+    int *q_slots_a, *q_slots_b, *q_slots_c;   // n_items each: item ids as they became ready
+    int *q_ctr;                   // [a.claim, a.fill, b.claim, b.fill, c.claim, c.fill]
     int *q_pending;               // n_items: outstanding dependencies
-    const int32_t *init_small, *init_big, *init_fwd, *init_bwd;
-    int n_init_small, n_init_big, n_init_fwd, n_init_bwd;
+    const int32_t *init_small, *init_med, *init_big, *init_fwd, *init_bwd;
+    int n_init_small, n_init_med, n_init_big, n_init_fwd, n_init_bwd;
     const int32_t *pend_factor;   // dependencies counted by the factorization phases
     const int32_t *nchild;        // child items per item
 };

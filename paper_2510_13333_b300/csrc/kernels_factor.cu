@@ -25,6 +25,7 @@
 // The matrix handed to the factorization is the symmetric equilibration
 // D K D (Ruiz scaling, D > 0 diagonal): the inertia is unchanged (Sylvester)
 // and FP32 fronts keep far more accuracy than on the raw barrier-scaled KKT.
+#include <algorithm>
 #include <cmath>
 
 #include "dense_ldlt.cuh"
@@ -150,21 +151,23 @@ __device__ __forceinline__ void push_children(const QueueView &Q, const DevFront
     }
 }
 
-// both queues of a run: slots from their seed lists, counters, pending
-__global__ void k_queue_reset(int n, int *slots_a, const int32_t *init_a, int n_a, int *slots_b,
-                              const int32_t *init_b, int n_b, int *pending,
-                              const int32_t *pend, int *ctr) {
+// the queues of a run: slots from their seed lists, counters, pending
+struct QueueSeeds {
+    const int32_t *init[3];
+    int n[3];
+};
+__global__ void k_queue_reset(int n, int *slots_a, int *slots_b, int *slots_c, QueueSeeds seeds,
+                              int *pending, const int32_t *pend, int *ctr) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i < n) {
-        slots_a[i] = i < n_a ? init_a[i] : -1;
-        slots_b[i] = i < n_b ? init_b[i] : -1;
+        slots_a[i] = i < seeds.n[0] ? seeds.init[0][i] : -1;
+        slots_b[i] = i < seeds.n[1] ? seeds.init[1][i] : -1;
+        slots_c[i] = i < seeds.n[2] ? seeds.init[2][i] : -1;
         pending[i] = pend ? pend[i] : 0;
     }
-    if (i == 0) {
-        ctr[0] = 0;
-        ctr[1] = n_a;
-        ctr[2] = 0;
-        ctr[3] = n_b;
+    if (i < 3) {
+        ctr[2 * i] = 0;
+        ctr[2 * i + 1] = seeds.n[i];
     }
 }
 
@@ -191,6 +194,9 @@ QueueView queue_a(const DevFront &F, int n_items) {
 }
 QueueView queue_b(const DevFront &F, int n_items) {
     return QueueView{F.q_slots_b, F.q_ctr + 2, F.q_pending, n_items};
+}
+QueueView queue_c(const DevFront &F, int n_items) {
+    return QueueView{F.q_slots_c, F.q_ctr + 4, F.q_pending, n_items};
 }
 
 template <int GS>
@@ -454,50 +460,15 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
     }
 }
 
-// one medium buffer per CTA, taken by a warp with a bounded shared lock
-__device__ __forceinline__ bool take_medium(int *lock, int spin_limit) {
-    int ok = 1;
-    if ((threadIdx.x & 31) == 0) {
-        int spins = 0;
-        unsigned ns = 64;
-        while (atomicCAS(lock, 0, 1) != 0) {
-            if (++spins > spin_limit) {
-                ok = 0;
-                break;
-            }
-            __nanosleep(ns);
-            if (ns < 1024) ns <<= 1;
-        }
-        __threadfence_block();
-    }
-    ok = __shfl_sync(0xffffffffu, ok, 0);
-    __syncwarp();
-    return ok != 0;
-}
-__device__ __forceinline__ void give_medium(int *lock) {
-    __syncwarp();
-    if ((threadIdx.x & 31) == 0) {
-        __threadfence_block();
-        atomicExch(lock, 0);
-    }
-}
-
-// Phase 1: small fronts, one warp per front.
-constexpr int kFT = 256;   // threads per CTA of the phase-1 kernel
+// Phase 1: tile-sized fronts, one warp per front (32 x 33 shared tile each).
+constexpr int kFT = 256;   // threads per CTA of the warp-per-front phases
 template <typename T>
-__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 2) k_factor(DevFront F, T *__restrict__ fronts,
-                                                FactorStatus *st, QueueView Q, double pivot_tol,
-                                                int spin_limit) {
-    // dynamic shared memory: one 32 x 33 tile per warp, then the CTA's
-    // 64 x 65 medium buffer, then its lock
-    extern __shared__ __align__(16) unsigned char factor_smem[];
-    T (*tiles)[33] = reinterpret_cast<T (*)[33]>(factor_smem);
+__global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 3)
+    k_factor(DevFront F, T *__restrict__ fronts, FactorStatus *st, QueueView Q, double pivot_tol,
+             int spin_limit) {
+    extern __shared__ __align__(16) unsigned char tile_smem[];
     const int lane = threadIdx.x & 31;
-    T (*tile)[33] = tiles + 32 * (threadIdx.x >> 5);
-    T (*medium)[kMedF + 1] = reinterpret_cast<T (*)[kMedF + 1]>(tiles + 32 * (kFT / 32));
-    int *lock = reinterpret_cast<int *>(medium + kMedF);
-    if (threadIdx.x == 0) *lock = 0;
-    __syncthreads();
+    T (*tile)[33] = reinterpret_cast<T (*)[33]>(tile_smem) + 32 * (threadIdx.x >> 5);
     int n_pos = 0, n_neg = 0, n_zero = 0;
     int item = -1;
     while (true) {
@@ -509,26 +480,51 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 2) k_factor(DevFront
         TaskInfo ti = task_info(F, t0);
         for (int task = t0; task < t1; task++) {
             const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
-            if (ti.f <= 32) {
+            if (ti.f <= 32)
                 eliminate_front_tile<T>(F, fronts, ti, lane, tile, pivot_tol, n_pos, n_neg,
                                         n_zero);
-            } else if (ti.f <= kMedF) {
-                if (take_medium(lock, spin_limit)) {
-                    eliminate_front_medium<T>(F, fronts, ti, lane, medium, pivot_tol, n_pos,
-                                              n_neg, n_zero);
-                    give_medium(lock);
-                } else {
-                    if (lane == 0) atomicExch(&st->error, 1);
-                }
-            } else {
+            else   // not produced by the phase split; kept as a safe fallback
                 eliminate_front<T, 32>(F, fronts, ti, lane, pivot_tol, n_pos, n_neg, n_zero);
-            }
             __syncwarp();   // the next front of the item reads this one
             ti = nx;
         }
         if (F.trace && lane == 0) trace_item(F, 2, item, tc, ts);
         const int par = F.item_parent[item];
         item = (par >= 0 && par < F.n_items_small && warp_complete_child(Q, par)) ? par : -1;
+    }
+    if (lane == 0) {
+        if (n_pos) atomicAdd(&st->n_pos, n_pos);
+        if (n_neg) atomicAdd(&st->n_neg, n_neg);
+        if (n_zero) atomicAdd(&st->n_zero, n_zero);
+    }
+}
+
+// Phase 2: medium fronts and their ancestors (all f <= 64), one warp per
+// front with its own 64 x 65 shared front.
+template <typename T>
+__global__ void __launch_bounds__(kWT)
+    k_factor_med(DevFront F, T *__restrict__ fronts, FactorStatus *st, QueueView Q,
+                 double pivot_tol, int spin_limit) {
+    extern __shared__ __align__(16) unsigned char med_smem[];
+    const int lane = threadIdx.x & 31;
+    T (*M)[kMedF + 1] = reinterpret_cast<T (*)[kMedF + 1]>(med_smem) + kMedF * (threadIdx.x >> 5);
+    int n_pos = 0, n_neg = 0, n_zero = 0;
+    int item = -1;
+    while (true) {
+        const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
+        if (item < 0) item = warp_claim(Q, spin_limit, st, 1);
+        if (item < 0) break;
+        const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
+        const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per item
+        if (ti.f <= kMedF)
+            eliminate_front_medium<T>(F, fronts, ti, lane, M, pivot_tol, n_pos, n_neg, n_zero);
+        else   // not produced by the phase split; kept as a safe fallback
+            eliminate_front<T, 32>(F, fronts, ti, lane, pivot_tol, n_pos, n_neg, n_zero);
+        __syncwarp();
+        if (F.trace && lane == 0) trace_item(F, 3, item, tc, ts);
+        const int par = F.item_parent[item];
+        item = (par >= F.n_items_small && par < F.n_items_med && warp_complete_child(Q, par))
+                   ? par : -1;
     }
     if (lane == 0) {
         if (n_pos) atomicAdd(&st->n_pos, n_pos);
@@ -641,7 +637,7 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
             eliminate_front<T, kBT>(F, fronts, ti, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
         __syncthreads();   // orders every thread's writes before the release below
         if (threadIdx.x == 0) {
-            if (F.trace) trace_item(F, 3, item, tc, ts);
+            if (F.trace) trace_item(F, 4, item, tc, ts);
             const int par = F.item_parent[item];
             s_task = (par >= 0 && complete_child(Q, par)) ? par : -1;
         }
@@ -1157,40 +1153,56 @@ void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s) {
                                                                F.kkt_col, F.scale, F.kval, ovals);
 }
 
-void launch_queue_reset(const DevFront &F, const int32_t *init_a, int n_a, const int32_t *init_b,
-                        int n_b, const int32_t *pend, cudaStream_t s) {
+void launch_queue_reset(const DevFront &F, QueueSeeds seeds, const int32_t *pend, cudaStream_t s) {
     const int t = 256;
     const int n = F.n_items > 0 ? F.n_items : 1;
-    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, init_a, n_a, F.q_slots_b,
-                                                init_b, n_b, F.q_pending, pend, F.q_ctr);
+    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, F.q_slots_b, F.q_slots_c,
+                                                seeds, F.q_pending, pend, F.q_ctr);
+}
+
+// CTAs of `kernel` that fit on the device at once with `smem` bytes each
+static int resident_grid(const void *kernel, int threads, size_t smem) {
+    int dev = 0, sms = 148, occ = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kernel, threads, smem);
+    return sms * (occ > 0 ? occ : 1);
 }
 
 template <typename T>
 void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_tol,
                    int spin_limit, cudaStream_t s) {
-    // queue a: phase 1 (small fronts), queue b: phase 2 (large fronts)
-    launch_queue_reset(F, F.init_small, F.n_init_small, F.init_big, F.n_init_big, F.pend_factor, s);
-    const size_t sm1 = sizeof(T) * (33 * 32 * (kFT / 32) + kMedF * (kMedF + 1)) + 16;
-    static int grid1[2] = {0, 0};   // resident CTAs (float, double)
-    int &g1 = grid1[sizeof(T) == 4 ? 0 : 1];
-    if (!g1) {
+    // queues a, b, c: the three phases
+    QueueSeeds seeds{{F.init_small, F.init_med, F.init_big},
+                     {F.n_init_small, F.n_init_med, F.n_init_big}};
+    launch_queue_reset(F, seeds, F.pend_factor, s);
+    static int grids[2][2] = {{0, 0}, {0, 0}};   // [float, double][phase 1, 2]
+    const size_t sm1 = sizeof(T) * (size_t)(kFT / 32) * 32 * 33;
+    const size_t sm2 = sizeof(T) * (size_t)(kWT / 32) * kMedF * (kMedF + 1);
+    int *g = grids[sizeof(T) == 4 ? 0 : 1];
+    if (!g[0]) {
         for (const void *k : {(const void *)k_factor<float>, (const void *)k_factor<double>}) {
-            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 120 * 1024);
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
-        int dev = 0, sms = 148, occ = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_factor<T>, kFT, sm1);
-        g1 = sms * (occ > 0 ? occ : 1);
+        for (const void *k : {(const void *)k_factor_med<float>, (const void *)k_factor_med<double>}) {
+            cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 140 * 1024);
+            cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
+        }
+        g[0] = resident_grid((const void *)k_factor<T>, kFT, sm1);
+        g[1] = resident_grid((const void *)k_factor_med<T>, kWT, sm2);
     }
-    int grid = g1;
-    const int need = (F.n_items_small + kFT / 32 - 1) / (kFT / 32);
-    if (grid > need) grid = need;
-    if (F.n_items_small > 0)
-        k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, F.n_items_small), pivot_tol,
-                                           spin_limit);
-    const int nbig = F.n_items - F.n_items_small;
+    const int n1 = F.n_items_small, n2 = F.n_items_med - F.n_items_small;
+    if (n1 > 0) {
+        const int grid = std::min(g[0], (n1 + kFT / 32 - 1) / (kFT / 32));
+        k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, n1), pivot_tol, spin_limit);
+    }
+    if (n2 > 0) {
+        const int grid = std::min(g[1], (n2 + kWT / 32 - 1) / (kWT / 32));
+        k_factor_med<T><<<grid, kWT, sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
+                                               spin_limit);
+    }
+    const int nbig = F.n_items - F.n_items_med;
     if (nbig > 0) {
         int dev = 0, sms = 148;
         cudaGetDevice(&dev);
@@ -1205,7 +1217,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
         }
         int g2 = sms * 2;
         if (g2 > nbig) g2 = nbig;
-        k_factor_big<T><<<g2, kBT, kBigPanelBytes, s>>>(F, fronts, st, queue_b(F, nbig), pivot_tol,
+        k_factor_big<T><<<g2, kBT, kBigPanelBytes, s>>>(F, fronts, st, queue_c(F, nbig), pivot_tol,
                                                         spin_limit);
     }
 }
@@ -1238,8 +1250,9 @@ template <typename T>
 void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
                   const double *scale, const double *b, double *x, double *border_work,
                   FactorStatus *st, int spin_limit, cudaStream_t s) {
-    // queue a: forward sweep (all tasks), queue b: backward sweep (non-border)
-    launch_queue_reset(F, F.init_fwd, F.n_init_fwd, F.init_bwd, F.n_init_bwd, F.nchild, s);
+    // queue a: forward sweep (all items), queue b: backward sweep (non-border)
+    QueueSeeds seeds{{F.init_fwd, F.init_bwd, F.init_bwd}, {F.n_init_fwd, F.n_init_bwd, 0}};
+    launch_queue_reset(F, seeds, F.nchild, s);
     int grid = warp_grid();
     const int need = (F.n_items + kWT / 32 - 1) / (kWT / 32);
     if (grid > need) grid = need;
