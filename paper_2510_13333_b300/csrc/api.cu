@@ -113,6 +113,22 @@ int setup_device(scopf_handle *h) {
         TRY(upload(h, krow, &d.kkt_row));
     }
     TRY(upload(h, M.row_kind, &d.row_kind));
+    {
+        // stored position of the diagonal entry of every primal row (the
+        // inertia correction delta_w shifts exactly these)
+        std::vector<int64_t> pos;
+        for (int64_t i = 0; i < M.n_kkt; i++) {
+            if (M.row_kind[i] != 0) continue;
+            for (int64_t q = M.kkt_ptr[i]; q < M.kkt_ptr[i + 1]; q++)
+                if (M.kkt_col[q] == i) {
+                    pos.push_back(q);
+                    break;
+                }
+        }
+        h->n_pdiag = (int64_t)pos.size();
+        TRY(upload(h, pos, &h->pdiag_pos));
+        TRY(alloc(h, pos.size(), &h->pdiag_base));
+    }
     TRY(upload(h, M.row_index, &d.row_index));
     {
         std::vector<int8_t> is_long(M.n_kkt, 0);
@@ -241,6 +257,11 @@ int setup_device(scopf_handle *h) {
     }
     TRY(alloc(h, 1, &h->fstat));
     TRY(alloc(h, 1024, &h->red_scratch));
+    TRY(alloc(h, (size_t)ipm_partials(), &h->ipm_part));
+    for (int64_t i = 0; i < M.n; i++) {
+        if (std::isfinite(M.wl[i])) h->n_lower++;
+        if (std::isfinite(M.wu[i])) h->n_upper++;
+    }
     TRY(alloc(h, 16, &h->red_out));
     // iterate, NCL parameters, IPM scratch
     for (scopf_state *s : {&h->st, &h->dir, &h->trial}) {
@@ -656,6 +677,7 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
     launch_gradient(d, it->w, h->g, s);
     launch_diag_terms(d, it->w, it->zl, it->zu, it->s, it->zs, rho, delta_w, h->diag, s);
     launch_assemble(d, h->ev, h->diag, h->kval, s);
+    launch_diag_gather(h->n_pdiag, h->pdiag_pos, h->kval, h->pdiag_base, s);
     launch_dual_product(d, h->kval, h->g, it->lam, it->yc, h->gw, s);
     if (rhs) {
         RhsArgs a{it->w, it->r, it->t, it->s, it->lam, it->yc, it->zs, h->gw, h->c, lam_n, nu0_n,
@@ -671,7 +693,22 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
     h->assembled = true;
     h->factored = false;
     h->last_delta_w = delta_w;
+    h->assembled_delta_w = delta_w;
     h->last_rho = rho;
+    return SCOPF_OK;
+}
+
+// K(delta) from the assembled K(delta_a): the primal diagonal entries
+// become (assembled value) + (delta - delta_a); nothing else depends on
+// delta_w
+int set_delta_w(scopf_handle *h, double delta_w) {
+    if (!h->assembled) return SCOPF_ERR_NOT_FACTORED;
+    h->timer.begin(PH_ASSEMBLE, h->stream);
+    launch_diag_set(h->n_pdiag, h->pdiag_pos, h->pdiag_base, delta_w - h->assembled_delta_w,
+                    h->kval, h->stream);
+    h->timer.end(PH_ASSEMBLE, h->stream);
+    h->factored = false;
+    h->last_delta_w = delta_w;
     return SCOPF_OK;
 }
 
@@ -730,6 +767,9 @@ static int solve_once(scopf_handle *h, const double *b, double *x) {
 // iterative refinement: it converges where classical refinement with FP32
 // factors stalls, for condition numbers up to about 1/u_fp32^2).  The
 // preconditioner applications after the first count as refinement steps.
+// Gram-Schmidt coefficients, the Hessenberg column, its Givens rotations and
+// the small triangular solve stay on the device; the host reads one scalar
+// per Krylov step (the residual estimate) and one pair per residual check.
 int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel, int *steps) {
     cudaStream_t s = h->stream;
     const int64_t n = h->M.n_kkt;
@@ -738,48 +778,43 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         return mixed ? solve_once<float>(h, rhs, out) : solve_once<double>(h, rhs, out);
     };
     constexpr int m = 16;
+    const GmresLayout GL = gmres_layout(m);
     if (!h->kv) {
         TRY(alloc(h, (size_t)(m + 1) * n, &h->kv));
         TRY(alloc(h, (size_t)m * n, &h->kz));
         TRY(alloc(h, (size_t)kDotBlocks * kMaxKrylov, &h->kpart));
+        TRY(alloc(h, (size_t)GL.total, &h->kst));
     }
-    CK(cudaMemcpyAsync(h->res, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
-    once(h->res, x);
-    const double bnorm = device_maxabs(h, h->res, n);
-    const double bden = bnorm > 0 ? bnorm : 1.0;
-    std::vector<double> part((size_t)kDotBlocks * kMaxKrylov);
-    auto dots = [&](const double *V, int k, const double *w, double *out) {
-        launch_multi_dot(V, n, k, w, h->kpart, s);
-        cudaMemcpyAsync(part.data(), h->kpart, sizeof(double) * kDotBlocks * k,
-                        cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
-        for (int j = 0; j < k; j++) {
-            double a = 0;
-            for (int bb = 0; bb < kDotBlocks; bb++) a += part[(size_t)bb * k + j];
-            out[j] = a;
-        }
-    };
-    int it = 0;
-    double r = 0;
-    while (true) {
-        // r = b - K x
+    double *sc = h->kst + GL.sc;
+    // |b|_inf and |b - K x|_inf in one round trip
+    auto residual_check = [&](double &bn, double &rn) {
         h->timer.begin(PH_RESIDUAL, s);
         launch_residual(h->dm, h->kval, x, h->res, h->tmp_kkt, s);
         h->timer.end(PH_RESIDUAL, s);
-        r = device_maxabs(h, h->tmp_kkt, n) / bden;
+        reduce_maxabs2(h->res, h->tmp_kkt, n, h->red_out, h->red_scratch, s);
+        double v[2] = {0, 0};
+        cudaMemcpyAsync(v, h->red_out, sizeof(v), cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
+        bn = v[0];
+        rn = v[1];
+    };
+    CK(cudaMemcpyAsync(h->res, b, sizeof(double) * n, cudaMemcpyDeviceToDevice, s));
+    once(h->res, x);
+    double bnorm = 0, rn = 0;
+    residual_check(bnorm, rn);
+    const double bden = bnorm > 0 ? bnorm : 1.0;
+    int it = 0;
+    double r = rn / bden;
+    while (true) {
         if (h->opt.verbose >= 2)
             std::printf("    refine: %d preconditioner applications, |b-Kx|/|b| = %.3e (%s)\n", it,
                         r, mixed ? "fp32 factors" : "fp64 factors");
         if (!(r > h->opt.refine_tol) || it >= max_refine || !std::isfinite(r)) break;
-        // one FGMRES(m) cycle on K e = r
-        double beta = 0;
-        dots(h->tmp_kkt, 1, h->tmp_kkt, &beta);
-        beta = std::sqrt(beta);
-        if (!(beta > 0)) break;
-        launch_scale_copy(n, 1.0 / beta, h->tmp_kkt, h->kv, s);
-        double H[m + 1][m], cs[m], sn[m], g[m + 1];
-        for (int i = 0; i <= m; i++) g[i] = 0;
-        g[0] = beta;
+        // one FGMRES(m) cycle on K e = r (r = tmp_kkt, nonzero here)
+        launch_multi_dot(h->tmp_kkt, n, 1, h->tmp_kkt, h->kpart, s);
+        launch_dot_finish(h->kpart, 1, sc + 0, true, s);
+        launch_gmres_init(h->kst, m, s);
+        launch_scale_inv(n, sc + 0, h->tmp_kkt, h->kv, s);
         int jend = 0;
         const double target = h->opt.refine_tol * bnorm * 0.5;
         for (int j = 0; j < m && it < max_refine; j++) {
@@ -788,41 +823,27 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
             once(vj, zj);
             it++;
             launch_spmv(h->dm, h->kval, zj, w, s);
-            double hc[kMaxKrylov], hc2[kMaxKrylov];
-            dots(h->kv, j + 1, w, hc);
-            launch_multi_axpy(w, h->kv, n, j + 1, hc, s);
-            dots(h->kv, j + 1, w, hc2);
-            launch_multi_axpy(w, h->kv, n, j + 1, hc2, s);
-            for (int i = 0; i <= j; i++) H[i][j] = hc[i] + hc2[i];
-            double hn = 0;
-            dots(w, 1, w, &hn);
-            hn = std::sqrt(hn);
-            H[j + 1][j] = hn;
-            if (hn > 0) launch_scale_copy(n, 1.0 / hn, w, w, s);
-            for (int i = 0; i < j; i++) {
-                const double a = cs[i] * H[i][j] + sn[i] * H[i + 1][j];
-                H[i + 1][j] = -sn[i] * H[i][j] + cs[i] * H[i + 1][j];
-                H[i][j] = a;
-            }
-            const double den = std::hypot(H[j][j], H[j + 1][j]);
-            cs[j] = den > 0 ? H[j][j] / den : 1.0;
-            sn[j] = den > 0 ? H[j + 1][j] / den : 0.0;
-            H[j][j] = den;
-            H[j + 1][j] = 0;
-            g[j + 1] = -sn[j] * g[j];
-            g[j] = cs[j] * g[j];
+            // classical Gram-Schmidt, twice
+            launch_multi_dot(h->kv, n, j + 1, w, h->kpart, s);
+            launch_dot_finish(h->kpart, j + 1, h->kst + GL.c1, false, s);
+            launch_multi_axpy_dev(w, h->kv, n, j + 1, h->kst + GL.c1, 1.0, s);
+            launch_multi_dot(h->kv, n, j + 1, w, h->kpart, s);
+            launch_dot_finish(h->kpart, j + 1, h->kst + GL.c2, false, s);
+            launch_multi_axpy_dev(w, h->kv, n, j + 1, h->kst + GL.c2, 1.0, s);
+            launch_multi_dot(w, n, 1, w, h->kpart, s);
+            launch_dot_finish(h->kpart, 1, sc + 1, true, s);
+            launch_scale_inv(n, sc + 1, w, w, s);
+            launch_gmres_column(h->kst, m, j, s);
+            double gj = 0;
+            cudaMemcpyAsync(&gj, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
+            cudaStreamSynchronize(s);
             jend = j + 1;
-            if (std::fabs(g[j + 1]) <= target || !(hn > 0)) break;
+            if (!(gj > target)) break;
         }
-        double y[m];
-        for (int i = jend - 1; i >= 0; i--) {
-            double a = g[i];
-            for (int k = i + 1; k < jend; k++) a -= H[i][k] * y[k];
-            y[i] = H[i][i] != 0 ? a / H[i][i] : 0.0;
-        }
-        double negy[kMaxKrylov];
-        for (int i = 0; i < jend; i++) negy[i] = -y[i];
-        launch_multi_axpy(x, h->kz, n, jend, negy, s);
+        launch_gmres_solve(h->kst, m, jend, s);
+        launch_multi_axpy_dev(x, h->kz, n, jend, h->kst + GL.c1, 1.0, s);
+        residual_check(bnorm, rn);
+        r = rn / bden;
     }
     h->n_refine += it;
     FactorStatus fs;

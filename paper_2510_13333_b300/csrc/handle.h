@@ -107,12 +107,19 @@ struct scopf_handle {
     double *S = nullptr, *border_work = nullptr;
     double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
+    double *kst = nullptr;                                  // FGMRES small dense state
     double *ovals = nullptr;                                // scaled front originals
     scopf::FactorStatus *fstat = nullptr;
     double *red_scratch = nullptr, *red_out = nullptr;
     bool assembled = false, factored = false;
     int factored_precision = SCOPF_PREC_FP64;
     double last_delta_w = 0.0, last_rho = 0.0;
+    double assembled_delta_w = 0.0;           // delta_w of the last full assembly
+    int64_t n_lower = 0, n_upper = 0;         // finite variable bounds
+    double *ipm_part = nullptr;               // per-block partials of the IPM reductions
+    int64_t n_pdiag = 0;                      // primal rows
+    const int64_t *pdiag_pos = nullptr;       // their diagonal entries in kval
+    double *pdiag_base = nullptr;             // those entries at the last assembly
     // iterate and NCL parameters owned by the handle
     scopf_state st{};
     double *lam_n = nullptr, *nu0_n = nullptr;
@@ -132,9 +139,11 @@ struct scopf_handle {
 
 namespace scopf {
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res);
+int ipm_partials();   // doubles of the IPM reduction partial buffer
 int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n,
                   const double *nu0_n, double rho, double mu, double delta_w, double *rhs);
 int factor_impl(scopf_handle *h, int precision, int inertia[3]);
+int set_delta_w(scopf_handle *h, double delta_w);
 int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel,
                int *steps);
 double device_maxabs(scopf_handle *h, const double *x, int64_t n);

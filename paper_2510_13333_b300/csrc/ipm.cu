@@ -334,6 +334,8 @@ struct Timer {
 
 }  // namespace
 
+int ipm_partials() { return kB * 9; }
+
 // ===========================================================================
 struct Ipm {
     scopf_handle *h;
@@ -347,20 +349,18 @@ struct Ipm {
     bool force_fp64 = false;
     int fallbacks = 0;
 
+    // bound counts and the partial-sum buffer are set up once per handle
     explicit Ipm(scopf_handle *hh) : h(hh), o(hh->opt), s(hh->stream) {
         const Model &M = h->M;
         n = M.n;
         m = M.m;
         p = M.p;
         D = Dev{h->wl, h->wu, h->dm.comp1, h->dm.comp2, n, m, p};
-        for (int64_t i = 0; i < n; i++) {
-            if (std::isfinite(M.wl[i])) n_il++;
-            if (std::isfinite(M.wu[i])) n_iu++;
-        }
+        n_il = h->n_lower;
+        n_iu = h->n_upper;
         part.resize(kB * 9);
-        cudaMalloc(&dpart, sizeof(double) * kB * 9);
+        dpart = h->ipm_part;
     }
-    ~Ipm() { cudaFree(dpart); }
 
     // fetch kB x k partials and combine in block order
     void fetch(int k) {
@@ -488,12 +488,14 @@ struct Ipm {
                     ? (dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last))
                     : 0.0;
         tries = 0;
-        double assembled = 0.0;   // K at delta = 0 and the RHS were assembled by the caller
+        // K at delta = 0 and the RHS were assembled by the caller; other
+        // delta_w values only shift the primal diagonal
+        double current = 0.0;
         while (true) {
-            if (delta != assembled) {
-                int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, delta, nullptr);
+            if (delta != current) {
+                int r = set_delta_w(h, delta);
                 if (r != SCOPF_OK) return r;
-                assembled = delta;
+                current = delta;
             }
             const int prec = force_fp64 ? SCOPF_PREC_FP64 : h->precision;
             int in[3];

@@ -79,6 +79,40 @@ void launch_multi_axpy(double *w, const double *V, int64_t n, int k, const doubl
                        cudaStream_t s);
 // y = a * x
 void launch_scale_copy(int64_t n, double a, const double *x, double *y, cudaStream_t s);
+
+// ---- FGMRES(m) with its small dense algebra on the device (no host round
+// trip per Gram-Schmidt pass).  State layout (doubles), m <= kMaxKrylov:
+// H (m+1) x m column-major, cs[m], sn[m], g[m+1], coef[kMaxKrylov] (first
+// pass), coef2[kMaxKrylov] (second pass), sc[8] (0 beta, 1 h_{j+1,j},
+// 2 |g_{j+1}|)
+struct GmresLayout {
+    int m;
+    int H, cs, sn, g, c1, c2, sc, total;
+};
+GmresLayout gmres_layout(int m);
+// out[j] = sum over the kDotBlocks partials of V_j' w (fixed order); with
+// take_sqrt the single result is replaced by its square root
+void launch_dot_finish(const double *partial, int k, double *out, bool take_sqrt, cudaStream_t s);
+// w -= sum_j c[j] V_j, coefficients in device memory (sign: +1 or -1)
+void launch_multi_axpy_dev(double *w, const double *V, int64_t n, int k, const double *c,
+                           double sign, cudaStream_t s);
+// y = x / *den (y = 0 if *den == 0)
+void launch_scale_inv(int64_t n, const double *den, const double *x, double *y, cudaStream_t s);
+// new cycle: g = beta e1 (beta = sc[0])
+void launch_gmres_init(double *st, int m, cudaStream_t s);
+// column j: H(:, j) = coef + coef2, H(j+1, j) = sc[1]; previous Givens
+// rotations, a new one, g updated; sc[2] = |g(j+1)|
+void launch_gmres_column(double *st, int m, int j, cudaStream_t s);
+// y = H(0:k, 0:k)^-1 g(0:k) by back substitution, stored (negated) in coef
+void launch_gmres_solve(double *st, int m, int k, cudaStream_t s);
+// base[i] = kval[pos[i]];  kval[pos[i]] = base[i] + shift
+void launch_diag_gather(int64_t n, const int64_t *pos, const double *kval, double *base,
+                        cudaStream_t s);
+void launch_diag_set(int64_t n, const int64_t *pos, const double *base, double shift,
+                     double *kval, cudaStream_t s);
+// out[0] = max |a|, out[1] = max |b| (two deterministic reductions)
+void reduce_maxabs2(const double *a, const double *b, int64_t n, double *d_out, double *scratch,
+                    cudaStream_t s);
 // y = K x (FP64)
 void launch_spmv(const DevModel &M, const double *kval, const double *x, double *y,
                  cudaStream_t s);

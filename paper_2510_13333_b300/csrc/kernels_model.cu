@@ -384,7 +384,154 @@ __global__ void k_scale_copy(int64_t n, double a, const double *__restrict__ x,
     if (i < n) y[i] = a * x[i];
 }
 
+// one warp per column: lanes stride over the partials, then a fixed-order
+// warp reduction
+__global__ void k_dot_finish(const double *__restrict__ partial, int k, double *__restrict__ out,
+                             int take_sqrt) {
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j >= k) return;
+    double a = 0.0;
+    for (int b = lane; b < kDotBlocks; b += 32) a += partial[(int64_t)b * k + j];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[j] = take_sqrt ? sqrt(fmax(a, 0.0)) : a;
+}
+
+__global__ void k_multi_axpy_dev(double *__restrict__ w, const double *__restrict__ V, int64_t n,
+                                 int k, const double *__restrict__ c, double sign) {
+    __shared__ double cs[kMaxKrylov];
+    if (threadIdx.x < k) cs[threadIdx.x] = sign * c[threadIdx.x];
+    __syncthreads();
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int j = 0; j < k; j++) acc -= cs[j] * V[(int64_t)j * n + i];
+    w[i] = acc;
+}
+
+__global__ void k_scale_inv(int64_t n, const double *__restrict__ den, const double *__restrict__ x,
+                            double *__restrict__ y) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = *den;
+    y[i] = d != 0.0 ? x[i] / d : 0.0;
+}
+
+__global__ void k_gmres_init(double *st, GmresLayout L) {
+    for (int i = threadIdx.x; i <= L.m; i += blockDim.x) st[L.g + i] = 0.0;
+    __syncthreads();
+    if (threadIdx.x == 0) st[L.g] = st[L.sc + 0];
+}
+
+// Givens rotations on the Hessenberg column (Saad, Iterative Methods for
+// Sparse Linear Systems, Alg. 6.9 with the flexible variant of Alg. 9.6)
+__global__ void k_gmres_column(double *st, GmresLayout L, int j) {
+    if (threadIdx.x != 0) return;
+    double *H = st + L.H;
+    const int ld = L.m + 1;
+    double *col = H + (int64_t)j * ld;
+    for (int i = 0; i <= j; i++) col[i] = st[L.c1 + i] + st[L.c2 + i];
+    col[j + 1] = st[L.sc + 1];
+    double *cs = st + L.cs, *sn = st + L.sn, *g = st + L.g;
+    for (int i = 0; i < j; i++) {
+        const double a = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = a;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    cs[j] = den > 0.0 ? col[j] / den : 1.0;
+    sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    st[L.sc + 2] = fabs(g[j + 1]);
+}
+
+__global__ void k_gmres_solve(double *st, GmresLayout L, int k) {
+    if (threadIdx.x != 0) return;
+    const double *H = st + L.H;
+    const int ld = L.m + 1;
+    double y[kMaxKrylov];
+    for (int i = k - 1; i >= 0; i--) {
+        double a = st[L.g + i];
+        for (int q = i + 1; q < k; q++) a -= H[(int64_t)q * ld + i] * y[q];
+        const double d = H[(int64_t)i * ld + i];
+        y[i] = d != 0.0 ? a / d : 0.0;
+    }
+    for (int i = 0; i < k; i++) st[L.c1 + i] = -y[i];
+}
+
+__global__ void k_diag_gather(int64_t n, const int64_t *__restrict__ pos,
+                              const double *__restrict__ kval, double *__restrict__ base) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) base[i] = kval[pos[i]];
+}
+
+__global__ void k_diag_set(int64_t n, const int64_t *__restrict__ pos,
+                           const double *__restrict__ base, double shift,
+                           double *__restrict__ kval) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) kval[pos[i]] = base[i] + shift;
+}
+
 }  // namespace
+
+void launch_diag_gather(int64_t n, const int64_t *pos, const double *kval, double *base,
+                        cudaStream_t s) {
+    if (n) k_diag_gather<<<nblocks(n), kThreads, 0, s>>>(n, pos, kval, base);
+}
+
+void launch_diag_set(int64_t n, const int64_t *pos, const double *base, double shift,
+                     double *kval, cudaStream_t s) {
+    if (n) k_diag_set<<<nblocks(n), kThreads, 0, s>>>(n, pos, base, shift, kval);
+}
+
+GmresLayout gmres_layout(int m) {
+    GmresLayout L;
+    L.m = m;
+    L.H = 0;
+    L.cs = L.H + (m + 1) * m;
+    L.sn = L.cs + m;
+    L.g = L.sn + m;
+    L.c1 = L.g + m + 1;
+    L.c2 = L.c1 + kMaxKrylov;
+    L.sc = L.c2 + kMaxKrylov;
+    L.total = L.sc + 8;
+    return L;
+}
+
+void launch_dot_finish(const double *partial, int k, double *out, bool take_sqrt, cudaStream_t s) {
+    k_dot_finish<<<1, 32 * k, 0, s>>>(partial, k, out, take_sqrt ? 1 : 0);
+}
+
+void launch_multi_axpy_dev(double *w, const double *V, int64_t n, int k, const double *c,
+                           double sign, cudaStream_t s) {
+    if (n) k_multi_axpy_dev<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, c, sign);
+}
+
+void launch_scale_inv(int64_t n, const double *den, const double *x, double *y, cudaStream_t s) {
+    if (n) k_scale_inv<<<nblocks(n), kThreads, 0, s>>>(n, den, x, y);
+}
+
+void launch_gmres_init(double *st, int m, cudaStream_t s) {
+    k_gmres_init<<<1, 64, 0, s>>>(st, gmres_layout(m));
+}
+
+void launch_gmres_column(double *st, int m, int j, cudaStream_t s) {
+    k_gmres_column<<<1, 32, 0, s>>>(st, gmres_layout(m), j);
+}
+
+void launch_gmres_solve(double *st, int m, int k, cudaStream_t s) {
+    k_gmres_solve<<<1, 32, 0, s>>>(st, gmres_layout(m), k);
+}
+
+void reduce_maxabs2(const double *a, const double *b, int64_t n, double *d_out, double *scratch,
+                    cudaStream_t s) {
+    k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(a, n, scratch);
+    k_reduce<0><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
+    k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(b, n, scratch + kReduceBlocks);
+    k_reduce<0><<<1, kThreads, 0, s>>>(scratch + kReduceBlocks, kReduceBlocks, d_out + 1);
+}
 
 void launch_multi_dot(const double *V, int64_t n, int k, const double *w, double *partial,
                       cudaStream_t s) {
