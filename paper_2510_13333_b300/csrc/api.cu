@@ -224,6 +224,8 @@ int setup_device(scopf_handle *h) {
         F.n_items_small = HF.n_items_small;
         F.n_items_med = HF.n_items_med;
         TRY(upload(h, HF.item_ptr, &F.item_ptr));
+        F.n_rows = (int64_t)HF.vpos_of_row.size();
+        TRY(upload(h, HF.vpos_of_row, &F.vpos_of_row));
         {
             const int32_t *tr = nullptr, *cr = nullptr;
             TRY(upload(h, HF.task_rec, &tr));

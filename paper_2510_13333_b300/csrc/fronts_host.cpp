@@ -392,6 +392,9 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         r[5] = H.child_ptr[t];
         r[6] = (int32_t)H.orig_ptr[t];
     }
+    H.vpos_of_row.assign(M.n_kkt, -1);
+    for (int t = 0; t < nt; t++)
+        for (int i = 0; i < H.npiv[t]; i++) H.vpos_of_row[H.rows[H.vec_off[t] + i]] = H.vec_off[t] + i;
     H.child_rec.assign(8 * H.child.size(), 0);
     for (size_t q = 0; q < H.child.size(); q++) {
         const int c = H.child[q];

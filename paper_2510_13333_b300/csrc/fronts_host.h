@@ -21,6 +21,7 @@ struct HostFronts {
     std::vector<int32_t> init_small, init_med, init_big, init_fwd, init_bwd, pend_factor, nchild;
     // packed records (see kernels.h: DevFront::task_rec, child_rec)
     std::vector<int32_t> task_rec, child_rec;
+    std::vector<int64_t> vpos_of_row;   // per KKT row: vector slot of its pivot, -1 border
     int64_t front_elems = 0, vec_elems = 0, nnz_L = 0;
     double flops = 0;
 };

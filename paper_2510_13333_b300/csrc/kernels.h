@@ -161,6 +161,10 @@ struct DevFront {
     // child slot q: front_off (2), vec_off (2), rel_off, f | npiv << 16,
     // task id, 0
     const int4 *task_rec, *child_rec;
+    // vector slot of every KKT row's pivot (-1 for border rows): the forward
+    // sweep finds D b there
+    int64_t n_rows;
+    const int64_t *vpos_of_row;
     // scheduler trace (NULL = off): 4 kinds x n_items x 4 uint64
     unsigned long long *trace;
     const int32_t *item_ptr, *item_parent, *item_child_ptr, *item_child;

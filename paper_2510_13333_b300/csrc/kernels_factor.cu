@@ -751,21 +751,14 @@ __global__ void k_dense_trailing(double *S, int n, int k0, int k1) {
 // triangular solve runs on shuffles
 template <typename T, int NP>
 __device__ __forceinline__ void fwd_small(const DevFront &F, const T *__restrict__ L,
-                                          T *__restrict__ v, const int64_t *__restrict__ rows,
-                                          const double *__restrict__ b,
-                                          const double *__restrict__ scale,
-                                          const T *__restrict__ vec, const TaskInfo &ti, int lane,
-                                          T *sv) {
+                                          T *__restrict__ v, const T *__restrict__ vec,
+                                          const TaskInfo &ti, int lane, T *sv) {
     const int f = ti.f, np = ti.np;
     T Lr[NP];
 #pragma unroll
     for (int c = 0; c < NP; c++) Lr[c] = (c < np && lane > c && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
     const T dl = lane < np ? L[(int64_t)lane * f + lane] : (T)1;
-    T vi = (T)0;
-    if (lane < np) {
-        const int64_t r = rows[lane];
-        vi = (T)(scale[r] * b[r]);
-    }
+    T vi = lane < np ? v[lane] : (T)0;   // D b, placed in the front's slots before the sweep
     sv[lane] = vi;
     __syncwarp();
     for (int q0 = ti.c0; q0 < ti.c1; q0 += 4) {
@@ -803,44 +796,64 @@ __device__ __forceinline__ void fwd_small(const DevFront &F, const T *__restrict
     if (lane < f) v[lane] = vi;
 }
 
-// Forward sweep of one front: gather D b on its pivot rows plus the
-// children's update vectors, then y = D^-1 L^-1 (.) on the pivot rows and
-// the update vector -L21 y for the parent on the others.
+// Forward sweep of one front: D b on its pivot rows (placed in the front's
+// vector slots before the sweep) plus the children's update vectors, then
+// y = D^-1 L^-1 (.) on the pivot rows and the update vector -L21 y for the
+// parent on the others.
 template <typename T>
 __device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict__ fronts,
-                                          T *__restrict__ vec, const double *__restrict__ b,
-                                          const double *__restrict__ scale, const TaskInfo &ti,
-                                          int lane, T *sv) {
+                                          T *__restrict__ vec, const TaskInfo &ti, int lane,
+                                          T *sv) {
     const int f = ti.f, np = ti.np;
     const T *L = fronts + ti.front_off;
     T *v = vec + ti.vo;
-    const int64_t *rows = F.rows + ti.vo;
     if (f <= 32) {
         if (np <= 8)
-            fwd_small<T, 8>(F, L, v, rows, b, scale, vec, ti, lane, sv);
+            fwd_small<T, 8>(F, L, v, vec, ti, lane, sv);
         else
-            fwd_small<T, 32>(F, L, v, rows, b, scale, vec, ti, lane, sv);
+            fwd_small<T, 32>(F, L, v, vec, ti, lane, sv);
         return;
     }
     // f > 32: the front's vector is staged in the warp's shared buffer; the
     // pivot block is solved in 32-row tiles (rows in registers, shuffles),
     // and the update rows take the mat-vec -L21 y with independent loads
-    for (int i = lane; i < f; i += 32) {
-        T x = (T)0;
-        if (i < np) {
-            const int64_t r = rows[i];
-            x = (T)(scale[r] * b[r]);
-        }
-        sv[i] = x;
-    }
+    for (int i = lane; i < f; i += 32) sv[i] = i < np ? v[i] : (T)0;
     __syncwarp();
-    for (int q = ti.c0; q < ti.c1; q++) {
-        const ChildInfo c = child_info(F, q);
-        const int nu = c.fc - c.npc;
-        const T *vc = vec + c.vo + c.npc;
-        const int32_t *rel = F.rel + c.rel_off;
-        for (int i = lane; i < nu; i += 32) sv[rel[i]] += vc[i];
-        __syncwarp();
+    // children four at a time: all their loads in flight, then the adds in
+    // a fixed order (child by child within each 32-row chunk)
+    for (int q0 = ti.c0; q0 < ti.c1; q0 += 4) {
+        int nuk[4];
+        const T *vck[4];
+        const int32_t *relk[4];
+        int numax = 0;
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            nuk[k] = 0;
+            vck[k] = vec;
+            relk[k] = F.rel;
+            if (q0 + k < ti.c1) {
+                const ChildInfo c = child_info(F, q0 + k);
+                nuk[k] = c.fc - c.npc;
+                vck[k] = vec + c.vo + c.npc;
+                relk[k] = F.rel + c.rel_off;
+                numax = max(numax, nuk[k]);
+            }
+        }
+        for (int i0 = 0; i0 < numax; i0 += 32) {
+            int rr[4];
+            T vv[4];
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                const int i = i0 + lane;
+                rr[k] = i < nuk[k] ? relk[k][i] : -1;
+                vv[k] = i < nuk[k] ? vck[k][i] : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < 4; k++) {
+                if (rr[k] >= 0) sv[rr[k]] += vv[k];
+                __syncwarp();
+            }
+        }
     }
     for (int k0 = 0; k0 < np; k0 += 32) {
         const int kn = min(32, np - k0);
@@ -879,8 +892,7 @@ __device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict
 // block's contribution to the border right-hand side)
 template <typename T>
 __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
-    k_solve_fwd(DevFront F, const T *__restrict__ fronts, T *__restrict__ vec,
-                const double *__restrict__ b, const double *__restrict__ scale, QueueView Q,
+    k_solve_fwd(DevFront F, const T *__restrict__ fronts, T *__restrict__ vec, QueueView Q,
                 FactorStatus *st, int spin_limit) {
     extern __shared__ unsigned char solve_smem[];
     const int lane = threadIdx.x & 31;
@@ -895,7 +907,7 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
         TaskInfo ti = task_info(F, t0);
         for (int task = t0; task < t1; task++) {
             const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
-            fwd_front<T>(F, fronts, vec, b, scale, ti, lane, sv);
+            fwd_front<T>(F, fronts, vec, ti, lane, sv);
             __syncwarp();
             ti = nx;
         }
@@ -903,6 +915,17 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
         const int par = F.item_parent[item];
         item = (par >= 0 && warp_complete_child(Q, par)) ? par : -1;
     }
+}
+
+// vec[vpos[r]] = scale[r] b[r] for every block row r (its pivot slot)
+template <typename T>
+__global__ void k_rhs_to_fronts(int64_t n, const int64_t *__restrict__ vpos,
+                                const double *__restrict__ scale, const double *__restrict__ b,
+                                T *__restrict__ vec) {
+    int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= n) return;
+    const int64_t p = vpos[r];
+    if (p >= 0) vec[p] = (T)(scale[r] * b[r]);
 }
 
 // Border right-hand side y = D b_border + sum_k (update vector of block k's
@@ -1009,13 +1032,23 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
     for (int k0 = ((np - 1) >> 5) << 5; k0 >= 0; k0 -= 32) {
         const int kn = min(32, np - k0);
         T zi = lane < kn ? sv[k0 + lane] : (T)0;
-        for (int j = 0; j < kn; j++) {
-            const T *col = L + (int64_t)(k0 + j) * f;
-            T p = (T)0;
-#pragma unroll 4
-            for (int i = k0 + kn + lane; i < f; i += 32) p += col[i] * sv[i];
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == j) zi -= p;
+        // eight column dot products at a time: their loads are independent
+        for (int j0 = 0; j0 < kn; j0 += 8) {
+            T pj[8];
+#pragma unroll
+            for (int u = 0; u < 8; u++) pj[u] = (T)0;
+            for (int i = k0 + kn + lane; i < f; i += 32) {
+                const T xi = sv[i];
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (j0 + u < kn) pj[u] += L[(int64_t)(k0 + j0 + u) * f + i] * xi;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                T p = pj[u];
+                for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
+                if (lane == j0 + u) zi -= p;
+            }
         }
         T Lr[32];
 #pragma unroll
@@ -1070,6 +1103,8 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
 }
 
 // ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
+// one thread per row: a warp's rows are contiguous, so after the first
+// entry of each row the later ones come from L1
 __global__ void k_ruiz(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
                        const double *__restrict__ kval, const double *__restrict__ s_in,
                        double *__restrict__ s_out, const int8_t *__restrict__ is_long) {
@@ -1133,8 +1168,9 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     const int64_t n = M.n_kkt;
     const int g = (int)((n + t - 1) / t);
     const int gl = (int)((32 * M.n_long + t - 1) / t);
-    k_fill<<<g, t, 0, s>>>(n, 1.0, scale);
-    double *a = scale, *b = tmp;
+    // start in the buffer that makes the last sweep land in `scale`
+    double *a = (iters & 1) ? tmp : scale, *b = (iters & 1) ? scale : tmp;
+    k_fill<<<g, t, 0, s>>>(n, 1.0, a);
     for (int it = 0; it < iters; it++) {
         k_ruiz<<<g, t, 0, s>>>(n, M.kkt_ptr, M.kkt_col, kval, a, b, M.is_long);
         if (M.n_long)
@@ -1264,8 +1300,9 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, b, scale, queue_a(F, F.n_items), st,
-                                         spin_limit);
+    k_rhs_to_fronts<T><<<(int)((F.n_rows + 255) / 256), 256, 0, s>>>(F.n_rows, F.vpos_of_row,
+                                                                     scale, b, vec);
+    k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, queue_a(F, F.n_items), st, spin_limit);
     {
         const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
         k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
