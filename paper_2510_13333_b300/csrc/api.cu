@@ -221,6 +221,13 @@ int setup_device(scopf_handle *h) {
         F.n_items = HF.n_items;
         F.max_f = 32;
         for (int t = 0; t < HF.n_tasks; t++) F.max_f = std::max(F.max_f, (int)HF.f[t]);
+        // the large-front kernel stages np x f panels up to 96 KB (FP64)
+        F.big_panel = 1;
+        const int t3 = HF.n_items > HF.n_items_med ? HF.item_ptr[HF.n_items_med] : HF.n_tasks;
+        for (int t = t3; t < HF.n_tasks; t++) {
+            const int64_t pe = (int64_t)HF.f[t] * HF.npiv[t];
+            if (pe <= 12288) F.big_panel = std::max<int>(F.big_panel, (int)pe);
+        }
         F.n_items_small = HF.n_items_small;
         F.n_items_med = HF.n_items_med;
         TRY(upload(h, HF.item_ptr, &F.item_ptr));

@@ -155,6 +155,7 @@ struct DevFront {
     // and theirs
     int n_items, n_items_small, n_items_med;
     int max_f;                    // largest front (rows), at least 32
+    int big_panel;                // largest np x f of the large-front phase (elements, capped)
     // packed records, 8 int32 each.  task_rec[t] (t <= n_tasks, the last a
     // sentinel): front_off (2 words), vec_off (2), f | npiv << 16,
     // first child slot, first original entry, parent.  child_rec[q] for

@@ -631,7 +631,7 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
         const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per large item
-        if ((int64_t)ti.f * ti.np <= kBigPanel)
+        if ((int64_t)ti.f * ti.np <= F.big_panel)
             eliminate_front_big<T>(F, fronts, ti, pivot_tol, n_pos, n_neg, n_zero);
         else
             eliminate_front<T, kBT>(F, fronts, ti, threadIdx.x, pivot_tol, n_pos, n_neg, n_zero);
@@ -1240,21 +1240,21 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     }
     const int nbig = F.n_items - F.n_items_med;
     if (nbig > 0) {
-        int dev = 0, sms = 148;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_factor_big<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kBigPanelBytes);
-            cudaFuncSetAttribute(k_factor_big<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                 kBigPanelBytes);
-            attr = true;
+        // shared panel sized to the largest np x f of this phase (at most
+        // kBigPanel elements); larger panels take the global-memory path
+        const size_t sm3 = sizeof(T) * (size_t)std::max(1, F.big_panel);
+        static int g3[2] = {0, 0};
+        static size_t g3_sm[2] = {0, 0};
+        const int pi = sizeof(T) == 4 ? 0 : 1;
+        if (g3_sm[pi] != sm3) {
+            for (const void *k : {(const void *)k_factor_big<float>, (const void *)k_factor_big<double>})
+                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigPanelBytes);
+            g3[pi] = resident_grid((const void *)k_factor_big<T>, kBT, sm3);
+            g3_sm[pi] = sm3;
         }
-        int g2 = sms * 2;
-        if (g2 > nbig) g2 = nbig;
-        k_factor_big<T><<<g2, kBT, kBigPanelBytes, s>>>(F, fronts, st, queue_c(F, nbig), pivot_tol,
-                                                        spin_limit);
+        const int grid = std::min(g3[pi], nbig);
+        k_factor_big<T><<<grid, kBT, sm3, s>>>(F, fronts, st, queue_c(F, nbig), pivot_tol,
+                                               spin_limit);
     }
 }
 
