@@ -35,6 +35,25 @@ FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
 FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 
 
+# DRAM bytes (read + write) of one solve's forward and backward sweeps,
+# from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
+# valid only for the sweep kernels' source it was taken with
+SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
+                 "sha1": "8561b4d3ff2b1dc0e98e2cc723a11dcac7b96df1",
+                 "bytes_per_solve": 255.4e6 + 305.9e6}
+
+
+def sweep_traffic():
+    import hashlib
+    try:
+        with open(os.path.join(ROOT, SWEEP_TRAFFIC["source"]), "rb") as fh:
+            if hashlib.sha1(fh.read()).hexdigest() != SWEEP_TRAFFIC["sha1"]:
+                return None
+    except OSError:
+        return None
+    return SWEEP_TRAFFIC["bytes_per_solve"]
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -193,6 +212,8 @@ def run_ours(args):
     def step(l):
         return l.scopf_newton_step(st, lam_n, nu0_n, rho, mu, dw_last, direction)
 
+    launches = [0]
+
     def timed(l, k):
         for _ in range(args.warmup):
             step(l)
@@ -203,6 +224,7 @@ def run_ours(args):
         s = torch.cuda.current_stream()
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         l.scopf_timing(True)
+        n0 = P.scopf_launch_count()
         torch.cuda.nvtx.range_push("timed")
         e0.record(s)
         for _ in range(k):
@@ -210,6 +232,7 @@ def run_ours(args):
         e1.record(s)
         torch.cuda.nvtx.range_pop()
         torch.cuda.synchronize()
+        launches[0] = P.scopf_launch_count() - n0
         phases = l.scopf_timing(False)
         ms = e0.elapsed_time(e1)
         if dist:
@@ -221,6 +244,7 @@ def run_ours(args):
     clocks = Clocks()
     clocks.start()
     ms_mixed, ph_mixed = timed(lib, args.steps)
+    launches_mixed = launches[0]
     clk = clocks.stop()
     lib.set_precision(P.PREC_FP64)
     ms_fp64, ph_fp64 = timed(lib, max(2, args.steps // 4))
@@ -284,13 +308,14 @@ def run_ours(args):
                 "kernel": "k_factor<float> (persistent supernodal LDL^T, all blocks)",
                 "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
     else:
-        # forward + backward sweeps read every FP32 factor entry once each
+        # one solve = forward sweep + border solve + backward sweep: every FP32
+        # factor entry is read twice, plus D b in, x out and the scaling
         bytes_ = 2 * 4 * sz.nnz_L + 3 * 8 * sz.n_kkt
         achieved = bytes_ / (sol_ms / sol_calls / 1e3) / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "kernel": "k_solve_fwd/k_solve_bwd<float> (multifrontal sweeps)",
-                "peak_kind": peak_kind}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": sweep_traffic(),
+                "kernel": "k_solve_fwd + k_border_solve + k_solve_bwd <float> (one solve)",
+                "algorithmic_bytes": bytes_, "peak_kind": peak_kind}
     try:
         cpu_s, cpu_desc, cores = oracle_step_sample()
         cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
@@ -298,7 +323,6 @@ def run_ours(args):
     except Exception as exc:  # keep the GPU number even if the CPU sample fails
         cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                "sample": f"failed: {exc}"}
-    launches_per_step = None
     line = {
         "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_mixed / K,
@@ -324,7 +348,7 @@ def run_ours(args):
         "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "Newton steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk,
-        "gpu_launches": None,
+        "gpu_launches": launches_mixed,
     }
     print(json.dumps(line), flush=True)
     if dist:

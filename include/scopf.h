@@ -242,6 +242,10 @@ int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls
  * fronts in the item, parent item (-1 none), factorization phase (1-3),
  * largest front (rows), total pivots, block; returns n_items through
  * *n_items (out may be NULL). */
+/* Number of kernels the library has launched in this process so far
+ * (all handles; host only, no synchronization). */
+int scopf_launch_count(int64_t *out);
+
 int scopf_trace(scopf_handle *h, int32_t enable);
 int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out);
 int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out);

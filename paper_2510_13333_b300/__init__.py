@@ -144,6 +144,7 @@ def lib():
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
             "scopf_trace": (c_i32, [H, c_i32]),
+            "scopf_launch_count": (c_i32, [P_i64]),
             "scopf_trace_read": (c_i32, [H, c_i32, ctypes.POINTER(ctypes.c_uint64)]),
             "scopf_trace_items": (c_i32, [H, P_i32, P_i32]),
             "scopf_dense_ldlt_solve": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32, ctypes.c_void_p]),
@@ -163,6 +164,13 @@ def exported_symbols():
     import re
     hdr = open(os.path.join(_HERE, "..", "include", "scopf.h")).read()
     return sorted(set(re.findall(r"^\s*(?:int|void|const char \*)\s*\*?(\w+)\(", hdr, re.M)))
+
+
+def scopf_launch_count() -> int:
+    """Kernels launched by the library in this process so far."""
+    n = ctypes.c_int64()
+    _check("scopf_launch_count", lib().scopf_launch_count(ctypes.byref(n)))
+    return n.value
 
 
 def scopf_dense_ldlt_solve(S, b):

@@ -20,6 +20,10 @@ using namespace scopf;
         }                                                                                          \
     } while (0)
 
+namespace scopf {
+std::atomic<long long> g_kernel_launches{0};
+}  // namespace scopf
+
 namespace {
 
 template <typename T>
@@ -503,6 +507,12 @@ int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n, co
     if (r != SCOPF_OK) return r;
     CK(cudaStreamSynchronize(h->stream));
     h->timer.collect();
+    return SCOPF_OK;
+}
+
+int scopf_launch_count(int64_t *out) {
+    if (!out) return SCOPF_ERR_INVALID_ARG;
+    *out = (int64_t)scopf::g_kernel_launches.load(std::memory_order_relaxed);
     return SCOPF_OK;
 }
 

@@ -31,7 +31,7 @@ int dense_factor_solve(double *F, int n, const double *b, double *x, double *y, 
                        int32_t inertia[3], cudaStream_t s) {
     cudaMemsetAsync(st, 0, sizeof(FactorStatus), s);
     launch_dense_ldlt(F, n, st, 0.0, s);
-    k_dense_rhs_solve<<<1, kDT, 0, s>>>(F, n, b, x, y);
+    note_launch(), k_dense_rhs_solve<<<1, kDT, 0, s>>>(F, n, b, x, y);
     FactorStatus fs;
     cudaMemcpyAsync(&fs, st, sizeof(fs), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)

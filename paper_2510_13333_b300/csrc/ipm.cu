@@ -383,20 +383,20 @@ struct Ipm {
     };
     Norms norms(const scopf_state &st, double rho) {
         Norms N{};
-        k_red_w<<<kB, kT, 0, s>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
+        note_launch(), k_red_w<<<kB, kT, 0, s>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
         fetch(7);
         double dw = comb(7, 0, 0);
         double cmin = std::fmin(comb(7, 1, 1), comb(7, 3, 1));
         double cmax = std::fmax(comb(7, 2, 0), comb(7, 4, 0));
         double zsum = comb(7, 5, 2) + comb(7, 6, 2);
-        k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart);
+        note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart);
         fetch(5);
         double gr = comb(5, 0, 0), pc = comb(5, 1, 0), pcs = comb(5, 2, 2), lsum = comb(5, 3, 2);
         N.rmax = comb(5, 4, 0);
         double gt = 0, gs = 0, py = 0, pys = 0, ycs = 0, zss = 0;
         N.tmax = 0;
         if (p) {
-            k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho, dpart);
+            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho, dpart);
             fetch(9);
             gt = comb(9, 0, 0);
             gs = comb(9, 1, 0);
@@ -433,7 +433,7 @@ struct Ipm {
         return f;
     }
     double barrier(const scopf_state &st, double rho, double mu, double phi) {
-        k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho, dpart);
+        note_launch(), k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho, dpart);
         fetch(5);
         if (comb(5, 4, 2) > 0) return INFINITY;
         return phi + comb(5, 2, 2) + comb(5, 3, 2) - mu * (comb(5, 0, 2) + comb(5, 1, 2));
@@ -442,11 +442,11 @@ struct Ipm {
         // c(w) at the trial point, then sum|c - r| + sum|w1 w2 - t + s|
         launch_eval_elements(h->dm, st.w, st.lam, st.yc, h->ev, 0, s);
         launch_constraints(h->dm, st.w, h->ev, h->c, s);
-        k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, 1.0, dpart);
+        note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, 1.0, dpart);
         fetch(5);
         double th = comb(5, 2, 2);
         if (p) {
-            k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, 1.0, dpart);
+            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, 1.0, dpart);
             fetch(9);
             th += comb(9, 3, 2);
         }
@@ -462,17 +462,17 @@ struct Ipm {
     }
 
     void step(scopf_state &out, const scopf_state &st, const scopf_state &d, double a, double az) {
-        k_step<<<nb(n), kT, 0, s>>>(n, st.w, d.w, a, out.w);
-        if (m) k_step<<<nb(m), kT, 0, s>>>(m, st.r, d.r, a, out.r);
-        if (m) k_step<<<nb(m), kT, 0, s>>>(m, st.lam, d.lam, a, out.lam);
+        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.w, d.w, a, out.w);
+        if (m) note_launch(), k_step<<<nb(m), kT, 0, s>>>(m, st.r, d.r, a, out.r);
+        if (m) note_launch(), k_step<<<nb(m), kT, 0, s>>>(m, st.lam, d.lam, a, out.lam);
         if (p) {
-            k_step<<<nb(p), kT, 0, s>>>(p, st.t, d.t, a, out.t);
-            k_step<<<nb(p), kT, 0, s>>>(p, st.s, d.s, a, out.s);
-            k_step<<<nb(p), kT, 0, s>>>(p, st.yc, d.yc, a, out.yc);
-            k_step<<<nb(p), kT, 0, s>>>(p, st.zs, d.zs, az, out.zs);
+            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.t, d.t, a, out.t);
+            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.s, d.s, a, out.s);
+            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.yc, d.yc, a, out.yc);
+            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.zs, d.zs, az, out.zs);
         }
-        k_step<<<nb(n), kT, 0, s>>>(n, st.zl, d.zl, az, out.zl);
-        k_step<<<nb(n), kT, 0, s>>>(n, st.zu, d.zu, az, out.zu);
+        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.zl, d.zl, az, out.zl);
+        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.zu, d.zu, az, out.zu);
     }
 
     // Newton direction with inertia correction; returns status, fills h->dir
@@ -637,13 +637,13 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             }
             if (delta > 0.0) dw_last = delta;
             // split + recover
-            k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol,
+            note_launch(), k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol,
                                                d.w, d.lam, d.yc);
-            k_recover<<<nb(n + m + p), kT, 0, s>>>(D, st.w, st.r, st.t, st.s, st.lam, st.yc,
+            note_launch(), k_recover<<<nb(n + m + p), kT, 0, s>>>(D, st.w, st.r, st.t, st.s, st.lam, st.yc,
                                                    st.zl, st.zu, st.zs, h->lam_n, h->nu0_n, rho,
                                                    mu, d.w, d.lam, d.yc, d.r, d.t, d.s, d.zl,
                                                    d.zu, d.zs);
-            k_ftb<<<kB, kT, 0, s>>>(D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu,
+            note_launch(), k_ftb<<<kB, kT, 0, s>>>(D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu,
                                     d.zs, tau, I.dpart);
             I.fetch(2);
             double ap = 1.0, az = 1.0;
@@ -655,7 +655,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             const double th = N.theta;
             const double phi_cur = I.objective(st.w);
             const double ph = I.barrier(st, rho, mu, phi_cur);
-            k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
+            note_launch(), k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
                                          mu, d.w, d.r, d.t, d.s, I.dpart);
             I.fetch(5);
             double gd = 0;
@@ -704,12 +704,12 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
                 I.step(tr, st, d, a, az);
                 launch_eval_elements(h->dm, tr.w, tr.lam, tr.yc, h->ev, 0, s);
                 launch_constraints(h->dm, tr.w, h->ev, tr.r, s);
-                if (p) k_reset_t<<<nb(p), kT, 0, s>>>(D, tr.w, tr.s, tr.t);
+                if (p) note_launch(), k_reset_t<<<nb(p), kT, 0, s>>>(D, tr.w, tr.s, tr.t);
                 filt.clear();
             } else if (!ftype) {
                 filt.push_back({(1 - o.gamma_theta) * th, ph - o.gamma_phi * th});
             }
-            k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
+            note_launch(), k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
             std::swap(st, tr);
             inner++;
             cudaStreamSynchronize(s);
@@ -806,13 +806,13 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     r = I.direction(st, rho, mu, dwl, delta, tries);
     if (r != SCOPF_OK) return r;
     h->timer.begin(PH_IPM, s);
-    k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol, d.w,
+    note_launch(), k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol, d.w,
                                        d.lam, d.yc);
-    k_recover<<<nb(n + m + p), kT, 0, s>>>(I.D, st.w, st.r, st.t, st.s, st.lam, st.yc, st.zl,
+    note_launch(), k_recover<<<nb(n + m + p), kT, 0, s>>>(I.D, st.w, st.r, st.t, st.s, st.lam, st.yc, st.zl,
                                            st.zu, st.zs, h->lam_n, h->nu0_n, rho, mu, d.w, d.lam,
                                            d.yc, d.r, d.t, d.s, d.zl, d.zu, d.zs);
     const double tau = std::fmax(h->opt.tau_min, 1.0 - mu);
-    k_ftb<<<kB, kT, 0, s>>>(I.D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu, d.zs, tau,
+    note_launch(), k_ftb<<<kB, kT, 0, s>>>(I.D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu, d.zs, tau,
                             I.dpart);
     I.fetch(2);
     double ap = 1.0, az = 1.0;

@@ -4,7 +4,14 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 namespace scopf {
+
+// Every kernel launch of the library is counted here (scopf_launch_count).
+extern std::atomic<long long> g_kernel_launches;
+inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
+
 
 // ---------------------------------------------------------------- model
 struct DevModel {

@@ -1170,11 +1170,11 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     const int gl = (int)((32 * M.n_long + t - 1) / t);
     // start in the buffer that makes the last sweep land in `scale`
     double *a = (iters & 1) ? tmp : scale, *b = (iters & 1) ? scale : tmp;
-    k_fill<<<g, t, 0, s>>>(n, 1.0, a);
+    note_launch(), k_fill<<<g, t, 0, s>>>(n, 1.0, a);
     for (int it = 0; it < iters; it++) {
-        k_ruiz<<<g, t, 0, s>>>(n, M.kkt_ptr, M.kkt_col, kval, a, b, M.is_long);
+        note_launch(), k_ruiz<<<g, t, 0, s>>>(n, M.kkt_ptr, M.kkt_col, kval, a, b, M.is_long);
         if (M.n_long)
-            k_ruiz_long<<<gl, t, 0, s>>>(M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, a, b);
+            note_launch(), k_ruiz_long<<<gl, t, 0, s>>>(M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, a, b);
         double *c = a;
         a = b;
         b = c;
@@ -1185,14 +1185,14 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
 void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s) {
     const int t = 256;
     if (F.n_orig > 0)
-        k_orig_vals<<<(int)((F.n_orig + t - 1) / t), t, 0, s>>>(F.n_orig, F.orig_nz, F.kkt_row,
+        note_launch(), k_orig_vals<<<(int)((F.n_orig + t - 1) / t), t, 0, s>>>(F.n_orig, F.orig_nz, F.kkt_row,
                                                                F.kkt_col, F.scale, F.kval, ovals);
 }
 
 void launch_queue_reset(const DevFront &F, QueueSeeds seeds, const int32_t *pend, cudaStream_t s) {
     const int t = 256;
     const int n = F.n_items > 0 ? F.n_items : 1;
-    k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, F.q_slots_b, F.q_slots_c,
+    note_launch(), k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, F.q_slots_b, F.q_slots_c,
                                                 seeds, F.q_pending, pend, F.q_ctr);
 }
 
@@ -1231,11 +1231,11 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     const int n1 = F.n_items_small, n2 = F.n_items_med - F.n_items_small;
     if (n1 > 0) {
         const int grid = std::min(g[0], (n1 + kFT / 32 - 1) / (kFT / 32));
-        k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, n1), pivot_tol, spin_limit);
+        note_launch(), k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, n1), pivot_tol, spin_limit);
     }
     if (n2 > 0) {
         const int grid = std::min(g[1], (n2 + kWT / 32 - 1) / (kWT / 32));
-        k_factor_med<T><<<grid, kWT, sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
+        note_launch(), k_factor_med<T><<<grid, kWT, sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
                                                spin_limit);
     }
     const int nbig = F.n_items - F.n_items_med;
@@ -1253,7 +1253,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
             g3_sm[pi] = sm3;
         }
         const int grid = std::min(g3[pi], nbig);
-        k_factor_big<T><<<grid, kBT, sm3, s>>>(F, fronts, st, queue_c(F, nbig), pivot_tol,
+        note_launch(), k_factor_big<T><<<grid, kBT, sm3, s>>>(F, fronts, st, queue_c(F, nbig), pivot_tol,
                                                spin_limit);
     }
 }
@@ -1262,7 +1262,7 @@ template <typename T>
 void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s) {
     const int nb = F.n_border;
     if (nb == 0) return;
-    k_schur_sum<T><<<(nb * nb + 255) / 256, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
+    note_launch(), k_schur_sum<T><<<(nb * nb + 255) / 256, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
 }
 
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
@@ -1273,11 +1273,11 @@ void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cud
             cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
             attr = true;
         }
-        k_dense_panel<<<1, 256, sizeof(double) * (size_t)(n - k0) * (k1 - k0), s>>>(S, n, k0, k1, st, pivot_tol);
+        note_launch(), k_dense_panel<<<1, 256, sizeof(double) * (size_t)(n - k0) * (k1 - k0), s>>>(S, n, k0, k1, st, pivot_tol);
         const int rem = n - k1;
         if (rem > 0) {
             const int tiles = (rem + 31) / 32;
-            k_dense_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(S, n, k0, k1);
+            note_launch(), k_dense_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(S, n, k0, k1);
         }
     }
 }
@@ -1300,17 +1300,17 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
         attr = true;
     }
-    k_rhs_to_fronts<T><<<(int)((F.n_rows + 255) / 256), 256, 0, s>>>(F.n_rows, F.vpos_of_row,
+    note_launch(), k_rhs_to_fronts<T><<<(int)((F.n_rows + 255) / 256), 256, 0, s>>>(F.n_rows, F.vpos_of_row,
                                                                      scale, b, vec);
-    k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, queue_a(F, F.n_items), st, spin_limit);
+    note_launch(), k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, queue_a(F, F.n_items), st, spin_limit);
     {
         const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
-        k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
+        note_launch(), k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
             F, vec, S, nS, b, scale, x, border_work);
     }
     const int nb = F.n_items - F.n_blocks;   // every item but the border fronts
     if (nb > 0)
-        k_solve_bwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, scale, x, queue_b(F, nb), st,
+        note_launch(), k_solve_bwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, scale, x, queue_b(F, nb), st,
                                              spin_limit);
 }
 

@@ -340,7 +340,7 @@ __global__ void k_axpy(int64_t n, double a, const double *__restrict__ x, double
 }  // namespace
 
 void launch_axpy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
-    if (n) k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
+    if (n) note_launch(), k_axpy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
 }
 
 namespace {
@@ -478,12 +478,12 @@ __global__ void k_diag_set(int64_t n, const int64_t *__restrict__ pos,
 
 void launch_diag_gather(int64_t n, const int64_t *pos, const double *kval, double *base,
                         cudaStream_t s) {
-    if (n) k_diag_gather<<<nblocks(n), kThreads, 0, s>>>(n, pos, kval, base);
+    if (n) note_launch(), k_diag_gather<<<nblocks(n), kThreads, 0, s>>>(n, pos, kval, base);
 }
 
 void launch_diag_set(int64_t n, const int64_t *pos, const double *base, double shift,
                      double *kval, cudaStream_t s) {
-    if (n) k_diag_set<<<nblocks(n), kThreads, 0, s>>>(n, pos, base, shift, kval);
+    if (n) note_launch(), k_diag_set<<<nblocks(n), kThreads, 0, s>>>(n, pos, base, shift, kval);
 }
 
 GmresLayout gmres_layout(int m) {
@@ -501,133 +501,133 @@ GmresLayout gmres_layout(int m) {
 }
 
 void launch_dot_finish(const double *partial, int k, double *out, bool take_sqrt, cudaStream_t s) {
-    k_dot_finish<<<1, 32 * k, 0, s>>>(partial, k, out, take_sqrt ? 1 : 0);
+    note_launch(), k_dot_finish<<<1, 32 * k, 0, s>>>(partial, k, out, take_sqrt ? 1 : 0);
 }
 
 void launch_multi_axpy_dev(double *w, const double *V, int64_t n, int k, const double *c,
                            double sign, cudaStream_t s) {
-    if (n) k_multi_axpy_dev<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, c, sign);
+    if (n) note_launch(), k_multi_axpy_dev<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, c, sign);
 }
 
 void launch_scale_inv(int64_t n, const double *den, const double *x, double *y, cudaStream_t s) {
-    if (n) k_scale_inv<<<nblocks(n), kThreads, 0, s>>>(n, den, x, y);
+    if (n) note_launch(), k_scale_inv<<<nblocks(n), kThreads, 0, s>>>(n, den, x, y);
 }
 
 void launch_gmres_init(double *st, int m, cudaStream_t s) {
-    k_gmres_init<<<1, 64, 0, s>>>(st, gmres_layout(m));
+    note_launch(), k_gmres_init<<<1, 64, 0, s>>>(st, gmres_layout(m));
 }
 
 void launch_gmres_column(double *st, int m, int j, cudaStream_t s) {
-    k_gmres_column<<<1, 32, 0, s>>>(st, gmres_layout(m), j);
+    note_launch(), k_gmres_column<<<1, 32, 0, s>>>(st, gmres_layout(m), j);
 }
 
 void launch_gmres_solve(double *st, int m, int k, cudaStream_t s) {
-    k_gmres_solve<<<1, 32, 0, s>>>(st, gmres_layout(m), k);
+    note_launch(), k_gmres_solve<<<1, 32, 0, s>>>(st, gmres_layout(m), k);
 }
 
 void reduce_maxabs2(const double *a, const double *b, int64_t n, double *d_out, double *scratch,
                     cudaStream_t s) {
-    k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(a, n, scratch);
-    k_reduce<0><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
-    k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(b, n, scratch + kReduceBlocks);
-    k_reduce<0><<<1, kThreads, 0, s>>>(scratch + kReduceBlocks, kReduceBlocks, d_out + 1);
+    note_launch(), k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(a, n, scratch);
+    note_launch(), k_reduce<0><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
+    note_launch(), k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(b, n, scratch + kReduceBlocks);
+    note_launch(), k_reduce<0><<<1, kThreads, 0, s>>>(scratch + kReduceBlocks, kReduceBlocks, d_out + 1);
 }
 
 void launch_multi_dot(const double *V, int64_t n, int k, const double *w, double *partial,
                       cudaStream_t s) {
-    k_multi_dot<<<kDotBlocks, kThreads, 0, s>>>(V, n, k, w, partial);
+    note_launch(), k_multi_dot<<<kDotBlocks, kThreads, 0, s>>>(V, n, k, w, partial);
 }
 
 void launch_multi_axpy(double *w, const double *V, int64_t n, int k, const double *c,
                        cudaStream_t s) {
     Coefs cf;
     for (int j = 0; j < k && j < kMaxKrylov; j++) cf.c[j] = c[j];
-    k_multi_axpy<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, cf);
+    note_launch(), k_multi_axpy<<<nblocks(n), kThreads, 0, s>>>(w, V, n, k, cf);
 }
 
 void launch_scale_copy(int64_t n, double a, const double *x, double *y, cudaStream_t s) {
-    if (n) k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
+    if (n) note_launch(), k_scale_copy<<<nblocks(n), kThreads, 0, s>>>(n, a, x, y);
 }
 
 void launch_spmv(const DevModel &M, const double *kval, const double *x, double *y,
                  cudaStream_t s) {
-    k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x,
+    note_launch(), k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x,
                                                      nullptr, y, M.is_long, 1.0);
     if (M.n_long)
-        k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+        note_launch(), k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
             M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, x, nullptr, y, 1.0);
 }
 
 void launch_eval_elements(const DevModel &M, const double *w, const double *lam, const double *yc,
                           double *ev, int mode, cudaStream_t s) {
     if (M.n_be)
-        k_branch<<<nblocks(M.n_be), kThreads, 0, s>>>(M.n_be, M.be_x, M.be_lam, M.be_th, M.be_par,
+        note_launch(), k_branch<<<nblocks(M.n_be), kThreads, 0, s>>>(M.n_be, M.be_x, M.be_lam, M.be_th, M.be_par,
                                                       w, lam, ev + M.ev_branch0, mode);
     if (M.n_se)
-        k_shunt<<<nblocks(M.n_se), kThreads, 0, s>>>(M.n_se, M.se_v, M.se_P, M.se_Q, M.se_G,
+        note_launch(), k_shunt<<<nblocks(M.n_se), kThreads, 0, s>>>(M.n_se, M.se_v, M.se_P, M.se_Q, M.se_G,
                                                      M.se_B, w, lam, ev + M.ev_shunt0, mode);
     if (M.p && mode)
-        k_comp<<<nblocks(M.p), kThreads, 0, s>>>(M.p, M.comp1, M.comp2, w, yc, ev + M.ev_comp0);
+        note_launch(), k_comp<<<nblocks(M.p), kThreads, 0, s>>>(M.p, M.comp1, M.comp2, w, yc, ev + M.ev_comp0);
 }
 
 void launch_constraints(const DevModel &M, const double *w, const double *ev, double *c,
                         cudaStream_t s) {
     if (M.m)
-        k_cons<<<nblocks(M.m), kThreads, 0, s>>>(M.m, M.c_const, M.cf_ptr, M.cf_idx, M.cf_coef, ev,
+        note_launch(), k_cons<<<nblocks(M.m), kThreads, 0, s>>>(M.m, M.c_const, M.cf_ptr, M.cf_idx, M.cf_coef, ev,
                                                  w, c);
 }
 
 void launch_gradient(const DevModel &M, const double *w, double *g, cudaStream_t s) {
     cudaMemsetAsync(g, 0, sizeof(double) * M.n, s);
-    k_grad<<<nblocks(M.ng), kThreads, 0, s>>>(M.ng, M.border0, M.c2, M.c1, w, g);
+    note_launch(), k_grad<<<nblocks(M.ng), kThreads, 0, s>>>(M.ng, M.border0, M.c2, M.c1, w, g);
 }
 
 void launch_diag_terms(const DevModel &M, const double *w, const double *zl, const double *zu,
                        const double *sv, const double *zs, double rho, double delta_w,
                        double *diag, cudaStream_t s) {
-    k_diag<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.row_kind, M.row_index, M.wl, M.wu, w,
+    note_launch(), k_diag<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.row_kind, M.row_index, M.wl, M.wu, w,
                                                  zl, zu, sv, zs, rho, delta_w, diag);
 }
 
 void launch_assemble(const DevModel &M, const double *ev, const double *diag, double *kval,
                      cudaStream_t s) {
-    k_assemble<<<nblocks(M.nnz), kThreads, 0, s>>>(M.nnz, M.kkt_row, M.kkt_col, M.ctr_ptr,
+    note_launch(), k_assemble<<<nblocks(M.nnz), kThreads, 0, s>>>(M.nnz, M.kkt_row, M.kkt_col, M.ctr_ptr,
                                                    M.ctr_src, M.ctr_coef, ev, diag, kval);
 }
 
 void launch_dual_product(const DevModel &M, const double *kval, const double *g, const double *lam,
                          const double *yc, double *gw, cudaStream_t s) {
-    k_dual_product<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, M.row_kind,
+    note_launch(), k_dual_product<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, M.row_kind,
                                                          M.row_index, kval, g, lam, yc, gw,
                                                          M.is_long);
     if (M.n_long)
-        k_dual_product_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+        note_launch(), k_dual_product_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
             M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, M.row_kind, M.row_index, kval, g, lam,
             yc, gw);
 }
 
 void launch_rhs(const DevModel &M, const RhsArgs &a, double *rhs, cudaStream_t s) {
-    k_rhs<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.row_kind, M.row_index, M.wl, M.wu,
+    note_launch(), k_rhs<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.row_kind, M.row_index, M.wl, M.wu,
                                                 M.comp1, M.comp2, a, rhs);
 }
 
 void launch_residual(const DevModel &M, const double *kval, const double *x, const double *b,
                      double *y, cudaStream_t s) {
-    k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, b, y,
+    note_launch(), k_residual<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.kkt_ptr, M.kkt_col, kval, x, b, y,
                                                      M.is_long, -1.0);
     if (M.n_long)
-        k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
+        note_launch(), k_residual_long<<<nblocks(32 * M.n_long), kThreads, 0, s>>>(
             M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, x, b, y, -1.0);
 }
 
 void reduce_maxabs(const double *x, int64_t n, double *d_out, double *scratch, cudaStream_t s) {
-    k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(x, n, scratch);
-    k_reduce<0><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
+    note_launch(), k_reduce<0><<<kReduceBlocks, kThreads, 0, s>>>(x, n, scratch);
+    note_launch(), k_reduce<0><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
 }
 
 void reduce_sumabs(const double *x, int64_t n, double *d_out, double *scratch, cudaStream_t s) {
-    k_reduce<1><<<kReduceBlocks, kThreads, 0, s>>>(x, n, scratch);
-    k_reduce<1><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
+    note_launch(), k_reduce<1><<<kReduceBlocks, kThreads, 0, s>>>(x, n, scratch);
+    note_launch(), k_reduce<1><<<1, kThreads, 0, s>>>(scratch, kReduceBlocks, d_out);
 }
 
 }  // namespace scopf
