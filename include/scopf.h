@@ -286,11 +286,26 @@ int scopf_load_state(scopf_handle *h, const scopf_state *src);
 /* NCL multiplier estimates of the last solve (device views, m and p), rho. */
 int scopf_get_ncl_params(scopf_handle *h, double **lam_n, double **nu0_n, double *rho);
 
-/* Adjoint of the converged solution: gradients of
- * J = seed_pg0' p_g^0 + seed_cost * objective with respect to the bus loads
- * Pd, Qd (n_bus each) and the linear cost coefficients c1 (n_gen), by one
- * transposed solve with the final factorisation (K is symmetric).
- * seed_pg0: device, n_gen (may be NULL = zero); outputs device. */
+/* Parameters of the instance that the adjoint differentiates: bus loads Pd,
+ * Qd (n_bus, per unit) and linear cost coefficients c1 (n_gen), host arrays
+ * copied into the handle (any may be NULL = unchanged).  The structure is
+ * unchanged, so no symbolic work is redone; a later ncl_solve uses them. */
+int scopf_set_params(scopf_handle *h, const double *Pd, const double *Qd, const double *c1);
+
+/* Make the handle's current state (scopf_load_state) and these NCL
+ * parameters (device lam_n: m, nu0_n: p; rho > 0, barrier mu > 0) the
+ * solution that scopf_adjoint differentiates; ncl_solve sets them itself. */
+int scopf_set_ncl_params(scopf_handle *h, const double *lam_n, const double *nu0_n, double rho,
+                         double mu);
+
+/* Adjoint of the converged solution (implicit function theorem on the
+ * barrier KKT conditions of eq. (newtonsystem) at the final iterate):
+ * gradients of J = seed_pg0' p_g^0 + seed_cost * objective with respect to
+ * the bus loads Pd, Qd (n_bus each) and the linear cost coefficients c1
+ * (n_gen), from one symmetric solve K a = dJ/dz.  K is refactored in FP64 at
+ * the final iterate with the method's inertia correction, and the solve is
+ * refined against the unshifted K.  seed_pg0: device, n_gen (NULL = zero);
+ * outputs: device.  SCOPF_ERR_NOT_FACTORED if no solution is loaded. */
 int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
                   double *grad_Pd, double *grad_Qd, double *grad_c1);
 

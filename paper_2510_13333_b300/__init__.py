@@ -140,6 +140,8 @@ def lib():
             "scopf_get_ncl_params": (c_i32, [H, ctypes.POINTER(P_dbl), ctypes.POINTER(P_dbl),
                                              P_dbl]),
             "scopf_adjoint": (c_i32, [H, P_dbl, c_dbl, P_dbl, P_dbl, P_dbl]),
+            "scopf_set_params": (c_i32, [H, P_dbl, P_dbl, P_dbl]),
+            "scopf_set_ncl_params": (c_i32, [H, P_dbl, P_dbl, c_dbl, c_dbl]),
             "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
@@ -444,7 +446,27 @@ class SCOPF:
                               ctypes.c_size_t(8 * s.p), 3)
         return lam_n, nu0_n, rho
 
+    def set_params(self, Pd=None, Qd=None, c1=None):
+        """Replace the bus loads and linear cost coefficients (host arrays)."""
+        def h(a, n):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+            assert a.shape == (n,)
+            return a
+        Pd, Qd, c1 = h(Pd, self.n_bus), h(Qd, self.n_bus), h(c1, self.n_gen)
+        _check("scopf_set_params", lib().scopf_set_params(
+            self.h, None if Pd is None else _hp(Pd, c_dbl), None if Qd is None else _hp(Qd, c_dbl),
+            None if c1 is None else _hp(c1, c_dbl)))
+
+    def set_ncl_params(self, lam_n, nu0_n, rho, mu):
+        """Declare the loaded state a solution with these NCL parameters."""
+        _check("scopf_set_ncl_params", lib().scopf_set_ncl_params(
+            self.h, _dp(lam_n), _dp(nu0_n), float(rho), float(mu)))
+
     def scopf_adjoint(self, seed_pg0=None, seed_cost=0.0):
+        """Gradients of seed_pg0' p_g^0 + seed_cost * objective with respect
+        to (Pd, Qd, c1) at the converged solution (torch tensors)."""
         import torch
         net_nb, ng = self.n_bus, self.n_gen
         gP = torch.zeros(net_nb, dtype=torch.float64, device="cuda")
@@ -453,3 +475,40 @@ class SCOPF:
         _check("scopf_adjoint", lib().scopf_adjoint(self.h, _dp(seed_pg0), float(seed_cost),
                                                     _dp(gP), _dp(gQ), _dp(gc)))
         return gP, gQ, gc
+
+
+class SCOPFLayer:
+    """Differentiable SCOPF solve: ``pg0, cost = SCOPFLayer.apply(model, Pd, Qd, c1)``.
+
+    forward solves the NCL problem for the given loads and linear costs (the
+    structure of ``model``, a :class:`SCOPF` handle, is kept); backward is one
+    adjoint solve (scopf_adjoint) with the final factorization's matrix."""
+
+    @staticmethod
+    def apply(model, Pd, Qd, c1):
+        import torch
+
+        class _Fn(torch.autograd.Function):
+            @staticmethod
+            def forward(ctx, Pd_, Qd_, c1_):
+                ctx.devices = (Pd_.device, Qd_.device, c1_.device)
+                model.set_params(Pd_.detach().cpu().numpy(), Qd_.detach().cpu().numpy(),
+                                 c1_.detach().cpu().numpy())
+                res = model.ncl_solve()
+                if res["status"] != 0:
+                    raise ScopfError("ncl_solve", res["status"])
+                st = model.get_state()
+                s = model.sizes
+                b0 = int(s.n) - int(s.n_border)
+                pg0 = st["w"][b0:b0 + model.n_gen].clone()
+                return pg0.to(Pd_.device), torch.tensor(res["objective"], dtype=torch.float64,
+                                                         device=Pd_.device)
+
+            @staticmethod
+            def backward(ctx, g_pg0, g_cost):
+                seed = g_pg0.to("cuda", torch.float64).contiguous()
+                gP, gQ, gc = model.scopf_adjoint(seed, float(g_cost))
+                dP, dQ, dc = ctx.devices
+                return gP.to(dP), gQ.to(dQ), gc.to(dc)
+
+        return _Fn.apply(Pd, Qd, c1)

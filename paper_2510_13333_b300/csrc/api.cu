@@ -880,9 +880,4 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
 
 }  // namespace scopf
 
-extern "C" int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
-                             double *grad_Pd, double *grad_Qd, double *grad_c1) {
-    (void)seed_pg0; (void)seed_cost; (void)grad_Pd; (void)grad_Qd; (void)grad_c1;
-    if (!h) return SCOPF_ERR_INVALID_ARG;
-    return SCOPF_ERR_INVALID_ARG;
-}
+

@@ -124,6 +124,13 @@ struct scopf_handle {
     scopf_state st{};
     double *lam_n = nullptr, *nu0_n = nullptr;
     double rho = 0.0;
+    double mu_last = 0.0, dw_last = 0.0;   // barrier parameter and delta_w at the last solve's end
+    bool has_solution = false;             // st, lam_n, nu0_n, rho, mu_last describe a solution
+    // adjoint index sets (built on first use): KKT row of every p_g^0, and
+    // per bus the KKT rows of its P and Q balance in every block
+    int64_t *adj_pg = nullptr, *adj_ptr = nullptr, *adj_rowsP = nullptr, *adj_rowsQ = nullptr;
+    int64_t *adj_dpos = nullptr, adj_ndual = 0;   // diagonal entries of the dual rows
+    double *adj_g = nullptr, *adj_a = nullptr;
     // IPM scratch (directions and trial point)
     scopf_state dir{}, trial{};
     double *tmp_n = nullptr, *tmp_m = nullptr, *tmp_p = nullptr, *tmp_kkt = nullptr;
@@ -144,6 +151,10 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n,
                   const double *nu0_n, double rho, double mu, double delta_w, double *rhs);
 int factor_impl(scopf_handle *h, int precision, int inertia[3]);
 int set_delta_w(scopf_handle *h, double delta_w);
+// FP64 or mixed factorization of K(delta_w) with the inertia correction of
+// the interior-point method (the first delta_w tried follows dw_last);
+// delta_w used on return
+int factor_inertia(scopf_handle *h, int precision, double dw_last, double &delta, int &tries);
 int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel,
                int *steps);
 double device_maxabs(scopf_handle *h, const double *x, int64_t n);

@@ -336,6 +336,46 @@ struct Timer {
 
 int ipm_partials() { return kB * 9; }
 
+// Inertia correction (W&B 2006, Alg. IC) around the factorization of the
+// assembled K: delta_w = 0 first (unless it already showed zero pivots),
+// then growing delta_w until the inertia is (n, m + p, 0).  Once a
+// delta_w = 0 factorization has shown zero pivots -- variables entering only
+// linearly (p^k, Delta^k, free q^k) are eliminated before their rows, so
+// these zeros recur at every iterate -- the trial at 0 is skipped: it would
+// fail again and the delta_w sequence is unchanged.  K's primal diagonal is
+// left shifted by the delta_w returned.
+int factor_inertia(scopf_handle *h, int precision, double dw_last, double &delta, int &tries) {
+    const scopf_options &o = h->opt;
+    const int64_t npos = h->M.n, nneg = h->M.m + h->M.p;
+    delta = h->skip_delta0
+                ? (dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last))
+                : 0.0;
+    tries = 0;
+    double current = h->assembled_delta_w;   // the shift of the assembled K
+    while (true) {
+        if (delta != current) {
+            int r = set_delta_w(h, delta);
+            if (r != SCOPF_OK) return r;
+            current = delta;
+        }
+        int in[3];
+        int r = factor_impl(h, precision, in);
+        if (r != SCOPF_OK) return r;
+        tries++;
+        if (delta == 0.0 && in[2] > 0) h->skip_delta0 = true;
+        if (o.verbose >= 2)
+            std::printf("    factor (%s) delta_w %.2e inertia (%d, %d, %d), want (%lld, %lld, 0)\n",
+                        precision == SCOPF_PREC_MIXED ? "fp32" : "fp64", delta, in[0], in[1],
+                        in[2], (long long)npos, (long long)nneg);
+        if (in[0] == npos && in[1] == nneg && in[2] == 0) return SCOPF_OK;
+        if (delta == 0.0)
+            delta = dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
+        else
+            delta *= dw_last > 0.0 ? o.kappa_w_plus : o.kappa_w_plus_bar;
+        if (delta > o.delta_w_max) return SCOPF_ERR_WRONG_INERTIA;
+    }
+}
+
 // ===========================================================================
 struct Ipm {
     scopf_handle *h;
@@ -476,47 +516,13 @@ struct Ipm {
     }
 
     // Newton direction with inertia correction; returns status, fills h->dir
-    int direction(const scopf_state &st, double rho, double mu, double &dw_last, double &delta,
-                  int &tries) {
-        const int64_t npos = n, nneg = m + p;
-        // Inertia correction (W&B 2006, Alg. IC).  Once a delta_w = 0
-        // factorization has shown zero pivots -- variables entering only
-        // linearly (p^k, Delta^k, free q^k) are eliminated before their rows,
-        // so these zeros recur at every iterate -- the trial at 0 is skipped:
-        // it would fail again and the delta_w sequence is unchanged.
-        delta = h->skip_delta0
-                    ? (dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last))
-                    : 0.0;
-        tries = 0;
-        // K at delta = 0 and the RHS were assembled by the caller; other
-        // delta_w values only shift the primal diagonal
-        double current = 0.0;
-        while (true) {
-            if (delta != current) {
-                int r = set_delta_w(h, delta);
-                if (r != SCOPF_OK) return r;
-                current = delta;
-            }
-            const int prec = force_fp64 ? SCOPF_PREC_FP64 : h->precision;
-            int in[3];
-            int r = factor_impl(h, prec, in);
-            if (r != SCOPF_OK) return r;
-            tries++;
-            if (delta == 0.0 && in[2] > 0) h->skip_delta0 = true;
-            if (o.verbose >= 2)
-                std::printf("    factor (%s) delta_w %.2e inertia (%d, %d, %d), want (%lld, %lld, 0)\n",
-                            prec == SCOPF_PREC_MIXED ? "fp32" : "fp64", delta, in[0], in[1], in[2],
-                            (long long)npos, (long long)nneg);
-            if (in[0] == npos && in[1] == nneg && in[2] == 0) break;
-            if (delta == 0.0)
-                delta = dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
-            else
-                delta *= dw_last > 0.0 ? o.kappa_w_plus : o.kappa_w_plus_bar;
-            if (delta > o.delta_w_max) return SCOPF_ERR_WRONG_INERTIA;
-        }
+    int direction(double &dw_last, double &delta, int &tries) {
+        const int prec = force_fp64 ? SCOPF_PREC_FP64 : h->precision;
+        int r = factor_inertia(h, prec, dw_last, delta, tries);
+        if (r != SCOPF_OK) return r;
         double rel = 0;
         int steps = 0;
-        int r = solve_impl(h, h->rhs, h->sol, o.max_refine, &rel, &steps);
+        r = solve_impl(h, h->rhs, h->sol, o.max_refine, &rel, &steps);
         if (r == SCOPF_ERR_REFINE_STALL && h->factored_precision == SCOPF_PREC_MIXED) {
             // FP32 factors no longer accurate enough: redo this step in FP64 and stay there
             force_fp64 = true;
@@ -630,7 +636,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             }
             double delta = 0.0;
             int tries = 0;
-            r = I.direction(st, rho, mu, dw_last, delta, tries);
+            r = I.direction(dw_last, delta, tries);
             if (r != SCOPF_OK) {
                 inner_status = r == SCOPF_ERR_WRONG_INERTIA ? SCOPF_ERR_NUMERICAL : r;
                 break;
@@ -748,6 +754,9 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     if (outer > o.max_outer) outer = o.max_outer;
     cudaStreamSynchronize(s);
     h->rho = rho;
+    h->mu_last = mu;
+    h->dw_last = dw_last;
+    h->has_solution = status == SCOPF_OK;
     // final report
     res->status = status;
     res->outer_iters = outer;
@@ -803,7 +812,7 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     if (r != SCOPF_OK) return r;
     double delta = 0.0, dwl = dw_last;
     int tries = 0;
-    r = I.direction(st, rho, mu, dwl, delta, tries);
+    r = I.direction(dwl, delta, tries);
     if (r != SCOPF_OK) return r;
     h->timer.begin(PH_IPM, s);
     note_launch(), k_split<<<nb(M.n_kkt), kT, 0, s>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index, h->sol, d.w,

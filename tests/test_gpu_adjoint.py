@@ -1,0 +1,84 @@
+"""GPU adjoint (scopf_adjoint): parity with the oracle adjoint at the
+oracle's own solution, and agreement with finite differences of GPU solves."""
+import numpy as np
+import pytest
+
+from oracle.adjoint import scopf_adjoint
+from oracle.linsolve import SparseLDLSolver
+from oracle.ncl import NCLSolver
+from oracle.scopf_model import SCOPFModel
+from oracle import symbolic
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("which", ["small", "cfg0"])
+def test_adjoint_matches_oracle(cuda, which):
+    import torch
+    import paper_2510_13333_b300 as P
+    inst = H.small_instance() if which == "small" else H.instance(0)
+    M = SCOPFModel(inst)
+    perm, _ = symbolic.kkt_permutation(M)
+    S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm))
+    r = S.solve()
+    assert r.status == "ok"
+    rng = np.random.default_rng(4)
+    seed = rng.standard_normal(M.ng)
+    ref = scopf_adjoint(S, r.state, r.params, seed, 0.7)
+    lib = P.SCOPF(inst, precision=P.PREC_FP64)
+    lib.load_state(H.to_device_state(S, r.state, torch))
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), dtype=torch.float64, device="cuda")
+    lib.set_ncl_params(t(r.params.lam_n), t(r.params.nu0_n), r.params.rho, r.mu)
+    got = lib.scopf_adjoint(t(seed), 0.7)
+    for g, e in zip(got, ref):
+        g = g.cpu().numpy()
+        np.testing.assert_allclose(g, e, rtol=1e-6, atol=1e-8 * max(1.0, np.abs(e).max()))
+
+
+def test_adjoint_matches_gpu_finite_differences(cuda):
+    import torch
+    import paper_2510_13333_b300 as P
+    inst = H.instance(0)
+    lib = P.SCOPF(inst, precision=P.PREC_FP64)
+    ng = inst.net.n_gen
+    rng = np.random.default_rng(5)
+    seed = rng.standard_normal(ng)
+
+    def J(Pd):
+        lib.set_params(Pd=Pd)
+        res = lib.ncl_solve()
+        assert res["status"] == 0
+        st = lib.get_state()
+        s = lib.sizes
+        b0 = int(s.n) - int(s.n_border)
+        return float(seed @ st["w"][b0:b0 + ng].cpu().numpy()) + res["objective"]
+
+    Pd0 = np.asarray(inst.net.Pd, dtype=float).copy()
+    J(Pd0)
+    gPd, _, _ = lib.scopf_adjoint(torch.tensor(seed, device="cuda"), 1.0)
+    d = rng.standard_normal(len(Pd0))
+    d /= np.linalg.norm(d)
+    # the solves stop at tol 1e-6 (J accurate to about 1e-6; tighter stops are
+    # out of reach at biactive complementarity pairs), so the step is large
+    # enough that this error over 2h stays near 1e-3: h = 1e-3 p.u. of load
+    h = 1e-3
+    fd = (J(Pd0 + h * d) - J(Pd0 - h * d)) / (2 * h)
+    adj = float(gPd.cpu().numpy() @ d)
+    assert abs(adj - fd) <= 2e-3 * abs(fd) + 1e-3, (adj, fd)
+
+
+def test_autograd_layer_backward(cuda):
+    """torch.autograd through SCOPFLayer: backward = scopf_adjoint."""
+    import torch
+    import paper_2510_13333_b300 as P
+    inst = H.instance(0)
+    lib = P.SCOPF(inst, precision=P.PREC_FP64)
+    Pd = torch.tensor(inst.net.Pd, dtype=torch.float64, requires_grad=True)
+    Qd = torch.tensor(inst.net.Qd, dtype=torch.float64, requires_grad=True)
+    c1 = torch.tensor(inst.net.c1, dtype=torch.float64, requires_grad=True)
+    pg0, cost = P.SCOPFLayer.apply(lib, Pd, Qd, c1)
+    (pg0.sum() + 2.0 * cost).backward()
+    gP, gQ, gc = lib.scopf_adjoint(torch.ones(inst.net.n_gen, dtype=torch.float64, device="cuda"), 2.0)
+    np.testing.assert_allclose(Pd.grad.numpy(), gP.cpu().numpy(), rtol=1e-12, atol=1e-14)
+    np.testing.assert_allclose(c1.grad.numpy(), gc.cpu().numpy(), rtol=1e-12, atol=1e-14)
