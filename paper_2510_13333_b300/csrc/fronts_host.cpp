@@ -215,10 +215,15 @@ std::string build_fronts(const Model &M, const std::vector<BlockSymbolic> &syms,
         H.border_vec_off[k] = H.vec_off[tid[border_task[k]]];
     }
     for (int j = 0; j < nbor; j++) H.border_rows.push_back(M.kkt_border0 + j);
-    // children lists in task order, relative maps
+    // children lists, relative maps.  Children are listed in the block's
+    // postorder (their supernode index), not in task order: the extend-add
+    // sums children in list order, so the arithmetic, and with it every
+    // result, does not depend on how tasks are grouped or scheduled.
     std::vector<std::vector<int>> ch(nt);
     for (int i = 0; i < nt; i++)
         if (H.parent[i] >= 0) ch[H.parent[i]].push_back(i);
+    for (auto &c : ch)
+        std::sort(c.begin(), c.end(), [&](int a, int b) { return order[a] < order[b]; });
     H.child_ptr.assign(nt + 1, 0);
     for (int i = 0; i < nt; i++) {
         H.child_ptr[i + 1] = H.child_ptr[i] + (int)ch[i].size();

@@ -313,6 +313,51 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
     }
 }
 
+// Trailing update U -= L21 D L21' of a front held in a shared tile with
+// row stride S (lower triangle; columns < np hold L, the diagonal D), for all
+// entries np <= j <= i < f.  W = L D is first written to the unused upper
+// triangle (W[c][j] at tile[c][j], c < np <= j); then columns are folded in
+// pairs (np + k with f - 1 - k, m + 1 entries together, m = f - np) and the
+// lanes take one entry each, so every multiply-add of the update is done by
+// an active lane: np multiply-adds per entry, no triangular idle lanes.
+template <typename T, int S, int R>
+__device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int lane) {
+    const int m = f - np;
+    if (np == 0 || m <= 0) return;
+    for (int c = 0; c < np; c++) {
+        const T d = tile[c][c];
+        for (int j = np + lane; j < f; j += 32) tile[c][j] = tile[j][c] * d;
+    }
+    __syncwarp();
+    for (int k = 0; 2 * k < m; k++) {
+        const int a = np + k, la = m - k, b = f - 1 - k;
+        const int lb = b > a ? k + 1 : 0;
+#pragma unroll
+        for (int r = 0; r < R; r++) {
+            const int e = lane + 32 * r;
+            int i = -1, j = 0;
+            if (e < la) {
+                i = a + e;
+                j = a;
+            } else if (e < la + lb) {
+                i = b + (e - la);
+                j = b;
+            }
+            if (i >= 0) {
+                T acc = (T)0;
+#pragma unroll 4
+                for (int c = 0; c < np; c++) acc += tile[i][c] * tile[c][j];
+                tile[i][j] -= acc;
+            }
+        }
+    }
+    __syncwarp();
+}
+template <typename T>
+__device__ __forceinline__ void trailing_update_tile(T (*tile)[33], int f, int np, int lane) {
+    trailing_update<T, 33, 1>(tile, f, np, lane);
+}
+
 // A front with f <= 32 rows held in one warp's shared-memory tile (lane i
 // owns row i): originals, extend-add, unblocked right-looking elimination,
 // then one coalesced write of the whole front (L panel, D, update block).
@@ -353,6 +398,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         }
         __syncwarp();
     }
+    // panel: the np pivot columns, rank-1 updates restricted to the panel
     for (int c = 0; c < np; c++) {
         const T d = tile[c][c];
         if (lane == 0) {
@@ -367,13 +413,15 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
             l = tile[lane][c] * dinv;
             tile[lane][c] = l;
         }
+        const T ld = l * d;
         __syncwarp();
-        for (int j = c + 1; j < f; j++) {
-            const T lj = __shfl_sync(0xffffffffu, l, j) * d;
+        for (int j = c + 1; j < np; j++) {
+            const T lj = __shfl_sync(0xffffffffu, ld, j);
             if (lane >= j && lane < f) tile[lane][j] -= l * lj;
         }
         __syncwarp();
     }
+    trailing_update_tile<T>(tile, f, np, lane);
     for (int j = 0; j < f; j++)
         if (lane < f) Fr[(int64_t)j * f + lane] = tile[lane][j];
 }
@@ -446,13 +494,14 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
             M[i1][c] = l1;
         }
         __syncwarp();
-        for (int j = c + 1; j < f; j++) {
+        for (int j = c + 1; j < np; j++) {   // panel columns only
             const T lj = M[j][c] * d;
             if (i0 >= j && i0 < f) M[i0][j] -= l0 * lj;
             if (i1 >= j && i1 < f) M[i1][j] -= l1 * lj;
         }
         __syncwarp();
     }
+    trailing_update<T, kMedF + 1, 2>(M, f, np, lane);
     for (int j = 0; j < f; j++) {
         T *colj = Fr + (int64_t)j * f;
         if (i0 < f) colj[i0] = M[i0][j];
