@@ -549,9 +549,12 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 3)
 }
 
 // Phase 2: medium fronts and their ancestors (all f <= 64), one warp per
-// front with its own 64 x 65 shared front.
+// front with its own 64 x 65 shared front.  FP64 fronts take 33 KB: one
+// warp per CTA lets six of them share an SM (four-warp CTAs fit only one).
 template <typename T>
-__global__ void __launch_bounds__(kWT)
+constexpr int med_threads() { return sizeof(T) == 4 ? kWT : 32; }
+template <typename T>
+__global__ void __launch_bounds__(med_threads<T>())
     k_factor_med(DevFront F, T *__restrict__ fronts, FactorStatus *st, QueueView Q,
                  double pivot_tol, int spin_limit) {
     extern __shared__ __align__(16) unsigned char med_smem[];
@@ -1263,7 +1266,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     launch_queue_reset(F, seeds, F.pend_factor, s);
     static int grids[2][2] = {{0, 0}, {0, 0}};   // [float, double][phase 1, 2]
     const size_t sm1 = sizeof(T) * (size_t)(kFT / 32) * 32 * 33;
-    const size_t sm2 = sizeof(T) * (size_t)(kWT / 32) * kMedF * (kMedF + 1);
+    const size_t sm2 = sizeof(T) * (size_t)(med_threads<T>() / 32) * kMedF * (kMedF + 1);
     int *g = grids[sizeof(T) == 4 ? 0 : 1];
     if (!g[0]) {
         for (const void *k : {(const void *)k_factor<float>, (const void *)k_factor<double>}) {
@@ -1275,7 +1278,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
             cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, 100);
         }
         g[0] = resident_grid((const void *)k_factor<T>, kFT, sm1);
-        g[1] = resident_grid((const void *)k_factor_med<T>, kWT, sm2);
+        g[1] = resident_grid((const void *)k_factor_med<T>, med_threads<T>(), sm2);
     }
     const int n1 = F.n_items_small, n2 = F.n_items_med - F.n_items_small;
     if (n1 > 0) {
@@ -1283,8 +1286,9 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
         note_launch(), k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, n1), pivot_tol, spin_limit);
     }
     if (n2 > 0) {
-        const int grid = std::min(g[1], (n2 + kWT / 32 - 1) / (kWT / 32));
-        note_launch(), k_factor_med<T><<<grid, kWT, sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
+        const int wpc = med_threads<T>() / 32;
+        const int grid = std::min(g[1], (n2 + wpc - 1) / wpc);
+        note_launch(), k_factor_med<T><<<grid, med_threads<T>(), sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
                                                spin_limit);
     }
     const int nbig = F.n_items - F.n_items_med;
