@@ -219,6 +219,7 @@ int setup_device(scopf_handle *h) {
     h->fronts = fr;
     h->vec = vv;
     TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->S));
+    TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->Sinv));
     TRY(alloc(h, (size_t)M.nborder + 1, &h->border_work));
     {
         const size_t nt = HF.n_items > 0 ? (size_t)HF.n_items : 1;
@@ -746,6 +747,10 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     h->timer.begin(PH_SCHUR, s);
     launch_schur_sum<T>(h->df, fr, h->S, s);
     launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s);
+    // FP32 block factors: the border block is applied through S^-1 (a mat-vec
+    // per solve instead of two sequential triangular solves); the refinement
+    // corrects its rounding like that of the block factors
+    if (sizeof(T) == 4) launch_dense_inverse(h->S, (int)h->M.nborder, h->Sinv, s);
     h->timer.end(PH_SCHUR, s);
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
@@ -774,8 +779,8 @@ template <typename T>
 static int solve_once(scopf_handle *h, const double *b, double *x) {
     h->timer.begin(PH_SOLVE, h->stream);
     launch_solve<T>(h->df, reinterpret_cast<T *>(h->fronts), reinterpret_cast<T *>(h->vec), h->S,
-                    (int)h->M.nborder, h->scale, b, x, h->border_work, h->fstat,
-                    h->opt.spin_limit, h->stream);
+                    sizeof(T) == 4 ? h->Sinv : nullptr, (int)h->M.nborder, h->scale, b, x,
+                    h->border_work, h->fstat, h->opt.spin_limit, h->stream);
     h->timer.end(PH_SOLVE, h->stream);
     return SCOPF_OK;
 }

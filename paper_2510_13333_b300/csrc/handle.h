@@ -105,6 +105,7 @@ struct scopf_handle {
     double *wl = nullptr, *wu = nullptr;
     void *fronts = nullptr, *vec = nullptr;
     double *S = nullptr, *border_work = nullptr;
+    double *Sinv = nullptr;                           // S^-1 (mixed-precision solves)
     double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
     double *kst = nullptr;                                  // FGMRES small dense state

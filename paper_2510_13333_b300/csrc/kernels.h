@@ -203,11 +203,15 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
 template <typename T>
 void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s);
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s);
+// Sinv = S^-1 from the LDL^T factors in S (one triangular solve pair per column)
+void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s);
 
 // x = K^-1 b through the factors of D K D: x = D (DKD)^-1 D b
 template <typename T>
-void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
-                  const double *scale, const double *b, double *x, double *border_work,
+// Sinv: explicit inverse of S (n x n, column-major) or NULL to solve with
+// the LDL^T factors held in S
+void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, const double *Sinv,
+                  int nS, const double *scale, const double *b, double *x, double *border_work,
                   FactorStatus *st, int spin_limit, cudaStream_t s);
 
 }  // namespace scopf

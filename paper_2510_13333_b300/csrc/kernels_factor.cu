@@ -986,7 +986,8 @@ __global__ void k_rhs_to_fronts(int64_t n, const int64_t *__restrict__ vpos,
 constexpr int kBS = 1024;   // threads of the border solve
 template <typename T>
 __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__restrict__ vec,
-                                                      const double *__restrict__ S, int n,
+                                                      const double *__restrict__ S,
+                                                      const double *__restrict__ Sinv, int n,
                                                       const double *__restrict__ b,
                                                       const double *__restrict__ scale,
                                                       double *__restrict__ x,
@@ -1015,6 +1016,18 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
         y[j] = acc;
     }
     __syncthreads();
+    if (Sinv) {
+        // S^-1 y with the explicit inverse (one independent dot per row)
+        for (int j = tid; j < n; j += kBS) sm[j] = y[j];
+        __syncthreads();
+        for (int j = tid; j < n; j += kBS) {
+            double acc = 0.0;
+            for (int k = 0; k < n; k++) acc += Sinv[(int64_t)k * n + j] * sm[k];
+            const int64_t r = F.border_rows[j];
+            x[r] = scale[r] * acc;
+        }
+        return;
+    }
     block_ldlt_solve<kBS>(S, n, y);
     for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
@@ -1022,32 +1035,48 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
     }
 }
 
-// f <= 32: lane i owns row i; L' z = y on the pivot rows with the update
-// rows' final values, column dot products by warp reductions
-template <typename T, int NP>
+// column j of S^-1 from the LDL^T factors of S (one CTA per column)
+__global__ void __launch_bounds__(256) k_dense_inverse(const double *__restrict__ S, int n,
+                                                       double *__restrict__ Sinv) {
+    const int j = blockIdx.x;
+    double *y = Sinv + (int64_t)j * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = i == j ? 1.0 : 0.0;
+    __syncthreads();
+    block_ldlt_solve<256>(S, n, y);
+}
+
+// f <= FB <= 32: lane c < np holds column c of the L panel (rows below c);
+// every lane holds one row's value z (pivot rows: y, update rows: the final
+// solution of ancestors and border).  Rows are finished from the last one up:
+// row i's final value is broadcast once and each column lane adds its
+// L[i][c] z_i, so pivot c's sum is complete when its turn comes.  One shuffle
+// per front row.
+template <typename T, int FB>
 __device__ __forceinline__ void bwd_small(const T *__restrict__ L, const T *__restrict__ v,
                                           const int64_t *__restrict__ rows,
                                           const double *__restrict__ scale,
                                           double *__restrict__ x, int f, int np, int lane) {
-    T Lr[NP];
+    T Lc[FB];
 #pragma unroll
-    for (int c = 0; c < NP; c++) Lr[c] = (c < np && lane > c && lane < f) ? L[(int64_t)c * f + lane] : (T)0;
-    T vi = (T)0;
+    for (int i = 0; i < FB; i++)
+        Lc[i] = (lane < np && i > lane && i < f) ? L[(int64_t)lane * f + i] : (T)0;
+    T z = (T)0;
     int64_t r = 0;
     if (lane < f) r = rows[lane];
     if (lane < np)
-        vi = v[lane];
+        z = v[lane];
     else if (lane < f)
-        vi = (T)(x[r] / scale[r]);
+        z = (T)(x[r] / scale[r]);
+    T acc = (T)0;
 #pragma unroll
-    for (int c = NP - 1; c >= 0; c--) {
-        if (c < np) {
-            T p = Lr[c] * vi;
-            for (int o = 16; o > 0; o >>= 1) p += __shfl_xor_sync(0xffffffffu, p, o);
-            if (lane == c) vi -= p;
+    for (int i = FB - 1; i >= 0; i--) {
+        if (i < f) {
+            if (lane == i && i < np) z -= acc;
+            const T zi = __shfl_sync(0xffffffffu, z, i);
+            acc += Lc[i] * zi;
         }
     }
-    if (lane < np) x[r] = scale[r] * (double)vi;
+    if (lane < np) x[r] = scale[r] * (double)z;
 }
 
 // Backward sweep of one (non-border) front: its update rows hold the final
@@ -1062,8 +1091,8 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
     T *v = vec + ti.vo;
     const int64_t *rows = F.rows + ti.vo;
     if (f <= 32) {
-        if (np <= 8)
-            bwd_small<T, 8>(L, v, rows, scale, x, f, np, lane);
+        if (f <= 16)
+            bwd_small<T, 16>(L, v, rows, scale, x, f, np, lane);
         else
             bwd_small<T, 32>(L, v, rows, scale, x, f, np, lane);
         return;
@@ -1318,6 +1347,10 @@ void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_
     note_launch(), k_schur_sum<T><<<(nb * nb + 255) / 256, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
 }
 
+void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s) {
+    if (n > 0) note_launch(), k_dense_inverse<<<n, 256, 0, s>>>(S, n, Sinv);
+}
+
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
     for (int k0 = 0; k0 < n; k0 += kPanel) {
         const int k1 = k0 + kPanel < n ? k0 + kPanel : n;
@@ -1336,8 +1369,8 @@ void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cud
 }
 
 template <typename T>
-void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, int nS,
-                  const double *scale, const double *b, double *x, double *border_work,
+void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, const double *Sinv,
+                  int nS, const double *scale, const double *b, double *x, double *border_work,
                   FactorStatus *st, int spin_limit, cudaStream_t s) {
     // queue a: forward sweep (all items), queue b: backward sweep (non-border)
     QueueSeeds seeds{{F.init_fwd, F.init_bwd, F.init_bwd}, {F.n_init_fwd, F.n_init_bwd, 0}};
@@ -1359,7 +1392,7 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
     {
         const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
         note_launch(), k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
-            F, vec, S, nS, b, scale, x, border_work);
+            F, vec, S, Sinv, nS, b, scale, x, border_work);
     }
     const int nb = F.n_items - F.n_blocks;   // every item but the border fronts
     if (nb > 0)
@@ -1371,9 +1404,9 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, i
     template void launch_factor<T>(const DevFront &, T *, FactorStatus *, double, int,           \
                                    cudaStream_t);                                                \
     template void launch_schur_sum<T>(const DevFront &, const T *, double *, cudaStream_t);      \
-    template void launch_solve<T>(const DevFront &, const T *, T *, const double *, int,          \
-                                  const double *, const double *, double *, double *,             \
-                                  FactorStatus *, int, cudaStream_t);
+    template void launch_solve<T>(const DevFront &, const T *, T *, const double *,               \
+                                  const double *, int, const double *, const double *, double *,  \
+                                  double *, FactorStatus *, int, cudaStream_t);
 INST(float)
 INST(double)
 
