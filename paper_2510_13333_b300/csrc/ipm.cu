@@ -334,7 +334,8 @@ struct Timer {
 
 }  // namespace
 
-int ipm_partials() { return kB * 9; }
+constexpr int kPartSlots = 24;   // partial-sum slots per reduction block
+int ipm_partials() { return kB * kPartSlots; }
 
 // Inertia correction (W&B 2006, Alg. IC) around the factorization of the
 // assembled K: delta_w = 0 first (unless it already showed zero pivots),
@@ -398,19 +399,22 @@ struct Ipm {
         D = Dev{h->wl, h->wu, h->dm.comp1, h->dm.comp2, n, m, p};
         n_il = h->n_lower;
         n_iu = h->n_upper;
-        part.resize(kB * 9);
+        part.resize(kB * kPartSlots);
         dpart = h->ipm_part;
     }
 
-    // fetch kB x k partials and combine in block order
+    // Several reductions write kB x k partials into consecutive regions of
+    // dpart; one copy and one synchronisation bring them all to the host,
+    // where each is combined in block order.
     void fetch(int k) {
         cudaMemcpyAsync(part.data(), dpart, sizeof(double) * kB * k, cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
     }
-    double comb(int k, int slot, int op) {
+    double comb(int k, int slot, int op, int region = 0) {
         double a = op == 0 ? -INFINITY : (op == 1 ? INFINITY : 0.0);
+        const double *pp = part.data() + (size_t)kB * region;
         for (int b = 0; b < kB; b++) {
-            const double v = part[(size_t)b * k + slot];
+            const double v = pp[(size_t)b * k + slot];
             a = op == 0 ? std::fmax(a, v) : (op == 1 ? std::fmin(a, v) : a + v);
         }
         return a;
@@ -423,30 +427,32 @@ struct Ipm {
     };
     Norms norms(const scopf_state &st, double rho) {
         Norms N{};
+        // regions: w (7 slots) at 0, constraint rows (5) at 7, pairs (9) at 12
         note_launch(), k_red_w<<<kB, kT, 0, s>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
-        fetch(7);
+        note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart + kB * 7);
+        if (p)
+            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho,
+                                                      dpart + kB * 12);
+        fetch(p ? 21 : 12);
         double dw = comb(7, 0, 0);
         double cmin = std::fmin(comb(7, 1, 1), comb(7, 3, 1));
         double cmax = std::fmax(comb(7, 2, 0), comb(7, 4, 0));
         double zsum = comb(7, 5, 2) + comb(7, 6, 2);
-        note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart);
-        fetch(5);
-        double gr = comb(5, 0, 0), pc = comb(5, 1, 0), pcs = comb(5, 2, 2), lsum = comb(5, 3, 2);
-        N.rmax = comb(5, 4, 0);
+        double gr = comb(5, 0, 0, 7), pc = comb(5, 1, 0, 7), pcs = comb(5, 2, 2, 7),
+               lsum = comb(5, 3, 2, 7);
+        N.rmax = comb(5, 4, 0, 7);
         double gt = 0, gs = 0, py = 0, pys = 0, ycs = 0, zss = 0;
         N.tmax = 0;
         if (p) {
-            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho, dpart);
-            fetch(9);
-            gt = comb(9, 0, 0);
-            gs = comb(9, 1, 0);
-            py = comb(9, 2, 0);
-            pys = comb(9, 3, 2);
-            cmin = std::fmin(cmin, comb(9, 4, 1));
-            cmax = std::fmax(cmax, comb(9, 5, 0));
-            ycs = comb(9, 6, 2);
-            zss = comb(9, 7, 2);
-            N.tmax = comb(9, 8, 0);
+            gt = comb(9, 0, 0, 12);
+            gs = comb(9, 1, 0, 12);
+            py = comb(9, 2, 0, 12);
+            pys = comb(9, 3, 2, 12);
+            cmin = std::fmin(cmin, comb(9, 4, 1, 12));
+            cmax = std::fmax(cmax, comb(9, 5, 0, 12));
+            ycs = comb(9, 6, 2, 12);
+            zss = comb(9, 7, 2, 12);
+            N.tmax = comb(9, 8, 0, 12);
         }
         N.dual = std::fmax(std::fmax(dw, gr), std::fmax(gt, gs));
         N.prim = std::fmax(pc, py);
@@ -472,27 +478,48 @@ struct Ipm {
         scopf_eval(h, w, &f, nullptr, nullptr);
         return f;
     }
-    double barrier(const scopf_state &st, double rho, double mu, double phi) {
-        note_launch(), k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho, dpart);
-        fetch(5);
-        if (comb(5, 4, 2) > 0) return INFINITY;
-        return phi + comb(5, 2, 2) + comb(5, 3, 2) - mu * (comb(5, 0, 2) + comb(5, 1, 2));
+    // partials of k regions and p_g^0 of w in one copy + synchronisation
+    std::vector<double> p0h;
+    void fetch_p0(int k, const double *w) {
+        const Model &M = h->M;
+        p0h.resize(M.ng);
+        cudaMemcpyAsync(part.data(), dpart, sizeof(double) * kB * k, cudaMemcpyDeviceToHost, s);
+        if (M.ng)
+            cudaMemcpyAsync(p0h.data(), w + M.border0, sizeof(double) * M.ng,
+                            cudaMemcpyDeviceToHost, s);
+        cudaStreamSynchronize(s);
     }
-    double theta_trial(const scopf_state &st) {
-        // c(w) at the trial point, then sum|c - r| + sum|w1 w2 - t + s|
+    // phi from the fetched p_g^0 (same formula as scopf_eval)
+    double phi_host() const {
+        const Model &M = h->M;
+        double f = 0;
+        for (int i = 0; i < M.ng; i++) {
+            const double pv = 100.0 * p0h[i];
+            f += M.c2[i] * pv * pv + M.c1[i] * pv + M.c0[i];
+        }
+        return f / 1.0e4;
+    }
+    // barrier function from its partials (5 slots at `region`)
+    double barrier_value(double phi, double mu, int region) {
+        if (comb(5, 4, 2, region) > 0) return INFINITY;
+        return phi + comb(5, 2, 2, region) + comb(5, 3, 2, region) -
+               mu * (comb(5, 0, 2, region) + comb(5, 1, 2, region));
+    }
+    // theta and the barrier function at a trial point, one round trip:
+    // constraint rows at region 0 (5), pairs at 5 (9), barrier at 14 (5)
+    void trial_eval(const scopf_state &st, double rho, double mu, double &theta, double &phib) {
         launch_eval_elements(h->dm, st.w, st.lam, st.yc, h->ev, 0, s);
         launch_constraints(h->dm, st.w, h->ev, h->c, s);
         note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, 1.0, dpart);
-        fetch(5);
-        double th = comb(5, 2, 2);
-        if (p) {
-            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, 1.0, dpart);
-            fetch(9);
-            th += comb(9, 3, 2);
-        }
-        return th;
+        if (p)
+            note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, 1.0,
+                                                      dpart + kB * 5);
+        note_launch(), k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
+                                                    dpart + kB * 14);
+        fetch_p0(19, st.w);
+        theta = comb(5, 2, 2) + (p ? comb(9, 3, 2, 5) : 0.0);
+        phib = barrier_value(phi_host(), mu, 14);
     }
-
     void copy(scopf_state &dst, const scopf_state &src) {
         const int64_t len[9] = {n, m, p, p, m, p, n, n, p};
         double *const *a[9] = {&dst.w, &dst.r, &dst.t, &dst.s, &dst.lam, &dst.yc, &dst.zl, &dst.zu, &dst.zs};
@@ -649,24 +676,26 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
                                                    st.zl, st.zu, st.zs, h->lam_n, h->nu0_n, rho,
                                                    mu, d.w, d.lam, d.yc, d.r, d.t, d.s, d.zl,
                                                    d.zu, d.zs);
+            // fraction to the boundary (region 0, 2 slots), barrier function at
+            // the current point (region 2, 5 slots) and its directional
+            // derivative (region 7, 5 slots; h->g holds grad phi): one round trip
             note_launch(), k_ftb<<<kB, kT, 0, s>>>(D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu,
                                     d.zs, tau, I.dpart);
-            I.fetch(2);
+            note_launch(), k_barrier<<<kB, kT, 0, s>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
+                                                        I.dpart + kB * 2);
+            note_launch(), k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
+                                         mu, d.w, d.r, d.t, d.s, I.dpart + kB * 7);
+            I.fetch_p0(12, st.w);
             double ap = 1.0, az = 1.0;
             for (int b = 0; b < kB; b++) {
                 ap = std::fmin(ap, I.part[2 * b]);
                 az = std::fmin(az, I.part[2 * b + 1]);
             }
-            // line search quantities at the current point (h->g holds grad phi)
             const double th = N.theta;
-            const double phi_cur = I.objective(st.w);
-            const double ph = I.barrier(st, rho, mu, phi_cur);
-            note_launch(), k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
-                                         mu, d.w, d.r, d.t, d.s, I.dpart);
-            I.fetch(5);
+            const double ph = I.barrier_value(I.phi_host(), mu, 2);
             double gd = 0;
             for (int b = 0; b < kB; b++)
-                for (int q = 0; q < 5; q++) gd += I.part[(size_t)b * 5 + q];
+                for (int q = 0; q < 5; q++) gd += I.part[(size_t)kB * 7 + (size_t)b * 5 + q];
             double amin;
             if (gd < 0)
                 amin = o.gamma_alpha * std::fmin(o.gamma_theta, std::fmin(o.gamma_phi * th / -gd,
@@ -678,8 +707,8 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             int nback = 0;
             while (true) {
                 I.step(tr, st, d, a, az);
-                const double tht = I.theta_trial(tr);
-                const double pht = I.barrier(tr, rho, mu, I.objective(tr.w));
+                double tht, pht;
+                I.trial_eval(tr, rho, mu, tht, pht);
                 bool ok = false;
                 ftype = false;
                 bool in_filter = false;
@@ -830,8 +859,8 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
         az = std::fmin(az, I.part[2 * b + 1]);
     }
     I.step(h->trial, st, d, ap, az);
-    const double tht = I.theta_trial(h->trial);
-    const double pht = I.barrier(h->trial, rho, mu, I.objective(h->trial.w));
+    double tht, pht;
+    I.trial_eval(h->trial, rho, mu, tht, pht);
     cudaStreamSynchronize(s);
     h->timer.end(PH_IPM, s);
     cudaStreamSynchronize(s);
