@@ -348,7 +348,7 @@ void scopf_default_options(scopf_options *o) {
     o->verbose = 0;
     o->spin_limit = 1 << 24;
     o->host_only = 0;
-    o->cluster_max_tasks = 8;
+    o->cluster_max_tasks = 16;
     o->relax_max_front = 0;
 }
 
