@@ -205,8 +205,9 @@ def make_network(rng: SplitMix64, n_bus: int, mean_degree: float, n_gen: int,
     d2 = ((xy[:, None, :] - xy[None, :, :]) ** 2).sum(-1)
     np.fill_diagonal(d2, np.inf)
     cand = set()
+    k = min(knn, n_bus - 1)   # never the bus itself (its distance is inf)
     for i in range(n_bus):
-        nbrs = np.argsort(d2[i], kind="stable")[:knn]
+        nbrs = np.argsort(d2[i], kind="stable")[:k]
         for j in nbrs.tolist():
             cand.add((min(i, j), max(i, j)))
     cand = sorted(cand)
