@@ -309,6 +309,30 @@ int scopf_set_ncl_params(scopf_handle *h, const double *lam_n, const double *nu0
 int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
                   double *grad_Pd, double *grad_Qd, double *grad_c1);
 
+/* Per-scenario infeasibility of the handle's current iterate: viol[k] =
+ * |(r_k, t_k)|_inf over the constraint rows and complementarity pairs of
+ * scenario k (k = 0 base case), the relaxations of eq. (nclsubpb).  viol:
+ * host, n_blocks = K + 1.  A NaN entry of r or t reports as +inf. */
+int scopf_block_violation(scopf_handle *h, double *viol);
+
+/* Batched contingency screening (Section V-B, eqs. (screening), (feaspb)):
+ * every scenario of the handle is checked for feasibility at the base-case
+ * control u0 in one NCL solve.  u0 (host, n_border) boxes the first-stage
+ * variables to [max(lo, u0 - eps), min(hi, u0 + eps)], widened to width eps
+ * where u0 sits on a limit (eps > 0; a tiny eps decouples the scenarios into
+ * the per-contingency systems); u0 = NULL leaves them free.  The outer loop
+ * runs per block: while one scenario drives rho up, every scenario with
+ * |(r_k, t_k)|_inf <= eta still takes its multiplier update.  The solve caps rho at rho_cap (the
+ * handle's iteration limits apply); res receives its outcome, viol[k] (host, K + 1) the scenario's
+ * |(r_k, t_k)|_inf at the end, and accepted[k] (host, K + 1) is 1 when
+ * viol[k] <= accept_tol and the solve ended by convergence, by the rho cap
+ * (SCOPF_ERR_INFEASIBLE) or by the outer-iteration limit, else 0.  The
+ * handle's bounds and options are restored on return; its iterate is the
+ * screening solve's final one.  Returns SCOPF_OK whenever the verdicts were
+ * computed (res->status carries the solve's own status). */
+int scopf_screen(scopf_handle *h, const double *u0, double eps, double rho_cap,
+                 double accept_tol, scopf_result *res, double *viol, int32_t *accepted);
+
 #ifdef __cplusplus
 }
 #endif

@@ -446,7 +446,14 @@ class NCLSolver:
                                      tries=tries, backtracks=nback, restored=not accepted))
 
     # ---------------------------------------------------------- outer loop
-    def solve(self, warm: State | None = None, params: Params | None = None, mu: float | None = None):
+    def solve(self, warm: State | None = None, params: Params | None = None, mu: float | None = None,
+              blocks=None):
+        """NCL outer loop.  ``blocks`` (a list of (c0, nrow, p0, ncomp) row
+        ranges of r and t that no constraint couples, as for scenarios at a
+        fixed first stage) switches on the per-block rule of batched
+        screening: when max(|r|, |t|) > eta, every block whose own
+        max(|r_k|, |t_k|) <= eta still takes its multiplier update -- as it
+        would in a solve of its own -- before rho grows."""
         o = self.o
         t0 = time.perf_counter()
         st = warm.copy() if warm is not None else self.initial_state()
@@ -477,10 +484,18 @@ class NCLSolver:
                 eta = max(eta / 10.0, o.tol)
                 omega = max(omega / 10.0, o.tol)
             else:
+                lam_n, nu0_n = prm.lam_n, prm.nu0_n
+                if blocks is not None:
+                    lam_n, nu0_n = lam_n.copy(), nu0_n.copy()
+                    for c0, nrow, p0, ncomp in blocks:
+                        rk, tk = st.r[c0:c0 + nrow], st.t[p0:p0 + ncomp]
+                        if max(_inf(rk), _inf(tk)) <= max(eta, o.tol):
+                            lam_n[c0:c0 + nrow] += prm.rho * rk
+                            nu0_n[p0:p0 + ncomp] += prm.rho * tk
                 if prm.rho * 10.0 > o.rho_max:
                     status = "infeasible"
                     break
-                prm = Params(rho=prm.rho * 10.0, lam_n=prm.lam_n, nu0_n=prm.nu0_n)
+                prm = Params(rho=prm.rho * 10.0, lam_n=lam_n, nu0_n=nu0_n)
         res = self.residuals(st, prm)
         viol = self.max_violation(st.w, res["c"])
         return Result(status=status, state=st, params=prm, objective=self.P.objective(st.w),

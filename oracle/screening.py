@@ -56,6 +56,18 @@ def base_opf(inst, opts: Options | None = None, derate: float | None = None,
     return res, u0
 
 
+def box_first_stage(M, u0, eps):
+    """Hold the first-stage variables within eps of u0: bounds
+    [max(lo, u0 - eps), min(hi, u0 + eps)], widened to width eps where u0
+    sits on (or beyond) a limit."""
+    b = np.arange(M.border0, M.border0 + M.nborder)
+    lo, hi = M.wl[b].copy(), M.wu[b].copy()
+    M.wl[b] = np.maximum(lo, u0 - eps)
+    M.wu[b] = np.minimum(hi, u0 + eps)
+    M.wl[b] = np.minimum(M.wl[b], M.wu[b] - eps)
+    M.wu[b] = np.maximum(M.wu[b], M.wl[b] + eps)
+
+
 def screen_candidate(inst, cand, u0, eps: float | None = None, rho_cap: float = 1e6,
                      accept_tol: float = 1e-4, opts: Options | None = None):
     """Feasibility of one contingency at the base control u0.
@@ -63,13 +75,7 @@ def screen_candidate(inst, cand, u0, eps: float | None = None, rho_cap: float = 
     Returns (accepted, |(r,t)|_inf, status)."""
     M = SCOPFModel(sub_instance(inst, [cand]))
     if eps is not None:
-        b = np.arange(M.border0, M.border0 + M.nborder)
-        lo, hi = M.wl[b].copy(), M.wu[b].copy()
-        M.wl[b] = np.maximum(lo, u0 - eps)
-        M.wu[b] = np.minimum(hi, u0 + eps)
-        # keep a nonempty interval when u0 sits on a limit
-        M.wl[b] = np.minimum(M.wl[b], M.wu[b] - eps)
-        M.wu[b] = np.maximum(M.wu[b], M.wl[b] + eps)
+        box_first_stage(M, u0, eps)
     o = opts or Options()
     o = Options(**{**o.__dict__, "rho_max": rho_cap, "max_inner": 1000})
     res = _solver(M, o).solve()
@@ -78,3 +84,37 @@ def screen_candidate(inst, cand, u0, eps: float | None = None, rho_cap: float = 
     # to the complementarity floor sqrt(mu_min / rho) of the capped penalty
     ok = res.feas_rt <= accept_tol and res.status in ("ok", "infeasible", "max_outer")
     return ok, float(res.feas_rt), res.status
+
+
+def block_violation(M, st):
+    """|(r_k, t_k)|_inf of every scenario block (k = 0 base case)."""
+    def inf(x):
+        return float(np.max(np.abs(x))) if len(x) else 0.0
+    return np.array([max(inf(st.r[b.c0:b.c0 + b.nrow]), inf(st.t[b.p0:b.p0 + b.ncomp]))
+                     for b in M.blocks])
+
+
+def screen_batch(inst, u0, eps: float = 1e-6, rho_cap: float = 1e6, accept_tol: float = 1e-4,
+                 opts: Options | None = None):
+    """All contingencies of ``inst`` screened at u0 in one NCL solve.
+
+    The base case and every contingency are the scenarios of one model whose
+    first stage is held within eps of u0; at a tiny eps the scenarios
+    decouple into the per-contingency systems of eq. (screening).  The
+    outer loop runs the per-block rule of ``NCLSolver.solve`` (a block that
+    is feasible to eta takes its multiplier update even while another block
+    drives rho up), so each block ends as it would alone: at a feasible
+    point, or at the capped-penalty minimiser of its own infeasibility
+    (eq. (feaspb)).  Scenario k is accepted when its |(r_k, t_k)|_inf <=
+    accept_tol and the solve did not stop at the inner-iteration limit.
+
+    Returns (accepted[K + 1], viol[K + 1], result)."""
+    M = SCOPFModel(inst)
+    box_first_stage(M, np.asarray(u0, dtype=float), eps)
+    o = opts or Options()
+    o = Options(**{**o.__dict__, "rho_max": rho_cap})
+    blocks = [(b.c0, b.nrow, b.p0, b.ncomp) for b in M.blocks]
+    res = _solver(M, o).solve(blocks=blocks)
+    viol = block_violation(M, res.state)
+    ended = res.status in ("ok", "infeasible", "max_outer")
+    return ended & (viol <= accept_tol), viol, res

@@ -142,6 +142,9 @@ def lib():
             "scopf_adjoint": (c_i32, [H, P_dbl, c_dbl, P_dbl, P_dbl, P_dbl]),
             "scopf_set_params": (c_i32, [H, P_dbl, P_dbl, P_dbl]),
             "scopf_set_ncl_params": (c_i32, [H, P_dbl, P_dbl, c_dbl, c_dbl]),
+            "scopf_block_violation": (c_i32, [H, P_dbl]),
+            "scopf_screen": (c_i32, [H, P_dbl, c_dbl, c_dbl, c_dbl, ctypes.POINTER(Result), P_dbl,
+                                     P_i32]),
             "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
                                           c_dbl, ctypes.POINTER(State), P_dbl, P_i32]),
             "scopf_timing": (c_i32, [H, c_i32, P_dbl, P_i32]),
@@ -463,6 +466,31 @@ class SCOPF:
         """Declare the loaded state a solution with these NCL parameters."""
         _check("scopf_set_ncl_params", lib().scopf_set_ncl_params(
             self.h, _dp(lam_n), _dp(nu0_n), float(rho), float(mu)))
+
+    def block_violation(self):
+        """|(r_k, t_k)|_inf of the current iterate per scenario (numpy, K + 1)."""
+        v = np.zeros(self.sizes.n_blocks)
+        _check("scopf_block_violation", lib().scopf_block_violation(self.h, _hp(v, c_dbl)))
+        return v
+
+    def scopf_screen(self, u0=None, eps=1e-6, rho_cap=1e6, accept_tol=1e-4):
+        """Screen every scenario at the base control u0 (numpy, n_border) in
+        one solve (first stage held within eps of u0).  Returns (accepted bool[K + 1], |(r_k, t_k)|_inf[K + 1],
+        result dict); entry 0 is the base case."""
+        R = Result()
+        nblk = self.sizes.n_blocks
+        v = np.zeros(nblk)
+        acc = np.zeros(nblk, dtype=np.int32)
+        u = None
+        if u0 is not None:
+            u = np.ascontiguousarray(u0, dtype=np.float64)
+            if u.shape != (self.sizes.n_border,):
+                raise ValueError(f"u0 needs shape ({self.sizes.n_border},)")
+        _check("scopf_screen", lib().scopf_screen(
+            self.h, None if u is None else _hp(u, c_dbl), float(eps), float(rho_cap),
+            float(accept_tol), ctypes.byref(R), _hp(v, c_dbl), _hp(acc, ctypes.c_int32)))
+        out = {f: getattr(R, f) for f, _ in Result._fields_}
+        return acc.astype(bool), v, out
 
     def scopf_adjoint(self, seed_pg0=None, seed_cost=0.0):
         """Gradients of seed_pg0' p_g^0 + seed_cost * objective with respect

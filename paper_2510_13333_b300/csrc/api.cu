@@ -22,6 +22,20 @@ using namespace scopf;
 
 namespace scopf {
 std::atomic<long long> g_kernel_launches{0};
+
+// Bounds the interior-point method works with: every finite bound moved
+// outwards by bound_relax * max(1, |bound|) (W&B 2006, Section 3.5).
+void relaxed_bounds(const Model &M, double bound_relax, std::vector<double> &wl,
+                    std::vector<double> &wu) {
+    wl.resize(M.n);
+    wu.resize(M.n);
+    for (int64_t i = 0; i < M.n; i++) {
+        wl[i] = std::isfinite(M.wl[i]) ? M.wl[i] - bound_relax * std::fmax(1.0, std::fabs(M.wl[i]))
+                                       : -INFINITY;
+        wu[i] = std::isfinite(M.wu[i]) ? M.wu[i] + bound_relax * std::fmax(1.0, std::fabs(M.wu[i]))
+                                       : INFINITY;
+    }
+}
 }  // namespace scopf
 
 namespace {
@@ -147,12 +161,8 @@ int setup_device(scopf_handle *h) {
         d.n_long = (int64_t)long_rows.size();
     }
     {
-        const double rf = h->opt.bound_relax;
-        std::vector<double> wl(M.n), wu(M.n);
-        for (int64_t i = 0; i < M.n; i++) {
-            wl[i] = std::isfinite(M.wl[i]) ? M.wl[i] - rf * std::fmax(1.0, std::fabs(M.wl[i])) : -INFINITY;
-            wu[i] = std::isfinite(M.wu[i]) ? M.wu[i] + rf * std::fmax(1.0, std::fabs(M.wu[i])) : INFINITY;
-        }
+        std::vector<double> wl, wu;
+        relaxed_bounds(M, h->opt.bound_relax, wl, wu);
         const double *pl, *pu;
         TRY(upload(h, wl, &pl));
         TRY(upload(h, wu, &pu));

@@ -127,6 +127,11 @@ struct scopf_handle {
     double rho = 0.0;
     double mu_last = 0.0, dw_last = 0.0;   // barrier parameter and delta_w at the last solve's end
     bool has_solution = false;             // st, lam_n, nu0_n, rho, mu_last describe a solution
+    bool inner_limit = false;              // the last solve stopped at max_inner
+    bool screen_blocks = false;            // NCL outer loop with the per-block screening rule
+    // per-scenario ranges of r and t (c0, nrow, p0, ncomp) and their maxima
+    int64_t *blk_rt = nullptr;
+    double *blk_viol = nullptr;
     // adjoint index sets (built on first use): KKT row of every p_g^0, and
     // per bus the KKT rows of its P and Q balance in every block
     int64_t *adj_pg = nullptr, *adj_ptr = nullptr, *adj_rowsP = nullptr, *adj_rowsQ = nullptr;
@@ -147,6 +152,9 @@ struct scopf_handle {
 
 namespace scopf {
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res);
+int block_multiplier_update(scopf_handle *h, double rho, double thr);
+void relaxed_bounds(const Model &M, double bound_relax, std::vector<double> &wl,
+                    std::vector<double> &wu);
 int ipm_partials();   // doubles of the IPM reduction partial buffer
 int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n,
                   const double *nu0_n, double rho, double mu, double delta_w, double *rhs);

@@ -627,6 +627,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     double mu = o.mu_init, eta = o.eta_init, omega = o.omega_init, dw_last = 0.0;
     int status = SCOPF_ERR_MAX_ITER;
     int outer = 0, inner = 0;
+    bool inner_limit = false;
     double E0 = INFINITY, feas = INFINITY;
     double t_newton = 0.0;
     const int fact0 = h->n_factor, ref0 = h->n_refine;
@@ -761,6 +762,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             std::printf("outer %d rho %.1e |r,t| %.2e E0 %.2e inner %d\n", outer, rho, feas, E0, inner);
         if (inner_status != SCOPF_OK) {
             status = inner_status;
+            inner_limit = inner_status == SCOPF_ERR_MAX_ITER;
             break;
         }
         if (feas <= std::fmax(eta, o.tol)) {
@@ -777,6 +779,11 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
                 status = SCOPF_ERR_INFEASIBLE;
                 break;
             }
+            if (h->screen_blocks) {
+                // batched screening: blocks within eta update their multipliers
+                r = block_multiplier_update(h, rho, std::fmax(eta, o.tol));
+                if (r != SCOPF_OK) return r;
+            }
             rho *= 10.0;
         }
     }
@@ -786,6 +793,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     h->mu_last = mu;
     h->dw_last = dw_last;
     h->has_solution = status == SCOPF_OK;
+    h->inner_limit = inner_limit;
     // final report
     res->status = status;
     res->outer_iters = outer;

@@ -444,3 +444,33 @@ def config_instance(idx: int, screened: bool = True) -> Instance:
         scale = data.get("load_scale", 1.0)
     return make_instance(seed=1000 + seed_of, name=name, accepted=accepted,
                          load_scale=scale, **c)
+
+
+def screening_batch(idx: int):
+    """The candidates the oracle's screening of workload ``idx`` examined,
+    as one instance (base case + every examined outage as a scenario, line
+    outages then generator outages, each in candidate order), with the
+    stored base control u0, box half-width eps and the oracle's verdicts
+    (True = accepted) in scenario order."""
+    import json
+    with open(screening_file(idx)) as fh:
+        data = json.load(fh)
+    c = dict(CONFIGS[idx])
+    name = c.pop("name")
+    seed_of = c.pop("network_seed_of", idx)
+    c.pop("screen_as", None)
+    inst = make_instance(seed=1000 + seed_of, name=name, load_scale=data.get("load_scale", 1.0),
+                         **c)
+    acc = {"line": set(data["accepted_lines"]), "gen": set(data["accepted_gens"])}
+    rej = {"line": set(), "gen": set()}
+    for r in data["rejected"]:
+        rej[r["kind"]].add(int(r["element"]))
+    ctgs, verdict = [], []
+    for kind, cands in (("line", inst.candidates.lines), ("gen", inst.candidates.gens)):
+        for cand in cands:
+            if cand.element in acc[kind] or cand.element in rej[kind]:
+                ctgs.append(cand)
+                verdict.append(cand.element in acc[kind])
+    inst.ctgs = ctgs
+    inst.recipe = dict(inst.recipe, screening_batch=True)
+    return inst, np.asarray(data["u0"]), float(data["fix_eps"]), verdict
