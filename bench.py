@@ -9,8 +9,10 @@ factor, solves with FP64 iterative refinement, recovery of the eliminated
 directions, fraction-to-boundary and one trial evaluation.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                    [--workload newton|screen]
 
-Prints one JSON line.  With --impl reference the CPU oracle is timed on a
+Prints one JSON line.  --workload screen times batched contingency
+screening (Section V-B) of the same network's candidate outages instead.  With --impl reference the CPU oracle is timed on a
 bounded sample of the same workload (the reference arm of this build).
 """
 from __future__ import annotations
@@ -39,8 +41,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
 # valid only for the sweep kernels' source it was taken with
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "8561b4d3ff2b1dc0e98e2cc723a11dcac7b96df1",
-                 "bytes_per_solve": 255.4e6 + 305.9e6}
+                 "sha1": "4bd2bb1b9a1ddcdcab3094fd9f53dc772b80e629",
+                 "bytes_per_solve": 254.0e6 + 303.6e6}
 
 
 def sweep_traffic():
@@ -161,6 +163,29 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "Newton steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def roofline(sz, phases, dom):
+    """Roofline object of the dominant phase (factor: FP32 ALU; solve: HBM)."""
+    peaks, peak_kind = measured_peaks()
+    fac_ms, fac_calls = phases["factor"]
+    sol_ms, sol_calls = phases["solve"]
+    if dom == "factor":
+        achieved = sz.factor_flops / (fac_ms / fac_calls / 1e3) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+                "kernel": "k_factor<float> (persistent supernodal LDL^T, all blocks)",
+                "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+    else:
+        # one solve = forward sweep + border solve + backward sweep: every FP32
+        # factor entry is read twice, plus D b in, x out and the scaling
+        bytes_ = 2 * 4 * sz.nnz_L + 3 * 8 * sz.n_kkt
+        achieved = bytes_ / (sol_ms / sol_calls / 1e3) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": sweep_traffic(),
+                "kernel": "k_solve_fwd + k_border_solve + k_solve_bwd <float> (one solve)",
+                "algorithmic_bytes": bytes_, "peak_kind": peak_kind}
+    return roof
 
 
 # -------------------------------------------------------------------- our arm
@@ -298,24 +323,7 @@ def run_ours(args):
     # roofline of the dominant phase (from CUDA events on the handle's stream)
     dom = max(("factor", "solve", "assemble", "residual", "schur", "front_init", "ipm"),
               key=lambda k: ph_mixed[k][0])
-    fac_ms, fac_calls = ph_mixed["factor"]
-    sol_ms, sol_calls = ph_mixed["solve"]
-    peaks, peak_kind = measured_peaks()
-    if dom == "factor":
-        achieved = sz.factor_flops / (fac_ms / fac_calls / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_factor<float> (persistent supernodal LDL^T, all blocks)",
-                "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
-    else:
-        # one solve = forward sweep + border solve + backward sweep: every FP32
-        # factor entry is read twice, plus D b in, x out and the scaling
-        bytes_ = 2 * 4 * sz.nnz_L + 3 * 8 * sz.n_kkt
-        achieved = bytes_ / (sol_ms / sol_calls / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": sweep_traffic(),
-                "kernel": "k_solve_fwd + k_border_solve + k_solve_bwd <float> (one solve)",
-                "algorithmic_bytes": bytes_, "peak_kind": peak_kind}
+    roof = roofline(sz, ph_mixed, dom)
     try:
         cpu_s, cpu_desc, cores = oracle_step_sample()
         cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
@@ -355,6 +363,116 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
+# --------------------------------------------------------- screening workload
+SCREEN_EPS = 1e-6      # first stage held within 1e-6 of u0 (scenarios decouple)
+SCREEN_RHO_CAP = 1e6
+SCREEN_TOL = 1e-4
+
+
+def oracle_screen_sample(n_sample: int = 8):
+    """The CPU oracle screening candidates one by one (screen_candidate, a
+    two-scenario NCL solve each) on the first n_sample candidates of the
+    500-bus screening batch; returns (seconds per contingency, description)."""
+    import synthgrid
+    from oracle.screening import screen_candidate
+    inst, u0, _, _ = synthgrid.screening_batch(CONFIG_IDX)
+    t0 = time.perf_counter()
+    for cand in inst.ctgs[:n_sample]:
+        screen_candidate(inst, cand, u0, eps=SCREEN_EPS, rho_cap=SCREEN_RHO_CAP,
+                         accept_tol=SCREEN_TOL)
+    t = time.perf_counter() - t0
+    desc = (f"oracle screen_candidate (numpy/scipy + C LDL^T, 1 thread), one two-scenario NCL "
+            f"solve per candidate, first {n_sample} of {len(inst.ctgs)} candidates of the "
+            f"500-bus screening batch ({t:.1f} s)")
+    return t / n_sample, desc
+
+
+def run_screen(args):
+    """Batched screening of the 500-bus workload's candidate outages at the
+    stored base-case control u0 (Section V-B, Table 1's task): one step is
+    one scopf_screen call over all candidates."""
+    import numpy as np
+    import torch
+    import synthgrid
+    import paper_2510_13333_b300 as P
+
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:        # replicas only: one screening batch per process
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    inst, u0, _, stored = synthgrid.screening_batch(CONFIG_IDX)
+    n_ctg = len(inst.ctgs)
+    lib = P.SCOPF(inst, precision=P.PREC_MIXED)
+    sz = lib.sizes
+    steps = max(1, min(args.steps, 10))
+
+    def screen():
+        return lib.scopf_screen(u0, eps=SCREEN_EPS, rho_cap=SCREEN_RHO_CAP,
+                                accept_tol=SCREEN_TOL)
+
+    for _ in range(args.warmup):
+        acc, viol, res = screen()
+    torch.cuda.synchronize()
+    s = torch.cuda.current_stream()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    clocks = Clocks()
+    clocks.start()
+    lib.scopf_timing(True)
+    n0 = P.scopf_launch_count()
+    t0 = time.perf_counter()
+    e0.record(s)
+    for _ in range(steps):
+        acc, viol, res = screen()
+    e1.record(s)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = P.scopf_launch_count() - n0
+    phases = lib.scopf_timing(False)
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1)
+    value = n_ctg * steps / (ms / 1e3)
+    dom = max(("factor", "solve", "assemble", "residual", "schur", "front_init", "ipm"),
+              key=lambda k: phases[k][0])
+    try:
+        cpu_s, cpu_desc = oracle_screen_sample()
+        cpu = {"value": 1.0 / cpu_s, "unit": "contingencies/s", "cores": 1, "kind": "oracle",
+               "sample": cpu_desc}
+    except Exception as exc:
+        cpu = {"value": None, "unit": "contingencies/s", "cores": 1, "kind": "oracle",
+               "sample": f"failed: {exc}"}
+    stored = np.array(stored)
+    line = {
+        "metric": "contingencies screened/s at a fixed base-case control (500-bus, all "
+                  "candidates in one batch)",
+        "value": value, "unit": "contingencies/s", "n_gpus": 1, "steps": steps,
+        "warmup": args.warmup, "ms_per_step": ms / steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32 block factors + f64 (model, Schur, refinement)", "data": "synthetic",
+        "config": {"workload": f"syn500 screening batch: 500-bus grid, base case + {n_ctg} "
+                               f"candidate outages examined by the oracle's screening, u0 "
+                               f"+- {SCREEN_EPS:g}, rho cap {SCREEN_RHO_CAP:g}, accept "
+                               f"|(r_k,t_k)|_inf <= {SCREEN_TOL:g}",
+                   "n_kkt": sz.n_kkt, "blocks": sz.n_blocks, "flush_l2": False,
+                   "inputs_exceed_l2": True},
+        "s_per_contingency": ms / 1e3 / steps / n_ctg,
+        "screen": {"status": res["status"], "outer_iters": res["outer_iters"],
+                   "inner_iters": res["inner_iters"], "fp64_fallbacks": res["fp64_fallbacks"],
+                   "accepted": int(acc[1:].sum()), "rejected": int((~acc[1:]).sum()),
+                   "base_accepted": bool(acc[0]),
+                   "agree_with_stored_u0pm1e-3_verdicts": int(np.sum(acc[1:] == stored))},
+        "phases_ms_per_step": {k: v[0] / steps for k, v in phases.items()},
+        "roofline": roofline(sz, phases, dom),
+        "cpu_baseline": cpu,
+        "e2e": {"value": n_ctg * steps / wall, "unit": "contingencies/s",
+                "h2d_bytes_per_step": 8 * sz.n_border,
+                "d2h_bytes_per_step": 12 * sz.n_blocks,
+                "note": "scopf_screen takes u0 and returns verdicts in host memory; host clock"},
+        "clocks": clk,
+        "gpu_launches": launches,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -364,9 +482,27 @@ def main():
     ap.add_argument("--iterate-at", type=int, default=30)
     ap.add_argument("--tts", default="both", choices=["none", "mixed", "both"],
                     help="which full NCL solves to time (time to solution)")
+    ap.add_argument("--workload", default="newton", choices=["newton", "screen"],
+                    help="newton: the Newton step (default); screen: batched screening")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "screen":
+        if args.impl == "reference":
+            if int(os.environ.get("RANK", "0")) == 0:
+                cpu_s, desc = oracle_screen_sample()
+                v = 1.0 / cpu_s
+                print(json.dumps({"metric": "contingencies screened/s", "value": v,
+                                  "unit": "contingencies/s", "impl": "reference",
+                                  "higher_is_better": True, "data": "synthetic",
+                                  "cpu_baseline": {"value": v, "unit": "contingencies/s",
+                                                   "cores": 1, "kind": "oracle", "sample": desc},
+                                  "e2e": {"value": v, "unit": "contingencies/s",
+                                          "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}),
+                      flush=True)
+        else:
+            run_screen(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:
