@@ -129,6 +129,7 @@ int setup_device(scopf_handle *h) {
         for (int64_t r = 0; r < M.n_kkt; r++)
             for (int64_t q = M.kkt_ptr[r]; q < M.kkt_ptr[r + 1]; q++) krow[q] = (int32_t)r;
         TRY(upload(h, krow, &d.kkt_row));
+        d.nnz_kkt = (int64_t)M.kkt_col.size();
     }
     TRY(upload(h, M.row_kind, &d.row_kind));
     {
@@ -214,6 +215,7 @@ int setup_device(scopf_handle *h) {
     TRY(alloc(h, M.n_kkt, &h->dx));
     TRY(alloc(h, M.n_kkt, &h->scale));
     TRY(alloc(h, M.n_kkt, &h->scale_tmp));
+    TRY(alloc(h, M.n_kkt, &h->ruiz_mx));
     F.kval = h->kval;
     F.scale = h->scale;
     {
@@ -748,7 +750,7 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     T *fr = reinterpret_cast<T *>(h->fronts);
     CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
     h->timer.begin(PH_FRONT_INIT, s);
-    launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, 3, s);
+    launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, h->ruiz_mx, 3, s);
     launch_orig_vals(h->df, h->ovals, s);
     h->timer.end(PH_FRONT_INIT, s);
     h->timer.begin(PH_FACTOR, s);

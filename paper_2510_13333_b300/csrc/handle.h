@@ -107,6 +107,7 @@ struct scopf_handle {
     double *S = nullptr, *border_work = nullptr;
     double *Sinv = nullptr;                           // S^-1 (mixed-precision solves)
     double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
+    unsigned long long *ruiz_mx = nullptr;          // per-row maxima of a Ruiz sweep (zeros)
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
     double *kst = nullptr;                                  // FGMRES small dense state
     double *ovals = nullptr;                                // scaled front originals

@@ -27,6 +27,7 @@ struct DevModel {
     const double *cf_coef;
     const int64_t *kkt_ptr, *kkt_col, *ctr_ptr;
     const int32_t *kkt_row;       // row of every stored entry
+    int64_t nnz_kkt;              // stored entries
     const int64_t *ctr_src;
     const double *ctr_coef;
     const int8_t *row_kind;
@@ -195,8 +196,10 @@ struct FactorStatus {             // device-side counters
 };
 
 // Symmetric Ruiz equilibration of K (scale[i] > 0, `iters` sweeps).
+// iters Ruiz sweeps of K into scale (tmp: ping-pong buffer; mx: n_kkt
+// zeros on entry and on return)
 void launch_equilibrate(const DevModel &M, const double *kval, double *scale, double *tmp,
-                        int iters, cudaStream_t s);
+                        unsigned long long *mx, int iters, cudaStream_t s);
 template <typename T>
 void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_tol,
                    int spin_limit, cudaStream_t s);

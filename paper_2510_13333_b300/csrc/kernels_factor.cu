@@ -1186,31 +1186,94 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
 // ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
 // one thread per row: a warp's rows are contiguous, so after the first
 // entry of each row the later ones come from L1
-__global__ void k_ruiz(int64_t n, const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
-                       const double *__restrict__ kval, const double *__restrict__ s_in,
-                       double *__restrict__ s_out, const int8_t *__restrict__ is_long) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= n || is_long[i]) return;
-    double mx = 0.0;
-    const double si = s_in[i];
-    for (int64_t q = ptr[i]; q < ptr[i + 1]; q++) mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
-    s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
+// One Ruiz sweep, entry-parallel: thread t takes the kRE stored entries
+// [kRE t, kRE t + kRE) (vector loads; the entries of a row are consecutive)
+// and forms v = |s_i a_ij s_j| for each, keeping a running maximum per run of
+// equal rows.  A run inside the chunk is the whole row: a plain store.  A run
+// that touches either end of the chunk may continue in a neighbouring one:
+// an atomic max on the bit pattern (v >= 0 orders like an unsigned integer).
+// mx must be zero on entry; k_ruiz_finish consumes and re-zeroes it.
+constexpr int kRE = 8;
+__device__ __forceinline__ void ruiz_flush(unsigned long long *mx, int r, double m, bool edge) {
+    if (r < 0 || !(m == m)) return;
+    const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+    if (edge) atomicMax(&mx[r], b);
+    else mx[r] = b;
 }
 
-__global__ void k_ruiz_long(int64_t n_long, const int64_t *__restrict__ rows,
-                            const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
-                            const double *__restrict__ kval, const double *__restrict__ s_in,
-                            double *__restrict__ s_out) {
-    const int64_t w = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int lane = threadIdx.x & 31;
-    if (w >= n_long) return;
-    const int64_t i = rows[w];
+__global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t *__restrict__ row,
+                                                      const int64_t *__restrict__ col,
+                                                      const double *__restrict__ kval,
+                                                      const double *__restrict__ s_in,
+                                                      unsigned long long *__restrict__ mx) {
+    const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kRE < nnz; t += nthr) {
+        const int64_t e0 = t * kRE;
+        int rr[kRE];
+        int64_t cc[kRE];
+        double vv[kRE];
+        int cnt = kRE;
+        if (e0 + kRE <= nnz) {
+            const int4 *r4 = reinterpret_cast<const int4 *>(row + e0);
+            const longlong2 *c2 = reinterpret_cast<const longlong2 *>(col + e0);
+            const double2 *v2 = reinterpret_cast<const double2 *>(kval + e0);
+#pragma unroll
+            for (int k = 0; k < kRE / 4; k++) {
+                const int4 a = __ldg(r4 + k);
+                rr[4 * k] = a.x;
+                rr[4 * k + 1] = a.y;
+                rr[4 * k + 2] = a.z;
+                rr[4 * k + 3] = a.w;
+            }
+#pragma unroll
+            for (int k = 0; k < kRE / 2; k++) {
+                const longlong2 a = __ldg(c2 + k);
+                const double2 b = __ldg(v2 + k);
+                cc[2 * k] = a.x;
+                cc[2 * k + 1] = a.y;
+                vv[2 * k] = b.x;
+                vv[2 * k + 1] = b.y;
+            }
+        } else {
+            cnt = (int)(nnz - e0);
+#pragma unroll
+            for (int k = 0; k < kRE; k++) {
+                rr[k] = k < cnt ? row[e0 + k] : -1;
+                cc[k] = k < cnt ? col[e0 + k] : 0;
+                vv[k] = k < cnt ? kval[e0 + k] : 0.0;
+            }
+        }
+        double sj[kRE];
+#pragma unroll
+        for (int k = 0; k < kRE; k++) sj[k] = k < cnt ? s_in[cc[k]] : 0.0;
+        int cur = rr[0];
+        double si = s_in[cur];
+        double m = fabs(si * vv[0] * sj[0]);
+        bool at_start = true;
+#pragma unroll
+        for (int k = 1; k < kRE; k++) {
+            if (k >= cnt) break;
+            if (rr[k] != cur) {
+                ruiz_flush(mx, cur, m, at_start);
+                at_start = false;
+                cur = rr[k];
+                si = s_in[cur];
+                m = 0.0;
+            }
+            m = fmax(m, fabs(si * vv[k] * sj[k]));
+        }
+        ruiz_flush(mx, cur, m, true);
+    }
+}
+
+__global__ void k_ruiz_finish(int64_t n, const double *__restrict__ s_in, double *__restrict__ s_out,
+                              unsigned long long *__restrict__ mx) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double m = __longlong_as_double((long long)mx[i]);
+    mx[i] = 0ull;
     const double si = s_in[i];
-    double mx = 0.0;
-    for (int64_t q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
-        mx = fmax(mx, fabs(si * kval[q] * s_in[col[q]]));
-    for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, o));
-    if (lane == 0) s_out[i] = mx > 0.0 ? si / sqrt(mx) : si;
+    s_out[i] = m > 0.0 ? si / sqrt(m) : si;
 }
 
 // scaled original entries of every front, in task order
@@ -1244,18 +1307,27 @@ int warp_grid() {
 }  // namespace
 
 void launch_equilibrate(const DevModel &M, const double *kval, double *scale, double *tmp,
-                        int iters, cudaStream_t s) {
+                        unsigned long long *mx, int iters, cudaStream_t s) {
     const int t = 256;
     const int64_t n = M.n_kkt;
     const int g = (int)((n + t - 1) / t);
-    const int gl = (int)((32 * M.n_long + t - 1) / t);
+    // entry sweep: resident warps over the stored entries
+    static int resident = 0;
+    if (!resident) {
+        int dev = 0, sms = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        resident = (sms > 0 ? sms : 148) * (2048 / t);
+    }
+    const int64_t chunks = (M.nnz_kkt + kRE - 1) / kRE;
+    const int ge = (int)std::min<int64_t>((chunks + t - 1) / t, (int64_t)resident);
     // start in the buffer that makes the last sweep land in `scale`
     double *a = (iters & 1) ? tmp : scale, *b = (iters & 1) ? scale : tmp;
     note_launch(), k_fill<<<g, t, 0, s>>>(n, 1.0, a);
     for (int it = 0; it < iters; it++) {
-        note_launch(), k_ruiz<<<g, t, 0, s>>>(n, M.kkt_ptr, M.kkt_col, kval, a, b, M.is_long);
-        if (M.n_long)
-            note_launch(), k_ruiz_long<<<gl, t, 0, s>>>(M.n_long, M.long_rows, M.kkt_ptr, M.kkt_col, kval, a, b);
+        if (M.nnz_kkt)
+            note_launch(), k_ruiz_entries<<<ge, t, 0, s>>>(M.nnz_kkt, M.kkt_row, M.kkt_col, kval, a, mx);
+        note_launch(), k_ruiz_finish<<<g, t, 0, s>>>(n, a, b, mx);
         double *c = a;
         a = b;
         b = c;
