@@ -590,6 +590,12 @@ __global__ void __launch_bounds__(med_threads<T>())
 constexpr int kBT = 256;
 constexpr int kBigPanelBytes = 96 * 1024;
 constexpr int kBigPanel = kBigPanelBytes / 8;   // panel elements that fit (FP64 bound)
+constexpr int kEA = 4;                          // row chunks per column in one extend-add pass
+// byte offset of the staged child->parent map behind the shared panel
+template <typename T>
+__host__ __device__ constexpr size_t big_rel_offset(int big_panel) {
+    return (sizeof(T) * (size_t)(big_panel > 1 ? big_panel : 1) + 15) & ~(size_t)15;
+}
 
 // Large front: zero + originals and extend-add in global memory, then the
 // np x f panel is copied to shared memory and eliminated there (rank-1
@@ -609,15 +615,47 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
     __syncthreads();
     for (int q = ti.o0 + tid; q < ti.o1; q += kBT) Fr[F.orig_off[q]] = (T)F.ovals[q];
     __syncthreads();
+    // children's update blocks: the child->parent map is staged in shared
+    // memory, and each warp pass takes two columns with up to kEA row chunks
+    // of 32 each, all their loads in flight before the adds (a child's
+    // destinations are distinct; children are added one after another)
+    int *srel = reinterpret_cast<int *>(big_smem + big_rel_offset<T>(F.big_panel));
     for (int ci = ti.c0; ci < ti.c1; ci++) {
         const ChildInfo c = child_info(F, ci);
         const T *Fc = fronts + c.front_off;
         const int fc = c.fc, npc = c.npc, nu = fc - npc;
         const int32_t *rel = F.rel + c.rel_off;
-        for (int jj = warp; jj < nu; jj += nw) {
-            const int64_t dst = (int64_t)rel[jj] * f;
-            const T *src = Fc + (int64_t)(npc + jj) * fc + npc;
-            for (int ii = jj + lane; ii < nu; ii += 32) Fr[dst + rel[ii]] += src[ii];
+        for (int i = tid; i < nu; i += kBT) srel[i] = rel[i];
+        __syncthreads();
+        for (int j0 = 2 * warp; j0 < nu; j0 += 2 * nw) {
+            const int j1 = j0 + 1;
+            const int64_t d0 = (int64_t)srel[j0] * f;
+            const int64_t d1 = j1 < nu ? (int64_t)srel[j1] * f : 0;
+            const T *s0 = Fc + (int64_t)(npc + j0) * fc + npc;
+            const T *s1 = s0 + fc;
+            for (int r0 = 0; j0 + r0 < nu; r0 += 32 * kEA) {
+                T a[2][kEA], b[2][kEA];
+                int64_t q[2][kEA];
+#pragma unroll
+                for (int k = 0; k < kEA; k++) {
+                    const int i0 = j0 + r0 + 32 * k + lane, i1 = i0 + 1;
+                    q[0][k] = i0 < nu ? d0 + srel[i0] : -1;
+                    q[1][k] = (j1 < nu && i1 < nu) ? d1 + srel[i1] : -1;
+                }
+#pragma unroll
+                for (int k = 0; k < kEA; k++) {
+                    const int i0 = j0 + r0 + 32 * k + lane, i1 = i0 + 1;
+                    a[0][k] = q[0][k] >= 0 ? s0[i0] : (T)0;
+                    a[1][k] = q[1][k] >= 0 ? s1[i1] : (T)0;
+                    b[0][k] = q[0][k] >= 0 ? Fr[q[0][k]] : (T)0;
+                    b[1][k] = q[1][k] >= 0 ? Fr[q[1][k]] : (T)0;
+                }
+#pragma unroll
+                for (int k = 0; k < kEA; k++) {
+                    if (q[0][k] >= 0) Fr[q[0][k]] = b[0][k] + a[0][k];
+                    if (q[1][k] >= 0) Fr[q[1][k]] = b[1][k] + a[1][k];
+                }
+            }
         }
         __syncthreads();
     }
@@ -644,14 +682,35 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
         __syncthreads();
     }
     for (int e = tid; e < np * f; e += kBT) Fr[e] = P[e];
-    const int m = f - np;
-    for (int jj = warp; jj < m; jj += nw) {
-        const int j = np + jj;
-        T *colj = Fr + (int64_t)j * f;
-        for (int i = j + lane; i < f; i += 32) {
-            T acc = 0;
-            for (int c = 0; c < np; c++) acc += P[c * f + i] * (P[c * f + j] * P[c * f + c]);
-            colj[i] -= acc;
+    // trailing update: two columns per warp pass, the pass's destination
+    // values loaded before the dot products (from the shared panel) run
+    for (int j0 = np + 2 * warp; j0 < f; j0 += 2 * nw) {
+        const int j1 = j0 + 1;
+        T *col0 = Fr + (int64_t)j0 * f;
+        T *col1 = col0 + f;
+        for (int r0 = 0; j0 + r0 < f; r0 += 32 * kEA) {
+            T u[2][kEA];
+#pragma unroll
+            for (int k = 0; k < kEA; k++) {
+                const int i0 = j0 + r0 + 32 * k + lane, i1 = i0 + 1;
+                u[0][k] = i0 < f ? col0[i0] : (T)0;
+                u[1][k] = (j1 < f && i1 < f) ? col1[i1] : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < kEA; k++) {
+                const int i0 = j0 + r0 + 32 * k + lane, i1 = i0 + 1;
+                if (i0 < f) {
+                    T a0 = 0, a1 = 0;
+                    for (int c = 0; c < np; c++) {
+                        const T *pc = P + c * f;
+                        const T dc = pc[c];
+                        a0 += pc[i0] * (pc[j0] * dc);
+                        if (j1 < f && i1 < f) a1 += pc[i1] * (pc[j1] * dc);
+                    }
+                    col0[i0] = u[0][k] - a0;
+                    if (j1 < f && i1 < f) col1[i1] = u[1][k] - a1;
+                }
+            }
         }
     }
     __syncthreads();
@@ -1396,13 +1455,14 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     if (nbig > 0) {
         // shared panel sized to the largest np x f of this phase (at most
         // kBigPanel elements); larger panels take the global-memory path
-        const size_t sm3 = sizeof(T) * (size_t)std::max(1, F.big_panel);
+        // plus the staged child->parent map of one child (at most max_f rows)
+        const size_t sm3 = big_rel_offset<T>(F.big_panel) + sizeof(int) * (size_t)F.max_f;
         static int g3[2] = {0, 0};
         static size_t g3_sm[2] = {0, 0};
         const int pi = sizeof(T) == 4 ? 0 : 1;
         if (g3_sm[pi] != sm3) {
-            for (const void *k : {(const void *)k_factor_big<float>, (const void *)k_factor_big<double>})
-                cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, kBigPanelBytes);
+            cudaFuncSetAttribute((const void *)k_factor_big<T>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm3);
             g3[pi] = resident_grid((const void *)k_factor_big<T>, kBT, sm3);
             g3_sm[pi] = sm3;
         }
