@@ -238,6 +238,11 @@ int setup_device(scopf_handle *h) {
         F.n_items = HF.n_items;
         F.max_f = 32;
         for (int t = 0; t < HF.n_tasks; t++) F.max_f = std::max(F.max_f, (int)HF.f[t]);
+        // in-front offsets are 32-bit in the large-front kernel
+        if ((int64_t)F.max_f * F.max_f >= ((int64_t)1 << 31)) {
+            h->last_error = "a front has more than 46340 rows";
+            return SCOPF_ERR_INVALID_ARG;
+        }
         // the large-front kernel stages np x f panels up to 96 KB (FP64)
         F.big_panel = 1;
         const int t3 = HF.n_items > HF.n_items_med ? HF.item_ptr[HF.n_items_med] : HF.n_tasks;

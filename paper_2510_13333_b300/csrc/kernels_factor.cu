@@ -590,7 +590,9 @@ __global__ void __launch_bounds__(med_threads<T>())
 constexpr int kBT = 256;
 constexpr int kBigPanelBytes = 96 * 1024;
 constexpr int kBigPanel = kBigPanelBytes / 8;   // panel elements that fit (FP64 bound)
-constexpr int kEA = 4;                          // row chunks per column in one extend-add pass
+// row chunks of 32 per column in one extend-add / trailing-update pass
+template <typename T>
+__host__ __device__ constexpr int big_chunks() { return sizeof(T) == 4 ? 4 : 2; }
 // byte offset of the staged child->parent map behind the shared panel
 template <typename T>
 __host__ __device__ constexpr size_t big_rel_offset(int big_panel) {
@@ -608,6 +610,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
     extern __shared__ unsigned char big_smem[];
     T *P = reinterpret_cast<T *>(big_smem);   // P[c * f + i]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBT >> 5;
+    constexpr int kEA = big_chunks<T>();
     T *Fr = fronts + ti.front_off;
     const int f = ti.f;
     const int np = ti.np;
@@ -629,13 +632,13 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
         __syncthreads();
         for (int j0 = 2 * warp; j0 < nu; j0 += 2 * nw) {
             const int j1 = j0 + 1;
-            const int64_t d0 = (int64_t)srel[j0] * f;
-            const int64_t d1 = j1 < nu ? (int64_t)srel[j1] * f : 0;
+            const int d0 = srel[j0] * f;
+            const int d1 = j1 < nu ? srel[j1] * f : 0;
             const T *s0 = Fc + (int64_t)(npc + j0) * fc + npc;
             const T *s1 = s0 + fc;
             for (int r0 = 0; j0 + r0 < nu; r0 += 32 * kEA) {
                 T a[2][kEA], b[2][kEA];
-                int64_t q[2][kEA];
+                int q[2][kEA];
 #pragma unroll
                 for (int k = 0; k < kEA; k++) {
                     const int i0 = j0 + r0 + 32 * k + lane, i1 = i0 + 1;
