@@ -455,19 +455,22 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
         const T *Fc = fronts + c.front_off + (int64_t)c.npc * fc + c.npc;
         const int32_t *rel = F.rel + c.rel_off;
         const int r0 = lane < nu ? rel[lane] : 0, r1 = lane + 32 < nu ? rel[lane + 32] : 0;
-        for (int j0 = 0; j0 < nu; j0 += 8) {
-            T v0[8], v1[8];
+        // kMB columns' loads in flight per step; column jj's map entry comes
+        // from the lane holding it (a shuffle)
+        constexpr int kMB = sizeof(T) == 4 ? 16 : 8;
+        for (int j0 = 0; j0 < nu; j0 += kMB) {
+            T v0[kMB], v1[kMB];
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int k = 0; k < kMB; k++) {
                 const int jj = j0 + k;
                 v0[k] = (jj < nu && lane < nu && lane >= jj) ? Fc[(int64_t)jj * fc + lane] : (T)0;
                 v1[k] = (jj < nu && lane + 32 < nu) ? Fc[(int64_t)jj * fc + lane + 32] : (T)0;
             }
 #pragma unroll
-            for (int k = 0; k < 8; k++) {
+            for (int k = 0; k < kMB; k++) {
                 const int jj = j0 + k;
+                const int rj = __shfl_sync(0xffffffffu, jj < 32 ? r0 : r1, jj & 31);
                 if (jj < nu) {
-                    const int rj = F.rel[c.rel_off + jj];   // broadcast (same address)
                     if (lane < nu && lane >= jj) M[r0][rj] += v0[k];
                     if (lane + 32 < nu) M[r1][rj] += v1[k];
                 }
