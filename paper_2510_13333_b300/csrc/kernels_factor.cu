@@ -487,6 +487,19 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        if (sizeof(T) == 8) {
+            // FP64 runs at a fraction of the FP32 rate: lanes take rows j, j+1, ...
+            // of each updated column, so no instruction carries the idle rows
+            // above the diagonal (one or two chunks of 32 per column)
+            for (int i = c + 1 + lane; i < f; i += 32) M[i][c] *= dinv;
+            __syncwarp();
+            for (int j = c + 1; j < np; j++) {   // panel columns only
+                const T lj = M[j][c] * d;
+                for (int i = j + lane; i < f; i += 32) M[i][j] -= M[i][c] * lj;
+            }
+            __syncwarp();
+            continue;
+        }
         T l0 = (T)0, l1 = (T)0;
         if (i0 > c && i0 < f) {
             l0 = M[i0][c] * dinv;
