@@ -473,6 +473,65 @@ def run_screen(args):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------ ill-conditioning study (q_min -> q_max)
+ILLCOND_DELTAS = (1.0, 0.3, 0.1, 0.03, 0.01, 0.003)
+
+
+def run_illcond(args):
+    """Full NCL solves with the generators' reactive bands narrowed around
+    the base-case reactive output q* of the unstressed solution:
+    [max(q_min, q* - delta w), min(q_max, q* + delta w)], w = (q_max -
+    q_min) / 2.  q_min close to q_max is the regime Section V-C names as the
+    source of ill-conditioning (the eq. pvpq complementarity).  Per delta and
+    precision: status, IPM iterations, factorizations per iteration (the
+    inertia corrections), refinement steps per iteration, FP64 fallbacks and
+    time to solution."""
+    import numpy as np
+    import torch
+    import synthgrid
+    import paper_2510_13333_b300 as P
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    rows = []
+    for idx in (1, CONFIG_IDX):
+        base = synthgrid.config_instance(idx)
+        nb, ng = base.net.n_bus, base.net.n_gen
+        lib = P.SCOPF(base, precision=P.PREC_FP64)
+        r = lib.ncl_solve()
+        # base-case q_g^0 in the natural variable order: theta (nb - 1), v at the
+        # nb - ng buses without a generator, then q_g^0 per generator
+        q0 = lib.get_state()["w"][(nb - 1) + (nb - ng):(nb - 1) + (nb - ng) + ng].cpu().numpy()
+        del lib
+        half = 0.5 * (base.net.qmax - base.net.qmin)
+        for delta in ILLCOND_DELTAS:
+            inst = synthgrid.config_instance(idx)
+            net = inst.net
+            net.qmin = np.maximum(base.net.qmin, q0 - delta * half)
+            net.qmax = np.minimum(base.net.qmax, q0 + delta * half)
+            lib = P.SCOPF(inst, precision=P.PREC_MIXED)
+            for name, prec in (("mixed", P.PREC_MIXED), ("fp64", P.PREC_FP64)):
+                lib.set_precision(prec)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                r = lib.ncl_solve()
+                torch.cuda.synchronize()
+                dt = time.perf_counter() - t0
+                rows.append({"network": inst.name, "K": len(inst.ctgs), "delta": delta,
+                             "band_pu": float(np.median(net.qmax - net.qmin)),
+                             "precision": name, "status": r["call_status"],
+                             "inner_iters": r["inner_iters"], "outer_iters": r["outer_iters"],
+                             "factorizations_per_iter": r["factorizations"] / max(1, r["inner_iters"]),
+                             "refine_steps_per_iter": r["refine_steps"] / max(1, r["inner_iters"]),
+                             "fp64_fallbacks": r["fp64_fallbacks"], "seconds": dt,
+                             "objective": r["objective"], "max_violation": r["max_violation"]})
+                print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+            del lib
+    print(json.dumps({"metric": "ill-conditioning study: NCL solves with q_min -> q_max",
+                      "unit": "see rows", "data": "synthetic", "rows": rows}), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -482,11 +541,16 @@ def main():
     ap.add_argument("--iterate-at", type=int, default=30)
     ap.add_argument("--tts", default="both", choices=["none", "mixed", "both"],
                     help="which full NCL solves to time (time to solution)")
-    ap.add_argument("--workload", default="newton", choices=["newton", "screen"],
-                    help="newton: the Newton step (default); screen: batched screening")
+    ap.add_argument("--workload", default="newton", choices=["newton", "screen", "illcond"],
+                    help="newton: the Newton step (default); screen: batched screening; "
+                         "illcond: NCL solves with narrowed reactive bands")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "illcond":
+        if args.impl != "reference":
+            run_illcond(args)
+        return
     if args.workload == "screen":
         if args.impl == "reference":
             if int(os.environ.get("RANK", "0")) == 0:
