@@ -1262,8 +1262,6 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
 }
 
 // ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
-// one thread per row: a warp's rows are contiguous, so after the first
-// entry of each row the later ones come from L1
 // One Ruiz sweep, entry-parallel: thread t takes the kRE stored entries
 // [kRE t, kRE t + kRE) (vector loads; the entries of a row are consecutive)
 // and forms v = |s_i a_ij s_j| for each, keeping a running maximum per run of
