@@ -275,39 +275,64 @@ def run_ours(args):
     ms_fp64, ph_fp64 = timed(lib, max(2, args.steps // 4))
     fp64_steps = max(2, args.steps // 4)
     lib.set_precision(P.PREC_MIXED)
-    # ---- end to end through host buffers (pinned), H2D inputs + D2H direction
+    # ---- end to end through host buffers (pinned): every step copies its inputs
+    # host->device and its direction device->host.  The copies run on their own
+    # stream, overlapped with the neighbouring steps' compute: inputs and
+    # directions are double-buffered on the device, and step i's inputs are
+    # uploaded (and step i-2's direction read back) while step i-1 computes.
     host = {k: v.cpu().pin_memory() for k, v in st.items()}
     host_l, host_n = lam_n.cpu().pin_memory(), nu0_n.cpu().pin_memory()
-    out_w = torch.empty(sz.n, dtype=torch.float64).pin_memory()
-    out_l = torch.empty(sz.m, dtype=torch.float64).pin_memory()
-    out_y = torch.empty(sz.p, dtype=torch.float64).pin_memory()
+    outs = [{"w": torch.empty(sz.n, dtype=torch.float64).pin_memory(),
+             "lam": torch.empty(sz.m, dtype=torch.float64).pin_memory(),
+             "yc": torch.empty(sz.p, dtype=torch.float64).pin_memory()} for _ in range(2)]
     h2d = sum(v.numel() * 8 for v in host.values()) + 8 * (host_l.numel() + host_n.numel())
     d2h = 8 * (sz.n + sz.m + sz.p)
-    dev_in = {k: torch.empty_like(v) for k, v in st.items()}
-    dl, dn = torch.empty_like(lam_n), torch.empty_like(nu0_n)
+    dev_in = [{k: torch.empty_like(v) for k, v in st.items()} for _ in range(2)]
+    dls = [torch.empty_like(lam_n) for _ in range(2)]
+    dns = [torch.empty_like(nu0_n) for _ in range(2)]
+    dirs = [direction, lib.new_state()]
+    comp = torch.cuda.current_stream()
+    copy = torch.cuda.Stream()
 
-    def e2e_step():
+    def upload(b):
         for k in st:
-            dev_in[k].copy_(host[k], non_blocking=True)
-        dl.copy_(host_l, non_blocking=True)
-        dn.copy_(host_n, non_blocking=True)
-        lib.scopf_newton_step(dev_in, dl, dn, rho, mu, dw_last, direction)
-        out_w.copy_(direction["w"], non_blocking=True)
-        out_l.copy_(direction["lam"], non_blocking=True)
-        out_y.copy_(direction["yc"], non_blocking=True)
-        torch.cuda.synchronize()
+            dev_in[b][k].copy_(host[k], non_blocking=True)
+        dls[b].copy_(host_l, non_blocking=True)
+        dns[b].copy_(host_n, non_blocking=True)
 
-    for _ in range(args.warmup):
-        e2e_step()
-    torch.cuda.synchronize()
-    s = torch.cuda.current_stream()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(s)
-    for _ in range(args.steps):
-        e2e_step()
-    e1.record(s)
-    torch.cuda.synchronize()
-    ms_e2e = e0.elapsed_time(e1)
+    def download(b):
+        for k in ("w", "lam", "yc"):
+            outs[b][k].copy_(dirs[b][k], non_blocking=True)
+
+    def e2e_run(nsteps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        done = [None, None]
+        with torch.cuda.stream(copy):
+            e0.record(copy)
+            upload(0)
+        ready = [copy.record_event(), None]
+        for i in range(nsteps):
+            b = i % 2
+            with torch.cuda.stream(copy):
+                if done[1 - b] is not None:       # step i-1 used buffer 1-b
+                    copy.wait_event(done[1 - b])
+                    download(1 - b)
+                if i + 1 < nsteps:
+                    upload(1 - b)
+                ready[1 - b] = copy.record_event()
+            comp.wait_event(ready[b])
+            lib.scopf_newton_step(dev_in[b], dls[b], dns[b], rho, mu, dw_last, dirs[b])
+            done[b] = comp.record_event()
+        with torch.cuda.stream(copy):
+            last = (nsteps - 1) % 2
+            copy.wait_event(done[last])
+            download(last)
+            e1.record(copy)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1)
+
+    e2e_run(args.warmup)
+    ms_e2e = e2e_run(args.steps)
     if dist:
         t = torch.tensor([ms_e2e], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
