@@ -313,6 +313,32 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
     }
 }
 
+// Rank-1 update of pivot step c restricted to the panel columns, packed for
+// FP64: the entries (i, j) with c < j < np, j <= i < f are numbered column
+// by column (column u = j - c - 1 holds rows j..f-1 and starts at entry
+// u L0 - u (u - 1) / 2, L0 = f - c - 1) and dealt to the lanes 32 at a time,
+// so every issued FP64 multiply-add updates an entry (the row-per-lane form
+// idles the lanes above each column's diagonal).  Column c holds l = L[., c]
+// (already divided by d); the update is M[i][j] -= l_i (l_j d).
+template <typename T, int S>
+__device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, int c, T d,
+                                                    int lane) {
+    const int j0 = c + 1, ncol = np - j0, L0 = f - j0;
+    if (ncol <= 0) return;
+    const int total = ncol * L0 - ncol * (ncol - 1) / 2;
+    const float b = 2.0f * (float)L0 + 1.0f;
+    for (int e = lane; e < total; e += 32) {
+        // column from the quadratic u L0 - u (u - 1) / 2 <= e, then corrected
+        int u = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))));
+        u = min(max(u, 0), ncol - 1);
+        while (u > 0 && u * L0 - u * (u - 1) / 2 > e) u--;
+        while (u + 1 < ncol && (u + 1) * L0 - (u + 1) * u / 2 <= e) u++;
+        const int j = j0 + u;
+        const int i = j + (e - (u * L0 - u * (u - 1) / 2));
+        M[i][j] -= M[i][c] * (M[j][c] * d);
+    }
+}
+
 // Trailing update U -= L21 D L21' of a front held in a shared tile with
 // row stride S (lower triangle; columns < np hold L, the diagonal D), for all
 // entries np <= j <= i < f.  W = L D is first written to the unused upper
@@ -408,6 +434,13 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        if (sizeof(T) == 8) {
+            if (lane > c && lane < f) tile[lane][c] *= dinv;
+            __syncwarp();
+            panel_update_packed<T, 33>(tile, f, np, c, d, lane);
+            __syncwarp();
+            continue;
+        }
         T l = (T)0;
         if (lane > c && lane < f) {
             l = tile[lane][c] * dinv;
