@@ -41,8 +41,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
 # valid only for the sweep kernels' source it was taken with
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "4bd2bb1b9a1ddcdcab3094fd9f53dc772b80e629",
-                 "bytes_per_solve": 254.0e6 + 303.6e6}
+                 "sha1": "d3ddb0af57b60b7c9c8b084d2cf7c505527c886b",
+                 "bytes_per_solve": 253.3e6 + 300.9e6}
 
 
 def sweep_traffic():
