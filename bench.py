@@ -56,6 +56,22 @@ def sweep_traffic():
     return SWEEP_TRAFFIC["bytes_per_solve"]
 
 
+def max_over_ranks(ms, dist, device):
+    """The largest per-rank time: a job's step time is its slowest replica's."""
+    if dist is None:
+        return ms
+    import torch
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(units_per_rank, world, ms):
+    """Whole-job throughput: the units every replica processed over the slowest
+    replica's time (ms)."""
+    return world * units_per_rank / (ms / 1e3)
+
+
 def measured_peaks():
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -259,11 +275,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         launches[0] = P.scopf_launch_count() - n0
         phases = l.scopf_timing(False)
-        ms = e0.elapsed_time(e1)
-        if dist:
-            t = torch.tensor([ms], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         return ms, phases
 
     clocks = Clocks()
@@ -332,19 +344,17 @@ def run_ours(args):
         return e0.elapsed_time(e1)
 
     e2e_run(args.warmup)
-    ms_e2e = e2e_run(args.steps)
     if dist:
-        t = torch.tensor([ms_e2e], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_e2e = float(t.item())
+        dist.barrier()
+    ms_e2e = max_over_ranks(e2e_run(args.steps), dist, "cuda")
 
     if rank != 0:
         if dist:
             dist.destroy_process_group()
         return
     K = args.steps
-    value = world * K / (ms_mixed / 1e3)
-    fp64_value = world * fp64_steps / (ms_fp64 / 1e3)
+    value = job_rate(K, world, ms_mixed)
+    fp64_value = job_rate(fp64_steps, world, ms_fp64)
     # roofline of the dominant phase (from CUDA events on the handle's stream)
     dom = max(("factor", "solve", "assemble", "residual", "schur", "front_init", "ipm"),
               key=lambda k: ph_mixed[k][0])
@@ -378,7 +388,7 @@ def run_ours(args):
         "phases_ms_per_step_fp64": {k: v[0] / fp64_steps for k, v in ph_fp64.items()},
         "roofline": roof,
         "cpu_baseline": cpu,
-        "e2e": {"value": world * K / (ms_e2e / 1e3), "unit": "Newton steps/s",
+        "e2e": {"value": job_rate(K, world, ms_e2e), "unit": "Newton steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
         "clocks": clk,
         "gpu_launches": launches_mixed,
