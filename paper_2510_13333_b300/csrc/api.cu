@@ -827,7 +827,8 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         TRY(alloc(h, (size_t)GL.total, &h->kst));
     }
     double *sc = h->kst + GL.sc;
-    // |b|_inf and |b - K x|_inf in one round trip
+    // |b|_inf and |b - K x|_inf, and the sweeps' status, in one round trip
+    FactorStatus fs{};
     auto residual_check = [&](double &bn, double &rn) {
         h->timer.begin(PH_RESIDUAL, s);
         launch_residual(h->dm, h->kval, x, h->res, h->tmp_kkt, s);
@@ -835,6 +836,7 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         reduce_maxabs2(h->res, h->tmp_kkt, n, h->red_out, h->red_scratch, s);
         double v[2] = {0, 0};
         cudaMemcpyAsync(v, h->red_out, sizeof(v), cudaMemcpyDeviceToHost, s);
+        cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         bn = v[0];
         rn = v[1];
@@ -887,9 +889,8 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         r = rn / bden;
     }
     h->n_refine += it;
-    FactorStatus fs;
-    CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    // every exit follows a residual check, whose round trip also read the
+    // sweeps' status after the last solve
     h->timer.collect();
     CK(cudaGetLastError());
     *rel = r;

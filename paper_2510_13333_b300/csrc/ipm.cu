@@ -295,6 +295,51 @@ __global__ void k_step(int64_t n, const double *x, const double *d, double a, do
     if (i < n) y[i] = x[i] + a * d[i];
 }
 
+// The trial point of every iterate vector in one launch: y = x + a d over
+// the segments w, r, lam, t, s, yc (primal step a) and zs, zl, zu (dual step
+// az).  With alpha != nullptr the two steps are read from the device (the
+// fraction-to-boundary result), otherwise a and az are used.
+struct StepSegs {
+    const double *x[9];
+    const double *d[9];
+    double *y[9];
+    int64_t end[9];   // cumulative lengths
+    int dual_from;    // segments >= dual_from take az
+};
+__global__ void k_step_all(StepSegs S, double a, double az, const double *alpha) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.end[8]) return;
+    int k = 0;
+    while (i >= S.end[k]) k++;
+    const int64_t j = i - (k ? S.end[k - 1] : 0);
+    const double st = alpha ? alpha[k >= S.dual_from ? 1 : 0] : (k >= S.dual_from ? az : a);
+    S.y[k][j] = S.x[k][j] + st * S.d[k][j];
+}
+
+// Fraction-to-boundary step lengths from the per-CTA partial minima
+__global__ void k_ftb_finish(const double *part, int nblk, double *alpha) {
+    __shared__ double sa[kT], sz[kT];
+    double ap = 1.0, az = 1.0;
+    for (int b = threadIdx.x; b < nblk; b += kT) {
+        ap = fmin(ap, part[2 * b]);
+        az = fmin(az, part[2 * b + 1]);
+    }
+    sa[threadIdx.x] = ap;
+    sz[threadIdx.x] = az;
+    __syncthreads();
+    for (int o = kT / 2; o > 0; o >>= 1) {
+        if (threadIdx.x < o) {
+            sa[threadIdx.x] = fmin(sa[threadIdx.x], sa[threadIdx.x + o]);
+            sz[threadIdx.x] = fmin(sz[threadIdx.x], sz[threadIdx.x + o]);
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        alpha[0] = sa[0];
+        alpha[1] = sz[0];
+    }
+}
+
 // kappa_sigma safeguard of the bound multipliers (W&B 2006, eq. 16)
 __global__ void k_zsafe(Dev D, const double *w, const double *s, double *zl, double *zu,
                         double *zs, double mu, double ks) {
@@ -528,18 +573,24 @@ struct Ipm {
             if (len[i]) cudaMemcpyAsync(*a[i], *b[i], sizeof(double) * len[i], cudaMemcpyDeviceToDevice, s);
     }
 
-    void step(scopf_state &out, const scopf_state &st, const scopf_state &d, double a, double az) {
-        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.w, d.w, a, out.w);
-        if (m) note_launch(), k_step<<<nb(m), kT, 0, s>>>(m, st.r, d.r, a, out.r);
-        if (m) note_launch(), k_step<<<nb(m), kT, 0, s>>>(m, st.lam, d.lam, a, out.lam);
-        if (p) {
-            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.t, d.t, a, out.t);
-            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.s, d.s, a, out.s);
-            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.yc, d.yc, a, out.yc);
-            note_launch(), k_step<<<nb(p), kT, 0, s>>>(p, st.zs, d.zs, az, out.zs);
+    // out = st + (a, az) d; alpha (device, 2 values) replaces (a, az) when given
+    void step(scopf_state &out, const scopf_state &st, const scopf_state &d, double a, double az,
+              const double *alpha = nullptr) {
+        StepSegs S;
+        const double *xs[9] = {st.w, st.r, st.lam, st.t, st.s, st.yc, st.zs, st.zl, st.zu};
+        const double *ds[9] = {d.w, d.r, d.lam, d.t, d.s, d.yc, d.zs, d.zl, d.zu};
+        double *ys[9] = {out.w, out.r, out.lam, out.t, out.s, out.yc, out.zs, out.zl, out.zu};
+        const int64_t len[9] = {n, m, m, p, p, p, p, n, n};
+        int64_t acc = 0;
+        for (int k = 0; k < 9; k++) {
+            S.x[k] = xs[k];
+            S.d[k] = ds[k];
+            S.y[k] = ys[k];
+            acc += len[k];
+            S.end[k] = acc;
         }
-        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.zl, d.zl, az, out.zl);
-        note_launch(), k_step<<<nb(n), kT, 0, s>>>(n, st.zu, d.zu, az, out.zu);
+        S.dual_from = 6;
+        if (acc > 0) note_launch(), k_step_all<<<nb(acc), kT, 0, s>>>(S, a, az, alpha);
     }
 
     // Newton direction with inertia correction; returns status, fills h->dir
@@ -860,16 +911,17 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     const double tau = std::fmax(h->opt.tau_min, 1.0 - mu);
     note_launch(), k_ftb<<<kB, kT, 0, s>>>(I.D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl, d.zu, d.zs, tau,
                             I.dpart);
-    I.fetch(2);
-    double ap = 1.0, az = 1.0;
-    for (int b = 0; b < kB; b++) {
-        ap = std::fmin(ap, I.part[2 * b]);
-        az = std::fmin(az, I.part[2 * b + 1]);
-    }
-    I.step(h->trial, st, d, ap, az);
+    // step lengths reduced on the device; the trial point and its filter
+    // values follow without a round trip, and the step lengths come back with
+    // the trial's partial sums
+    double *d_alpha = I.dpart + (size_t)kB * (kPartSlots - 1);
+    note_launch(), k_ftb_finish<<<1, kT, 0, s>>>(I.dpart, kB, d_alpha);
+    double alpha[2] = {1.0, 1.0};
+    cudaMemcpyAsync(alpha, d_alpha, sizeof(alpha), cudaMemcpyDeviceToHost, s);
+    I.step(h->trial, st, d, 1.0, 1.0, d_alpha);
     double tht, pht;
     I.trial_eval(h->trial, rho, mu, tht, pht);
-    cudaStreamSynchronize(s);
+    const double ap = alpha[0], az = alpha[1];
     h->timer.end(PH_IPM, s);
     cudaStreamSynchronize(s);
     h->timer.collect();
