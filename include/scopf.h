@@ -90,8 +90,9 @@ typedef struct {
 } scopf_contingency;
 
 /* Algorithm constants.  tol and mu_min follow Section V-A; the others are
- * the published defaults of the NCL and interior-point methods the paper
- * builds on.  scopf_default_options fills every field. */
+ * the published defaults of the NCL (Montoison et al.) and interior-point
+ * (Waechter & Biegler 2006) methods the paper builds on.
+ * scopf_default_options fills every field. */
 typedef struct {
     double tol, mu_min, mu_init, kappa_eps, kappa_mu, theta_mu, tau_min, s_max;
     double kappa_sigma, bound_relax, bound_push, bound_frac, slack_init, comp_init;

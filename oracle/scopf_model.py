@@ -4,7 +4,7 @@ Follows Section II (eq. agc, droopmpec, pvpq, scopf) and the vertical form of
 Section III-A (eq. mpcc): every inequality gets a nonnegative slack, and the
 two complementarity systems become pairs (w1, w2) >= 0 with w1 * w2 <= 0.
 
-Readings where the paper is silent (each also listed in the design doc):
+Readings where the paper is silent:
   * flows use the textbook pi-model (tap 1, no phase shift):
       S_ij = V_i conj(y (V_i - V_j) + j b_c/2 V_i),  y = 1/(r + jx) = g + jb;
   * bus balance: sum_g p_g - Pd - Gs v^2 - sum_arcs p_arc = 0 (and Q with +Bs v^2);
