@@ -13,7 +13,7 @@ directions, fraction-to-boundary and one trial evaluation.
 
 Prints one JSON line.  --workload screen times batched contingency
 screening (Section V-B) of the same network's candidate outages instead.  With --impl reference the CPU oracle is timed on a
-bounded sample of the same workload (the reference arm of this build).
+bounded sample of the same workload (the reference arm).
 """
 from __future__ import annotations
 

@@ -2,7 +2,7 @@
 
 The pivot-free factorisation of eq. (newtonsystem) (Section IV-B) allows the
 whole symbolic analysis to be done once per structure.  The paper leaves the
-ordering to cuDSS; this build fixes one deterministic algorithm, implemented
+ordering to cuDSS; here one deterministic algorithm is fixed, implemented
 twice (here and in the CUDA library) and compared bit for bit:
 
 1. Each scenario block is compressed to a *node graph* whose nodes keep the
