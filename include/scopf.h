@@ -310,6 +310,22 @@ int scopf_set_ncl_params(scopf_handle *h, const double *lam_n, const double *nu0
 int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
                   double *grad_Pd, double *grad_Qd, double *grad_c1);
 
+/* Iteration log of the handle's last ncl_solve (or scopf_screen).
+ * which = 0: one record per interior-point iteration, 15 doubles: outer
+ *   iteration, inner iteration (cumulative), mu, rho, scaled KKT error E_0
+ *   before the step, constraint violation theta and barrier objective phi at
+ *   the iterate, accepted primal and dual step lengths, delta_w, number of
+ *   factorizations (inertia corrections and FP64 fallback included),
+ *   refinement steps, precision of the factors that produced the step
+ *   (SCOPF_PREC_*), 1 if the filter accepted the step (0: elastic reset),
+ *   backtracking steps.
+ * which = 1: one record per NCL outer iteration, 8 doubles: outer iteration,
+ *   rho, |r|_inf, |t|_inf, E_0, eta, omega, inner iterations so far.
+ * *n_records and *record_len receive the log's size; out (host, capacity
+ * records, may be NULL) receives the first min(n_records, capacity). */
+int scopf_history(scopf_handle *h, int32_t which, int64_t capacity, double *out,
+                  int64_t *n_records, int32_t *record_len);
+
 /* Per-scenario infeasibility of the handle's current iterate: viol[k] =
  * |(r_k, t_k)|_inf over the constraint rows and complementarity pairs of
  * scenario k (k = 0 base case), the relaxations of eq. (nclsubpb).  viol:

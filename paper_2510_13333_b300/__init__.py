@@ -143,6 +143,7 @@ def lib():
             "scopf_set_params": (c_i32, [H, P_dbl, P_dbl, P_dbl]),
             "scopf_set_ncl_params": (c_i32, [H, P_dbl, P_dbl, c_dbl, c_dbl]),
             "scopf_block_violation": (c_i32, [H, P_dbl]),
+            "scopf_history": (c_i32, [H, c_i32, c_i64, P_dbl, P_i64, P_i32]),
             "scopf_screen": (c_i32, [H, P_dbl, c_dbl, c_dbl, c_dbl, ctypes.POINTER(Result), P_dbl,
                                      P_i32]),
             "scopf_newton_step": (c_i32, [H, ctypes.POINTER(State), P_dbl, P_dbl, c_dbl, c_dbl,
@@ -466,6 +467,22 @@ class SCOPF:
         """Declare the loaded state a solution with these NCL parameters."""
         _check("scopf_set_ncl_params", lib().scopf_set_ncl_params(
             self.h, _dp(lam_n), _dp(nu0_n), float(rho), float(mu)))
+
+    HISTORY_INNER = ("outer", "inner", "mu", "rho", "E0", "theta", "phi", "alpha_p", "alpha_d",
+                     "delta_w", "factorizations", "refine_steps", "precision", "accepted",
+                     "backtracks")
+    HISTORY_OUTER = ("outer", "rho", "r_inf", "t_inf", "E0", "eta", "omega", "inner")
+
+    def history(self, which: int = 0):
+        """Iteration log of the last solve: (field names, numpy array with one
+        row per interior-point (which=0) or NCL outer (which=1) iteration)."""
+        n, ln = ctypes.c_int64(), c_i32()
+        _check("scopf_history", lib().scopf_history(self.h, which, 0, None, ctypes.byref(n),
+                                                    ctypes.byref(ln)))
+        out = np.zeros((n.value, ln.value))
+        _check("scopf_history", lib().scopf_history(self.h, which, n.value, _hp(out, c_dbl),
+                                                    ctypes.byref(n), ctypes.byref(ln)))
+        return (self.HISTORY_INNER if which == 0 else self.HISTORY_OUTER), out
 
     def block_violation(self):
         """|(r_k, t_k)|_inf of the current iterate per scenario (numpy, K + 1)."""

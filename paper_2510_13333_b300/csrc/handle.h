@@ -129,6 +129,8 @@ struct scopf_handle {
     double mu_last = 0.0, dw_last = 0.0;   // barrier parameter and delta_w at the last solve's end
     bool has_solution = false;             // st, lam_n, nu0_n, rho, mu_last describe a solution
     bool inner_limit = false;              // the last solve stopped at max_inner
+    // iteration log of the last ncl_solve (records of kHistInner / kHistOuter doubles)
+    std::vector<double> hist_inner, hist_outer;
     bool screen_blocks = false;            // NCL outer loop with the per-block screening rule
     // per-scenario ranges of r and t (c0, nrow, p0, ncomp) and their maxima
     int64_t *blk_rt = nullptr;
@@ -154,6 +156,8 @@ struct scopf_handle {
 namespace scopf {
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res);
 int block_multiplier_update(scopf_handle *h, double rho, double thr);
+constexpr int kHistInner = 15;   // fields of an inner-iteration record (scopf_history)
+constexpr int kHistOuter = 8;    // fields of an outer-iteration record
 void relaxed_bounds(const Model &M, double bound_relax, std::vector<double> &wl,
                     std::vector<double> &wu);
 int ipm_partials();   // doubles of the IPM reduction partial buffer

@@ -13,6 +13,7 @@
 //  * mixed precision: FP32 block factors with FP64 refinement; when the
 //    refinement stalls the step is redone with FP64 factors, and the rest of
 //    the solve stays in FP64.
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -679,6 +680,8 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     int status = SCOPF_ERR_MAX_ITER;
     int outer = 0, inner = 0;
     bool inner_limit = false;
+    h->hist_inner.clear();
+    h->hist_outer.clear();
     double E0 = INFINITY, feas = INFINITY;
     double t_newton = 0.0;
     const int fact0 = h->n_factor, ref0 = h->n_refine;
@@ -715,6 +718,8 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             }
             double delta = 0.0;
             int tries = 0;
+            const int fact_before = h->n_factor, refine_before = h->n_refine;
+            const double E0_step = E0;
             r = I.direction(dw_last, delta, tries);
             if (r != SCOPF_OK) {
                 inner_status = r == SCOPF_ERR_WRONG_INERTIA ? SCOPF_ERR_NUMERICAL : r;
@@ -801,6 +806,14 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             inner++;
             cudaStreamSynchronize(s);
             t_newton += tn.s();
+            {
+                const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th, ph,
+                                                a, az, delta, (double)(h->n_factor - fact_before),
+                                                (double)(h->n_refine - refine_before),
+                                                (double)h->factored_precision, accepted ? 1.0 : 0.0,
+                                                (double)nback};
+                h->hist_inner.insert(h->hist_inner.end(), rec, rec + kHistInner);
+            }
             if (o.verbose)
                 std::printf("  it %4d mu %.1e E0 %.2e th %.2e a %.2e dw %.1e tries %d%s\n", inner, mu,
                             E0, th, a, delta, tries, accepted ? "" : " R");
@@ -809,6 +822,11 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
             N = I.norms(st, rho);
         }
         feas = std::fmax(N.rmax, N.tmax);
+        {
+            const double rec[kHistOuter] = {(double)outer, rho, N.rmax, N.tmax, E0, eta, omega,
+                                            (double)inner};
+            h->hist_outer.insert(h->hist_outer.end(), rec, rec + kHistOuter);
+        }
         if (o.verbose)
             std::printf("outer %d rho %.1e |r,t| %.2e E0 %.2e inner %d\n", outer, rho, feas, E0, inner);
         if (inner_status != SCOPF_OK) {
@@ -942,6 +960,23 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     if (e != cudaSuccess) {
         h->last_error = cudaGetErrorString(e);
         return SCOPF_ERR_CUDA;
+    }
+    return SCOPF_OK;
+}
+
+extern "C" int scopf_history(scopf_handle *h, int32_t which, int64_t capacity, double *out,
+                             int64_t *n_records, int32_t *record_len) {
+    using namespace scopf;
+    if (!h || (which != 0 && which != 1) || !n_records || !record_len || capacity < 0)
+        return SCOPF_ERR_INVALID_ARG;
+    const std::vector<double> &v = which == 0 ? h->hist_inner : h->hist_outer;
+    const int len = which == 0 ? kHistInner : kHistOuter;
+    const int64_t n = (int64_t)v.size() / len;
+    *n_records = n;
+    *record_len = len;
+    if (out) {
+        const int64_t k = n < capacity ? n : capacity;
+        std::copy(v.begin(), v.begin() + k * len, out);
     }
     return SCOPF_OK;
 }

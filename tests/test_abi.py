@@ -74,3 +74,14 @@ def test_kkt_pattern_matches_oracle():
     assert ora_pat <= lib_pat
     # the library stores no structurally absent entry beyond zero-valued shunt terms
     assert len(lib_pat - ora_pat) <= 4 * inst.net.n_bus * (len(inst.ctgs) + 1)
+
+
+def test_history_empty_before_a_solve():
+    """The iteration log exists on a host-only handle and is empty until a
+    solve has run; its record lengths match the documented fields."""
+    import paper_2510_13333_b300 as P
+    h = P.SCOPF(H.instance(0), host_only=1)
+    names, rows = h.history(0)
+    assert rows.shape == (0, 15) and len(names) == 15
+    names, rows = h.history(1)
+    assert rows.shape == (0, 8) and len(names) == 8
