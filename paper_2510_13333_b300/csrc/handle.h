@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <string>
 #include <vector>
@@ -23,9 +24,16 @@ struct ScalarScratch {
     double *partial = nullptr;
 };
 
-// CUDA-event timers of the library's phases on the handle's stream.
+// CUDA-event timers of the library's phases on the handle's stream.  Each
+// phase is also an NVTX range (start/end form, so phases may interleave),
+// visible to a profiler whether or not the timers are on.
 struct PhaseTimer {
     static constexpr int kPhases = 7;
+    static constexpr const char *kNames[kPhases] = {"scopf assemble", "scopf front_init",
+                                                    "scopf factor",   "scopf schur",
+                                                    "scopf solve",    "scopf residual",
+                                                    "scopf ipm"};
+    nvtxRangeId_t range[kPhases] = {};
     bool on = false;
     double ms[kPhases] = {};
     int calls[kPhases] = {};
@@ -44,11 +52,17 @@ struct PhaseTimer {
         return e;
     }
     void begin(int ph, cudaStream_t s) {
+        if (range[ph]) nvtxRangeEnd(range[ph]);
+        range[ph] = nvtxRangeStartA(kNames[ph]);
         if (!on) return;
         open[ph] = get();
         cudaEventRecord(open[ph], s);
     }
     void end(int ph, cudaStream_t s) {
+        if (range[ph]) {
+            nvtxRangeEnd(range[ph]);
+            range[ph] = 0;
+        }
         if (!on || !open[ph]) return;
         cudaEvent_t e = get();
         cudaEventRecord(e, s);
