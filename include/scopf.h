@@ -277,6 +277,15 @@ int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, 
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */
 int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);
+
+/* Checkpoint / resume (the warm start between NCL outer iterations, Section
+ * IV-A): continue the method from the handle's current iterate and NCL
+ * parameters (lam_n, nu0_n, rho, mu, eta, omega).  These are left by the
+ * handle's last ncl_solve / ncl_resume, or restored on any handle of the
+ * same problem with scopf_load_state + scopf_set_ncl_params (which resets
+ * eta and omega to their initial values).  The inner-iteration count and
+ * limit start afresh.  SCOPF_ERR_INVALID_ARG if no parameters are set. */
+int ncl_resume(scopf_handle *h, scopf_result *res);
 /* Device views of the handle's current iterate (owned by the handle). */
 int scopf_get_state(scopf_handle *h, scopf_state *out);
 /* Copy the handle's iterate into caller-owned device buffers (dst fields

@@ -134,6 +134,7 @@ def lib():
             "kkt_factor": (c_i32, [H, c_i32, P_i32]),
             "kkt_solve": (c_i32, [H, P_dbl, P_dbl, c_i32, P_dbl, P_i32]),
             "ncl_solve": (c_i32, [H, ctypes.POINTER(State), ctypes.POINTER(Result)]),
+            "ncl_resume": (c_i32, [H, ctypes.POINTER(Result)]),
             "scopf_get_state": (c_i32, [H, ctypes.POINTER(State)]),
             "scopf_copy_state": (c_i32, [H, ctypes.POINTER(State)]),
             "scopf_load_state": (c_i32, [H, ctypes.POINTER(State)]),
@@ -371,6 +372,16 @@ class SCOPF:
         R = Result()
         S = self._state(warm) if warm is not None else None
         st = lib().ncl_solve(self.h, ctypes.byref(S) if S is not None else None, ctypes.byref(R))
+        out = {f: getattr(R, f) for f, _ in Result._fields_}
+        out["call_status"] = st
+        return out
+
+    def ncl_resume(self):
+        """Continue the NCL method from the handle's iterate and parameters
+        (the last solve's end, or a checkpoint restored with load_state +
+        set_ncl_params)."""
+        R = Result()
+        st = lib().ncl_resume(self.h, ctypes.byref(R))
         out = {f: getattr(R, f) for f, _ in Result._fields_}
         out["call_status"] = st
         return out

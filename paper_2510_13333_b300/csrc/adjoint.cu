@@ -163,6 +163,9 @@ extern "C" int scopf_set_ncl_params(scopf_handle *h, const double *lam_n, const 
     h->rho = rho;
     h->mu_last = mu;
     h->dw_last = 0.0;
+    h->eta_last = h->opt.eta_init;
+    h->omega_last = h->opt.omega_init;
+    h->have_ncl = true;
     h->has_solution = true;
     return SCOPF_OK;
 }

@@ -141,6 +141,8 @@ struct scopf_handle {
     double *lam_n = nullptr, *nu0_n = nullptr;
     double rho = 0.0;
     double mu_last = 0.0, dw_last = 0.0;   // barrier parameter and delta_w at the last solve's end
+    double eta_last = 0.0, omega_last = 0.0;   // NCL tolerances at the last solve's end
+    bool have_ncl = false;                 // rho, mu_last, lam_n, nu0_n, eta/omega_last are set
     bool has_solution = false;             // st, lam_n, nu0_n, rho, mu_last describe a solution
     bool inner_limit = false;              // the last solve stopped at max_inner
     // iteration log of the last ncl_solve (records of kHistInner / kHistOuter doubles)
@@ -168,7 +170,8 @@ struct scopf_handle {
 };
 
 namespace scopf {
-int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res);
+int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res,
+                   bool resume = false);
 int block_multiplier_update(scopf_handle *h, double rho, double thr);
 constexpr int kHistInner = 15;   // fields of an inner-iteration record (scopf_history)
 constexpr int kHistOuter = 8;    // fields of an outer-iteration record

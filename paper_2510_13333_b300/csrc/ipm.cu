@@ -617,7 +617,7 @@ struct Ipm {
     }
 };
 
-int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) {
+int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, bool resume) {
     Timer T;
     const scopf_options &o = h->opt;
     const Model &M = h->M;
@@ -628,11 +628,15 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     scopf_state &st = h->st;
     scopf_state &d = h->dir;
     scopf_state &tr = h->trial;
-    double rho = o.rho_init;
+    double rho = resume ? h->rho : o.rho_init;
     h->skip_delta0 = false;
-    cudaMemsetAsync(h->lam_n, 0, sizeof(double) * (m ? m : 1), s);
-    cudaMemsetAsync(h->nu0_n, 0, sizeof(double) * (p ? p : 1), s);
-    if (warm) {
+    if (!resume) {
+        cudaMemsetAsync(h->lam_n, 0, sizeof(double) * (m ? m : 1), s);
+        cudaMemsetAsync(h->nu0_n, 0, sizeof(double) * (p ? p : 1), s);
+    }
+    if (resume) {
+        // continue from the handle's iterate and NCL parameters (a checkpoint)
+    } else if (warm) {
         int r = scopf_load_state(h, warm);
         if (r != SCOPF_OK) return r;
     } else {
@@ -677,6 +681,12 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
         cudaStreamSynchronize(s);
     }
     double mu = o.mu_init, eta = o.eta_init, omega = o.omega_init, dw_last = 0.0;
+    if (resume) {
+        mu = h->mu_last;
+        eta = h->eta_last;
+        omega = h->omega_last;
+        dw_last = h->dw_last;
+    }
     int status = SCOPF_ERR_MAX_ITER;
     int outer = 0, inner = 0;
     bool inner_limit = false;
@@ -861,6 +871,9 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res) 
     h->rho = rho;
     h->mu_last = mu;
     h->dw_last = dw_last;
+    h->eta_last = eta;
+    h->omega_last = omega;
+    h->have_ncl = true;
     h->has_solution = status == SCOPF_OK;
     h->inner_limit = inner_limit;
     // final report
@@ -979,4 +992,13 @@ extern "C" int scopf_history(scopf_handle *h, int32_t which, int64_t capacity, d
         std::copy(v.begin(), v.begin() + k * len, out);
     }
     return SCOPF_OK;
+}
+
+// Continue the NCL method from the handle's current iterate and parameters:
+// the end of a previous solve on this handle, or a checkpoint restored with
+// scopf_load_state + scopf_set_ncl_params.
+extern "C" int ncl_resume(scopf_handle *h, scopf_result *res) {
+    using namespace scopf;
+    if (!h || h->host_only || !res || !h->have_ncl) return SCOPF_ERR_INVALID_ARG;
+    return ncl_solve_impl(h, nullptr, res, true);
 }

@@ -61,3 +61,41 @@ def test_iteration_log_consistent(cuda, prec):
     last = outer[-1]
     assert max(last[ocol["r_inf"]], last[ocol["t_inf"]]) <= 1e-6
     assert last[ocol["inner"]] == res["inner_iters"]
+
+
+def test_checkpoint_resume(cuda):
+    """Checkpoint / resume: the iterate and NCL parameters of a solve,
+    restored on a new handle (load_state + set_ncl_params), continue the
+    method.  A converged checkpoint resumes to the same objective with no
+    further interior-point iteration; a checkpoint taken when a solve hit
+    its iteration limit resumes to the uninterrupted solve's objective."""
+    import paper_2510_13333_b300 as P
+    inst = H.instance(1)
+    lib = P.SCOPF(inst, precision=P.PREC_FP64)
+    cold = lib.ncl_solve()
+    assert cold["call_status"] == 0
+
+    def restore(src, dst, mu):
+        st = src.get_state()
+        lam_n, nu0_n, rho = src.ncl_params_tensors()
+        dst.load_state(st)
+        dst.set_ncl_params(lam_n, nu0_n, rho, mu)
+
+    # converged checkpoint
+    again = P.SCOPF(inst, precision=P.PREC_FP64)
+    restore(lib, again, cold["mu"])
+    res = again.ncl_resume()
+    assert res["call_status"] == 0 and res["inner_iters"] == 0
+    assert res["objective"] == cold["objective"]
+    # checkpoint at the inner-iteration limit
+    part = P.SCOPF(inst, precision=P.PREC_FP64, max_inner=30)
+    first = part.ncl_solve()
+    assert first["call_status"] == -7 and first["inner_iters"] == 30
+    rest = P.SCOPF(inst, precision=P.PREC_FP64)
+    restore(part, rest, first["mu"])
+    res = rest.ncl_resume()
+    assert res["call_status"] == 0
+    assert abs(res["objective"] - cold["objective"]) <= 1e-6 * abs(cold["objective"])
+    # resuming needs parameters
+    fresh = P.SCOPF(inst, precision=P.PREC_FP64)
+    assert fresh.ncl_resume()["call_status"] == -1
