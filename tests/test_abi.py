@@ -85,3 +85,21 @@ def test_history_empty_before_a_solve():
     assert rows.shape == (0, 15) and len(names) == 15
     names, rows = h.history(1)
     assert rows.shape == (0, 8) and len(names) == 8
+
+
+def test_symbolic_bit_exact_full_size_sampled_blocks():
+    """The 500-bus x 256 workload of the benchmark: the symbolic analysis of
+    the base case and of sampled contingency blocks equals the oracle's bit
+    for bit (each block's analysis depends only on its own graph)."""
+    inst = H.instance(2)
+    M = SCOPFModel(inst)
+    lib = P.SCOPF(inst, host_only=1)
+    gen = H.generic_of_natural(M)
+    graphs = symbolic.attach_adjacency(symbolic.block_graphs(M), symbolic.structural_kkt(M))
+    for k in (0, 1, 37, 128, 221, len(graphs) - 1):
+        S = symbolic.Symbolic(graphs[k])
+        c = lib.scopf_symbolic_block(k)
+        assert np.array_equal(c["post"], S.post), k
+        assert np.array_equal(c["node_parent"], S.parent), k
+        assert np.array_equal(c["sn_start"], S.sn_start), k
+        assert np.array_equal(gen[c["rows"]], S.rows), k
