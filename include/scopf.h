@@ -116,6 +116,10 @@ typedef struct {
     int32_t relax_max_front;  /* relaxed amalgamation: a supernode absorbs a child
                                  while its front stays within this many rows
                                  (0 = off) */
+    int32_t device_loop;      /* 1: the FGMRES Krylov steps of a refinement cycle
+                                 run as one CUDA graph (a WHILE node repeating one
+                                 captured step) with no host round trip per step;
+                                 0: host-driven loop */
 } scopf_options;
 
 /* Sizes of the handle's problem. */

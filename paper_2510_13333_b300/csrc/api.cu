@@ -367,6 +367,7 @@ void scopf_default_options(scopf_options *o) {
     o->host_only = 0;
     o->cluster_max_tasks = 16;
     o->relax_max_front = 0;
+    o->device_loop = 1;
 }
 
 const char *scopf_strerror(int s) {
@@ -438,6 +439,8 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
 
 void scopf_destroy(scopf_handle *h) {
     if (!h) return;
+    for (auto &g : h->kgraph)
+        if (g.exec) cudaGraphExecDestroy(g.exec);
     for (void *p : h->allocations) cudaFree(p);
     if (h->trace) cudaFree(h->trace);
     delete h;
@@ -537,6 +540,7 @@ int scopf_launch_count(int64_t *out) {
 int scopf_trace(scopf_handle *h, int32_t enable) {
     if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
     CK(cudaStreamSynchronize(h->stream));
+    h->kgraph_stale = true;   // the graphs captured the trace pointer
     if (h->trace) {
         cudaFree(h->trace);
         h->trace = nullptr;
@@ -802,6 +806,80 @@ static int solve_once(scopf_handle *h, const double *b, double *x) {
     return SCOPF_OK;
 }
 
+// One Krylov step of the FGMRES cycle below, captured once per factor
+// precision into a CUDA graph whose WHILE node repeats it: the column j,
+// the counts and the loop decision live in h->kctl, so the cycle runs with
+// no host round trip per step.  The step is the host loop's, kernel for
+// kernel (same arithmetic), except that the basis vector is copied into a
+// fixed input buffer and the preconditioned vector and the new direction are
+// formed in fixed buffers and copied out.
+template <typename T>
+static int build_krylov_graph(scopf_handle *h, scopf_handle::KrylovGraph &G) {
+    const int64_t n = h->M.n_kkt;
+    constexpr int m = 16;
+    const GmresLayout GL = gmres_layout(m);
+    double *sc = h->kst + GL.sc;
+    double *vb = h->kry_buf, *zb = vb + n, *wb = zb + n;
+    cudaStream_t cs = nullptr;
+    cudaGraph_t g = nullptr;
+    auto fail = [&](cudaError_t e) {
+        if (cs) cudaStreamDestroy(cs);
+        if (g) cudaGraphDestroy(g);
+        cudaGetLastError();
+        h->last_error = cudaGetErrorString(e);
+        G.failed = true;
+        return SCOPF_OK;   // the host-driven loop takes over
+    };
+    cudaError_t e = cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking);
+    if (e != cudaSuccess) return fail(e);
+    if ((e = cudaGraphCreate(&g, 0)) != cudaSuccess) return fail(e);
+    cudaGraphConditionalHandle loop;
+    if ((e = cudaGraphConditionalHandleCreate(&loop, g, 1, cudaGraphCondAssignDefault)) != cudaSuccess)
+        return fail(e);
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = loop;
+    np.conditional.type = cudaGraphCondTypeWhile;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np)) != cudaSuccess) return fail(e);
+    cudaGraph_t body = np.conditional.phGraph_out[0];
+    if ((e = cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                           cudaStreamCaptureModeRelaxed)) != cudaSuccess)
+        return fail(e);
+    cudaStream_t keep = h->stream;
+    const bool timing = h->timer.on;
+    h->stream = cs;
+    h->timer.on = false;
+    const long long k0 = g_kernel_launches.load();
+    launch_kry_gather(n, h->kv, h->kctl, vb, cs);
+    solve_once<T>(h, vb, zb);
+    launch_kry_scatter(n, zb, h->kz, h->kctl, cs);
+    launch_spmv(h->dm, h->kval, zb, wb, cs);
+    for (double *coef : {h->kst + GL.c1, h->kst + GL.c2}) {   // classical Gram-Schmidt, twice
+        launch_kry_multi_dot(h->kv, n, h->kctl, wb, h->kpart, cs);
+        launch_kry_dot_finish(h->kpart, h->kctl, coef, cs);
+        launch_kry_axpy(wb, h->kv, n, h->kctl, false, coef, cs);
+    }
+    launch_multi_dot(wb, n, 1, wb, h->kpart, cs);
+    launch_dot_finish(h->kpart, 1, sc + 1, true, cs);
+    launch_kry_scale_out(n, sc + 1, wb, h->kv, h->kctl, cs);
+    launch_kry_column_next(h->kst, m, h->kctl, loop, cs);
+    G.body_kernels = g_kernel_launches.load() - k0;
+    g_kernel_launches -= G.body_kernels;   // counted when they run
+    h->stream = keep;
+    h->timer.on = timing;
+    e = cudaStreamEndCapture(cs, &body);
+    if (e != cudaSuccess) return fail(e);
+    if ((e = cudaGraphInstantiate(&G.exec, g, 0)) != cudaSuccess) {
+        G.exec = nullptr;
+        return fail(e);
+    }
+    cudaGraphDestroy(g);
+    cudaStreamDestroy(cs);
+    return SCOPF_OK;
+}
+
 // Solve K x = b.  First x = M^-1 b with the factors M of K (FP64 or FP32);
 // if the FP64 residual is not yet below refine_tol, continue with restarted
 // FGMRES in FP64 on the correction, right-preconditioned by M (GMRES-based
@@ -827,7 +905,30 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         TRY(alloc(h, (size_t)GL.total, &h->kst));
     }
     double *sc = h->kst + GL.sc;
-    // |b|_inf and |b - K x|_inf, and the sweeps' status, in one round trip
+    // device-resident Krylov loop (one graph per factor precision)
+    scopf_handle::KrylovGraph *G = nullptr;
+    if (h->opt.device_loop) {
+        if (!h->kctl) {
+            TRY(alloc(h, 1, &h->kctl));
+            TRY(alloc(h, (size_t)3 * n, &h->kry_buf));
+        }
+        if (h->kgraph_stale) {
+            for (auto &g : h->kgraph) {
+                if (g.exec) cudaGraphExecDestroy(g.exec);
+                g = scopf_handle::KrylovGraph{};
+            }
+            h->kgraph_stale = false;
+        }
+        G = &h->kgraph[mixed ? 0 : 1];
+        if (!G->exec && !G->failed) {
+            if (mixed) build_krylov_graph<float>(h, *G);
+            else build_krylov_graph<double>(h, *G);
+        }
+        if (!G->exec) G = nullptr;
+    }
+    KrylovCtl ctl{};
+    // |b|_inf and |b - K x|_inf, the sweeps' status and the Krylov loop's
+    // counts, in one round trip
     FactorStatus fs{};
     auto residual_check = [&](double &bn, double &rn) {
         h->timer.begin(PH_RESIDUAL, s);
@@ -837,6 +938,7 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         double v[2] = {0, 0};
         cudaMemcpyAsync(v, h->red_out, sizeof(v), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s);
+        if (G) cudaMemcpyAsync(&ctl, h->kctl, sizeof(ctl), cudaMemcpyDeviceToHost, s);
         cudaStreamSynchronize(s);
         bn = v[0];
         rn = v[1];
@@ -860,6 +962,21 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         launch_scale_inv(n, sc + 0, h->tmp_kkt, h->kv, s);
         int jend = 0;
         const double target = h->opt.refine_tol * bnorm * 0.5;
+        if (G) {
+            launch_kry_start(h->kctl, it, max_refine, target, s);
+            cudaError_t ge = cudaGraphLaunch(G->exec, s);
+            if (ge != cudaSuccess) {
+                h->last_error = cudaGetErrorString(ge);
+                return SCOPF_ERR_CUDA;
+            }
+            launch_kry_solve(h->kst, m, h->kctl, s);
+            launch_kry_axpy(x, h->kz, n, h->kctl, true, h->kst + GL.c1, s);
+            residual_check(bnorm, rn);
+            g_kernel_launches += G->body_kernels * ctl.jend;
+            it = ctl.it;
+            r = rn / bden;
+            continue;
+        }
         for (int j = 0; j < m && it < max_refine; j++) {
             double *vj = h->kv + (size_t)j * n, *zj = h->kz + (size_t)j * n;
             double *w = h->kv + (size_t)(j + 1) * n;

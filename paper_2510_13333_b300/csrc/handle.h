@@ -124,6 +124,17 @@ struct scopf_handle {
     unsigned long long *ruiz_mx = nullptr;          // per-row maxima of a Ruiz sweep (zeros)
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch
     double *kst = nullptr;                                  // FGMRES small dense state
+    // device-resident Krylov loop: control block, fixed step buffers (the
+    // preconditioner's input and output, the new direction) and, per factor
+    // precision, the instantiated graph whose WHILE node repeats the step
+    scopf::KrylovCtl *kctl = nullptr;
+    double *kry_buf = nullptr;
+    struct KrylovGraph {
+        cudaGraphExec_t exec = nullptr;
+        long long body_kernels = 0;
+        bool failed = false;
+    } kgraph[2];
+    bool kgraph_stale = false;   // a kernel argument captured in the graphs changed
     double *ovals = nullptr;                                // scaled front originals
     scopf::FactorStatus *fstat = nullptr;
     double *red_scratch = nullptr, *red_out = nullptr;

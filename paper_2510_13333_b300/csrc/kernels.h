@@ -98,6 +98,29 @@ struct GmresLayout {
     int H, cs, sn, g, c1, c2, sc, total;
 };
 GmresLayout gmres_layout(int m);
+
+// Device-resident Krylov loop: control block in device memory (the graph's
+// WHILE node repeats one captured Krylov step; see solve_impl)
+struct KrylovCtl {
+    int j;          // current column
+    int it;         // preconditioner applications so far in the solve
+    int max_it;     // refinement budget
+    int jend;       // columns completed in this cycle
+    double target;  // residual estimate at which the cycle stops
+};
+void launch_kry_start(KrylovCtl *c, int it, int max_it, double target, cudaStream_t s);
+void launch_kry_gather(int64_t n, const double *V, const KrylovCtl *c, double *out, cudaStream_t s);
+void launch_kry_scatter(int64_t n, const double *in, double *Z, const KrylovCtl *c, cudaStream_t s);
+void launch_kry_multi_dot(const double *V, int64_t n, const KrylovCtl *c, const double *w,
+                          double *partial, cudaStream_t s);
+void launch_kry_dot_finish(const double *partial, const KrylovCtl *c, double *out, cudaStream_t s);
+void launch_kry_axpy(double *w, const double *V, int64_t n, const KrylovCtl *c, bool use_jend,
+                     const double *coef, cudaStream_t s);
+void launch_kry_scale_out(int64_t n, const double *den, const double *w, double *V,
+                          const KrylovCtl *c, cudaStream_t s);
+void launch_kry_column_next(double *st, int m, KrylovCtl *c, cudaGraphConditionalHandle loop,
+                            cudaStream_t s);
+void launch_kry_solve(double *st, int m, const KrylovCtl *c, cudaStream_t s);
 // out[j] = sum over the kDotBlocks partials of V_j' w (fixed order); with
 // take_sqrt the single result is replaced by its square root
 void launch_dot_finish(const double *partial, int k, double *out, bool take_sqrt, cudaStream_t s);

@@ -500,6 +500,178 @@ GmresLayout gmres_layout(int m) {
     return L;
 }
 
+// ---- device-resident Krylov loop (kernels of a CUDA graph whose WHILE node
+// repeats one Krylov step): the column j and the counts come from KrylovCtl
+// in device memory, so one captured step serves every j.
+namespace {
+
+__global__ void k_kry_start(KrylovCtl *c, int it, int max_it, double target) {
+    c->j = 0;
+    c->it = it;
+    c->max_it = max_it;
+    c->jend = 0;
+    c->target = target;
+}
+
+// out = V_j (the current basis vector, into the preconditioner's input)
+__global__ void k_kry_gather(int64_t n, const double *__restrict__ V, const KrylovCtl *__restrict__ c,
+                             double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = V[(int64_t)c->j * n + i];
+}
+
+// Z_j = in (the preconditioned vector, kept for the solution update)
+__global__ void k_kry_scatter(int64_t n, const double *__restrict__ in, double *__restrict__ Z,
+                              const KrylovCtl *__restrict__ c) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) Z[(int64_t)c->j * n + i] = in[i];
+}
+
+// partial dot products of V_0 .. V_j with w (k = j + 1 from the device)
+__global__ void k_kry_multi_dot(const double *__restrict__ V, int64_t n,
+                                const KrylovCtl *__restrict__ c, const double *__restrict__ w,
+                                double *__restrict__ partial) {
+    __shared__ double sh[kThreads];
+    const int k = c->j + 1;
+    for (int j = 0; j < k; j++) {
+        const double *v = V + (int64_t)j * n;
+        double acc = 0.0;
+        for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+             i += (int64_t)gridDim.x * blockDim.x)
+            acc += v[i] * w[i];
+        sh[threadIdx.x] = acc;
+        __syncthreads();
+        for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+            if ((int)threadIdx.x < s) sh[threadIdx.x] += sh[threadIdx.x + s];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0) partial[(int64_t)blockIdx.x * k + j] = sh[0];
+        __syncthreads();
+    }
+}
+
+__global__ void k_kry_dot_finish(const double *__restrict__ partial,
+                                 const KrylovCtl *__restrict__ c, double *__restrict__ out) {
+    const int k = c->j + 1;
+    const int j = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (j >= k) return;
+    double a = 0.0;
+    for (int b = lane; b < kDotBlocks; b += 32) a += partial[(int64_t)b * k + j];
+    for (int o = 16; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    if (lane == 0) out[j] = a;
+}
+
+// w -= sum_{q <= j} coef[q] V_q (kadd = 1), or x -= sum_{q < jend} coef[q] Z_q
+// (kadd = 0 with use_jend)
+__global__ void k_kry_axpy(double *__restrict__ w, const double *__restrict__ V, int64_t n,
+                           const KrylovCtl *__restrict__ c, int use_jend,
+                           const double *__restrict__ coef) {
+    __shared__ double cs[kMaxKrylov];
+    const int k = use_jend ? c->jend : c->j + 1;
+    if ((int)threadIdx.x < k) cs[threadIdx.x] = coef[threadIdx.x];
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    double acc = w[i];
+    for (int q = 0; q < k; q++) acc -= cs[q] * V[(int64_t)q * n + i];
+    w[i] = acc;
+}
+
+// V_{j+1} = w / *den (0 if *den == 0)
+__global__ void k_kry_scale_out(int64_t n, const double *__restrict__ den,
+                                const double *__restrict__ w, double *__restrict__ V,
+                                const KrylovCtl *__restrict__ c) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double d = *den;
+    V[(int64_t)(c->j + 1) * n + i] = d != 0.0 ? w[i] / d : 0.0;
+}
+
+// column j of the Hessenberg matrix and its Givens rotations (the same
+// arithmetic as k_gmres_column), then the loop control: advance j, count the
+// preconditioner application, and keep looping while the residual estimate
+// is above target, columns remain and the refinement budget is not spent
+__global__ void k_kry_column_next(double *st, GmresLayout L, KrylovCtl *c,
+                                  cudaGraphConditionalHandle loop) {
+    if (threadIdx.x != 0) return;
+    const int j = c->j;
+    double *H = st + L.H;
+    const int ld = L.m + 1;
+    double *col = H + (int64_t)j * ld;
+    for (int i = 0; i <= j; i++) col[i] = st[L.c1 + i] + st[L.c2 + i];
+    col[j + 1] = st[L.sc + 1];
+    double *cs = st + L.cs, *sn = st + L.sn, *g = st + L.g;
+    for (int i = 0; i < j; i++) {
+        const double a = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = a;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    cs[j] = den > 0.0 ? col[j] / den : 1.0;
+    sn[j] = den > 0.0 ? col[j + 1] / den : 0.0;
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    st[L.sc + 2] = fabs(g[j + 1]);
+    const int jn = j + 1;
+    c->j = jn;
+    c->jend = jn;
+    c->it += 1;
+    const bool more = st[L.sc + 2] > c->target && jn < L.m && c->it < c->max_it;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
+// small triangular solve for the jend columns of the cycle
+__global__ void k_kry_solve(double *st, GmresLayout L, const KrylovCtl *c) {
+    if (threadIdx.x != 0) return;
+    const int k = c->jend;
+    const double *H = st + L.H;
+    const int ld = L.m + 1;
+    double y[kMaxKrylov];
+    for (int i = k - 1; i >= 0; i--) {
+        double a = st[L.g + i];
+        for (int q = i + 1; q < k; q++) a -= H[(int64_t)q * ld + i] * y[q];
+        const double d = H[(int64_t)i * ld + i];
+        y[i] = d != 0.0 ? a / d : 0.0;
+    }
+    for (int i = 0; i < k; i++) st[L.c1 + i] = -y[i];
+}
+
+}  // namespace
+
+void launch_kry_start(KrylovCtl *c, int it, int max_it, double target, cudaStream_t s) {
+    note_launch(), k_kry_start<<<1, 1, 0, s>>>(c, it, max_it, target);
+}
+void launch_kry_gather(int64_t n, const double *V, const KrylovCtl *c, double *out, cudaStream_t s) {
+    note_launch(), k_kry_gather<<<nblocks(n), kThreads, 0, s>>>(n, V, c, out);
+}
+void launch_kry_scatter(int64_t n, const double *in, double *Z, const KrylovCtl *c, cudaStream_t s) {
+    note_launch(), k_kry_scatter<<<nblocks(n), kThreads, 0, s>>>(n, in, Z, c);
+}
+void launch_kry_multi_dot(const double *V, int64_t n, const KrylovCtl *c, const double *w,
+                          double *partial, cudaStream_t s) {
+    note_launch(), k_kry_multi_dot<<<kDotBlocks, kThreads, 0, s>>>(V, n, c, w, partial);
+}
+void launch_kry_dot_finish(const double *partial, const KrylovCtl *c, double *out, cudaStream_t s) {
+    note_launch(), k_kry_dot_finish<<<1, 32 * kMaxKrylov, 0, s>>>(partial, c, out);
+}
+void launch_kry_axpy(double *w, const double *V, int64_t n, const KrylovCtl *c, bool use_jend,
+                     const double *coef, cudaStream_t s) {
+    if (n) note_launch(), k_kry_axpy<<<nblocks(n), kThreads, 0, s>>>(w, V, n, c, use_jend ? 1 : 0, coef);
+}
+void launch_kry_scale_out(int64_t n, const double *den, const double *w, double *V,
+                          const KrylovCtl *c, cudaStream_t s) {
+    note_launch(), k_kry_scale_out<<<nblocks(n), kThreads, 0, s>>>(n, den, w, V, c);
+}
+void launch_kry_column_next(double *st, int m, KrylovCtl *c, cudaGraphConditionalHandle loop,
+                            cudaStream_t s) {
+    note_launch(), k_kry_column_next<<<1, 32, 0, s>>>(st, gmres_layout(m), c, loop);
+}
+void launch_kry_solve(double *st, int m, const KrylovCtl *c, cudaStream_t s) {
+    note_launch(), k_kry_solve<<<1, 32, 0, s>>>(st, gmres_layout(m), c);
+}
+
 void launch_dot_finish(const double *partial, int k, double *out, bool take_sqrt, cudaStream_t s) {
     note_launch(), k_dot_finish<<<1, 32 * k, 0, s>>>(partial, k, out, take_sqrt ? 1 : 0);
 }
