@@ -218,8 +218,10 @@ int kkt_solve(scopf_handle *h, const double *b, double *x, int32_t max_refine,
  * fraction-to-boundary step and one trial evaluation at the full step.
  * dir: device buffers for the direction (may be NULL: kept in the handle).
  * out (host, 6): alpha_primal, alpha_dual, theta at the trial point,
- * barrier objective at the trial point, delta_w used, refinement residual.
- * inertia (host, 3): inertia of the accepted factorization. */
+ * barrier objective at the trial point, delta_w used, preconditioner
+ * applications (block solves: one per kkt solve plus its refinement steps).
+ * inertia (host, 3): n and m + p (the inertia the correction reached), then
+ * the number of factorizations it took. */
 int scopf_newton_step(scopf_handle *h, const scopf_state *it, const double *lam_n,
                       const double *nu0_n, double rho, double mu, double dw_last,
                       scopf_state *dir, double out[6], int32_t inertia[3]);

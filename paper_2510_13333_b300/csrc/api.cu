@@ -1006,6 +1006,7 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         r = rn / bden;
     }
     h->n_refine += it;
+    h->n_solve_calls++;
     // every exit follows a residual check, whose round trip also read the
     // sweeps' status after the last solve
     h->timer.collect();

@@ -156,6 +156,7 @@ struct scopf_handle {
     bool have_ncl = false;                 // rho, mu_last, lam_n, nu0_n, eta/omega_last are set
     bool has_solution = false;             // st, lam_n, nu0_n, rho, mu_last describe a solution
     bool inner_limit = false;              // the last solve stopped at max_inner
+    long long n_solve_calls = 0;           // kkt solves (each: one preconditioner application + refinement)
     // iteration log of the last ncl_solve (records of kHistInner / kHistOuter doubles)
     std::vector<double> hist_inner, hist_outer;
     bool screen_blocks = false;            // NCL outer loop with the per-block screening rule

@@ -925,6 +925,7 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     if (m) cudaMemcpyAsync(h->lam_n, lam_n, sizeof(double) * m, cudaMemcpyDeviceToDevice, s);
     if (p) cudaMemcpyAsync(h->nu0_n, nu0_n, sizeof(double) * p, cudaMemcpyDeviceToDevice, s);
     Ipm I(h);
+    const long long apply0 = h->n_refine + h->n_solve_calls;
     const scopf_state &st = *it;
     scopf_state &d = dir ? *dir : h->dir;
     int r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, h->rhs);
@@ -962,7 +963,7 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
         out[2] = tht;
         out[3] = pht;
         out[4] = delta;
-        out[5] = 0.0;
+        out[5] = (double)(h->n_refine + h->n_solve_calls - apply0);
     }
     if (inertia) {
         inertia[0] = (int32_t)n;
