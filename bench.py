@@ -134,7 +134,8 @@ def oracle_step_sample(n_ctg_sample: int = 8):
     inst = synthgrid.config_instance(CONFIG_IDX)
     full_blocks = inst.K + 1
     inst.ctgs = inst.ctgs[:n_ctg_sample]
-    if True:  # scipy sparse kernels and the C LDL^T run on one thread
+    from threadpoolctl import threadpool_limits
+    with threadpool_limits(limits=1):   # BLAS on one thread; the C LDL^T is single-threaded
         M = SCOPFModel(inst)
         perm, _ = symbolic.kkt_permutation(M)
         S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm))
@@ -430,12 +431,14 @@ def oracle_screen_sample(n_sample: int = 8):
     500-bus screening batch; returns (seconds per contingency, description)."""
     import synthgrid
     from oracle.screening import screen_candidate
+    from threadpoolctl import threadpool_limits
     inst, u0, _, _ = synthgrid.screening_batch(CONFIG_IDX)
-    t0 = time.perf_counter()
-    for cand in inst.ctgs[:n_sample]:
-        screen_candidate(inst, cand, u0, eps=SCREEN_EPS, rho_cap=SCREEN_RHO_CAP,
-                         accept_tol=SCREEN_TOL)
-    t = time.perf_counter() - t0
+    with threadpool_limits(limits=1):
+        t0 = time.perf_counter()
+        for cand in inst.ctgs[:n_sample]:
+            screen_candidate(inst, cand, u0, eps=SCREEN_EPS, rho_cap=SCREEN_RHO_CAP,
+                             accept_tol=SCREEN_TOL)
+        t = time.perf_counter() - t0
     desc = (f"oracle screen_candidate (numpy/scipy + C LDL^T, 1 thread), one two-scenario NCL "
             f"solve per candidate, first {n_sample} of {len(inst.ctgs)} candidates of the "
             f"500-bus screening batch ({t:.1f} s)")
