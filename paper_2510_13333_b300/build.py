@@ -54,7 +54,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
             sys.stderr.write(f"compilation of {src} failed\n")
     if failed:
         raise RuntimeError("nvcc failed")
-    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart"])
+    subprocess.check_call([nvcc, *ARCH, "-shared", "-o", LIB, *objs, "-lcudart", "-lpthread"])
     return LIB
 
 

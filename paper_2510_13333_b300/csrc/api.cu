@@ -1,7 +1,10 @@
 // C ABI of the library (include/scopf.h): handle management, device
 // uploads, and the assemble / factor / solve entry points of the Newton step
 // of eq. (newtonsystem).
+#include <atomic>
+#include <chrono>
 #include <cmath>
+#include <thread>
 #include <cstdio>
 #include <cstring>
 #include <new>
@@ -399,27 +402,52 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
         scopf_default_options(&h->opt);
     h->precision = h->opt.precision;
     h->host_only = h->opt.host_only != 0;
+    const auto tc = std::chrono::steady_clock::now();
+    auto since = [&tc]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - tc).count();
+    };
     std::string err = build_model(net, ctg, K, h->M);
+    const double t_model = since();
     if (!err.empty()) {
         if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
         delete h;
         return SCOPF_ERR_INVALID_ARG;
     }
-    h->syms.resize(h->M.blocks.size());
-    for (size_t k = 0; k < h->M.blocks.size(); k++) {
-        err = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes, h->opt.relax_max_front,
-                             h->syms[k]);
-        if (!err.empty()) {
-            if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
-            delete h;
-            return SCOPF_ERR_INVALID_ARG;
-        }
+    // the blocks' symbolic analyses are independent (each reads the model and
+    // writes its own result): spread them over the host's cores
+    const size_t nblk = h->M.blocks.size();
+    h->syms.resize(nblk);
+    {
+        std::vector<std::string> errs(nblk);
+        const unsigned hw = std::thread::hardware_concurrency();
+        const size_t nt = std::max<size_t>(1, std::min<size_t>(hw ? hw : 1, nblk));
+        std::atomic<size_t> next{0};
+        auto work = [&]() {
+            for (size_t k; (k = next.fetch_add(1)) < nblk;)
+                errs[k] = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes,
+                                         h->opt.relax_max_front, h->syms[k]);
+        };
+        std::vector<std::thread> pool;
+        for (size_t t = 1; t < nt; t++) pool.emplace_back(work);
+        work();
+        for (auto &th : pool) th.join();
+        for (size_t k = 0; k < nblk; k++)
+            if (!errs[k].empty()) {
+                if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", errs[k].c_str());
+                delete h;
+                return SCOPF_ERR_INVALID_ARG;
+            }
     }
+    const double t_symbolic = since();
     if (h->opt.cluster_max_tasks < 1) {
         delete h;
         return SCOPF_ERR_INVALID_ARG;
     }
     err = build_fronts(h->M, h->syms, h->opt.cluster_max_tasks, h->HF);
+    const double t_fronts = since();
+    if (h->opt.verbose)
+        std::printf("scopf_create: model %.2f s, symbolic %.2f s, fronts %.2f s\n", t_model,
+                    t_symbolic - t_model, t_fronts - t_symbolic);
     if (!err.empty()) {
         if (h->opt.verbose) std::fprintf(stderr, "scopf_create: %s\n", err.c_str());
         delete h;

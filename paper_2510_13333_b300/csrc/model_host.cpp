@@ -10,6 +10,7 @@
 //  * alpha_g = pmax_g / sum of pmax over generators in service in block k;
 //  * PV buses outside the switch set keep q in bounds, v free in bounds.
 #include <algorithm>
+#include <thread>
 #include <cmath>
 #include <numeric>
 
@@ -470,12 +471,35 @@ std::string build_model(const scopf_network *net, const scopf_contingency *ctg, 
     }
 
     // --------------------------------------------------- CSR + contributions
-    std::sort(tup.begin(), tup.end(), [](const Tuple &a, const Tuple &b) {
-        if (a.row != b.row) return a.row < b.row;
-        if (a.col != b.col) return a.col < b.col;
-        if (a.src != b.src) return a.src < b.src;
-        return a.coef < b.coef;
-    });
+    // order the tuples by (row, col, src, coef): a counting sort by row, then
+    // each row's few tuples sorted on (col, src, coef), rows spread over the
+    // host's cores (the same order a global sort gives)
+    {
+        std::vector<int64_t> start(M.n_kkt + 1, 0);
+        for (const Tuple &t : tup) start[t.row + 1]++;
+        for (int64_t r = 0; r < M.n_kkt; r++) start[r + 1] += start[r];
+        std::vector<Tuple> by_row(tup.size());
+        {
+            std::vector<int64_t> fill(start.begin(), start.end() - 1);
+            for (const Tuple &t : tup) by_row[fill[t.row]++] = t;
+        }
+        tup.swap(by_row);
+        auto less = [](const Tuple &a, const Tuple &b) {
+            if (a.col != b.col) return a.col < b.col;
+            if (a.src != b.src) return a.src < b.src;
+            return a.coef < b.coef;
+        };
+        const unsigned hw = std::thread::hardware_concurrency();
+        const int64_t nt = std::max<int64_t>(1, std::min<int64_t>(hw ? hw : 1, M.n_kkt));
+        std::vector<std::thread> pool;
+        auto work = [&](int64_t t) {
+            for (int64_t r = t; r < M.n_kkt; r += nt)
+                std::sort(tup.begin() + start[r], tup.begin() + start[r + 1], less);
+        };
+        for (int64_t t = 1; t < nt; t++) pool.emplace_back(work, t);
+        work(0);
+        for (auto &th : pool) th.join();
+    }
     M.kkt_ptr.assign(M.n_kkt + 1, 0);
     M.kkt_col.clear();
     M.ctr_ptr.clear();
