@@ -315,7 +315,21 @@ std::string build_model(const scopf_network *net, const scopf_contingency *ctg, 
     std::vector<Tuple> tup;
     tup.reserve((size_t)M.n_be * 72 + (size_t)M.n_kkt * 4);
     // residual contributions: per c row
-    std::vector<std::vector<std::pair<int64_t, double>>> cfun(M.m);
+    // residual contributions (row, (source, coefficient)) in insertion order;
+    // one flat list instead of a list per row (m small allocations)
+    struct RowLists {
+        std::vector<int64_t> row;
+        std::vector<std::pair<int64_t, double>> val;
+        struct Ref {
+            RowLists *L;
+            int64_t r;
+            void push_back(const std::pair<int64_t, double> &p) {
+                L->row.push_back(r);
+                L->val.push_back(p);
+            }
+        };
+        Ref operator[](int64_t r) { return Ref{this, r}; }
+    } cfun;
     M.c_const.assign(M.m, 0.0);
     auto sym = [&](int64_t i, int64_t j, int64_t src, double coef) {
         tup.push_back({i, j, src, coef});
@@ -504,6 +518,9 @@ std::string build_model(const scopf_network *net, const scopf_contingency *ctg, 
     M.kkt_col.clear();
     M.ctr_ptr.clear();
     M.ctr.clear();
+    M.kkt_col.reserve(tup.size());
+    M.ctr_ptr.reserve(tup.size() + 1);
+    M.ctr.reserve(tup.size());
     M.diag_pos.assign(M.n_kkt, -1);
     size_t i0 = 0;
     while (i0 < tup.size()) {
@@ -523,12 +540,18 @@ std::string build_model(const scopf_network *net, const scopf_contingency *ctg, 
     for (int64_t r0 = 0; r0 < M.n_kkt; r0++)
         if (M.diag_pos[r0] < 0) return "internal: missing KKT diagonal";
     // residual function CSR
+    // (stable counting sort by row: each row keeps its insertion order)
     M.cf_ptr.assign(M.m + 1, 0);
-    for (int64_t rr = 0; rr < M.m; rr++) {
-        M.cf_ptr[rr + 1] = M.cf_ptr[rr] + (int64_t)cfun[rr].size();
-        for (auto &pr : cfun[rr]) {
-            M.cf_idx.push_back(pr.first);
-            M.cf_coef.push_back(pr.second);
+    for (int64_t r : cfun.row) M.cf_ptr[r + 1]++;
+    for (int64_t rr = 0; rr < M.m; rr++) M.cf_ptr[rr + 1] += M.cf_ptr[rr];
+    M.cf_idx.assign(cfun.row.size(), 0);
+    M.cf_coef.assign(cfun.row.size(), 0.0);
+    {
+        std::vector<int64_t> fill(M.cf_ptr.begin(), M.cf_ptr.end() - 1);
+        for (size_t q = 0; q < cfun.row.size(); q++) {
+            const int64_t at = fill[cfun.row[q]]++;
+            M.cf_idx[at] = cfun.val[q].first;
+            M.cf_coef[at] = cfun.val[q].second;
         }
     }
     return "";
