@@ -120,6 +120,12 @@ typedef struct {
                                  run as one CUDA graph (a WHILE node repeating one
                                  captured step) with no host round trip per step;
                                  0: host-driven loop */
+    int32_t fp64_switch_refine;  /* mixed precision: switch to FP64 factors for the
+                                 rest of the solve once fp64_switch_streak Newton
+                                 steps in a row needed at least this many
+                                 refinement steps (0 = only when refinement
+                                 stalls) */
+    int32_t fp64_switch_streak;
 } scopf_options;
 
 /* Sizes of the handle's problem. */

@@ -371,6 +371,8 @@ void scopf_default_options(scopf_options *o) {
     o->cluster_max_tasks = 16;
     o->relax_max_front = 0;
     o->device_loop = 1;
+    o->fp64_switch_refine = 0;
+    o->fp64_switch_streak = 3;
 }
 
 const char *scopf_strerror(int s) {

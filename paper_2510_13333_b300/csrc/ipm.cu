@@ -613,8 +613,20 @@ struct Ipm {
         }
         if (r == SCOPF_ERR_REFINE_STALL) r = SCOPF_OK;  // FP64 factors: accept the refined step
         if (r != SCOPF_OK) return r;
+        // cost switch: FP32 factors whose steps keep needing many refinement
+        // steps cost more than FP64 factors (a factorization at the FP64 rate
+        // against that many extra solves); switch after o.fp64_switch_streak
+        // such steps in a row
+        if (!force_fp64 && o.fp64_switch_refine > 0 && h->factored_precision == SCOPF_PREC_MIXED) {
+            streak = steps >= o.fp64_switch_refine ? streak + 1 : 0;
+            if (streak >= std::max(1, o.fp64_switch_streak)) {
+                force_fp64 = true;
+                fallbacks++;
+            }
+        }
         return SCOPF_OK;
     }
+    int streak = 0;
 };
 
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, bool resume) {

@@ -77,3 +77,21 @@ def test_stalled_fp32_refinement_falls_back_to_fp64(cuda):
     assert mixed["call_status"] == 0 and fp64["call_status"] == 0
     assert mixed["fp64_fallbacks"] == 1 and fp64["fp64_fallbacks"] == 0
     assert abs(mixed["objective"] - fp64["objective"]) <= 1e-6 * abs(fp64["objective"])
+
+
+def test_cost_switch_to_fp64(cuda):
+    """With the refinement-cost switch set to one step, the first mixed
+    Newton step that needs refinement moves the solve to FP64 factors (one
+    switch), the solve converges to the FP64 solve's objective, and the
+    iteration log shows FP32 factors only before the switch."""
+    import paper_2510_13333_b300 as P
+    inst = H.instance(0)
+    lib = P.SCOPF(inst, precision=P.PREC_MIXED, fp64_switch_refine=1, fp64_switch_streak=1)
+    r = lib.ncl_solve()
+    ref = P.SCOPF(inst, precision=P.PREC_FP64).ncl_solve()
+    assert r["call_status"] == 0 and r["fp64_fallbacks"] == 1
+    assert abs(r["objective"] - ref["objective"]) <= 1e-6 * abs(ref["objective"])
+    names, log = lib.history(0)
+    prec = log[:, names.index("precision")]
+    first64 = int(np.argmax(prec == 0))
+    assert prec[first64] == 0 and np.all(prec[:first64] == 1) and np.all(prec[first64:] == 0)
