@@ -1242,16 +1242,18 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
                 if (lane == j0 + u) zi -= p;
             }
         }
-        T Lr[32];
+        // the tile, by columns: lane c holds column c of the tile's L and
+        // subtracts L[r][c] z_r as each z_r (r > c) becomes final and is
+        // broadcast (one shuffle per row instead of a reduction per column)
+        T Lc[32];
 #pragma unroll
-        for (int c = 0; c < 32; c++)
-            Lr[c] = (c < lane && lane < kn) ? L[(int64_t)(k0 + c) * f + k0 + lane] : (T)0;
+        for (int r = 0; r < 32; r++)
+            Lc[r] = (lane < r && r < kn) ? L[(int64_t)(k0 + lane) * f + k0 + r] : (T)0;
 #pragma unroll
-        for (int c = 31; c >= 0; c--) {
-            if (c < kn) {
-                T q = Lr[c] * zi;
-                for (int o = 16; o > 0; o >>= 1) q += __shfl_xor_sync(0xffffffffu, q, o);
-                if (lane == c) zi -= q;
+        for (int r = 31; r >= 0; r--) {
+            if (r < kn) {
+                const T zr = __shfl_sync(0xffffffffu, zi, r);
+                if (lane < r) zi -= Lc[r] * zr;
             }
         }
         if (lane < kn) sv[k0 + lane] = zi;
