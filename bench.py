@@ -41,8 +41,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
 # valid only for the sweep kernels' source it was taken with
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "d3ddb0af57b60b7c9c8b084d2cf7c505527c886b",
-                 "bytes_per_solve": 253.3e6 + 300.9e6}
+                 "sha1": "cdadb319562637753f5a7d515bd5c65e8425eb6f",
+                 "bytes_per_solve": 253.8e6 + 301.2e6}
 
 
 def sweep_traffic():
@@ -237,7 +237,8 @@ def run_ours(args):
         dist.init_process_group("nccl")
     inst = synthgrid.config_instance(CONFIG_IDX)
     t0 = time.perf_counter()
-    lib = P.SCOPF(inst, precision=P.PREC_MIXED)
+    loop = {"device_loop": 0} if args.host_loop else {}
+    lib = P.SCOPF(inst, precision=P.PREC_MIXED, **loop)
     t_create = time.perf_counter() - t0
     sz = lib.sizes
     # ---- time to solution (full NCL solve from the flat start)
@@ -598,6 +599,9 @@ def main():
     ap.add_argument("--iterate-at", type=int, default=30)
     ap.add_argument("--tts", default="both", choices=["none", "mixed", "both"],
                     help="which full NCL solves to time (time to solution)")
+    ap.add_argument("--host-loop", action="store_true",
+                    help="host-driven refinement loop (every kernel launched from the host, "
+                         "for profilers that attribute launches to NVTX ranges)")
     ap.add_argument("--workload", default="newton", choices=["newton", "screen", "illcond"],
                     help="newton: the Newton step (default); screen: batched screening; "
                          "illcond: NCL solves with narrowed reactive bands")
