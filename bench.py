@@ -27,6 +27,9 @@ import time
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# The CPU baseline times the oracle on one core: numpy's BLAS pool reads this
+# before it starts, so it is set ahead of every numpy import.
+os.environ["OPENBLAS_NUM_THREADS"] = "1"
 
 METRIC = ("Newton steps/s and SCOPF time-to-solution at 500-bus×256-ctg (1e-6), "
           "vs plain FP64 GPU")
@@ -121,6 +124,17 @@ class Clocks:
 
 
 # ------------------------------------------------------------- reference arm
+def one_blas_thread():
+    """BLAS limited to one thread around an oracle timing: threadpoolctl
+    where it is installed, else the OPENBLAS_NUM_THREADS setting above."""
+    try:
+        from threadpoolctl import threadpool_limits
+    except ImportError:
+        import contextlib
+        return contextlib.nullcontext()
+    return threadpool_limits(limits=1)
+
+
 def oracle_step_sample(n_ctg_sample: int = 8):
     """Time the CPU oracle's Newton step on the 500-bus network with a
     bounded number of contingency blocks; returns (seconds per full-size
@@ -134,8 +148,7 @@ def oracle_step_sample(n_ctg_sample: int = 8):
     inst = synthgrid.config_instance(CONFIG_IDX)
     full_blocks = inst.K + 1
     inst.ctgs = inst.ctgs[:n_ctg_sample]
-    from threadpoolctl import threadpool_limits
-    with threadpool_limits(limits=1):   # BLAS on one thread; the C LDL^T is single-threaded
+    with one_blas_thread():   # BLAS on one thread; the C LDL^T is single-threaded
         M = SCOPFModel(inst)
         perm, _ = symbolic.kkt_permutation(M)
         S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm))
@@ -432,9 +445,8 @@ def oracle_screen_sample(n_sample: int = 8):
     500-bus screening batch; returns (seconds per contingency, description)."""
     import synthgrid
     from oracle.screening import screen_candidate
-    from threadpoolctl import threadpool_limits
     inst, u0, _, _ = synthgrid.screening_batch(CONFIG_IDX)
-    with threadpool_limits(limits=1):
+    with one_blas_thread():
         t0 = time.perf_counter()
         for cand in inst.ctgs[:n_sample]:
             screen_candidate(inst, cand, u0, eps=SCREEN_EPS, rho_cap=SCREEN_RHO_CAP,
