@@ -1024,8 +1024,14 @@ __device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict
         T acc = (T)0;
         if (lane < kn) {
             acc = sv[row];
-#pragma unroll 4
-            for (int c = 0; c < k0; c++) acc -= L[(int64_t)c * f + row] * sv[c];
+            for (int c0 = 0; c0 < k0; c0 += 8) {   // 8 loads in flight
+                T l[8];
+#pragma unroll
+                for (int u = 0; u < 8; u++) l[u] = c0 + u < k0 ? L[(int64_t)(c0 + u) * f + row] : (T)0;
+#pragma unroll
+                for (int u = 0; u < 8; u++)
+                    if (c0 + u < k0) acc -= l[u] * sv[c0 + u];
+            }
         }
         T Lr[32];
 #pragma unroll
@@ -1041,11 +1047,39 @@ __device__ __forceinline__ void fwd_front(const DevFront &F, const T *__restrict
         if (lane < kn) sv[row] = acc;
         __syncwarp();
     }
-    for (int i = np + lane; i < f; i += 32) {
-        T acc = sv[i];
-#pragma unroll 8
-        for (int c = 0; c < np; c++) acc -= L[(int64_t)c * f + i] * sv[c];
-        v[i] = acc;
+    // update rows, two 32-row chunks at a time: the loads of eight columns
+    // for both chunks are in flight together, and every row's sum still
+    // runs over the columns in order
+    for (int i0 = np; i0 < f; i0 += 64) {
+        T acc[2];
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int i = i0 + 32 * j + lane;
+            acc[j] = i < f ? sv[i] : (T)0;
+        }
+        for (int c0 = 0; c0 < np; c0 += 8) {
+            T l[8][2];
+#pragma unroll
+            for (int u = 0; u < 8; u++)
+#pragma unroll
+                for (int j = 0; j < 2; j++) {
+                    const int i = i0 + 32 * j + lane;
+                    l[u][j] = (c0 + u < np && i < f) ? L[(int64_t)(c0 + u) * f + i] : (T)0;
+                }
+#pragma unroll
+            for (int u = 0; u < 8; u++) {
+                if (c0 + u < np) {
+                    const T sc = sv[c0 + u];
+#pragma unroll
+                    for (int j = 0; j < 2; j++) acc[j] -= l[u][j] * sc;
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 2; j++) {
+            const int i = i0 + 32 * j + lane;
+            if (i < f) v[i] = acc[j];
+        }
     }
     // diagonal: y = D^-1 (L^-1 b) on the pivot rows
     for (int c = lane; c < np; c += 32) v[c] = sv[c] / L[(int64_t)c * f + c];
@@ -1229,11 +1263,25 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
             T pj[8];
 #pragma unroll
             for (int u = 0; u < 8; u++) pj[u] = (T)0;
-            for (int i = k0 + kn + lane; i < f; i += 32) {
-                const T xi = sv[i];
+            // two 32-row chunks per round: their loads in flight together,
+            // each lane's rows still summed in increasing order
+            for (int i0 = k0 + kn; i0 < f; i0 += 64) {
+                T l[2][8], xv[2];
 #pragma unroll
-                for (int u = 0; u < 8; u++)
-                    if (j0 + u < kn) pj[u] += L[(int64_t)(k0 + j0 + u) * f + i] * xi;
+                for (int j = 0; j < 2; j++) {
+                    const int i = i0 + 32 * j + lane;
+                    xv[j] = i < f ? sv[i] : (T)0;
+#pragma unroll
+                    for (int u = 0; u < 8; u++)
+                        l[j][u] = (i < f && j0 + u < kn) ? L[(int64_t)(k0 + j0 + u) * f + i] : (T)0;
+                }
+#pragma unroll
+                for (int j = 0; j < 2; j++)
+                    if (i0 + 32 * j + lane < f) {
+#pragma unroll
+                        for (int u = 0; u < 8; u++)
+                            if (j0 + u < kn) pj[u] += l[j][u] * xv[j];
+                    }
             }
 #pragma unroll
             for (int u = 0; u < 8; u++) {
