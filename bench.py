@@ -44,8 +44,8 @@ FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
 # valid only for the sweep kernels' source it was taken with
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "6cdca5d5fd0a355f60b1769f96fd064664b534d7",
-                 "bytes_per_solve": 253.3e6 + 302.6e6}
+                 "sha1": "12ef02fde60a2bf105f5fb9e0ea33ab600252724",
+                 "bytes_per_solve": 253.5e6 + 302.8e6}
 
 
 def sweep_traffic():

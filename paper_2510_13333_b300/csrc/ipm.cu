@@ -291,11 +291,6 @@ __global__ void k_recover(Dev D, const double *w, const double *r, const double 
     }
 }
 
-__global__ void k_step(int64_t n, const double *x, const double *d, double a, double *y) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) y[i] = x[i] + a * d[i];
-}
-
 // The trial point of every iterate vector in one launch: y = x + a d over
 // the segments w, r, lam, t, s, yc (primal step a) and zs, zl, zu (dual step
 // az).  With alpha != nullptr the two steps are read from the device (the

@@ -637,8 +637,6 @@ __global__ void __launch_bounds__(med_threads<T>())
 // Phase 2: large fronts near the tree tops (they carry the border rows), one
 // CTA per front.  Launched after phase 1, so small children are complete.
 constexpr int kBT = 256;
-constexpr int kBigPanelBytes = 96 * 1024;
-constexpr int kBigPanel = kBigPanelBytes / 8;   // panel elements that fit (FP64 bound)
 // row chunks of 32 per column in one extend-add / trailing-update pass
 template <typename T>
 __host__ __device__ constexpr int big_chunks() { return sizeof(T) == 4 ? 4 : 2; }
@@ -1553,8 +1551,9 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     }
     const int nbig = F.n_items - F.n_items_med;
     if (nbig > 0) {
-        // shared panel sized to the largest np x f of this phase (at most
-        // kBigPanel elements); larger panels take the global-memory path
+        // shared panel sized to the largest np x f of this phase (capped at
+        // creation to 12,288 elements, 96 KB in FP64); larger panels take the
+        // global-memory path
         // plus the staged child->parent map of one child (at most max_f rows)
         const size_t sm3 = big_rel_offset<T>(F.big_panel) + sizeof(int) * (size_t)F.max_f;
         static int g3[2] = {0, 0};
