@@ -105,7 +105,7 @@ class Clocks:
                         self.samples.append([x.strip() for x in out.split(",")])
                 except Exception:
                     pass
-                self._stop.wait(0.2)
+                self._stop.wait(0.05)
         self._t = threading.Thread(target=run, daemon=True)
         self._t.start()
 
