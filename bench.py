@@ -84,43 +84,66 @@ def measured_peaks():
 
 
 class Clocks:
-    """nvidia-smi sampling during the timed region."""
+    """nvidia-smi sampling around the timed region: one nvidia-smi process
+    in loop mode (-lms 50).  Samples read between mark() (or start()) and
+    stop() count; if none landed there, the first one read after the mark
+    is kept."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
 
     def __init__(self):
-        self.samples = []
-        self._stop = threading.Event()
+        self.samples = []   # (host time read, fields)
+        self._p = None
         self._t = None
+        self.t0 = None
 
     def start(self):
+        self.t0 = time.perf_counter()
+        try:
+            self._p = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.Q}", "--format=csv,noheader,nounits", "-i",
+                 str(int(os.environ.get("LOCAL_RANK", "0"))), "-lms", "50"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self._p = None
+            return
+
         def run():
-            q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
-                 "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
-                 "clocks_event_reasons.sw_power_cap")
-            while not self._stop.is_set():
-                try:
-                    out = subprocess.run(["nvidia-smi", f"--query-gpu={q}", "--format=csv,noheader,nounits",
-                                          "-i", str(int(os.environ.get("LOCAL_RANK", "0")))],
-                                         capture_output=True, text=True, timeout=5).stdout.strip()
-                    if out:
-                        self.samples.append([x.strip() for x in out.split(",")])
-                except Exception:
-                    pass
-                self._stop.wait(0.05)
+            for line in self._p.stdout:
+                line = line.strip()
+                if line:
+                    self.samples.append((time.perf_counter(), [x.strip() for x in line.split(",")]))
         self._t = threading.Thread(target=run, daemon=True)
         self._t.start()
 
+    def mark(self):
+        """The timed region starts now."""
+        self.t0 = time.perf_counter()
+
     def stop(self):
-        self._stop.set()
+        t1 = time.perf_counter()
+        time.sleep(0.06)   # the sample taken at the end of the region
+        if self._p is not None:
+            self._p.terminate()
+            try:
+                self._p.wait(timeout=5)
+            except Exception:
+                self._p.kill()
         if self._t:
-            self._t.join(timeout=10)
-        sm = [float(s[0]) for s in self.samples if s[0].replace(".", "").isdigit()]
-        mx = [float(s[1]) for s in self.samples if s[1].replace(".", "").isdigit()]
+            self._t.join(timeout=5)
+        inside = [f for t, f in self.samples if self.t0 <= t <= t1 + 0.06]
+        if not inside:
+            inside = [f for t, f in self.samples if t >= self.t0][:1]
+        sm = [float(f[0]) for f in inside if f[0].replace(".", "").isdigit()]
+        mx = [float(f[1]) for f in inside if len(f) > 1 and f[1].replace(".", "").isdigit()]
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        reasons = sorted({names[i] for s in self.samples for i in range(4)
-                          if len(s) > 3 + i and s[3 + i].lower().startswith("active")})
+        reasons = sorted({names[i] for f in inside for i in range(4)
+                          if len(f) > 3 + i and f[3 + i].lower().startswith("active")})
         sm.sort()
         return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": max(mx) if mx else None,
-                "reasons": reasons, "samples": len(self.samples)}
+                "reasons": reasons, "samples": len(inside)}
 
 
 # ------------------------------------------------------------- reference arm
@@ -289,7 +312,7 @@ def run_ours(args):
 
     launches = [0]
 
-    def timed(l, k):
+    def timed(l, k, on_start=None):
         for _ in range(args.warmup):
             step(l)
         torch.cuda.synchronize()
@@ -301,6 +324,8 @@ def run_ours(args):
         l.scopf_timing(True)
         n0 = P.scopf_launch_count()
         torch.cuda.nvtx.range_push("timed")
+        if on_start:
+            on_start()
         e0.record(s)
         for _ in range(k):
             step(l)
@@ -314,7 +339,7 @@ def run_ours(args):
 
     clocks = Clocks()
     clocks.start()
-    ms_mixed, ph_mixed = timed(lib, args.steps)
+    ms_mixed, ph_mixed = timed(lib, args.steps, clocks.mark)
     launches_mixed = launches[0]
     apps_mixed = apps[0]
     clk = clocks.stop()
