@@ -1,6 +1,7 @@
 """bench.py's multi-replica host logic on CPU (gloo, world size 2): every
 rank sees the slowest rank's time, the job's throughput counts every
-replica's units over that time, and the reference arm runs on rank 0 only."""
+replica's units over that time, and the reference arm runs on rank 0 only.
+Also the clock sampler's timed-region window."""
 import io
 import os
 import socket
@@ -63,3 +64,31 @@ def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
     with redirect_stdout(buf):
         bench.run_reference(None)
     assert buf.getvalue() == ""
+
+
+def test_clock_samples_inside_the_timed_region():
+    """Only samples read inside [mark, stop] count; throttle reasons are
+    reported by name; with none inside, the first one after the mark is
+    kept.  (Samples are planted by hand: no nvidia-smi process runs.)"""
+    sys.path.insert(0, ROOT)
+    import time
+    import bench
+    c = bench.Clocks()
+    c.mark()
+    t = c.t0
+    row = lambda sm, thermal: [str(sm), "2032", "900.0", "Not Active",
+                               "Active" if thermal else "Not Active", "Not Active", "Active"]
+    c.samples = [(t - 1.0, row(1000, True)),      # before the region: ignored
+                 (t + 0.001, row(2032, False)),
+                 (t + 0.002, row(2010, False))]
+    out = c.stop()
+    assert out["samples"] == 2 and out["sm_max_mhz"] == 2032.0
+    assert out["sm_mhz"] in (2010.0, 2032.0)
+    assert out["reasons"] == ["sw_power_cap"]
+    c2 = bench.Clocks()
+    c2.mark()
+    c2.samples = [(c2.t0 + 10.0, row(1500, True))]   # read after the region ended
+    out2 = c2.stop()
+    assert out2["samples"] == 1 and out2["sm_mhz"] == 1500.0
+    assert out2["reasons"] == ["hw_thermal_slowdown", "sw_power_cap"]
+    assert time.perf_counter() > c2.t0
