@@ -126,6 +126,14 @@ typedef struct {
                                  refinement steps (0 = only when refinement
                                  stalls) */
     int32_t fp64_switch_streak;
+    int32_t known_zero_pivot; /* 1: the inertia correction's first trial, delta_w = 0
+                                 (IC-1 of Waechter & Biegler 2006), is taken as
+                                 failed without factoring when the factorization
+                                 must meet an exactly zero pivot: a primal row
+                                 with no stored entry eliminated before it and a
+                                 zero diagonal at delta_w = 0.  The outcome is
+                                 the one factoring would give, so iterates are
+                                 unchanged; 0: always factor at delta_w = 0 */
 } scopf_options;
 
 /* Sizes of the handle's problem. */
@@ -200,8 +208,9 @@ int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n,
  * row_ptr[n_kkt+1], col[nnz] (int64) and val[nnz]; any may be NULL. */
 int kkt_export(scopf_handle *h, int64_t *row_ptr, int64_t *col, double *val);
 
-/* Pivot-free LDL^T of every block (one persistent launch), Schur complement
- * onto u0 and its dense LDL^T.  inertia[0..2] = (#positive, #negative,
+/* Pivot-free LDL^T of every block (three persistent launches, one per
+ * front-size phase: tile-sized fronts, medium fronts, large fronts), Schur
+ * complement onto u0 and its dense LDL^T.  inertia[0..2] = (#positive, #negative,
  * #zero-or-tiny pivots) over the whole KKT (host out).  precision overrides
  * the handle's setting for this factorisation (-1 = handle's). */
 int kkt_factor(scopf_handle *h, int32_t precision, int32_t inertia[3]);
@@ -269,7 +278,10 @@ int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out);
  * n*n, read only (a private copy is factored); b, x: device, n (x may not
  * alias S).  inertia (host, 3, may be NULL): signs of D.  stream: a
  * cudaStream_t or NULL.  Allocates its scratch (n*n + n doubles) with
- * cudaMalloc and frees it before returning. */
+ * cudaMalloc and frees it before returning.  A zero pivot (singular S) is
+ * replaced by a tiny one and counted in inertia[2]; the call still returns
+ * SCOPF_OK with a huge or non-finite x, so a caller that may pass a
+ * singular S must pass inertia and check inertia[2] == 0. */
 int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *x,
                            int32_t inertia[3], void *stream);
 
@@ -281,8 +293,15 @@ int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *
  * Scratch is a static per-device array sized for n <= 768 (about 4.7 MB,
  * held by every GPU that loads the library until exit); n > 768 returns
  * SCOPF_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address; make it before any stream capture.  All calls on a device
- * share the array, so calls that overlap on the GPU race: order them. */
+ * device address (cudaGetSymbolAddress); make it before any stream capture.
+ * That address is cached per device ordinal for the life of the process: it
+ * goes stale if the caller resets the device (cudaDeviceReset) and goes on
+ * using the library.  Concurrent first calls from several host threads are
+ * safe (the cache is atomic).  Each call synchronises its stream before
+ * returning, so calls overlap on the GPU only when host threads call at
+ * once; all calls on a device share the array, so such calls race and must
+ * be ordered by the caller.  Zero pivots are reported as for
+ * scopf_dense_ldlt_solve (check inertia[2]). */
 int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, double *x,
                                    int32_t inertia[3], void *stream);
 

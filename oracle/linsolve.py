@@ -95,14 +95,35 @@ class SparseLDLSolver:
         self.perm = None
         self.pattern_key = None
 
-    def factor(self, K):
-        lib = _lib()
-        K = sp.csr_matrix(K)
+    def _order(self, K):
         n = K.shape[0]
         if self.perm is None or self.perm.shape[0] != n:
             self.perm = (np.asarray(self.perm_fn(K), dtype=np.int64) if self.perm_fn
                          else np.arange(n, dtype=np.int64))
-        perm = self.perm
+        return self.perm
+
+    def zero_pivot_certain(self, K) -> bool:
+        """True when factor(K) must report an exactly zero pivot.
+
+        A row of P K P' with no stored entry left of its diagonal gets no
+        update in the elimination (row k of L is empty: its pattern is the
+        union of the tree paths from those entries), so its pivot is its own
+        diagonal entry.  If one such entry is 0.0, the pivot is 0.0 whatever
+        the other values, and |d| <= pivot_tol counts it as zero.
+        """
+        K = sp.csr_matrix(K)
+        perm = self._order(K)
+        Kp = K[perm][:, perm]
+        above = sp.triu(Kp, k=1, format="csc")   # column k: stored rows i < k
+        above.sum_duplicates()
+        no_update = np.diff(above.indptr) == 0
+        return bool(np.any(no_update & (Kp.diagonal() == 0.0)))
+
+    def factor(self, K):
+        lib = _lib()
+        K = sp.csr_matrix(K)
+        n = K.shape[0]
+        perm = self._order(K)
         iperm = np.empty(n, dtype=np.int64)
         iperm[perm] = np.arange(n)
         # upper triangle of the permuted matrix, stored by columns (CSC)

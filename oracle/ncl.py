@@ -65,6 +65,9 @@ class Options:
     kappa_w_minus: float = 1.0 / 3.0
     kappa_w_plus: float = 8.0
     kappa_w_plus_bar: float = 100.0
+    # IC-1 at every iteration, its outcome taken without factoring when the
+    # pivot-free LDL^T must meet an exactly zero pivot (``newton_direction``)
+    known_zero_pivot: bool = True
     gamma_theta: float = 1e-5
     gamma_phi: float = 1e-8
     delta_sw: float = 1.0
@@ -151,7 +154,7 @@ class NCLSolver:
         self.n, self.m, self.p = P.n, P.m, P.p
         self.n_inner = 0
         self.history = []
-        self.skip_delta0 = False
+        self.n_known_zero = 0      # IC-1 trials whose zero pivot was certain
 
     # ------------------------------------------------------------ helpers
     def project_start(self, w):
@@ -290,29 +293,34 @@ class NCLSolver:
         return State(w=dw, r=dr, t=dt, s=ds, lam=dlam, yc=dyc, zl=dzl, zu=dzu, zs=dzs)
 
     def newton_direction(self, st, prm, res, mu, H, dw_last):
-        """Factor with inertia correction (Waechter & Biegler 2006, Alg. IC)."""
+        """Factor with inertia correction (Waechter & Biegler 2006, Alg. IC).
+
+        IC-1 tries delta_w = 0 at every iteration.  When the linear solver is
+        a pivot-free LDL^T whose order gives some row no update and a zero
+        diagonal (``zero_pivot_certain``), that factorization must report a
+        zero pivot, so its outcome -- wrong inertia -- is known without
+        computing it; the correction continues at IC-3 exactly as it would
+        after factoring.  ``Options.known_zero_pivot = False`` factors anyway.
+        """
         o = self.o
         n_pos, n_neg = self.n, self.m + self.p
         rhs = self.reduced_rhs(st, prm, res, mu)
-        # Once a delta_w = 0 factorization has shown zero pivots (variables
-        # that enter only linearly are eliminated before their rows, so the
-        # zeros recur at every iterate) the trial at 0 is skipped: it would
-        # fail again, and the delta_w sequence that follows is unchanged.
-        if self.skip_delta0:
-            delta = o.delta_w0 if dw_last == 0.0 else max(o.delta_w_min, o.kappa_w_minus * dw_last)
-        else:
-            delta = 0.0
+        ic3 = o.delta_w0 if dw_last == 0.0 else max(o.delta_w_min, o.kappa_w_minus * dw_last)
+        delta = 0.0
+        certain = getattr(self.lin, "zero_pivot_certain", None)
+        if o.known_zero_pivot and certain is not None:
+            if certain(self.kkt_matrix(st, prm, H, res["J"], 0.0)):
+                delta = ic3
+                self.n_known_zero += 1
         tries = 0
         while True:
             K = self.kkt_matrix(st, prm, H, res["J"], delta)
             ip, ineg, iz = self.lin.factor(K)
             tries += 1
-            if delta == 0.0 and iz > 0:
-                self.skip_delta0 = True
             if ip == n_pos and ineg == n_neg and iz == 0:
                 break
             if delta == 0.0:
-                delta = o.delta_w0 if dw_last == 0.0 else max(o.delta_w_min, o.kappa_w_minus * dw_last)
+                delta = ic3
             else:
                 delta *= o.kappa_w_plus if dw_last > 0.0 else o.kappa_w_plus_bar
             if delta > o.delta_w_max:

@@ -7,13 +7,14 @@ feasibility problem eq. (feaspb).  Only contingencies that are not
 structurally infeasible enter the SCOPF.
 
 With ``eps`` given, the first-stage variables are held at u0 by bounds
-u0 +- eps (clipped to their own limits), as in the paper.  With eps = None
-(the default used to build the synthetic workloads) u0 stays free: the
-candidate is solved together with the base case as a two-scenario SCOPF.
-The base-OPF optimum of the synthetic grids leaves no recovery margin for
-most outages, so the fixed-u0 test rejects nearly all of them.  The penalty
-is capped at ``rho_cap``: a candidate is accepted when |(r, t)|_inf falls
-below ``accept_tol`` before that cap.
+u0 +- eps (clipped to their own limits), as in the paper; the synthetic
+workloads were screened this way, with eps = 1e-3 around a base point
+computed with derated thermal limits and a narrowed voltage band, which
+leaves the outages a recovery margin (``make_screened.py``).  With
+eps = None u0 stays free and the candidate is solved together with the base
+case as a two-scenario SCOPF.  The penalty is capped at ``rho_cap``: a
+candidate is accepted when |(r, t)|_inf falls below ``accept_tol`` before
+that cap.
 """
 from __future__ import annotations
 

@@ -61,7 +61,8 @@ _OPT_DOUBLES = ["tol", "mu_min", "mu_init", "kappa_eps", "kappa_mu", "theta_mu",
                 "omega_init", "refine_tol", "pivot_tol"]
 _OPT_INTS = ["max_backtrack", "max_outer", "max_inner", "max_refine", "precision",
              "relax_max_nodes", "verbose", "spin_limit", "host_only", "cluster_max_tasks",
-             "relax_max_front", "device_loop", "fp64_switch_refine", "fp64_switch_streak"]
+             "relax_max_front", "device_loop", "fp64_switch_refine", "fp64_switch_streak",
+             "known_zero_pivot"]
 
 
 class Options(ctypes.Structure):

@@ -150,6 +150,29 @@ int setup_device(scopf_handle *h) {
         h->n_pdiag = (int64_t)pos.size();
         TRY(upload(h, pos, &h->pdiag_pos));
         TRY(alloc(h, pos.size(), &h->pdiag_base));
+        // Rows that receive no update in the pivot-free elimination: a block
+        // row none of whose stored neighbours is eliminated before it (block
+        // rows never touch another block's rows; border rows go last).  Row
+        // k of L is then empty and the pivot is the diagonal entry itself.
+        std::vector<int64_t> elim(M.n_kkt, INT64_MAX);
+        for (const BlockSymbolic &S : h->syms)
+            for (int64_t i = 0; i < S.n_block_rows; i++) elim[S.rows[i]] = i;
+        std::vector<int64_t> lead;
+        for (int64_t i = 0, j = 0; i < M.n_kkt; i++) {
+            if (M.row_kind[i] != 0) continue;
+            bool has_diag = false, first = M.block_of_kkt[i] >= 0;
+            for (int64_t q = M.kkt_ptr[i]; q < M.kkt_ptr[i + 1]; q++) {
+                const int64_t c = M.kkt_col[q];
+                if (c == i) has_diag = true;
+                else if (elim[c] < elim[i]) first = false;
+            }
+            if (!has_diag) continue;
+            if (first) lead.push_back(j);
+            j++;
+        }
+        h->n_lead = (int64_t)lead.size();
+        TRY(upload(h, lead, &h->lead_pdiag));
+        TRY(alloc(h, 1, &h->lead_zero));
     }
     TRY(upload(h, M.row_index, &d.row_index));
     {
@@ -373,6 +396,7 @@ void scopf_default_options(scopf_options *o) {
     o->device_loop = 1;
     o->fp64_switch_refine = 0;
     o->fp64_switch_streak = 3;
+    o->known_zero_pivot = 1;
 }
 
 const char *scopf_strerror(int s) {

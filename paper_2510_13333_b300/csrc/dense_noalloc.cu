@@ -15,10 +15,16 @@
 // library holds it until the process exits.  Its device address is looked
 // up once per device (cudaGetSymbolAddress, with that device current) by the
 // first call made on that device; make that first call before any stream
-// capture.  All calls on a device share the array and it keeps the last
-// call's contents, so calls that overlap on the GPU (different streams or
-// host threads without ordering between them) race and must not be issued.
+// capture.  The address is cached per device ordinal for the life of the
+// process, so it goes stale if the caller resets the device
+// (cudaDeviceReset) and keeps using the library.  All calls on a device
+// share the array and it keeps the last call's contents; each call
+// synchronises its stream before returning, so calls can only overlap on the
+// GPU when several host threads call at once (on different streams) --
+// those race and must be ordered by the caller.
 #include <cuda_runtime.h>
+
+#include <atomic>
 
 #include "../../include/scopf.h"
 #include "kernels.h"
@@ -39,19 +45,24 @@ constexpr size_t kScratchDoubles =
 static __device__ __align__(256) double g_noalloc_scratch[kScratchDoubles];
 
 constexpr int kMaxDevices = 64;
-double *g_scratch_ptr[kMaxDevices] = {};
+// Per device ordinal, the array's device address once looked up.  Atomic
+// because concurrent first calls from several host threads may all look it
+// up; each stores the same value.  The cached address belongs to the CUDA
+// context it was taken in: after cudaDeviceReset the next context may place
+// the array elsewhere, and the stale entry would be used.
+std::atomic<double *> g_scratch_ptr[kMaxDevices];
 
 // device address of the scratch array on the current device (set up once)
 int scratch_on_current_device(double **out) {
     int dev = 0;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SCOPF_ERR_CUDA;
-    if (!g_scratch_ptr[dev]) {
-        double *ptr = nullptr;
+    double *ptr = g_scratch_ptr[dev].load(std::memory_order_acquire);
+    if (!ptr) {
         if (cudaGetSymbolAddress((void **)&ptr, g_noalloc_scratch) != cudaSuccess || !ptr)
             return SCOPF_ERR_CUDA;
-        g_scratch_ptr[dev] = ptr;
+        g_scratch_ptr[dev].store(ptr, std::memory_order_release);
     }
-    *out = g_scratch_ptr[dev];
+    *out = ptr;
     return SCOPF_OK;
 }
 

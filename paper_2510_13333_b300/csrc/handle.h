@@ -147,6 +147,11 @@ struct scopf_handle {
     int64_t n_pdiag = 0;                      // primal rows
     const int64_t *pdiag_pos = nullptr;       // their diagonal entries in kval
     double *pdiag_base = nullptr;             // those entries at the last assembly
+    // primal rows whose pivot is their own diagonal entry (no stored entry of
+    // the row is eliminated before it), as indices into pdiag_pos / pdiag_base
+    int64_t n_lead = 0;
+    const int64_t *lead_pdiag = nullptr;
+    int *lead_zero = nullptr;                 // device count of those with a zero diagonal
     // iterate and NCL parameters owned by the handle
     scopf_state st{};
     double *lam_n = nullptr, *nu0_n = nullptr;
@@ -175,7 +180,7 @@ struct scopf_handle {
     // counters
     int n_factor = 0, n_refine = 0;
     bool force_fp64 = false;      // sticky FP64 fallback inside a solve
-    bool skip_delta0 = false;     // delta_w = 0 factorizations showed zero pivots
+    long long n_known_zero = 0;   // delta_w = 0 trials taken as failed without factoring
     unsigned long long *trace = nullptr;   // scheduler trace buffer (cudaMalloc'd)
     scopf::PhaseTimer timer;
     std::string last_error;

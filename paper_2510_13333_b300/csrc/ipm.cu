@@ -378,20 +378,35 @@ struct Timer {
 constexpr int kPartSlots = 24;   // partial-sum slots per reduction block
 int ipm_partials() { return kB * kPartSlots; }
 
+// Whether the factorization of the assembled K at delta_w = 0 must report a
+// zero pivot: one of the rows that receive no update in the elimination has
+// a diagonal entry of exactly zero (its pivot is that entry, whatever the
+// other values).  Only for a K assembled at delta_w = 0.
+static bool zero_pivot_certain(scopf_handle *h) {
+    if (h->n_lead == 0 || h->assembled_delta_w != 0.0) return false;
+    launch_count_zero_diag(h->n_lead, h->lead_pdiag, h->pdiag_base, h->lead_zero, h->stream);
+    int count = 0;
+    cudaMemcpyAsync(&count, h->lead_zero, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
+    cudaStreamSynchronize(h->stream);
+    return count > 0;
+}
+
 // Inertia correction (W&B 2006, Alg. IC) around the factorization of the
-// assembled K: delta_w = 0 first (unless it already showed zero pivots),
-// then growing delta_w until the inertia is (n, m + p, 0).  Once a
-// delta_w = 0 factorization has shown zero pivots -- variables entering only
-// linearly (p^k, Delta^k, free q^k) are eliminated before their rows, so
-// these zeros recur at every iterate -- the trial at 0 is skipped: it would
-// fail again and the delta_w sequence is unchanged.  K's primal diagonal is
-// left shifted by the delta_w returned.
+// assembled K: IC-1 tries delta_w = 0 at every iteration, then delta_w grows
+// from the IC-3 value until the inertia is (n, m + p, 0).  When the trial at
+// 0 must meet a zero pivot (zero_pivot_certain) its outcome is known without
+// factoring, and the correction starts at IC-3, as it would after factoring.
+// K's primal diagonal is left shifted by the delta_w returned.
 int factor_inertia(scopf_handle *h, int precision, double dw_last, double &delta, int &tries) {
     const scopf_options &o = h->opt;
     const int64_t npos = h->M.n, nneg = h->M.m + h->M.p;
-    delta = h->skip_delta0
-                ? (dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last))
-                : 0.0;
+    const double ic3 =
+        dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
+    delta = 0.0;
+    if (o.known_zero_pivot && zero_pivot_certain(h)) {
+        delta = ic3;
+        h->n_known_zero++;
+    }
     tries = 0;
     double current = h->assembled_delta_w;   // the shift of the assembled K
     while (true) {
@@ -404,14 +419,13 @@ int factor_inertia(scopf_handle *h, int precision, double dw_last, double &delta
         int r = factor_impl(h, precision, in);
         if (r != SCOPF_OK) return r;
         tries++;
-        if (delta == 0.0 && in[2] > 0) h->skip_delta0 = true;
         if (o.verbose >= 2)
             std::printf("    factor (%s) delta_w %.2e inertia (%d, %d, %d), want (%lld, %lld, 0)\n",
                         precision == SCOPF_PREC_MIXED ? "fp32" : "fp64", delta, in[0], in[1],
                         in[2], (long long)npos, (long long)nneg);
         if (in[0] == npos && in[1] == nneg && in[2] == 0) return SCOPF_OK;
         if (delta == 0.0)
-            delta = dw_last == 0.0 ? o.delta_w0 : std::fmax(o.delta_w_min, o.kappa_w_minus * dw_last);
+            delta = ic3;
         else
             delta *= dw_last > 0.0 ? o.kappa_w_plus : o.kappa_w_plus_bar;
         if (delta > o.delta_w_max) return SCOPF_ERR_WRONG_INERTIA;
@@ -636,7 +650,6 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
     scopf_state &d = h->dir;
     scopf_state &tr = h->trial;
     double rho = resume ? h->rho : o.rho_init;
-    h->skip_delta0 = false;
     if (!resume) {
         cudaMemsetAsync(h->lam_n, 0, sizeof(double) * (m ? m : 1), s);
         cudaMemsetAsync(h->nu0_n, 0, sizeof(double) * (p ? p : 1), s);

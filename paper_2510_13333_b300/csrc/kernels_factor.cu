@@ -1449,17 +1449,19 @@ __global__ void k_fill(int64_t n, double v, double *x) {
     if (i < n) x[i] = v;
 }
 
-int warp_grid() {
-    static int grid = 0;
-    if (!grid) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        grid = sms * (2048 / kWT);
-        if (grid <= 0) grid = 148 * 16;
-    }
-    return grid;
+// SMs of the current device (cached per device ordinal)
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
 }
+
+int warp_grid() { return sm_count() * (2048 / kWT); }
 
 }  // namespace
 
@@ -1469,13 +1471,7 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     const int64_t n = M.n_kkt;
     const int g = (int)((n + t - 1) / t);
     // entry sweep: resident warps over the stored entries
-    static int resident = 0;
-    if (!resident) {
-        int dev = 0, sms = 0;
-        cudaGetDevice(&dev);
-        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-        resident = (sms > 0 ? sms : 148) * (2048 / t);
-    }
+    const int resident = sm_count() * (2048 / t);
     const int64_t chunks = (M.nnz_kkt + kRE - 1) / kRE;
     const int ge = (int)std::min<int64_t>((chunks + t - 1) / t, (int64_t)resident);
     // start in the buffer that makes the last sweep land in `scale`
@@ -1506,6 +1502,15 @@ void launch_queue_reset(const DevFront &F, QueueSeeds seeds, const int32_t *pend
                                                 seeds, F.q_pending, pend, F.q_ctr);
 }
 
+// Function attributes and occupancy are per device: the launch caches below
+// are kept per device ordinal (beyond kMaxDev they are recomputed per call).
+constexpr int kMaxDev = 64;
+static int device_slot() {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return -1;
+    return dev;
+}
+
 // CTAs of `kernel` that fit on the device at once with `smem` bytes each
 static int resident_grid(const void *kernel, int threads, size_t smem) {
     int dev = 0, sms = 148, occ = 0;
@@ -1522,10 +1527,12 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     QueueSeeds seeds{{F.init_small, F.init_med, F.init_big},
                      {F.n_init_small, F.n_init_med, F.n_init_big}};
     launch_queue_reset(F, seeds, F.pend_factor, s);
-    static int grids[2][2] = {{0, 0}, {0, 0}};   // [float, double][phase 1, 2]
+    static int grids[kMaxDev][2][2] = {};   // [device][float, double][phase 1, 2]
     const size_t sm1 = sizeof(T) * (size_t)(kFT / 32) * 32 * 33;
     const size_t sm2 = sizeof(T) * (size_t)(med_threads<T>() / 32) * kMedF * (kMedF + 1);
-    int *g = grids[sizeof(T) == 4 ? 0 : 1];
+    const int dev = device_slot();
+    int gtmp[2] = {0, 0};
+    int *g = dev >= 0 ? grids[dev][sizeof(T) == 4 ? 0 : 1] : gtmp;
     if (!g[0]) {
         for (const void *k : {(const void *)k_factor<float>, (const void *)k_factor<double>}) {
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 80 * 1024);
@@ -1556,8 +1563,12 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
         // global-memory path
         // plus the staged child->parent map of one child (at most max_f rows)
         const size_t sm3 = big_rel_offset<T>(F.big_panel) + sizeof(int) * (size_t)F.max_f;
-        static int g3[2] = {0, 0};
-        static size_t g3_sm[2] = {0, 0};
+        static int g3_all[kMaxDev][2] = {};
+        static size_t g3_sm_all[kMaxDev][2] = {};
+        int g3_tmp[2] = {0, 0};
+        size_t g3_sm_tmp[2] = {0, 0};
+        int *g3 = dev >= 0 ? g3_all[dev] : g3_tmp;
+        size_t *g3_sm = dev >= 0 ? g3_sm_all[dev] : g3_sm_tmp;
         const int pi = sizeof(T) == 4 ? 0 : 1;
         if (g3_sm[pi] != sm3) {
             cudaFuncSetAttribute((const void *)k_factor_big<T>,
@@ -1583,13 +1594,12 @@ void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s) 
 }
 
 void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
+    // the shared-memory opt-in is a per-device attribute: set it on the
+    // current device before every factorization (a cheap host call)
+    if (n > 0)
+        cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
     for (int k0 = 0; k0 < n; k0 += kPanel) {
         const int k1 = k0 + kPanel < n ? k0 + kPanel : n;
-        static bool attr = false;
-        if (!attr) {
-            cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-            attr = true;
-        }
         note_launch(), k_dense_panel<<<1, 256, sizeof(double) * (size_t)(n - k0) * (k1 - k0), s>>>(S, n, k0, k1, st, pivot_tol);
         const int rem = n - k1;
         if (rem > 0) {
@@ -1610,13 +1620,10 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, c
     const int need = (F.n_items + kWT / 32 - 1) / (kWT / 32);
     if (grid > need) grid = need;
     const size_t sm = sizeof(T) * (size_t)(kWT / 32) * F.max_f;
-    static bool attr = false;
-    if (!attr && sm > 48 * 1024) {
-        for (const void *k : {(const void *)k_solve_fwd<float>, (const void *)k_solve_fwd<double>,
-                              (const void *)k_solve_bwd<float>, (const void *)k_solve_bwd<double>})
+    // per-device shared-memory opt-in, set on the current device each call
+    if (sm > 48 * 1024)
+        for (const void *k : {(const void *)k_solve_fwd<T>, (const void *)k_solve_bwd<T>})
             cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-        attr = true;
-    }
     note_launch(), k_rhs_to_fronts<T><<<(int)((F.n_rows + 255) / 256), 256, 0, s>>>(F.n_rows, F.vpos_of_row,
                                                                      scale, b, vec);
     note_launch(), k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, queue_a(F, F.n_items), st, spin_limit);

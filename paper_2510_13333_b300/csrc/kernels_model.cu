@@ -474,7 +474,22 @@ __global__ void k_diag_set(int64_t n, const int64_t *__restrict__ pos,
     if (i < n) kval[pos[i]] = base[i] + shift;
 }
 
+// count the listed primal rows whose diagonal entry is exactly zero
+__global__ void k_count_zero_diag(int64_t n, const int64_t *__restrict__ idx,
+                                  const double *__restrict__ base, int *__restrict__ count) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool z = i < n && base[idx[i]] == 0.0;
+    const unsigned b = __ballot_sync(0xffffffffu, z);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(count, __popc(b));
+}
+
 }  // namespace
+
+void launch_count_zero_diag(int64_t n, const int64_t *idx, const double *base, int *count,
+                            cudaStream_t s) {
+    cudaMemsetAsync(count, 0, sizeof(int), s);
+    if (n) note_launch(), k_count_zero_diag<<<nblocks(n), kThreads, 0, s>>>(n, idx, base, count);
+}
 
 void launch_diag_gather(int64_t n, const int64_t *pos, const double *kval, double *base,
                         cudaStream_t s) {

@@ -78,3 +78,48 @@ def library_matrix(H, vals, gen):
     n = len(ptr) - 1
     rows = np.repeat(np.arange(n), np.diff(ptr))
     return sp.csr_matrix((vals, (gen[rows], gen[col])), shape=(n, n))
+
+
+def group_scale(M: SCOPFModel, v: np.ndarray) -> np.ndarray:
+    """Per entry of a generic-order KKT vector [w; lam; yc]: max |v| over the
+    entries of the same scenario block and the same kind (variables,
+    equality rows, complementarity rows); the border variables form one
+    group.  An absolute tolerance tied to this scale checks small blocks on
+    their own scale instead of the largest entry of the whole vector."""
+    sc = np.zeros(len(v))
+    groups = []
+    for blk in M.blocks:
+        groups += [(blk.w0, blk.nvar), (M.n + blk.c0, blk.nrow), (M.n + M.m + blk.p0, blk.ncomp)]
+    groups.append((M.border0, M.nborder))
+    for a, k in groups:
+        if k:
+            sc[a:a + k] = np.abs(v[a:a + k]).max()
+    return sc
+
+
+def assert_entries_close(name, got, want, rtol, atol):
+    """|got - want| <= rtol |want| + atol for every entry (atol may be a
+    vector); the message names the worst entry."""
+    got = np.asarray(got)
+    want = np.asarray(want)
+    err = np.abs(got - want)
+    bound = rtol * np.abs(want) + atol
+    bad = ~(err <= bound)
+    if np.any(bad):
+        ratio = np.where(bound > 0, err / np.where(bound > 0, bound, 1.0), np.inf)
+        i = int(np.argmax(np.where(np.isnan(ratio), np.inf, ratio)))
+        raise AssertionError(f"{name}: {int(bad.sum())} of {len(err)} entries outside "
+                             f"rtol {rtol:g} + atol; worst index {i}: got {got[i]!r}, want "
+                             f"{want[i]!r}, err/bound {ratio[i]:.3g}")
+
+
+def assert_kkt_close(K_lib, K_or, rtol=1e-12, row_atol=1e-15):
+    """Every stored entry of either matrix: |K_lib - K_or| <= rtol |K_or| +
+    row_atol * (largest |entry| of the oracle's row).  Entries that are
+    small next to their row (1/rho, the NCL block, small curvature) are
+    checked on their own scale, not on that of the largest entry of K."""
+    K_or = sp.csr_matrix(K_or)
+    D = (sp.csr_matrix(K_lib) - K_or).tocoo()
+    rowmax = np.asarray(abs(K_or).max(axis=1).todense()).ravel()
+    want = np.asarray(K_or[D.row, D.col]).ravel()
+    assert_entries_close("KKT entries", want + D.data, want, rtol, row_atol * rowmax[D.row])

@@ -51,11 +51,10 @@ def test_fullsize_kkt_matches_oracle(bench_iterate):
     rhs_or = S.reduced_rhs(so, prm, res, mu)
     gen = H.generic_of_natural(M)
     K_lib = H.library_matrix(lib, lib.kkt_values(), gen)
-    scale = abs(K_or).max()
-    assert abs(K_lib - K_or).max() <= 1e-12 * scale
+    H.assert_kkt_close(K_lib, K_or, rtol=1e-12, row_atol=1e-15)
     r = np.empty_like(rhs_or)
     r[gen] = rhs.cpu().numpy()
-    np.testing.assert_allclose(r, rhs_or, rtol=1e-11, atol=1e-11 * np.abs(rhs_or).max())
+    H.assert_entries_close("rhs", r, rhs_or, 1e-11, 1e-14 * H.group_scale(M, rhs_or))
 
 
 def test_fullsize_step_inertia_and_solve(bench_iterate):

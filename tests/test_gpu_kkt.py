@@ -53,14 +53,12 @@ def test_kkt_assembly_matches_oracle(cuda, which):
             "cfg1": lambda: H.instance(1)}[which]()
     M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 11, rho=1e3, delta_w=0.3)
     K_lib = H.library_matrix(lib, lib.kkt_values(), gen)
-    diff = abs(K_lib - K_or)
-    scale = abs(K_or).max()
-    assert diff.max() <= 1e-12 * scale, diff.max()
+    H.assert_kkt_close(K_lib, K_or, rtol=1e-12, row_atol=1e-15)
     # same stored pattern (no entry of one missing from the other)
     assert K_lib.nnz >= K_or.count_nonzero()
     r = np.empty_like(rhs_or)
     r[gen] = rhs.cpu().numpy()
-    np.testing.assert_allclose(r, rhs_or, rtol=1e-11, atol=1e-11 * np.abs(rhs_or).max())
+    H.assert_entries_close("rhs", r, rhs_or, 1e-11, 1e-14 * H.group_scale(M, rhs_or))
 
 
 @pytest.mark.parametrize("which,prec", [("small", 0), ("cfg0", 0), ("cfg0", 1), ("cfg1", 0),
@@ -79,8 +77,7 @@ def test_factor_solve_matches_oracle(cuda, which, prec):
     x_or = ora.solve(rhs_or)
     xl = np.empty_like(x_or)
     xl[gen] = x.cpu().numpy()
-    err = np.abs(xl - x_or).max() / np.abs(x_or).max()
-    assert err <= 1e-8, err
+    H.assert_entries_close("solution", xl, x_or, 1e-8, 1e-8 * H.group_scale(M, x_or))
 
 
 def test_inertia_indefinite(cuda):

@@ -99,3 +99,26 @@ def test_checkpoint_resume(cuda):
     # resuming needs parameters
     fresh = P.SCOPF(inst, precision=P.PREC_FP64)
     assert fresh.ncl_resume()["call_status"] == -1
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_known_zero_pivot_changes_nothing(cuda, prec):
+    """IC-1 (delta_w = 0 first) at every iteration: taking a certain zero
+    pivot's outcome without factoring gives bit-identical solves and the same
+    delta_w at every iteration as factoring every trial, one factorization
+    fewer each time (118-bus: the rule fires at every iteration)."""
+    import paper_2510_13333_b300 as P
+    out = {}
+    for known in (1, 0):
+        lib = P.SCOPF(H.instance(1), precision=prec, known_zero_pivot=known)
+        res = lib.ncl_solve()
+        assert res["call_status"] == 0
+        names, inner = lib.history(0)
+        st = {f: v.cpu().numpy() for f, v in lib.get_state().items()}
+        out[known] = (res, inner[:, names.index("delta_w")], st)
+    (ra, da, sa), (rb, db, sb) = out[1], out[0]
+    assert np.array_equal(da, db)
+    assert ra["objective"] == rb["objective"] and ra["inner_iters"] == rb["inner_iters"]
+    for f in sa:
+        assert np.array_equal(sa[f], sb[f]), f
+    assert rb["factorizations"] - ra["factorizations"] >= ra["inner_iters"]

@@ -25,8 +25,11 @@ def test_noalloc_matches_allocating_entry_point(cuda):
     import paper_2510_13333_b300 as P
     # two calls in a row (different sizes: the second must not see stale
     # contents of the shared scratch), each compared with the regular call
-    for n1, n2, seed in ((120, 60, 3), (90, 47, 4)):
-        K = _sqd(n1, n2, seed)
+    # the largest order the static scratch takes (768: the panel kernel's
+    # shared memory is then close to its opt-in), two ordinary orders, and
+    # a 1 x 1 block
+    for n1, n2, seed in ((512, 256, 2), (120, 60, 3), (90, 47, 4), (1, 0, 5)):
+        K = _sqd(n1, n2, seed) if n2 else np.array([[2.5]])
         n = n1 + n2
         S = torch.tensor(K.T.copy(), device="cuda")
         b = torch.tensor(np.random.default_rng(seed).standard_normal(n), device="cuda")
