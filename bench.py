@@ -31,13 +31,21 @@ sys.path.insert(0, ROOT)
 # before it starts, so it is set ahead of every numpy import.
 os.environ["OPENBLAS_NUM_THREADS"] = "1"
 
+WORKLOADS = {
+    2: ("syn500_k256: 500-bus, 90-generator synthetic grid (mean degree 2.8), 256 contingencies "
+        "(220 line, 36 generator), random PV/PQ switch sets; seeded, screened"),
+    4: ("syn2000_k128: 2000-bus, 360-generator synthetic grid (mean degree 2.7), 128 "
+        "contingencies (100 line, 28 generator), random PV/PQ switch sets (blocks ~2x uneven); "
+        "seeded, screened"),
+}
+SCALE_IDX = 4
 METRIC = ("Newton steps/s and SCOPF time-to-solution at 500-bus×256-ctg (1e-6), "
           "vs plain FP64 GPU")
 CONFIG_IDX = 2
 # FP32 FMA peak from unit counts and clock: 148 SMs x 128 lanes x 2 flops x 2.032 GHz
 FP32_PEAK_TFLOPS = 148 * 128 * 2 * 2.032e9 / 1e12
-# FP64 FMA rate of B300 measured by the DFMA probe (1/64 of FP32 per SM)
-FP64_PEAK_TFLOPS = FP32_PEAK_TFLOPS / 64.0
+# FP64 peak of B300 from its nominal figure (1.25 TFLOP/s dense)
+FP64_PEAK_TFLOPS = 1.25
 
 
 # DRAM bytes (read + write) of one solve's forward and backward sweeps,
@@ -158,61 +166,117 @@ def one_blas_thread():
     return threadpool_limits(limits=1)
 
 
-def oracle_step_sample(n_ctg_sample: int = 8):
-    """Time the CPU oracle's Newton step on the 500-bus network with a
-    bounded number of contingency blocks; returns (seconds per full-size
-    step extrapolated per block, description, cores)."""
-    import numpy as np
-    import synthgrid
-    from oracle.linsolve import SparseLDLSolver
-    from oracle.ncl import NCLSolver, Params
-    from oracle.scopf_model import SCOPFModel
-    from oracle import symbolic
-    inst = synthgrid.config_instance(CONFIG_IDX)
-    full_blocks = inst.K + 1
-    inst.ctgs = inst.ctgs[:n_ctg_sample]
-    with one_blas_thread():   # BLAS on one thread; the C LDL^T is single-threaded
-        M = SCOPFModel(inst)
-        perm, _ = symbolic.kkt_permutation(M)
-        S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm))
-        st = S.initial_state()
-        prm = Params(rho=S.o.rho_init, lam_n=np.zeros(M.m), nu0_n=np.zeros(M.p))
-        mu = 0.1
-        times = []
-        for _ in range(2):
+ORACLE_SAMPLE_CTG = 8      # contingencies in the oracle's bounded sample
+ORACLE_SAMPLE_ITERATE = 30  # IPM iterations before the timed steps (as the GPU arm)
+
+
+class OracleSample:
+    """The CPU oracle on a bounded sample of the benchmark workload: the
+    500-bus network with the first ORACLE_SAMPLE_CTG of its 256 contingencies.
+    Like the GPU arm, the timed Newton steps are taken at the iterate the
+    oracle itself reaches after ORACLE_SAMPLE_ITERATE interior-point
+    iterations, from the delta_w it ended with."""
+
+    def __init__(self, n_ctg=ORACLE_SAMPLE_CTG, iterate_at=ORACLE_SAMPLE_ITERATE, idx=CONFIG_IDX):
+        import numpy as np
+        import synthgrid
+        from dataclasses import replace
+        from oracle.linsolve import SparseLDLSolver
+        from oracle.ncl import NCLSolver, Options
+        from oracle.scopf_model import SCOPFModel
+        from oracle import symbolic
+        inst = synthgrid.config_instance(idx)
+        self.net_name = f"{inst.net.n_bus}-bus"
+        self.full_blocks = inst.K + 1
+        inst.ctgs = inst.ctgs[:n_ctg]
+        self.blocks = n_ctg + 1
+        with one_blas_thread():   # BLAS on one thread; the C LDL^T is single-threaded
+            t0 = time.perf_counter()
+            M = SCOPFModel(inst)
+            perm, _ = symbolic.kkt_permutation(M)
+            S = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm),
+                          replace(Options(), max_inner=iterate_at))
+            r = S.solve()
+            self.setup_s = time.perf_counter() - t0
+        self.M, self.S, self.np = M, S, np
+        self.st, self.prm, self.mu = r.state, r.params, r.mu
+        self.dw_last = next((h["delta_w"] for h in reversed(r.history) if h["delta_w"] > 0), 0.0)
+        self.iterate = (f"oracle iterate after {r.inner_iters} IPM iterations (mu {r.mu:.1e}, "
+                        f"rho {r.params.rho:.0e})")
+        self.tries = []
+
+    def step(self):
+        """One oracle Newton step (model, KKT, LDL^T with inertia correction,
+        solve, recovery, fraction to boundary, one trial evaluation);
+        returns its wall time."""
+        S, st, prm, mu = self.S, self.st, self.prm, self.mu
+        with one_blas_thread():
             t0 = time.perf_counter()
             res = S.residuals(st, prm)
-            H = M.hessian(st.w, st.lam)
-            sol, delta, tries, _, _ = S.newton_direction(st, prm, res, mu, H, 0.0)
+            H = self.M.hessian(st.w, st.lam)
+            sol, delta, tries, _, _ = S.newton_direction(st, prm, res, mu, H, self.dw_last)
             d = S.recover(st, prm, res, mu, sol)
-            ap, az = S.frac_to_boundary(st, d, 0.99)
+            ap, az = S.frac_to_boundary(st, d, max(0.99, 1 - mu))
             trial = S.step(st, d, ap, az)
-            S.theta(trial, M.constraints(trial.w))
-            times.append(time.perf_counter() - t0)
-    t = min(times)
-    per_full = t * full_blocks / (n_ctg_sample + 1)
-    desc = (f"oracle Newton step (numpy/scipy + C LDL^T, 1 thread) on the 500-bus network with "
-            f"{n_ctg_sample} of 256 contingencies ({n_ctg_sample + 1} blocks, {t:.2f} s), "
-            f"scaled by blocks to {full_blocks}")
-    return per_full, desc, 1
+            S.theta(trial, self.M.constraints(trial.w))
+            dt = time.perf_counter() - t0
+        self.tries.append(tries)
+        return dt
+
+    def describe(self, n_steps, sec):
+        return (f"oracle Newton step (numpy/scipy + C LDL^T, 1 thread) on the {self.net_name} "
+                f"network with {self.blocks - 1} of {self.full_blocks - 1} contingencies ({self.blocks} of "
+                f"{self.full_blocks} blocks), {self.iterate}; {n_steps} steps timed, "
+                f"{sec / n_steps:.3f} s each, {np_mean(self.tries):.1f} factorizations per "
+                f"step; full-size rate extrapolated linearly in blocks "
+                f"(x {self.full_blocks / self.blocks:.1f})")
+
+
+def np_mean(v):
+    return sum(v) / len(v) if v else 0.0
+
+
+def oracle_step_sample(n_steps: int = 3, idx: int = CONFIG_IDX):
+    """The cpu_baseline leg: n_steps oracle Newton steps of the bounded
+    sample; returns (seconds per full-size step extrapolated in blocks,
+    description, cores)."""
+    o = OracleSample(idx=idx)
+    t = sum(o.step() for _ in range(n_steps))
+    return t / n_steps * o.full_blocks / o.blocks, o.describe(n_steps, t), 1
 
 
 def run_reference(args):
+    """The reference arm: the CPU oracle, as it stands, times --steps Newton
+    steps (after --warmup untimed ones) of its bounded sample.  ms_per_step
+    is the measured time of one sampled step; value is the full-size rate,
+    extrapolated linearly in contingency blocks (the step's work is per
+    block)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
-    per_full, desc, cores = oracle_step_sample()
-    # the oracle arm repeats its bounded sample once per step
+    o = OracleSample()
+    for _ in range(args.warmup):
+        o.step()
+    o.tries.clear()
     t0 = time.perf_counter()
-    value = 1.0 / per_full
+    for _ in range(args.steps):
+        o.step()
+    sec = time.perf_counter() - t0
+    ms_sample = 1e3 * sec / args.steps
+    value = 1e3 / (ms_sample * o.full_blocks / o.blocks)
     line = {"metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * per_full,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_sample,
+            "value_basis": (f"ms_per_step is one step of the {o.blocks}-block sample as timed; "
+                            f"value = 1000 / (ms_per_step x {o.full_blocks}/{o.blocks}), the "
+                            f"full-size rate extrapolated linearly in blocks"),
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "impl": "reference",
             "config": {"workload": "syn500_k256: 500-bus, 90-generator synthetic grid, 256 "
-                                   "contingencies (220 line, 36 generator)", "flush_l2": False},
-            "cpu_baseline": {"value": value, "unit": "Newton steps/s", "cores": cores,
-                             "kind": "oracle", "sample": desc},
+                                   "contingencies (220 line, 36 generator)",
+                       "sample_blocks": o.blocks, "full_blocks": o.full_blocks,
+                       "setup_s": o.setup_s, "flush_l2": False},
+            "cpu_baseline": {"value": value, "unit": "Newton steps/s", "cores": 1,
+                             "kind": "oracle", "sample": o.describe(args.steps, sec)},
             "e2e": {"value": value, "unit": "Newton steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -233,27 +297,83 @@ def dominant_phase(phases, solves):
     return max(PHASE_KEYS, key=lambda k: tot[k])
 
 
-def roofline(sz, phases, dom):
-    """Roofline object of the dominant phase (factor: FP32 ALU; solve: HBM)."""
-    peaks, peak_kind = measured_peaks()
-    fac_ms, fac_calls = phases["factor"]
-    sol_ms, sol_calls = phases["solve"]
-    if dom == "factor":
-        achieved = sz.factor_flops / (fac_ms / fac_calls / 1e3) / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
-                "kernel": "k_factor<float> (persistent supernodal LDL^T, all blocks)",
-                "peak_kind": "derived: 148 SMs x 128 FP32 lanes x 2 x 2.032 GHz"}
+def live_peaks():
+    """FP32 FMA, FP64 FMA and FP64 tensor-MMA throughput measured now with
+    the library's own probe kernels (TFLOP/s, best of 5 launches)."""
+    import paper_2510_13333_b300 as P
+    return {name: P.scopf_peak_probe(k) for k, name in P.PEAK_KINDS.items()}
+
+
+def phase_work(sz, prec_bytes):
+    """Algorithmic work of one call of each timed phase: (amount, unit, what).
+    Bytes are the data the method must move once per call; flops count an
+    FMA as 2."""
+    N, nnz, nnzL = sz.n_kkt, sz.nnz_kkt, sz.nnz_L
+    nc, nblk = sz.n_border, sz.n_blocks
+    b = prec_bytes
+    return {
+        "assemble": (8 * sz.n_elem_values + 24 * sz.n_contrib + 16 * nnz + 48 * N, "B",
+                     "element values written, (slot, coefficient, value) per contribution, "
+                     "pointer + value per stored entry, iterate and right-hand-side vectors"),
+        "front_init": (3 * 20 * nnz + 24 * nnz, "B",
+                       "3 Ruiz sweeps over (value, column, row) per stored entry, then each "
+                       "front original's value, offset, scales and write"),
+        "factor": (sz.factor_flops, "flop", "sum over pivots of (f-c-1)(f-c) on the fronts"),
+        "schur": (nblk * nc * nc * b + 8 * nc * nc, "B",
+                  "every block's border front read once, S written (the n_c^3/3 dense factor "
+                  "is negligible)"),
+        "solve": (2 * b * nnzL + 16 * N, "B", "factor entries read by both sweeps, plus the "
+                  "right-hand side in and the solution out (SURVEY 8(d) a6)"),
+        "residual": (16 * nnz + 24 * N, "B", "value + column per stored entry, x, b, r"),
+    }
+
+
+def phase_rooflines(sz, phases, solves, prec_bytes, peaks_live):
+    """Achieved fraction of each phase's roof.  Per call: the phase's CUDA-
+    event time over its calls; the solve phase's timers see only the first
+    block solve of each kkt solve, so its per-call time is the timed solves'
+    mean."""
+    peaks, kind = measured_peaks()
+    hbm = peaks["hbm_gbs"]
+    work = phase_work(sz, prec_bytes)
+    out = {}
+    for k, (amount, unit, what) in work.items():
+        ms, calls = phases.get(k, (0.0, 0))
+        if not calls or ms <= 0:
+            continue
+        per_call_s = ms / calls / 1e3
+        if unit == "flop":
+            key = "fp32_fma" if prec_bytes == 4 else "fp64_fma"
+            derived = FP32_PEAK_TFLOPS if prec_bytes == 4 else FP64_PEAK_TFLOPS
+            ach = amount / per_call_s / 1e12
+            out[k] = {"bound": "alu", "achieved": ach, "unit": "TFLOP/s", "peak": derived,
+                      "frac": ach / derived, "peak_probe": peaks_live.get(key),
+                      "frac_of_probe": ach / peaks_live[key] if peaks_live.get(key) else None,
+                      "per_call": amount, "ms_per_call": per_call_s * 1e3, "calls": calls,
+                      "work": what}
+        else:
+            ach = amount / per_call_s / 1e9
+            out[k] = {"bound": "hbm", "achieved": ach, "unit": "GB/s", "peak": hbm,
+                      "peak_kind": kind, "frac": ach / hbm, "per_call": amount,
+                      "ms_per_call": per_call_s * 1e3, "calls": calls, "work": what}
+    return out
+
+
+def roofline(sz, phases, dom, prec_bytes=4, peaks_live=None):
+    """Roofline object of the dominant phase (factor: ALU; else HBM)."""
+    ph = phase_rooflines(sz, phases, 0, prec_bytes, peaks_live or {})
+    r = dict(ph[dom])
+    r["phase"] = dom
+    if dom == "solve":
+        r["kernel"] = "k_solve_fwd + k_border_solve + k_solve_bwd (one solve)"
+        r["traffic"] = sweep_traffic()
+        r["algorithmic_bytes"] = r["per_call"]
+    elif dom == "factor":
+        r["kernel"] = "k_factor + k_factor_med + k_factor_big (block LDL^T, all blocks)"
+        r["traffic"] = None
     else:
-        # one solve = forward sweep + border solve + backward sweep: every FP32
-        # factor entry is read twice, plus D b in, x out and the scaling
-        bytes_ = 2 * 4 * sz.nnz_L + 3 * 8 * sz.n_kkt
-        achieved = bytes_ / (sol_ms / sol_calls / 1e3) / 1e9
-        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": sweep_traffic(),
-                "kernel": "k_solve_fwd + k_border_solve + k_solve_bwd <float> (one solve)",
-                "algorithmic_bytes": bytes_, "peak_kind": peak_kind}
-    return roof
+        r["traffic"] = None
+    return r
 
 
 # -------------------------------------------------------------------- our arm
@@ -271,11 +391,16 @@ def run_ours(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    inst = synthgrid.config_instance(CONFIG_IDX)
+    idx = SCALE_IDX if args.workload == "scale" else CONFIG_IDX
+    inst = synthgrid.config_instance(idx)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     t0 = time.perf_counter()
     loop = {"device_loop": 0} if args.host_loop else {}
     lib = P.SCOPF(inst, precision=P.PREC_MIXED, **loop)
     t_create = time.perf_counter() - t0
+    torch.cuda.synchronize()
+    handle_bytes = free0 - torch.cuda.mem_get_info()[0]
     sz = lib.sizes
     # ---- time to solution (full NCL solve from the flat start)
     tts = {}
@@ -337,6 +462,7 @@ def run_ours(args):
         ms = max_over_ranks(e0.elapsed_time(e1), dist, "cuda")
         return ms, phases
 
+    peaks_live = live_peaks()
     clocks = Clocks()
     clocks.start()
     ms_mixed, ph_mixed = timed(lib, args.steps, clocks.mark)
@@ -417,22 +543,22 @@ def run_ours(args):
     fp64_value = job_rate(fp64_steps, world, ms_fp64)
     # roofline of the dominant phase (from CUDA events on the handle's stream)
     dom = dominant_phase(ph_mixed, apps_mixed * K)
-    roof = roofline(sz, ph_mixed, dom)
+    roof = roofline(sz, ph_mixed, dom, 4, peaks_live)
     try:
-        cpu_s, cpu_desc, cores = oracle_step_sample()
+        cpu_s, cpu_desc, cores = oracle_step_sample(idx=idx)
         cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
                "sample": cpu_desc}
     except Exception as exc:  # keep the GPU number even if the CPU sample fails
         cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                "sample": f"failed: {exc}"}
     line = {
-        "metric": METRIC, "value": value, "unit": "Newton steps/s", "n_gpus": world,
+        "metric": METRIC if idx == CONFIG_IDX else
+        "Newton steps/s and SCOPF time-to-solution at 2000-bus×128-ctg (1e-6), vs plain FP64 GPU",
+        "value": value, "unit": "Newton steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_mixed / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 block factors + f64 (model, Schur, refinement)", "data": "synthetic",
-        "config": {"workload": "syn500_k256: 500-bus, 90-generator synthetic grid (mean degree "
-                               "2.8), 256 contingencies (220 line, 36 generator), random PV/PQ "
-                               "switch sets; seeded, screened",
+        "config": {"workload": WORKLOADS[idx],
                    "n_kkt": sz.n_kkt, "nnz_kkt": sz.nnz_kkt, "nnz_L": sz.nnz_L,
                    "blocks": sz.n_blocks, "border": sz.n_border,
                    "iterate": f"state after {args.iterate_at} IPM iterations (mu {mu:.1e}, "
@@ -443,10 +569,17 @@ def run_ours(args):
         "speedup_mixed_vs_fp64": value / fp64_value,
         "time_to_solution": tts,
         "create_s": t_create,
+        "memory": {"device_bytes_handle": handle_bytes, "front_bytes": sz.front_bytes,
+                   "bytes_per_block": handle_bytes / sz.n_blocks,
+                   "note": "device memory the handle holds (free-memory difference around "
+                           "scopf_create: model, KKT pattern and values, fronts, work vectors)"},
         "phases_ms_per_step": {k: v[0] / K for k, v in ph_mixed.items()},
         "block_solves_per_step": apps_mixed,
         "phases_ms_per_step_fp64": {k: v[0] / fp64_steps for k, v in ph_fp64.items()},
         "roofline": roof,
+        "roofline_phases": phase_rooflines(sz, ph_mixed, 0, 4, peaks_live),
+        "roofline_phases_fp64": phase_rooflines(sz, ph_fp64, 0, 8, peaks_live),
+        "peaks_probe_tflops": peaks_live,
         "cpu_baseline": cpu,
         "e2e": {"value": job_rate(K, world, ms_e2e), "unit": "Newton steps/s",
                 "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -556,7 +689,7 @@ def run_screen(args):
                    "base_accepted": bool(acc[0]),
                    "agree_with_stored_u0pm1e-3_verdicts": int(np.sum(acc[1:] == stored))},
         "phases_ms_per_step": {k: v[0] / steps for k, v in phases.items()},
-        "roofline": roofline(sz, phases, dom),
+        "roofline": roofline(sz, phases, dom, 4, live_peaks()),
         "cpu_baseline": cpu,
         "e2e": {"value": n_ctg * steps / wall, "unit": "contingencies/s",
                 "h2d_bytes_per_step": 8 * sz.n_border,
@@ -639,12 +772,24 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven refinement loop (every kernel launched from the host, "
                          "for profilers that attribute launches to NVTX ranges)")
-    ap.add_argument("--workload", default="newton", choices=["newton", "screen", "illcond"],
-                    help="newton: the Newton step (default); screen: batched screening; "
-                         "illcond: NCL solves with narrowed reactive bands")
+    ap.add_argument("--workload", default="newton",
+                    choices=["newton", "scale", "screen", "illcond", "peaks"],
+                    help="newton: the Newton step (default); scale: the same on the 2000-bus "
+                         "x 128 scale-up workload, with its memory footprint; screen: batched "
+                         "screening; illcond: NCL solves with narrowed reactive bands; peaks: "
+                         "the arithmetic probes")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
+    if args.workload == "peaks":
+        if args.impl != "reference" and int(os.environ.get("RANK", "0")) == 0:
+            import torch
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            print(json.dumps({"metric": "arithmetic throughput of the library's probe kernels",
+                              "unit": "TFLOP/s", "peaks": live_peaks(),
+                              "derived": {"fp32_fma": FP32_PEAK_TFLOPS,
+                                          "fp64_nominal": FP64_PEAK_TFLOPS}}), flush=True)
+        return
     if args.workload == "illcond":
         if args.impl != "reference":
             run_illcond(args)
@@ -668,7 +813,7 @@ def main():
     if args.impl == "reference":
         run_reference(args)
     else:
-        run_ours(args)
+        run_ours(args)   # newton (500-bus x 256) or scale (2000-bus x 128)
 
 
 if __name__ == "__main__":

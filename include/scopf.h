@@ -147,6 +147,8 @@ typedef struct {
     int64_t n_supernodes;
     double factor_flops;      /* flops of one block factorisation (all blocks) */
     int64_t front_bytes;      /* device bytes of the frontal storage */
+    int64_t n_elem_values;    /* model-evaluation value slots written per assembly */
+    int64_t n_contrib;        /* (slot, coefficient) contributions gathered into K */
 } scopf_sizes;
 
 /* Primal-dual iterate (device pointers, FP64).  zl and zu have length n and
@@ -304,6 +306,17 @@ int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *
  * scopf_dense_ldlt_solve (check inertia[2]). */
 int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, double *x,
                                    int32_t inertia[3], void *stream);
+
+/* Arithmetic-throughput probe (measurement support for the roofline
+ * fractions; the paper has no counterpart).  Launches one kernel on stream
+ * (a cudaStream_t or NULL) that keeps every SM busy with independent chains
+ * of kind 0: FP32 FMA, 1: FP64 FMA, 2: FP64 tensor MMA (mma.sync m8n8k4),
+ * iters iterations each, and returns the launch's flop count in *flops (host,
+ * an FMA counted as 2).  out: device, at least 8 bytes, written only in a
+ * case that never occurs (it keeps the chains from being optimised away).
+ * The caller times the launch (CUDA events on the same stream).  Does not
+ * synchronise. */
+int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *stream, double *flops);
 
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */

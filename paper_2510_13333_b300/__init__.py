@@ -72,7 +72,8 @@ class Options(ctypes.Structure):
 class Sizes(ctypes.Structure):
     _fields_ = [("n", c_i64), ("m", c_i64), ("p", c_i64), ("n_kkt", c_i64), ("n_border", c_i64),
                 ("n_blocks", c_i32), ("nnz_kkt", c_i64), ("nnz_L", c_i64),
-                ("n_supernodes", c_i64), ("factor_flops", c_dbl), ("front_bytes", c_i64)]
+                ("n_supernodes", c_i64), ("factor_flops", c_dbl), ("front_bytes", c_i64),
+                ("n_elem_values", c_i64), ("n_contrib", c_i64)]
 
 
 _STATE_FIELDS = ["w", "r", "t", "s", "lam", "yc", "zl", "zu", "zs"]
@@ -158,6 +159,7 @@ def lib():
             "scopf_dense_ldlt_solve": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32, ctypes.c_void_p]),
             "scopf_dense_ldlt_solve_noalloc": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32,
                                                        ctypes.c_void_p]),
+            "scopf_peak_probe": (c_i32, [c_i32, c_i64, P_dbl, ctypes.c_void_p, P_dbl]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -208,6 +210,32 @@ def scopf_dense_ldlt_solve_noalloc(S, b, x=None):
         _dp(S), n, _dp(b), _dp(x), _hp(inert, c_i32),
         ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
     return x, tuple(int(v) for v in inert), st
+
+
+PEAK_KINDS = {0: "fp32_fma", 1: "fp64_fma", 2: "fp64_mma"}
+
+
+def scopf_peak_probe(kind: int, iters: int = 1 << 14, repeats: int = 5):
+    """Measured arithmetic throughput (TFLOP/s) of one probe kind (0 FP32
+    FMA, 1 FP64 FMA, 2 FP64 tensor MMA): the best of `repeats` launches,
+    each timed with CUDA events on the current stream after one warm-up."""
+    import torch
+    s = torch.cuda.current_stream()
+    out = torch.zeros(1, dtype=torch.float64, device="cuda")
+    fl = c_dbl()
+    best = None
+    for r in range(repeats + 1):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        _check("scopf_peak_probe", lib().scopf_peak_probe(kind, iters, _dp(out),
+                                                          ctypes.c_void_p(s.cuda_stream),
+                                                          ctypes.byref(fl)))
+        e1.record(s)
+        torch.cuda.synchronize()
+        if r:
+            t = fl.value / (e0.elapsed_time(e1) / 1e3) / 1e12
+            best = t if best is None else max(best, t)
+    return best
 
 
 def default_options(**kw) -> Options:

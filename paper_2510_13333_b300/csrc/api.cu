@@ -513,6 +513,8 @@ int scopf_get_sizes(scopf_handle *h, scopf_sizes *o) {
     o->n_supernodes = h->HF.n_tasks - h->HF.n_blocks;
     o->factor_flops = h->HF.flops;
     o->front_bytes = h->HF.front_elems * 8;
+    o->n_elem_values = h->M.n_ev;
+    o->n_contrib = (int64_t)h->M.ctr.size();
     return SCOPF_OK;
 }
 

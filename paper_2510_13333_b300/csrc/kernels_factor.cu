@@ -1449,18 +1449,6 @@ __global__ void k_fill(int64_t n, double v, double *x) {
     if (i < n) x[i] = v;
 }
 
-// SMs of the current device (cached per device ordinal)
-int sm_count() {
-    static int cache[64] = {};
-    int dev = 0, sms = 0;
-    cudaGetDevice(&dev);
-    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-    if (dev >= 0 && dev < 64) cache[dev] = sms;
-    return sms;
-}
-
 int warp_grid() { return sm_count() * (2048 / kWT); }
 
 }  // namespace
@@ -1500,6 +1488,18 @@ void launch_queue_reset(const DevFront &F, QueueSeeds seeds, const int32_t *pend
     const int n = F.n_items > 0 ? F.n_items : 1;
     note_launch(), k_queue_reset<<<(n + t - 1) / t, t, 0, s>>>(F.n_items, F.q_slots_a, F.q_slots_b, F.q_slots_c,
                                                 seeds, F.q_pending, pend, F.q_ctr);
+}
+
+// SMs of the current device (cached per device ordinal)
+int sm_count() {
+    static int cache[64] = {};
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (dev >= 0 && dev < 64 && cache[dev]) return cache[dev];
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
 }
 
 // Function attributes and occupancy are per device: the launch caches below

@@ -1,0 +1,78 @@
+// Arithmetic-throughput probes for the roofline denominators of the block
+// factorization and the dense border factor: FP32 FFMA and FP64 DFMA
+// (independent dependent-FMA chains per thread, enough of them to cover the
+// pipelines' latency) and FP64 tensor MMA (mma.sync m8n8k4, several
+// independent accumulators per warp).  The caller times one launch with CUDA
+// events on the stream it passes; the entry point returns the launch's flop
+// count.  Not part of the paper's method: measurement support only.
+#include <cuda_runtime.h>
+
+#include "../../include/scopf.h"
+#include "kernels.h"
+
+namespace {
+
+constexpr int kPT = 256;     // threads per CTA
+constexpr int kChains = 8;   // independent FMA chains per thread
+constexpr int kAcc = 4;      // independent MMA accumulators per warp
+
+template <typename T>
+__global__ void __launch_bounds__(kPT) k_fma_chains(int64_t iters, T *__restrict__ out) {
+    T a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) a[j] = (T)(threadIdx.x + j) * (T)1e-3;
+    const T b = (T)0.999999, c = (T)1e-6;
+    for (int64_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < kChains; j++) a[j] = fma(a[j], b, c);
+    }
+    T s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) s += a[j];
+    if (s == (T)-1.2345) out[0] = s;   // never true: keeps the chains live
+}
+
+__global__ void __launch_bounds__(kPT) k_dmma_chains(int64_t iters, double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const double a = 1e-3 * (lane + 1), b = 1e-3 * (32 - lane);
+    double d[kAcc][2];
+#pragma unroll
+    for (int j = 0; j < kAcc; j++) d[j][0] = d[j][1] = 0.0;
+    for (int64_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < kAcc; j++)
+            asm volatile(
+                "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                : "+d"(d[j][0]), "+d"(d[j][1])
+                : "d"(a), "d"(b));
+    }
+    double s = 0;
+#pragma unroll
+    for (int j = 0; j < kAcc; j++) s += d[j][0] + d[j][1];
+    if (s == -1.2345) out[0] = s;
+}
+
+}  // namespace
+
+extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *stream,
+                                double *flops) {
+    using namespace scopf;
+    if (!out || iters <= 0 || kind < 0 || kind > 2) return SCOPF_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int grid = sm_count() * (2048 / kPT);
+    const double threads = (double)grid * kPT;
+    double f = 0;
+    if (kind == 0) {
+        note_launch(), k_fma_chains<float><<<grid, kPT, 0, s>>>(iters, reinterpret_cast<float *>(out));
+        f = threads * kChains * 2.0 * (double)iters;
+    } else if (kind == 1) {
+        note_launch(), k_fma_chains<double><<<grid, kPT, 0, s>>>(iters, out);
+        f = threads * kChains * 2.0 * (double)iters;
+    } else {
+        note_launch(), k_dmma_chains<<<grid, kPT, 0, s>>>(iters, out);
+        f = threads / 32.0 * kAcc * (8.0 * 8.0 * 4.0 * 2.0) * (double)iters;
+    }
+    if (cudaGetLastError() != cudaSuccess) return SCOPF_ERR_CUDA;
+    if (flops) *flops = f;
+    return SCOPF_OK;
+}

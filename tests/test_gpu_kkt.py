@@ -53,12 +53,16 @@ def test_kkt_assembly_matches_oracle(cuda, which):
             "cfg1": lambda: H.instance(1)}[which]()
     M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 11, rho=1e3, delta_w=0.3)
     K_lib = H.library_matrix(lib, lib.kkt_values(), gen)
-    H.assert_kkt_close(K_lib, K_or, rtol=1e-12, row_atol=1e-15)
+    # per entry: 1e-12 relative plus 1e-14 x the sum of |terms| the entry adds
+    # up (FP64 rounding of a sum in another order), so cancelling sums are
+    # not held to a bound below their rounding and small entries are checked
+    # on their own scale
+    H.assert_kkt_terms_close(K_lib, K_or, H.kkt_magnitude(S, st, prm, 0.3))
     # same stored pattern (no entry of one missing from the other)
     assert K_lib.nnz >= K_or.count_nonzero()
     r = np.empty_like(rhs_or)
     r[gen] = rhs.cpu().numpy()
-    H.assert_entries_close("rhs", r, rhs_or, 1e-11, 1e-14 * H.group_scale(M, rhs_or))
+    H.assert_entries_close("rhs", r, rhs_or, 1e-12, 1e-14 * H.rhs_magnitude(S, st, prm, 1e-2))
 
 
 @pytest.mark.parametrize("which,prec", [("small", 0), ("cfg0", 0), ("cfg0", 1), ("cfg1", 0),

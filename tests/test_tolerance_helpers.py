@@ -47,3 +47,38 @@ def test_vector_check_catches_small_block(kkt):
     assert np.abs(y - x).max() <= 1e-8 * np.abs(x).max()
     with pytest.raises(AssertionError):
         H.assert_entries_close("x", y, x, 1e-8, 1e-8 * H.group_scale(M, x))
+
+
+def test_term_magnitude_bounds_entries(kkt):
+    """sum |terms| >= |entry| for every stored KKT entry (triangle
+    inequality), on the same pattern; and the term-scaled check still
+    catches a planted error in an entry that is a single term."""
+    M, K = kkt
+    S = NCLSolver(M, DenseSolver())
+    st = H.random_interior_state(S, 4)
+    prm = Params(rho=1e6, lam_n=np.zeros(M.m), nu0_n=np.zeros(M.p))
+    Kmag = H.kkt_magnitude(S, st, prm, 0.0)
+    Kc = K.tocoo()
+    mag = np.asarray(Kmag[Kc.row, Kc.col]).ravel()
+    assert np.all(mag >= np.abs(Kc.data) * (1 - 1e-12))
+    # entries with cancellation exist (the magnitude is far above the value)
+    assert np.any(mag > 1e3 * np.abs(Kc.data) + 1e-300)
+    H.assert_kkt_terms_close(K.copy(), K, Kmag)
+    i = M.n
+    bad = K.tolil()
+    bad[i, i] = K[i, i] * (1 + 1e-9)
+    with pytest.raises(AssertionError):
+        H.assert_kkt_terms_close(bad.tocsr(), K, Kmag)
+
+
+def test_rhs_magnitude_bounds_entries(kkt):
+    M, _ = kkt
+    S = NCLSolver(M, DenseSolver())
+    st = H.random_interior_state(S, 4)
+    prm = Params(rho=1e3, lam_n=np.zeros(M.m) + 0.1, nu0_n=np.zeros(M.p) + 0.1)
+    res = S.residuals(st, prm)
+    mu = 1e-2
+    r = S.reduced_rhs(st, prm, res, mu)
+    mag = H.rhs_magnitude(S, st, prm, mu)
+    assert mag.shape == r.shape
+    assert np.all(mag >= np.abs(r) * (1 - 1e-12))
