@@ -271,10 +271,14 @@ int setup_device(scopf_handle *h) {
         }
         // the large-front kernel stages np x f panels up to 96 KB (FP64)
         F.big_panel = 1;
+        F.big_np = 1;
         const int t3 = HF.n_items > HF.n_items_med ? HF.item_ptr[HF.n_items_med] : HF.n_tasks;
         for (int t = t3; t < HF.n_tasks; t++) {
             const int64_t pe = (int64_t)HF.f[t] * HF.npiv[t];
-            if (pe <= 12288) F.big_panel = std::max<int>(F.big_panel, (int)pe);
+            if (pe <= 12288) {
+                F.big_panel = std::max<int>(F.big_panel, (int)pe);
+                F.big_np = std::max<int>(F.big_np, (int)HF.npiv[t]);
+            }
         }
         F.n_items_small = HF.n_items_small;
         F.n_items_med = HF.n_items_med;
@@ -823,11 +827,14 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     h->timer.end(PH_FACTOR, s);
     h->timer.begin(PH_SCHUR, s);
     launch_schur_sum<T>(h->df, fr, h->S, s);
-    launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s);
+    CK(launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s,
+                         h->opt.spin_limit));
     // FP32 block factors: the border block is applied through S^-1 (a mat-vec
     // per solve instead of two sequential triangular solves); the refinement
-    // corrects its rounding like that of the block factors
-    if (sizeof(T) == 4) launch_dense_inverse(h->S, (int)h->M.nborder, h->Sinv, s);
+    // corrects its rounding like that of the block factors.  S^-1 is formed
+    // by the first solve with these factors, so factorizations rejected by
+    // the inertia correction never pay for it.
+    h->sinv_stale = sizeof(T) == 4;
     h->timer.end(PH_SCHUR, s);
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
@@ -952,6 +959,12 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
     auto once = [&](const double *rhs, double *out) {
         return mixed ? solve_once<float>(h, rhs, out) : solve_once<double>(h, rhs, out);
     };
+    if (mixed && h->sinv_stale) {   // before any solve (or graph) uses it
+        h->timer.begin(PH_SCHUR, s);
+        launch_dense_inverse(h->S, (int)h->M.nborder, h->Sinv, s);
+        h->timer.end(PH_SCHUR, s);
+        h->sinv_stale = false;
+    }
     constexpr int m = 16;
     const GmresLayout GL = gmres_layout(m);
     if (!h->kv) {

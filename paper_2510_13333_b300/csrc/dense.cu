@@ -30,12 +30,13 @@ __global__ void __launch_bounds__(kDT) k_dense_rhs_solve(const double *__restric
 int dense_factor_solve(double *F, int n, const double *b, double *x, double *y, FactorStatus *st,
                        int32_t inertia[3], cudaStream_t s) {
     cudaMemsetAsync(st, 0, sizeof(FactorStatus), s);
-    launch_dense_ldlt(F, n, st, 0.0, s);
+    if (launch_dense_ldlt(F, n, st, 0.0, s) != cudaSuccess) return SCOPF_ERR_CUDA;
     note_launch(), k_dense_rhs_solve<<<1, kDT, 0, s>>>(F, n, b, x, y);
     FactorStatus fs;
     cudaMemcpyAsync(&fs, st, sizeof(fs), cudaMemcpyDeviceToHost, s);
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return SCOPF_ERR_CUDA;
+    if (fs.error) return SCOPF_ERR_TIMEOUT;
     if (inertia) {
         inertia[0] = fs.n_pos;
         inertia[1] = fs.n_neg;

@@ -8,11 +8,14 @@
 
 namespace scopf {
 
+// first: y is zero above this row on entry (the forward sweep starts at its
+// 32-row block)
 template <int NT>
-__device__ void block_ldlt_solve(const double *__restrict__ S, int n, double *__restrict__ y) {
+__device__ void block_ldlt_solve(const double *__restrict__ S, int n, double *__restrict__ y,
+                                 int first = 0) {
     __shared__ double blk[32][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = NT >> 5;
-    for (int b0 = 0; b0 < n; b0 += 32) {
+    for (int b0 = (first / 32) * 32; b0 < n; b0 += 32) {
         const int bs = n - b0 < 32 ? n - b0 : 32;
         for (int t = tid; t < 32 * 32; t += NT) {
             const int c = t >> 5, r = t & 31;

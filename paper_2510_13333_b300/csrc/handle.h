@@ -120,6 +120,7 @@ struct scopf_handle {
     void *fronts = nullptr, *vec = nullptr;
     double *S = nullptr, *border_work = nullptr;
     double *Sinv = nullptr;                           // S^-1 (mixed-precision solves)
+    bool sinv_stale = false;   // S was refactored since Sinv was formed (formed on first solve)
     double *scale = nullptr, *scale_tmp = nullptr;   // Ruiz equilibration of K
     unsigned long long *ruiz_mx = nullptr;          // per-row maxima of a Ruiz sweep (zeros)
     double *kv = nullptr, *kz = nullptr, *kpart = nullptr;  // FGMRES basis and scratch

@@ -190,6 +190,7 @@ struct DevFront {
     int n_items, n_items_small, n_items_med;
     int max_f;                    // largest front (rows), at least 32
     int big_panel;                // largest np x f of the large-front phase (elements, capped)
+    int big_np;                   // largest np among those staged panels
     // packed records, 8 int32 each.  task_rec[t] (t <= n_tasks, the last a
     // sentinel): front_off (2 words), vec_off (2), f | npiv << 16,
     // first child slot, first original entry, parent.  child_rec[q] for
@@ -218,7 +219,9 @@ struct DevFront {
 void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s);
 
 struct FactorStatus {             // device-side counters
-    int n_pos, n_neg, n_zero, error, timeout_task, pad[3];
+    int n_pos, n_neg, n_zero, error, timeout_task;
+    unsigned bar_count, bar_gen;     // grid barrier of the dense border factor
+    int pad;
 };
 
 // Symmetric Ruiz equilibration of K (scale[i] > 0, `iters` sweeps).
@@ -231,7 +234,8 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
                    int spin_limit, cudaStream_t s);
 template <typename T>
 void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s);
-void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s);
+cudaError_t launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol,
+                              cudaStream_t s, int spin_limit = 1 << 22);
 // Sinv = S^-1 from the LDL^T factors in S (one triangular solve pair per column)
 void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s);
 

@@ -319,10 +319,11 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
 // u L0 - u (u - 1) / 2, L0 = f - c - 1) and dealt to the lanes 32 at a time,
 // so every issued FP64 multiply-add updates an entry (the row-per-lane form
 // idles the lanes above each column's diagonal).  Column c holds l = L[., c]
-// (already divided by d); the update is M[i][j] -= l_i (l_j d).
+// (already divided by d) and row c of the unused upper triangle holds
+// l_j d for the panel columns (one multiply per column, not per entry); the
+// update is M[i][j] -= l_i (l_j d).
 template <typename T, int S>
-__device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, int c, T d,
-                                                    int lane) {
+__device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, int c, int lane) {
     const int j0 = c + 1, ncol = np - j0, L0 = f - j0;
     if (ncol <= 0) return;
     const int total = ncol * L0 - ncol * (ncol - 1) / 2;
@@ -335,7 +336,7 @@ __device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, in
         while (u + 1 < ncol && (u + 1) * L0 - (u + 1) * u / 2 <= e) u++;
         const int j = j0 + u;
         const int i = j + (e - (u * L0 - u * (u - 1) / 2));
-        M[i][j] -= M[i][c] * (M[j][c] * d);
+        M[i][j] -= M[i][c] * M[c][j];
     }
 }
 
@@ -437,7 +438,9 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         if (sizeof(T) == 8) {
             if (lane > c && lane < f) tile[lane][c] *= dinv;
             __syncwarp();
-            panel_update_packed<T, 33>(tile, f, np, c, d, lane);
+            if (lane > c && lane < np) tile[c][lane] = tile[lane][c] * d;
+            __syncwarp();
+            panel_update_packed<T, 33>(tile, f, np, c, lane);
             __syncwarp();
             continue;
         }
@@ -526,8 +529,11 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
             // above the diagonal (one or two chunks of 32 per column)
             for (int i = c + 1 + lane; i < f; i += 32) M[i][c] *= dinv;
             __syncwarp();
+            // l_j d once per panel column, kept in the unused upper triangle
+            for (int j = c + 1 + lane; j < np; j += 32) M[c][j] = M[j][c] * d;
+            __syncwarp();
             for (int j = c + 1; j < np; j++) {   // panel columns only
-                const T lj = M[j][c] * d;
+                const T lj = M[c][j];
                 for (int i = j + lane; i < f; i += 32) M[i][j] -= M[i][c] * lj;
             }
             __syncwarp();
@@ -640,10 +646,18 @@ constexpr int kBT = 256;
 // row chunks of 32 per column in one extend-add / trailing-update pass
 template <typename T>
 __host__ __device__ constexpr int big_chunks() { return sizeof(T) == 4 ? 4 : 2; }
-// byte offset of the staged child->parent map behind the shared panel
+// Shared memory of the large-front kernel: the np x f panel, then per warp
+// the products l_j d of its current pair of update columns (2 x big_np), then
+// the staged child->parent map of one child.
 template <typename T>
-__host__ __device__ constexpr size_t big_rel_offset(int big_panel) {
+__host__ __device__ constexpr size_t big_w_offset(int big_panel) {
     return (sizeof(T) * (size_t)(big_panel > 1 ? big_panel : 1) + 15) & ~(size_t)15;
+}
+template <typename T>
+__host__ __device__ constexpr size_t big_rel_offset(int big_panel, int big_np) {
+    return big_w_offset<T>(big_panel) +
+           ((sizeof(T) * (size_t)(kBT / 32) * 2 * (size_t)(big_np > 1 ? big_np : 1) + 15) &
+            ~(size_t)15);
 }
 
 // Large front: zero + originals and extend-add in global memory, then the
@@ -669,7 +683,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
     // memory, and each warp pass takes two columns with up to kEA row chunks
     // of 32 each, all their loads in flight before the adds (a child's
     // destinations are distinct; children are added one after another)
-    int *srel = reinterpret_cast<int *>(big_smem + big_rel_offset<T>(F.big_panel));
+    int *srel = reinterpret_cast<int *>(big_smem + big_rel_offset<T>(F.big_panel, F.big_np));
     for (int ci = ti.c0; ci < ti.c1; ci++) {
         const ChildInfo c = child_info(F, ci);
         const T *Fc = fronts + c.front_off;
@@ -733,11 +747,20 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
     }
     for (int e = tid; e < np * f; e += kBT) Fr[e] = P[e];
     // trailing update: two columns per warp pass, the pass's destination
-    // values loaded before the dot products (from the shared panel) run
+    // values loaded before the dot products (from the shared panel) run; the
+    // column factors l_j d_c are formed once per pass (not once per row)
+    T *wb = reinterpret_cast<T *>(big_smem + big_w_offset<T>(F.big_panel)) + warp * 2 * F.big_np;
     for (int j0 = np + 2 * warp; j0 < f; j0 += 2 * nw) {
         const int j1 = j0 + 1;
         T *col0 = Fr + (int64_t)j0 * f;
         T *col1 = col0 + f;
+        __syncwarp();
+        for (int c = lane; c < np; c += 32) {
+            const T dc = P[c * f + c];
+            wb[c] = P[c * f + j0] * dc;
+            wb[F.big_np + c] = j1 < f ? P[c * f + j1] * dc : (T)0;
+        }
+        __syncwarp();
         for (int r0 = 0; j0 + r0 < f; r0 += 32 * kEA) {
             T u[2][kEA];
 #pragma unroll
@@ -753,9 +776,8 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
                     T a0 = 0, a1 = 0;
                     for (int c = 0; c < np; c++) {
                         const T *pc = P + c * f;
-                        const T dc = pc[c];
-                        a0 += pc[i0] * (pc[j0] * dc);
-                        if (j1 < f && i1 < f) a1 += pc[i1] * (pc[j1] * dc);
+                        a0 += pc[i0] * wb[c];
+                        if (j1 < f && i1 < f) a1 += pc[i1] * wb[F.big_np + c];
                     }
                     col0[i0] = u[0][k] - a0;
                     if (j1 < f && i1 < f) col1[i1] = u[1][k] - a1;
@@ -834,74 +856,144 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
 }
 
 // ---- dense LDL^T of the border block (FP64, blocked right-looking) -------
-constexpr int kPanel = 32;
+// One cooperative launch of G co-resident CTAs.  Per panel of kDB columns:
+//  A. every CTA loads the kDB x kDB diagonal block and factors it in shared
+//     memory (tiny; CTA 0 counts the inertia and writes it back), so no
+//     barrier is needed before
+//  B. the rows below are solved for their L entries, L21 = A21 L11^-T D^-1,
+//     one row per thread over the whole grid;
+//  C. after a grid barrier, the trailing matrix takes the rank-kDB update
+//     A22 -= L21 D L21' in 32 x 32 tiles of its lower triangle, dealt to the
+//     CTAs; a second barrier ends the panel.
+// The grid barriers are bounded waits: a wait that runs out sets
+// st->error and every CTA then leaves without waiting again.
+constexpr int kDB = 16;     // panel width
+constexpr int kDT = 256;    // threads per CTA
 
-// Factor columns [k0, k1) of S in place (rows >= k0), counting inertia.  The
-// panel (n - k0 rows x pw columns) is staged in shared memory; panel columns
-// are updated by different warps in parallel.
-__global__ void k_dense_panel(double *S, int n, int k0, int k1, FactorStatus *st,
-                              double pivot_tol) {
-    extern __shared__ double P[];   // P[cl * R + il], R = n - k0
-    __shared__ int s_pos, s_neg, s_zero;
-    const int R = n - k0, pw = k1 - k0;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    if (threadIdx.x == 0) s_pos = s_neg = s_zero = 0;
-    for (int t = threadIdx.x; t < pw * R; t += blockDim.x) {
-        const int cl = t / R, il = t - cl * R;
-        P[t] = S[(int64_t)(k0 + cl) * n + k0 + il];
+__device__ __forceinline__ bool dense_grid_barrier(FactorStatus *st, int spin_limit) {
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile int *err = &st->error;
+        const int g = ld_acquire(reinterpret_cast<const int *>(&st->bar_gen));
+        __threadfence();
+        if (atomicAdd(&st->bar_count, 1u) == gridDim.x - 1) {
+            atomicExch(&st->bar_count, 0u);
+            __threadfence();
+            st_release(reinterpret_cast<int *>(&st->bar_gen), g + 1);
+        } else {
+            int spins = 0;
+            unsigned ns = 32;
+            while (ld_acquire(reinterpret_cast<const int *>(&st->bar_gen)) == g && *err == 0) {
+                if (++spins > spin_limit) {
+                    atomicExch(&st->error, 3);
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
     }
     __syncthreads();
-    for (int c = 0; c < pw; c++) {
-        double *colc = P + c * R;
-        const double d = colc[c];
-        if (threadIdx.x == 0) {
-            if (d > pivot_tol) s_pos++;
-            else if (d < -pivot_tol) s_neg++;
-            else s_zero++;
+    return *reinterpret_cast<volatile int *>(&st->error) == 0;
+}
+
+__global__ void __launch_bounds__(kDT) k_dense_ldlt(double *S, int n, FactorStatus *st,
+                                                    double pivot_tol, int spin_limit) {
+    __shared__ double A11[kDB][kDB + 1];
+    __shared__ double dinv[kDB];
+    __shared__ double Li[kDB][33], Wj[kDB][33];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    int s_pos = 0, s_neg = 0, s_zero = 0;
+    for (int k0 = 0; k0 < n; k0 += kDB) {
+        const int k1 = min(k0 + kDB, n), pw = k1 - k0;
+        // A: diagonal block (lower triangle), right-looking within the block
+        for (int t = tid; t < kDB * kDB; t += kDT) {
+            const int c = t / kDB, r = t - c * kDB;
+            A11[r][c] = (r < pw && c < pw && r >= c) ? S[(int64_t)(k0 + c) * n + k0 + r] : 0.0;
         }
-        const double dinv = 1.0 / (d == 0.0 ? 1e-300 : d);
-        for (int i = c + 1 + threadIdx.x; i < R; i += blockDim.x) colc[i] *= dinv;
         __syncthreads();
-        for (int j = c + 1 + warp; j < pw; j += nw) {
-            const double lj = colc[j] * d;
-            double *colj = P + j * R;
-            for (int i = j + lane; i < R; i += 32) colj[i] -= colc[i] * lj;
+        if (warp == 0) {
+            for (int c = 0; c < pw; c++) {
+                const double d = A11[c][c];
+                if (lane == 0) {
+                    if (d > pivot_tol) s_pos++;
+                    else if (d < -pivot_tol) s_neg++;
+                    else s_zero++;
+                    dinv[c] = 1.0 / (d == 0.0 ? 1e-300 : d);
+                }
+                __syncwarp();
+                const double di = dinv[c];
+                if (lane > c && lane < pw) A11[lane][c] *= di;
+                __syncwarp();
+                for (int j = c + 1; j < pw; j++) {
+                    const double ljd = A11[j][c] * d;
+                    if (lane >= j && lane < pw) A11[lane][j] -= A11[lane][c] * ljd;
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
+        // B: rows below the block, L21 = A21 L11^-T D^-1 (one row per thread)
+        for (int i = k1 + blockIdx.x * kDT + tid; i < n; i += gridDim.x * kDT) {
+            double w[kDB];
+#pragma unroll
+            for (int c = 0; c < kDB; c++) {
+                if (c < pw) {
+                    double v = S[(int64_t)(k0 + c) * n + i];
+#pragma unroll
+                    for (int c2 = 0; c2 < kDB; c2++)
+                        if (c2 < c) v -= w[c2] * A11[c][c2];
+                    w[c] = v;   // l_ic d_c
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < kDB; c++)
+                if (c < pw) S[(int64_t)(k0 + c) * n + i] = w[c] * dinv[c];
+        }
+        // CTA 0 stores the factored diagonal block once no CTA can still be
+        // loading it (after the barrier; the last block has no reader left)
+        const int R = n - k1;
+        const bool last = R <= 0;
+        if (!last && !dense_grid_barrier(st, spin_limit)) break;
+        if (blockIdx.x == 0)
+            for (int t = tid; t < pw * pw; t += kDT) {
+                const int c = t / pw, r = t - c * pw;
+                if (r >= c) S[(int64_t)(k0 + c) * n + k0 + r] = A11[r][c];
+            }
+        if (last) break;
+        // C: trailing update of the lower triangle, 32 x 32 tiles
+        const int T = (R + 31) / 32, ntiles = T * (T + 1) / 2;
+        for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+            // tile -> (ti, tj), ti >= tj, tiles numbered row by row
+            int ti = (int)((sqrtf(8.0f * (float)tile + 1.0f) - 1.0f) * 0.5f);
+            while (ti * (ti + 1) / 2 > tile) ti--;
+            while ((ti + 1) * (ti + 2) / 2 <= tile) ti++;
+            const int tj = tile - ti * (ti + 1) / 2;
+            const int i0 = k1 + 32 * ti, j0 = k1 + 32 * tj;
+            __syncthreads();
+            for (int t = tid; t < kDB * 32; t += kDT) {
+                const int c = t >> 5, r = t & 31;
+                const bool ok = c < pw;
+                Li[c][r] = (ok && i0 + r < n) ? S[(int64_t)(k0 + c) * n + i0 + r] : 0.0;
+                Wj[c][r] = (ok && j0 + r < n) ? S[(int64_t)(k0 + c) * n + j0 + r] * A11[c][c] : 0.0;
+            }
+            __syncthreads();
+            const int tx = lane, ty = warp;   // 32 x 8
+            for (int r = ty; r < 32; r += 8) {
+                const int i = i0 + tx, j = j0 + r;
+                if (i >= n || j >= n || i < j) continue;
+                double acc = 0.0;
+#pragma unroll
+                for (int c = 0; c < kDB; c++) acc += Li[c][tx] * Wj[c][r];
+                S[(int64_t)j * n + i] -= acc;
+            }
+        }
+        if (!dense_grid_barrier(st, spin_limit)) break;
     }
-    for (int t = threadIdx.x; t < pw * R; t += blockDim.x) {
-        const int cl = t / R, il = t - cl * R;
-        if (il >= cl) S[(int64_t)(k0 + cl) * n + k0 + il] = P[t];
-    }
-    if (threadIdx.x == 0) {
+    if (blockIdx.x == 0 && tid == 0) {
         atomicAdd(&st->n_pos, s_pos);
         atomicAdd(&st->n_neg, s_neg);
         atomicAdd(&st->n_zero, s_zero);
-    }
-}
-
-// Trailing update S[i,j] -= sum_{c in [k0,k1)} L[i,c] d_c L[j,c], i >= j >= k1
-// (one 32x32 tile per CTA of the lower triangle)
-__global__ void k_dense_trailing(double *S, int n, int k0, int k1) {
-    const int tj = blockIdx.x, ti = blockIdx.y;
-    if (ti < tj) return;
-    __shared__ double Li[kPanel][33], Lj[kPanel][33], dd[kPanel];
-    const int pw = k1 - k0;
-    const int i0 = k1 + ti * 32, j0 = k1 + tj * 32;
-    const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8
-    for (int c = ty; c < pw; c += 8) {
-        const double *col = S + (int64_t)(k0 + c) * n;
-        Li[c][tx] = (i0 + tx < n) ? col[i0 + tx] : 0.0;
-        Lj[c][tx] = (j0 + tx < n) ? col[j0 + tx] : 0.0;
-        if (tx == 0) dd[c] = col[k0 + c];
-    }
-    __syncthreads();
-    for (int r = ty; r < 32; r += 8) {
-        const int i = i0 + tx, j = j0 + r;
-        if (i >= n || j >= n || i < j) continue;
-        double acc = 0.0;
-        for (int c = 0; c < pw; c++) acc += Li[c][tx] * dd[c] * Lj[c][r];
-        S[(int64_t)j * n + i] -= acc;
     }
 }
 
@@ -1185,7 +1277,7 @@ __global__ void __launch_bounds__(256) k_dense_inverse(const double *__restrict_
     double *y = Sinv + (int64_t)j * n;
     for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = i == j ? 1.0 : 0.0;
     __syncthreads();
-    block_ldlt_solve<256>(S, n, y);
+    block_ldlt_solve<256>(S, n, y, j);   // L^-1 e_j is zero above row j
 }
 
 // f <= FB <= 32: lane c < np holds column c of the L panel (rows below c);
@@ -1562,7 +1654,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
         // creation to 12,288 elements, 96 KB in FP64); larger panels take the
         // global-memory path
         // plus the staged child->parent map of one child (at most max_f rows)
-        const size_t sm3 = big_rel_offset<T>(F.big_panel) + sizeof(int) * (size_t)F.max_f;
+        const size_t sm3 = big_rel_offset<T>(F.big_panel, F.big_np) + sizeof(int) * (size_t)F.max_f;
         static int g3_all[kMaxDev][2] = {};
         static size_t g3_sm_all[kMaxDev][2] = {};
         int g3_tmp[2] = {0, 0};
@@ -1593,20 +1685,17 @@ void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s) 
     if (n > 0) note_launch(), k_dense_inverse<<<n, 256, 0, s>>>(S, n, Sinv);
 }
 
-void launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol, cudaStream_t s) {
-    // the shared-memory opt-in is a per-device attribute: set it on the
-    // current device before every factorization (a cheap host call)
-    if (n > 0)
-        cudaFuncSetAttribute(k_dense_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024);
-    for (int k0 = 0; k0 < n; k0 += kPanel) {
-        const int k1 = k0 + kPanel < n ? k0 + kPanel : n;
-        note_launch(), k_dense_panel<<<1, 256, sizeof(double) * (size_t)(n - k0) * (k1 - k0), s>>>(S, n, k0, k1, st, pivot_tol);
-        const int rem = n - k1;
-        if (rem > 0) {
-            const int tiles = (rem + 31) / 32;
-            note_launch(), k_dense_trailing<<<dim3(tiles, tiles), 256, 0, s>>>(S, n, k0, k1);
-        }
-    }
+cudaError_t launch_dense_ldlt(double *S, int n, FactorStatus *st, double pivot_tol,
+                              cudaStream_t s, int spin_limit) {
+    if (n <= 0) return cudaSuccess;
+    // CTAs: enough for the first trailing update's tiles, at most one per SM
+    // (all co-resident: the launch is cooperative)
+    const int R = n - kDB > 0 ? n - kDB : 0, T = (R + 31) / 32;
+    int grid = std::max(1, std::min(sm_count(), T * (T + 1) / 2));
+    note_launch();
+    void *args[] = {&S, &n, &st, &pivot_tol, &spin_limit};
+    return cudaLaunchCooperativeKernel((const void *)k_dense_ldlt, dim3(grid), dim3(kDT), args, 0,
+                                       s);
 }
 
 template <typename T>
