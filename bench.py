@@ -397,6 +397,8 @@ def run_ours(args):
     free0 = torch.cuda.mem_get_info()[0]
     t0 = time.perf_counter()
     loop = {"device_loop": 0} if args.host_loop else {}
+    if args.workload == "condensed":
+        loop["dual_first"] = 1
     lib = P.SCOPF(inst, precision=P.PREC_MIXED, **loop)
     t_create = time.perf_counter() - t0
     torch.cuda.synchronize()
@@ -419,7 +421,8 @@ def run_ours(args):
                      "kkt_error": r["kkt_error"]}
     # ---- a mid-solve iterate: the state after a fixed number of IPM iterations
     lib.set_precision(P.PREC_MIXED)
-    lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at)
+    lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at,
+                   dual_first=loop.get("dual_first", 0))
     r = lib2.ncl_solve()
     st = lib2.get_state()
     lam_n, nu0_n, rho = lib2.ncl_params_tensors()
@@ -552,13 +555,18 @@ def run_ours(args):
         cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                "sample": f"failed: {exc}"}
     line = {
-        "metric": METRIC if idx == CONFIG_IDX else
-        "Newton steps/s and SCOPF time-to-solution at 2000-bus×128-ctg (1e-6), vs plain FP64 GPU",
+        "metric": (METRIC if idx == CONFIG_IDX else
+                   "Newton steps/s and SCOPF time-to-solution at 2000-bus×128-ctg (1e-6), vs "
+                   "plain FP64 GPU") + (", condensed primal variant (dual rows eliminated first)"
+                                        if args.workload == "condensed" else ""),
         "value": value, "unit": "Newton steps/s", "n_gpus": world,
         "steps": K, "warmup": args.warmup, "ms_per_step": ms_mixed / K,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f32 block factors + f64 (model, Schur, refinement)", "data": "synthetic",
-        "config": {"workload": WORKLOADS[idx],
+        "config": {"workload": WORKLOADS[idx] + ("; condensed primal variant (dual-first "
+                                                 "order: -C eliminated first, then a pivot-free "
+                                                 "Cholesky of A + B' C^-1 B)"
+                                                 if args.workload == "condensed" else ""),
                    "n_kkt": sz.n_kkt, "nnz_kkt": sz.nnz_kkt, "nnz_L": sz.nnz_L,
                    "blocks": sz.n_blocks, "border": sz.n_border,
                    "iterate": f"state after {args.iterate_at} IPM iterations (mu {mu:.1e}, "
@@ -773,9 +781,10 @@ def main():
                     help="host-driven refinement loop (every kernel launched from the host, "
                          "for profilers that attribute launches to NVTX ranges)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "scale", "screen", "illcond", "peaks"],
+                    choices=["newton", "scale", "condensed", "screen", "illcond", "peaks"],
                     help="newton: the Newton step (default); scale: the same on the 2000-bus "
-                         "x 128 scale-up workload, with its memory footprint; screen: batched "
+                         "x 128 scale-up workload, with its memory footprint; condensed: the "
+                         "newton workload on the condensed primal variant; screen: batched "
                          "screening; illcond: NCL solves with narrowed reactive bands; peaks: "
                          "the arithmetic probes")
     args = ap.parse_args()

@@ -134,6 +134,15 @@ typedef struct {
                                  zero diagonal at delta_w = 0.  The outcome is
                                  the one factoring would give, so iterates are
                                  unchanged; 0: always factor at delta_w = 0 */
+    int32_t dual_first;       /* 1: the condensed primal variant (Section IV-B,
+                                 "signed Cholesky"): the symbolic order puts every
+                                 block's dual rows (equality and complementarity
+                                 rows) before its primal rows.  -C is diagonal, so
+                                 the factorization first eliminates it exactly
+                                 (pivots -C) and then factors the condensed matrix
+                                 A + B' C^-1 B with positive pivots when K has the
+                                 wanted inertia (Haynsworth).  0: node minimum
+                                 degree over primal and dual rows together */
 } scopf_options;
 
 /* Sizes of the handle's problem. */

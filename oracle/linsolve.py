@@ -167,3 +167,53 @@ class SparseLDLSolver:
         n = self.n
         L = sp.csc_matrix((self.Lx[:self.nnzL], self.Li[:self.nnzL], self.Lp), shape=(n, n))
         return (L + sp.eye(n)).tocsc(), self.D.copy()
+
+
+class CondensedSolver:
+    """The condensed primal variant of eq. (newtonsystem) (Section IV-B,
+    "signed Cholesky" read as a Cholesky of the primal Schur complement).
+
+    K = [[A, B'], [B, -C]] in the order [w; dual rows] with C diagonal and
+    positive (the NCL block diag(1/rho, 1/rho + s/zs)).  Eliminating the dual
+    rows gives the condensed matrix
+
+        Kc = A + B' C^-1 B,     Kc dw = r1 + B' C^-1 r2,
+        dy = C^-1 (B dw - r2),
+
+    and Haynsworth's inertia formula In(K) = In(-C) + In(Kc) = (0, m+p, 0) +
+    In(Kc): K has the inertia (n, m+p, 0) the interior-point method wants
+    exactly when Kc is positive definite.  Kc is factored by the pivot-free
+    LDL^T of ``SparseLDLSolver`` (all pivots positive = Cholesky) under the
+    order ``perm_fn(Kc)`` (identity when None); ``factor`` returns the
+    inertia of K.  ``n`` is the number of primal rows."""
+
+    def __init__(self, n: int, perm_fn=None, pivot_tol: float = 0.0):
+        self.n = n
+        self.inner = SparseLDLSolver(perm_fn=perm_fn, pivot_tol=pivot_tol)
+
+    def condense(self, K):
+        K = sp.csr_matrix(K)
+        n = self.n
+        A = K[:n, :n]
+        B = K[n:, :n]
+        Kdd = K[n:, n:].tocoo()
+        off = Kdd.row != Kdd.col
+        if np.any(Kdd.data[off] != 0.0):
+            raise ValueError("the dual-dual block is not diagonal")
+        C = -K[n:, n:].diagonal()
+        if np.any(C <= 0.0):
+            raise ValueError("C must be positive")
+        Kc = (A + B.T @ sp.diags(1.0 / C) @ B).tocsr()
+        return Kc, B.tocsr(), C
+
+    def factor(self, K):
+        Kc, self.B, self.C = self.condense(K)
+        ip, ineg, iz = self.inner.factor(Kc)
+        return ip, ineg + len(self.C), iz
+
+    def solve(self, b):
+        n = self.n
+        r1, r2 = b[:n], b[n:]
+        dw = self.inner.solve(r1 + self.B.T @ (r2 / self.C))
+        dy = (self.B @ dw - r2) / self.C
+        return np.concatenate([dw, dy])

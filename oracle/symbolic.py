@@ -46,6 +46,19 @@ twice (here and in the CUDA library) and compared bit for bit:
 8. Rows: nodes in that order, each node's rows in the order of step 1, then
    the border rows.
 
+Dual-first order (``dual_first=True``: the condensed primal variant).  Every
+block node is split into its primal part (rows of w) and its dual part
+(equality and complementarity rows), keeping the row order of step 1 within
+each part.  Node ids: the primal parts in the original node order, then the
+dual parts in the original node order (empty parts dropped), then the border
+nodes.  Step 2 eliminates every dual node before any primal node (key: dual
+before primal, then current degree, then node id).  The -C block of eq.
+(newtonsystem) is diagonal, so dual nodes are never adjacent: eliminating
+them all first leaves on the primal nodes exactly the pattern of the
+condensed matrix A + B' C^-1 B, which the rest of the elimination factors
+with positive pivots when it is positive definite ("signed Cholesky",
+Section IV-B).  Steps 3-8 are unchanged.
+
 Parity: integer, compared exactly with the CUDA implementation; pinned by
 brute-force dense boolean elimination (fill and tree) and hand-checked
 minimum-degree orders on path and grid graphs in the tests.
@@ -60,15 +73,17 @@ import numpy as np
 class BlockGraph:
     """Node graph of one scenario block with the generic KKT rows of each node."""
 
-    def __init__(self, node_rows, adj, n_block_nodes):
+    def __init__(self, node_rows, adj, n_block_nodes, dual_from=None):
         self.node_rows = node_rows          # list of arrays (generic KKT indices)
         self.adj = adj                      # list of sets of node ids
         self.n_block = n_block_nodes        # nodes [0, n_block) are eliminable
         self.n_nodes = len(node_rows)
+        self.dual_from = dual_from          # dual-first order: nodes [dual_from, n_block) are dual
 
 
-def block_graphs(model):
-    """Build the node graph of every block of a ``SCOPFModel``."""
+def block_graphs(model, dual_first: bool = False):
+    """Build the node graph of every block of a ``SCOPFModel`` (with
+    ``dual_first``, every block node split into its primal and dual parts)."""
     M = model
     n, m = M.n, M.m
     out = []
@@ -108,12 +123,20 @@ def block_graphs(model):
             rows.append(r)
         if blk.k > 0:
             rows.append([blk.gdelta])
+        dual_from = None
+        if dual_first:
+            prim = [[x for x in r if x < n] for r in rows]
+            dual = [[x for x in r if x >= n] for r in rows]
+            rows = [r for r in prim if r]
+            dual_from = len(rows)
+            rows += [r for r in dual if r]
         n_block = len(rows)
         for g in range(M.ng):
             rows.append([M.border0 + g])
         for q in range(M.npv):
             rows.append([M.border0 + M.ng + q])
-        out.append(BlockGraph([np.asarray(r, dtype=np.int64) for r in rows], None, n_block))
+        out.append(BlockGraph([np.asarray(r, dtype=np.int64) for r in rows], None, n_block,
+                              dual_from))
     return out
 
 
@@ -141,19 +164,21 @@ def attach_adjacency(graphs, K):
     return graphs
 
 
-def min_degree(adj, n_block):
+def min_degree(adj, n_block, dual_from=None):
     """Exact minimum degree with smallest-id tie-break; nodes >= n_block are
-    never eliminated.  Returns (order, struct) where struct[p] is the set of
-    neighbours of p when it was eliminated."""
+    never eliminated; with ``dual_from`` the nodes [dual_from, n_block) are
+    all eliminated before the others.  Returns (order, struct) where
+    struct[p] is the set of neighbours of p when it was eliminated."""
     n = len(adj)
     A = [set(a) for a in adj]
-    heap = [(len(A[v]), v) for v in range(n_block)]
+    cls = [0 if dual_from is not None and v >= dual_from else 1 for v in range(n)]
+    heap = [(cls[v], len(A[v]), v) for v in range(n_block)]
     heapq.heapify(heap)
     alive = [True] * n
     order = []
     struct = [None] * n
     while heap:
-        d, v = heapq.heappop(heap)
+        _, d, v = heapq.heappop(heap)
         if not alive[v] or d != len(A[v]):
             continue
         alive[v] = False
@@ -165,7 +190,7 @@ def min_degree(adj, n_block):
             A[u].discard(u)
             A[u].discard(v)
             if u < n_block:
-                heapq.heappush(heap, (len(A[u]), u))
+                heapq.heappush(heap, (cls[u], len(A[u]), u))
         A[v] = set()
     return order, struct
 
@@ -174,7 +199,7 @@ class Symbolic:
     """Symbolic analysis of one block (see the module docstring)."""
 
     def __init__(self, G: BlockGraph, relax_max_nodes: int = 8, relax_max_front: int = 0):
-        order, struct = min_degree(G.adj, G.n_block)
+        order, struct = min_degree(G.adj, G.n_block, G.dual_from)
         nb_nodes = G.n_block
         self.elim_order = order
         pos = np.full(G.n_nodes, -1, dtype=np.int64)
@@ -358,12 +383,13 @@ def structural_kkt(model, seed: int = 12345):
     return S.kkt_matrix(st, prm, H, J, 0.5)
 
 
-def kkt_permutation(model, K=None, relax_max_nodes: int = 8, relax_max_front: int = 0):
+def kkt_permutation(model, K=None, relax_max_nodes: int = 8, relax_max_front: int = 0,
+                    dual_first: bool = False):
     """Global fill-reducing order of the reduced KKT matrix: each block's rows
     in its symbolic order, blocks 0..K in turn, then the border rows.  The
     node graphs come from the structural pattern (``structural_kkt``)."""
     Ks = structural_kkt(model)
-    graphs = attach_adjacency(block_graphs(model), Ks)
+    graphs = attach_adjacency(block_graphs(model, dual_first), Ks)
     syms = [Symbolic(G, relax_max_nodes, relax_max_front) for G in graphs]
     parts = [S.rows[:S.n_block_rows] for S in syms]
     border = np.arange(model.border0, model.border0 + model.nborder, dtype=np.int64)

@@ -401,6 +401,7 @@ void scopf_default_options(scopf_options *o) {
     o->fp64_switch_refine = 0;
     o->fp64_switch_streak = 3;
     o->known_zero_pivot = 1;
+    o->dual_first = 0;
 }
 
 const char *scopf_strerror(int s) {
@@ -455,7 +456,8 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
         auto work = [&]() {
             for (size_t k; (k = next.fetch_add(1)) < nblk;)
                 errs[k] = symbolic_block(h->M, (int)k, h->opt.relax_max_nodes,
-                                         h->opt.relax_max_front, h->syms[k]);
+                                         h->opt.relax_max_front, h->opt.dual_first != 0,
+                                         h->syms[k]);
         };
         std::vector<std::thread> pool;
         for (size_t t = 1; t < nt; t++) pool.emplace_back(work);

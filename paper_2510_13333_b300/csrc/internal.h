@@ -115,6 +115,6 @@ struct BlockSymbolic {
 };
 
 std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax_max_front,
-                           BlockSymbolic &S);
+                           bool dual_first, BlockSymbolic &S);
 
 }  // namespace scopf

@@ -13,10 +13,18 @@
 //  5. supernodes: an only child directly below its parent joins the
 //     parent's supernode while it has fewer than relax_max_nodes nodes;
 //  6. rows: nodes in postorder (node rows in their fixed order), then border.
+// Dual-first order (the condensed primal variant): every block node is split
+// into its primal part (rows of w) and its dual part (equality and
+// complementarity rows), each keeping its rows' order; ids: primal parts in
+// node order, then dual parts in node order (empty parts dropped), then the
+// border.  Minimum degree eliminates every dual node before any primal node
+// (key: dual first, degree, id).  The -C block is diagonal, so the dual nodes
+// are independent, and eliminating them leaves the pattern of A + B' C^-1 B.
 #include <algorithm>
 #include <functional>
 #include <queue>
 #include <set>
+#include <tuple>
 #include <unordered_map>
 
 #include "internal.h"
@@ -24,7 +32,7 @@
 namespace scopf {
 
 std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax_max_front,
-                           BlockSymbolic &S) {
+                           bool dual_first, BlockSymbolic &S) {
     const Block &B = M.blocks[k];
     const int nb = M.nb, ng = M.ng, npv = (int)M.pv.size();
     auto Kw = [&](int64_t local) { return B.kkt0 + local; };
@@ -76,6 +84,20 @@ std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax
         rows.push_back(r);
     }
     if (k > 0) rows.push_back({Kw(B.delta)});
+    int dual_from = -1;   // dual-first: block nodes [dual_from, n_block) are dual parts
+    if (dual_first) {
+        const int64_t w_end = B.kkt0 + B.nvar;   // rows below are the block's w
+        std::vector<std::vector<int64_t>> prim, dual;
+        for (const auto &r : rows) {
+            std::vector<int64_t> a, b;
+            for (int64_t x : r) (x < w_end ? a : b).push_back(x);
+            if (!a.empty()) prim.push_back(a);
+            if (!b.empty()) dual.push_back(b);
+        }
+        rows = prim;
+        dual_from = (int)rows.size();
+        rows.insert(rows.end(), dual.begin(), dual.end());
+    }
     const int n_block = (int)rows.size();
     for (int gi = 0; gi < ng; gi++) rows.push_back({M.kkt_border0 + gi});
     for (int q = 0; q < npv; q++) rows.push_back({M.kkt_border0 + ng + q});
@@ -100,18 +122,20 @@ std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax
                 A[u].insert(v);
             }
 
-    // exact minimum degree (ties: smallest id); border nodes never eliminated
-    using QE = std::pair<int, int>;
+    // exact minimum degree (ties: smallest id); border nodes never eliminated;
+    // dual-first: dual nodes before all others
+    using QE = std::tuple<int, int, int>;   // (class, degree, id)
+    auto cls = [&](int v) { return dual_from >= 0 && v >= dual_from ? 0 : 1; };
     std::priority_queue<QE, std::vector<QE>, std::greater<QE>> heap;
-    for (int v = 0; v < n_block; v++) heap.push({(int)A[v].size(), v});
+    for (int v = 0; v < n_block; v++) heap.push({cls(v), (int)A[v].size(), v});
     std::vector<char> alive(n_nodes, 1);
     std::vector<int> order;
     std::vector<std::set<int>> st(n_nodes);
     while (!heap.empty()) {
         QE top = heap.top();
         heap.pop();
-        int v = top.second;
-        if (!alive[v] || top.first != (int)A[v].size()) continue;
+        const int v = std::get<2>(top);
+        if (!alive[v] || std::get<1>(top) != (int)A[v].size()) continue;
         alive[v] = 0;
         order.push_back(v);
         std::set<int> nbv = A[v];
@@ -120,7 +144,7 @@ std::string symbolic_block(const Model &M, int k, int relax_max_nodes, int relax
             A[u].insert(nbv.begin(), nbv.end());
             A[u].erase(u);
             A[u].erase(v);
-            if (u < n_block) heap.push({(int)A[u].size(), u});
+            if (u < n_block) heap.push({cls(u), (int)A[u].size(), u});
         }
         A[v].clear();
     }

@@ -41,17 +41,17 @@ def test_invalid_network_rejected():
         P.SCOPF(inst, host_only=1)
 
 
-@pytest.mark.parametrize("rmf", [0, 32])
+@pytest.mark.parametrize("rmf,dual_first", [(0, 0), (32, 0), (0, 1), (32, 1)])
 @pytest.mark.parametrize("which", ["small", "cfg0", "cfg1"])
-def test_symbolic_bit_exact(which, rmf):
+def test_symbolic_bit_exact(which, rmf, dual_first):
     inst = {"small": H.small_instance, "cfg0": lambda: H.instance(0),
             "cfg1": lambda: H.instance(1)}[which]()
     M = SCOPFModel(inst)
-    lib = P.SCOPF(inst, host_only=1, relax_max_front=rmf)
+    lib = P.SCOPF(inst, host_only=1, relax_max_front=rmf, dual_first=dual_first)
     assert lib.sizes.n_kkt == M.n + M.m + M.p
     assert lib.sizes.n == M.n and lib.sizes.m == M.m and lib.sizes.p == M.p
     gen = H.generic_of_natural(M)
-    _, syms = symbolic.kkt_permutation(M, relax_max_front=rmf)
+    _, syms = symbolic.kkt_permutation(M, relax_max_front=rmf, dual_first=bool(dual_first))
     for k, S in enumerate(syms):
         c = lib.scopf_symbolic_block(k)
         assert np.array_equal(c["post"], S.post), k

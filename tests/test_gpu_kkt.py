@@ -12,7 +12,7 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 
-def _case(inst, seed, rho, delta_w, mu=1e-2, lin=None):
+def _case(inst, seed, rho, delta_w, mu=1e-2, lin=None, **opt):
     import torch
     import paper_2510_13333_b300 as P
     M = SCOPFModel(inst)
@@ -20,7 +20,7 @@ def _case(inst, seed, rho, delta_w, mu=1e-2, lin=None):
     st = H.random_interior_state(S, seed)
     rng = np.random.default_rng(seed + 1)
     prm = Params(rho=rho, lam_n=rng.standard_normal(M.m) * 0.1, nu0_n=rng.random(M.p) * 0.1)
-    lib = P.SCOPF(inst)
+    lib = P.SCOPF(inst, **opt)
     dst = H.to_device_state(S, st, torch)
     t = lambda a: torch.tensor(a, dtype=torch.float64, device="cuda")
     rhs = lib.kkt_assemble(dst, t(prm.lam_n), t(prm.nu0_n), rho, mu, delta_w)
@@ -91,4 +91,39 @@ def test_inertia_indefinite(cuda):
     M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 9, rho=1e2, delta_w=0.0)
     ev = np.linalg.eigvalsh(K_or.toarray())
     expect = (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    assert lib.kkt_factor(0) == expect
+
+
+@pytest.mark.parametrize("which,prec", [("cfg0", 0), ("cfg0", 1), ("cfg1", 0), ("cfg1", 1)])
+def test_condensed_factor_solve_matches_oracle(cuda, which, prec):
+    """The condensed primal variant (dual rows eliminated first): the
+    library's factorization reports the oracle's inertia (which is
+    Haynsworth's In(-C) + In(A + B' C^-1 B)), and the refined solve equals
+    the oracle's condensed solve entry by entry."""
+    from oracle.linsolve import CondensedSolver
+    inst = {"cfg0": lambda: H.instance(0), "cfg1": lambda: H.instance(1)}[which]()
+    M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 5, rho=1e2, delta_w=1.0,
+                                                            dual_first=1)
+    perm, _ = symbolic.kkt_permutation(M, dual_first=True)
+    pc = perm[perm < M.n]
+    ora = CondensedSolver(M.n, perm_fn=lambda Kc: pc)
+    inertia_or = ora.factor(K_or)
+    assert lib.kkt_factor(prec) == inertia_or
+    x, rel, steps, status = lib.kkt_solve(rhs, max_refine=20)
+    assert status == 0 and rel <= 1e-10, (rel, steps)
+    x_or = ora.solve(rhs_or)
+    xl = np.empty_like(x_or)
+    xl[gen] = x.cpu().numpy()
+    H.assert_entries_close("solution", xl, x_or, 1e-8, 1e-8 * H.group_scale(M, x_or))
+
+
+def test_condensed_inertia_wrong_at_small_shift(cuda):
+    """delta_w = 0 at a random point: the condensed matrix is indefinite and
+    the dual-first factorization reports K's exact (Sylvester) inertia."""
+    inst = H.instance(0)
+    M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 9, rho=1e2, delta_w=0.0,
+                                                            dual_first=1)
+    ev = np.linalg.eigvalsh(K_or.toarray())
+    expect = (int((ev > 0).sum()), int((ev < 0).sum()), 0)
+    assert expect != (M.n, M.m + M.p, 0)
     assert lib.kkt_factor(0) == expect

@@ -122,3 +122,27 @@ def test_known_zero_pivot_changes_nothing(cuda, prec):
     for f in sa:
         assert np.array_equal(sa[f], sb[f]), f
     assert rb["factorizations"] - ra["factorizations"] >= ra["inner_iters"]
+
+
+
+_ORACLE_DF = {}
+
+
+@pytest.mark.parametrize("idx,prec", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_condensed_ncl_solve_matches_oracle(cuda, idx, prec):
+    """Full NCL solves on the condensed primal variant (dual rows eliminated
+    first) against the oracle NCL solve on the same factorization order:
+    objective within 1e-6 relative, violation and KKT error within 1e-6."""
+    import paper_2510_13333_b300 as P
+    if idx not in _ORACLE_DF:
+        M = SCOPFModel(H.instance(idx))
+        perm, _ = symbolic.kkt_permutation(M, dual_first=True)
+        _ORACLE_DF[idx] = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm)).solve()
+    ref = _ORACLE_DF[idx]
+    assert ref.status == "ok"
+    lib = P.SCOPF(H.instance(idx), precision=prec, dual_first=1)
+    res = lib.ncl_solve()
+    assert res["call_status"] == 0, res
+    assert abs(res["objective"] - ref.objective) <= 1e-6 * abs(ref.objective), (res, ref.objective)
+    assert res["max_violation"] <= 1e-6
+    assert res["kkt_error"] <= 1e-6 and res["feas_rt"] <= 1e-6
