@@ -399,6 +399,21 @@ def run_ours(args):
     loop = {"device_loop": 0} if args.host_loop else {}
     if args.workload == "condensed":
         loop["dual_first"] = 1
+    tune = None
+    if not args.no_autotune:
+        # supernode tile shapes for this instance (scopf_autotune: Newton
+        # steps of each candidate from a common iterate, CUDA events)
+        t0 = time.perf_counter()
+        tuned, cands = P.autotune(inst, precision=P.PREC_MIXED, **loop)
+        loop["cluster_max_tasks"] = tuned.cluster_max_tasks
+        loop["relax_max_nodes"] = tuned.relax_max_nodes
+        tune = {"seconds": time.perf_counter() - t0,
+                "chosen": {"cluster_max_tasks": tuned.cluster_max_tasks,
+                           "relax_max_nodes": tuned.relax_max_nodes},
+                "candidates": cands}
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        t0 = time.perf_counter()
     lib = P.SCOPF(inst, precision=P.PREC_MIXED, **loop)
     t_create = time.perf_counter() - t0
     torch.cuda.synchronize()
@@ -422,7 +437,7 @@ def run_ours(args):
     # ---- a mid-solve iterate: the state after a fixed number of IPM iterations
     lib.set_precision(P.PREC_MIXED)
     lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at,
-                   dual_first=loop.get("dual_first", 0))
+                   **{k: v for k, v in loop.items() if k != "device_loop"})
     r = lib2.ncl_solve()
     st = lib2.get_state()
     lam_n, nu0_n, rho = lib2.ncl_params_tensors()
@@ -577,6 +592,7 @@ def run_ours(args):
         "speedup_mixed_vs_fp64": value / fp64_value,
         "time_to_solution": tts,
         "create_s": t_create,
+        "autotune": tune,
         "memory": {"device_bytes_handle": handle_bytes, "front_bytes": sz.front_bytes,
                    "bytes_per_block": handle_bytes / sz.n_blocks,
                    "note": "device memory the handle holds (free-memory difference around "
@@ -777,6 +793,8 @@ def main():
     ap.add_argument("--iterate-at", type=int, default=30)
     ap.add_argument("--tts", default="both", choices=["none", "mixed", "both"],
                     help="which full NCL solves to time (time to solution)")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="skip scopf_autotune and use the default tile shapes")
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven refinement loop (every kernel launched from the host, "
                          "for profilers that attribute launches to NVTX ranges)")

@@ -327,6 +327,29 @@ int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, 
  * synchronise. */
 int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *stream, double *flops);
 
+/* One candidate of scopf_autotune. */
+typedef struct {
+    int32_t cluster_max_tasks, relax_max_nodes;
+    double ms_per_step;       /* mean Newton step time from the common iterate */
+    int32_t chosen;           /* 1 for the candidate written back into the options */
+} scopf_tune_entry;
+
+/* Autotuner of the supernodal tile shapes (the paper leaves them to cuDSS
+ * and has no counterpart of this call): chooses cluster_max_tasks (small
+ * fronts per warp work item) and relax_max_nodes (nodes an only-child chain
+ * merges into one supernode) for this instance.  A short NCL run (iterate_at interior-point iterations from
+ * the flat start, options *opt) gives a common iterate; each candidate handle
+ * times `steps` Newton steps (scopf_newton_step, after one untimed step)
+ * from it with CUDA events.  Candidates: item sizes 4, 8, 16, 32 at the
+ * given amalgamation limit, then limits 4, 8, 16 at the best item size.  On
+ * return opt holds the fastest pair (every other field unchanged); entries
+ * (host, capacity, may be NULL) receive the candidates in the order tried,
+ * *n_entries their number.  Creates and destroys one handle per candidate on
+ * the current device (device memory of two handles at a time). */
+int scopf_autotune(const scopf_network *net, const scopf_contingency *ctg, int32_t K,
+                   scopf_options *opt, int32_t iterate_at, int32_t steps, int32_t capacity,
+                   scopf_tune_entry *entries, int32_t *n_entries);
+
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */
 int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);

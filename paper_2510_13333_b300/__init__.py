@@ -69,6 +69,11 @@ class Options(ctypes.Structure):
     _fields_ = [(n, c_dbl) for n in _OPT_DOUBLES] + [(n, c_i32) for n in _OPT_INTS]
 
 
+class TuneEntry(ctypes.Structure):
+    _fields_ = [("cluster_max_tasks", c_i32), ("relax_max_nodes", c_i32),
+                ("ms_per_step", c_dbl), ("chosen", c_i32)]
+
+
 class Sizes(ctypes.Structure):
     _fields_ = [("n", c_i64), ("m", c_i64), ("p", c_i64), ("n_kkt", c_i64), ("n_border", c_i64),
                 ("n_blocks", c_i32), ("nnz_kkt", c_i64), ("nnz_L", c_i64),
@@ -160,6 +165,9 @@ def lib():
             "scopf_dense_ldlt_solve_noalloc": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32,
                                                        ctypes.c_void_p]),
             "scopf_peak_probe": (c_i32, [c_i32, c_i64, P_dbl, ctypes.c_void_p, P_dbl]),
+            "scopf_autotune": (c_i32, [ctypes.POINTER(Network), ctypes.POINTER(Contingency),
+                                       c_i32, ctypes.POINTER(Options), c_i32, c_i32, c_i32,
+                                       ctypes.POINTER(TuneEntry), P_i32]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(L, name)
@@ -266,38 +274,63 @@ def _check(fn, status):
         raise ScopfError(fn, status)
 
 
+def _network_args(inst, keep):
+    """scopf_network and scopf_contingency array of an instance (host arrays
+    kept alive in `keep` for the duration of the call)."""
+    net = inst.net
+
+    def d(a):
+        a = np.ascontiguousarray(a, dtype=np.float64)
+        keep.append(a)
+        return _hp(a, c_dbl)
+
+    def i(a):
+        a = np.ascontiguousarray(a, dtype=np.int32)
+        keep.append(a)
+        return _hp(a, c_i32)
+
+    N = Network(net.n_bus, net.n_branch, net.n_gen, int(net.ref_bus), d(net.Pd), d(net.Qd),
+                d(net.Gs), d(net.Bs), d(net.vmin), d(net.vmax), i(net.f), i(net.t), d(net.r),
+                d(net.x), d(net.b), d(net.rate), i(net.gbus), d(net.pmin), d(net.pmax),
+                d(net.qmin), d(net.qmax), d(net.c2), d(net.c1), d(net.c0))
+    K = len(inst.ctgs)
+    C = (Contingency * max(1, K))()
+    for k, c in enumerate(inst.ctgs):
+        C[k] = Contingency(int(c.kind), int(c.element), len(c.switch_buses), i(c.switch_buses))
+    return N, C, K
+
+
+def autotune(inst, iterate_at: int = 10, steps: int = 3, options: Options | None = None,
+             **opt_kw):
+    """Run scopf_autotune on an instance: returns (the options with the
+    chosen tile shapes, list of candidate dicts in the order tried)."""
+    keep = []
+    N, C, K = _network_args(inst, keep)
+    o = options or default_options()
+    for k, v in opt_kw.items():
+        setattr(o, k, v)
+    cap = 16
+    E = (TuneEntry * cap)()
+    n = c_i32()
+    _check("scopf_autotune", lib().scopf_autotune(ctypes.byref(N), C, K, ctypes.byref(o),
+                                                  iterate_at, steps, cap, E, ctypes.byref(n)))
+    out = [{f: getattr(E[j], f) for f, _ in TuneEntry._fields_} for j in range(min(n.value, cap))]
+    return o, out
+
+
 class SCOPF:
     """A handle around one SCOPF instance (network + contingencies)."""
 
     def __init__(self, inst, options: Options | None = None, **opt_kw):
         L = lib()
-        net = inst.net
         self._keep = []
-
-        def d(a):
-            a = np.ascontiguousarray(a, dtype=np.float64)
-            self._keep.append(a)
-            return _hp(a, c_dbl)
-
-        def i(a):
-            a = np.ascontiguousarray(a, dtype=np.int32)
-            self._keep.append(a)
-            return _hp(a, c_i32)
-
-        N = Network(net.n_bus, net.n_branch, net.n_gen, int(net.ref_bus), d(net.Pd), d(net.Qd),
-                    d(net.Gs), d(net.Bs), d(net.vmin), d(net.vmax), i(net.f), i(net.t), d(net.r),
-                    d(net.x), d(net.b), d(net.rate), i(net.gbus), d(net.pmin), d(net.pmax),
-                    d(net.qmin), d(net.qmax), d(net.c2), d(net.c1), d(net.c0))
-        K = len(inst.ctgs)
-        C = (Contingency * max(1, K))()
-        for k, c in enumerate(inst.ctgs):
-            C[k] = Contingency(int(c.kind), int(c.element), len(c.switch_buses), i(c.switch_buses))
+        N, C, K = _network_args(inst, self._keep)
         o = options or default_options()
         for k, v in opt_kw.items():
             setattr(o, k, v)
         self.options = o
         self.host_only = bool(o.host_only)
-        self.n_bus, self.n_gen = net.n_bus, net.n_gen
+        self.n_bus, self.n_gen = inst.net.n_bus, inst.net.n_gen
         h = ctypes.c_void_p()
         _check("scopf_create", L.scopf_create(ctypes.byref(N), C, K, ctypes.byref(o),
                                               ctypes.byref(h)))

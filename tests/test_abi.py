@@ -60,6 +60,22 @@ def test_symbolic_bit_exact(which, rmf, dual_first):
         assert np.array_equal(gen[c["rows"]], S.rows), k
 
 
+@pytest.mark.parametrize("rmn", [4, 16])
+def test_symbolic_bit_exact_amalgamation_limits(rmn):
+    """The autotuner's amalgamation limits (relax_max_nodes) keep the
+    analysis bit-exact with the oracle's."""
+    inst = H.instance(1)
+    M = SCOPFModel(inst)
+    lib = P.SCOPF(inst, host_only=1, relax_max_nodes=rmn)
+    gen = H.generic_of_natural(M)
+    _, syms = symbolic.kkt_permutation(M, relax_max_nodes=rmn)
+    for k, S in enumerate(syms):
+        c = lib.scopf_symbolic_block(k)
+        assert np.array_equal(c["post"], S.post), k
+        assert np.array_equal(c["sn_start"], S.sn_start), k
+        assert np.array_equal(gen[c["rows"]], S.rows), k
+
+
 def test_kkt_pattern_matches_oracle():
     inst = H.small_instance()
     M = SCOPFModel(inst)
