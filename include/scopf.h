@@ -143,6 +143,12 @@ typedef struct {
                                  A + B' C^-1 B with positive pivots when K has the
                                  wanted inertia (Haynsworth).  0: node minimum
                                  degree over primal and dual rows together */
+    int32_t fixed_mu;         /* 1: the interior-point loop keeps the barrier
+                                 parameter at its starting value (mu_init, or the
+                                 handle's mu for ncl_resume) and stops on the
+                                 barrier error E_mu <= tol instead of E_0: the
+                                 solution of the barrier problem at that mu, the
+                                 smooth map scopf_adjoint differentiates */
 } scopf_options;
 
 /* Sizes of the handle's problem. */

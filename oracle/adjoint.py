@@ -56,3 +56,66 @@ def scopf_adjoint(solver, st, prm, seed_pg0=None, seed_cost=0.0):
         gQd += a[n + blk.grQ]
     gc1 = -(BASE_MVA / OBJ_SCALE) * a[pg] + seed_cost * (BASE_MVA / OBJ_SCALE) * st.w[pg]
     return gPd, gQd, gc1
+
+
+def polish_barrier(solver, st, mu, tol=1e-12, max_iter=15):
+    """Newton's method on the barrier KKT conditions of the NCL subproblem
+    with the relaxations r and t held at their values (Section IV-B,
+    eq. kktncl at the barrier parameter mu):
+
+        grad phi + J' lam + B_c' yc - zl + zu = 0,   yc - zs = 0,
+        c(w) - r = 0,   W1 W2 e - t + s = 0,
+        (w - l) zl = mu,   (u - w) zu = mu,   s zs = mu.
+
+    Eliminating the bound multipliers and s as the method does gives the
+    reduced matrix of eq. (newtonsystem) with C = diag(0, s/zs): the matrix
+    ``scopf_adjoint`` solves with (its rho -> infinity limit).  So the
+    solutions these steps converge to are the map whose derivative the
+    adjoint computes, and a parameter change of size h moves them by O(h):
+    from a nearby solution plain Newton steps (fraction to the boundary
+    only) converge quadratically.  Returns (state, residual history); the
+    residual is the infinity norm of the conditions above."""
+    from .ncl import Params
+    S = solver
+    P = S.P
+    n, m, p = S.n, S.m, S.p
+    hard = Params(rho=np.inf, lam_n=np.zeros(m), nu0_n=np.zeros(p))
+    st = st.copy()
+    hist = []
+    for _ in range(max_iter + 1):
+        res = S.residuals(st, Params(rho=1.0, lam_n=st.lam, nu0_n=st.yc))
+        sl, su = S.slacks(st)
+        F = max(np.abs(res["gwz"]).max(), np.abs(res["gs"]).max() if p else 0.0,
+                np.abs(res["pc"]).max(), np.abs(res["py"]).max() if p else 0.0,
+                np.abs(sl * st.zl - mu).max() if len(sl) else 0.0,
+                np.abs(su * st.zu - mu).max() if len(su) else 0.0,
+                np.abs(st.s * st.zs - mu).max() if p else 0.0)
+        hist.append(float(F))
+        if F <= tol or len(hist) > max_iter:
+            break
+        K = S.kkt_matrix(st, hard, P.hessian(st.w, st.lam), res["J"], 0.0).tocsc()
+        rw = res["gw"].copy()
+        rw[S.il] -= mu / sl
+        rw[S.iu] += mu / su
+        b_y = -res["py"] - (mu / st.s - st.yc) * st.s / st.zs
+        sol = spla.spsolve(K, np.concatenate([-rw, -res["pc"], b_y]))
+        dw, dlam, dyc = sol[:n], sol[n:n + m], sol[n + m:]
+        ds = (mu / st.s - st.yc - dyc) * st.s / st.zs
+        dzl = mu / sl - st.zl - st.zl / sl * dw[S.il]
+        dzu = mu / su - st.zu + st.zu / su * dw[S.iu]
+        dzs = mu / st.s - st.zs - st.zs / st.s * ds
+        # fraction to the boundary (tau = 0.99) on the positive quantities
+        a = 1.0
+        for x, dx in ((sl, dw[S.il]), (su, -dw[S.iu]), (st.s, ds), (st.zl, dzl), (st.zu, dzu),
+                      (st.zs, dzs)):
+            neg = dx < 0
+            if np.any(neg):
+                a = min(a, float(np.min(-0.99 * x[neg] / dx[neg])))
+        st.w = st.w + a * dw
+        st.lam = st.lam + a * dlam
+        st.yc = st.yc + a * dyc
+        st.s = st.s + a * ds
+        st.zl = st.zl + a * dzl
+        st.zu = st.zu + a * dzu
+        st.zs = st.zs + a * dzs
+    return st, hist

@@ -68,6 +68,11 @@ class Options:
     # IC-1 at every iteration, its outcome taken without factoring when the
     # pivot-free LDL^T must meet an exactly zero pivot (``newton_direction``)
     known_zero_pivot: bool = True
+    # keep the barrier parameter at its starting value and stop the inner
+    # loop on the barrier error E_mu instead of E_0 (solutions of the
+    # barrier problem at a fixed mu: the smooth map the adjoint
+    # differentiates)
+    fixed_mu: bool = False
     gamma_theta: float = 1e-5
     gamma_phi: float = 1e-8
     delta_sw: float = 1.0
@@ -382,13 +387,13 @@ class NCLSolver:
         theta_min = 1e-4 * max(1.0, th0)
         filt = []
         while True:
-            E0 = self.error(st, res, 0.0)[0]
+            E0 = self.error(st, res, mu if o.fixed_mu else 0.0)[0]
             if E0 <= omega:
                 return st, mu, dw_last, E0, "ok"
             if self.n_inner >= o.max_inner:
                 return st, mu, dw_last, E0, "max_iter"
             Emu = self.error(st, res, mu)[0]
-            while Emu <= o.kappa_eps * mu and mu > o.mu_min:
+            while not o.fixed_mu and Emu <= o.kappa_eps * mu and mu > o.mu_min:
                 mu = max(o.mu_min, min(o.kappa_mu * mu, mu ** o.theta_mu))
                 filt = []
                 Emu = self.error(st, res, mu)[0]

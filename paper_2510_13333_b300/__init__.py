@@ -62,7 +62,7 @@ _OPT_DOUBLES = ["tol", "mu_min", "mu_init", "kappa_eps", "kappa_mu", "theta_mu",
 _OPT_INTS = ["max_backtrack", "max_outer", "max_inner", "max_refine", "precision",
              "relax_max_nodes", "verbose", "spin_limit", "host_only", "cluster_max_tasks",
              "relax_max_front", "device_loop", "fp64_switch_refine", "fp64_switch_streak",
-             "known_zero_pivot", "dual_first"]
+             "known_zero_pivot", "dual_first", "fixed_mu"]
 
 
 class Options(ctypes.Structure):

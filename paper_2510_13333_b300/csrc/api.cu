@@ -402,6 +402,7 @@ void scopf_default_options(scopf_options *o) {
     o->fp64_switch_streak = 3;
     o->known_zero_pivot = 1;
     o->dual_first = 0;
+    o->fixed_mu = 0;
 }
 
 const char *scopf_strerror(int s) {

@@ -726,14 +726,14 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
         std::vector<std::pair<double, double>> filt;
         int inner_status = SCOPF_OK;
         while (true) {
-            E0 = I.error(N, 0.0);
+            E0 = I.error(N, o.fixed_mu ? mu : 0.0);   // fixed mu: the barrier error
             if (E0 <= om) break;
             if (inner >= o.max_inner) {
                 inner_status = SCOPF_ERR_MAX_ITER;
                 break;
             }
             double Emu = I.error(N, mu);
-            while (Emu <= o.kappa_eps * mu && mu > o.mu_min) {
+            while (!o.fixed_mu && Emu <= o.kappa_eps * mu && mu > o.mu_min) {
                 mu = std::fmax(o.mu_min, std::fmin(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
                 filt.clear();
                 Emu = I.error(N, mu);
