@@ -326,6 +326,7 @@ int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, 
  * fractions; the paper has no counterpart).  Launches one kernel on stream
  * (a cudaStream_t or NULL) that keeps every SM busy with independent chains
  * of kind 0: FP32 FMA, 1: FP64 FMA, 2: FP64 tensor MMA (mma.sync m8n8k4),
+ * 3: FP64 FMA on one lane per warp (flops of the active lanes only),
  * iters iterations each, and returns the launch's flop count in *flops (host,
  * an FMA counted as 2).  out: device, at least 8 bytes, written only in a
  * case that never occurs (it keeps the chains from being optimised away).

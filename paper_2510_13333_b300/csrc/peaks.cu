@@ -32,6 +32,24 @@ __global__ void __launch_bounds__(kPT) k_fma_chains(int64_t iters, T *__restrict
     if (s == (T)-1.2345) out[0] = s;   // never true: keeps the chains live
 }
 
+// FP64 FMA chains on lane 0 of every warp only (the other lanes idle): how
+// the FP64 pipe charges a warp instruction with one active lane
+__global__ void __launch_bounds__(kPT) k_fma_chains_one_lane(int64_t iters, double *__restrict__ out) {
+    if ((threadIdx.x & 31) != 0) return;
+    double a[kChains];
+#pragma unroll
+    for (int j = 0; j < kChains; j++) a[j] = (double)(threadIdx.x + j) * 1e-3;
+    const double b = 0.999999, c = 1e-6;
+    for (int64_t i = 0; i < iters; i++) {
+#pragma unroll
+        for (int j = 0; j < kChains; j++) a[j] = fma(a[j], b, c);
+    }
+    double s = 0;
+#pragma unroll
+    for (int j = 0; j < kChains; j++) s += a[j];
+    if (s == -1.2345) out[0] = s;
+}
+
 __global__ void __launch_bounds__(kPT) k_dmma_chains(int64_t iters, double *__restrict__ out) {
     const int lane = threadIdx.x & 31;
     const double a = 1e-3 * (lane + 1), b = 1e-3 * (32 - lane);
@@ -57,7 +75,7 @@ __global__ void __launch_bounds__(kPT) k_dmma_chains(int64_t iters, double *__re
 extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *stream,
                                 double *flops) {
     using namespace scopf;
-    if (!out || iters <= 0 || kind < 0 || kind > 2) return SCOPF_ERR_INVALID_ARG;
+    if (!out || iters <= 0 || kind < 0 || kind > 3) return SCOPF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = sm_count() * (2048 / kPT);
     const double threads = (double)grid * kPT;
@@ -68,9 +86,12 @@ extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *
     } else if (kind == 1) {
         note_launch(), k_fma_chains<double><<<grid, kPT, 0, s>>>(iters, out);
         f = threads * kChains * 2.0 * (double)iters;
-    } else {
+    } else if (kind == 2) {
         note_launch(), k_dmma_chains<<<grid, kPT, 0, s>>>(iters, out);
         f = threads / 32.0 * kAcc * (8.0 * 8.0 * 4.0 * 2.0) * (double)iters;
+    } else {
+        note_launch(), k_fma_chains_one_lane<<<grid, kPT, 0, s>>>(iters, out);
+        f = threads / 32.0 * kChains * 2.0 * (double)iters;   // active lanes only
     }
     if (cudaGetLastError() != cudaSuccess) return SCOPF_ERR_CUDA;
     if (flops) *flops = f;

@@ -12,12 +12,13 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 
-def _case(inst, seed, rho, delta_w, mu=1e-2, lin=None, **opt):
+def _case(inst, seed, rho, delta_w, mu=1e-2, lin=None, lam_scale=1.0, **opt):
     import torch
     import paper_2510_13333_b300 as P
     M = SCOPFModel(inst)
     S = NCLSolver(M, lin or DenseSolver())
     st = H.random_interior_state(S, seed)
+    st.lam = st.lam * lam_scale   # large multipliers: negative curvature in H
     rng = np.random.default_rng(seed + 1)
     prm = Params(rho=rho, lam_n=rng.standard_normal(M.m) * 0.1, nu0_n=rng.random(M.p) * 0.1)
     lib = P.SCOPF(inst, **opt)
@@ -118,11 +119,12 @@ def test_condensed_factor_solve_matches_oracle(cuda, which, prec):
 
 
 def test_condensed_inertia_wrong_at_small_shift(cuda):
-    """delta_w = 0 at a random point: the condensed matrix is indefinite and
-    the dual-first factorization reports K's exact (Sylvester) inertia."""
+    """delta_w = 0 at a point with large multipliers (negative curvature):
+    the condensed matrix is indefinite and the dual-first factorization
+    reports K's exact (Sylvester) inertia."""
     inst = H.instance(0)
     M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(inst, 9, rho=1e2, delta_w=0.0,
-                                                            dual_first=1)
+                                                            lam_scale=30.0, dual_first=1)
     ev = np.linalg.eigvalsh(K_or.toarray())
     expect = (int((ev > 0).sum()), int((ev < 0).sum()), 0)
     assert expect != (M.n, M.m + M.p, 0)
