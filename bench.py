@@ -236,6 +236,44 @@ def np_mean(v):
     return sum(v) / len(v) if v else 0.0
 
 
+def oracle_tts_118():
+    """The oracle's own time to solution on the 118-bus x 32 workload (the
+    smallest block-arrow case; one host core): seconds, IPM iterations and
+    seconds per iteration of a full NCL solve at tol 1e-6."""
+    import synthgrid
+    from oracle.linsolve import SparseLDLSolver
+    from oracle.ncl import NCLSolver
+    from oracle.scopf_model import SCOPFModel
+    from oracle import symbolic
+    inst = synthgrid.config_instance(1)
+    with one_blas_thread():
+        t0 = time.perf_counter()
+        M = SCOPFModel(inst)
+        perm, _ = symbolic.kkt_permutation(M)
+        t1 = time.perf_counter()
+        r = NCLSolver(M, SparseLDLSolver(perm_fn=lambda K: perm)).solve()
+        t2 = time.perf_counter()
+    return {"seconds": t2 - t1, "setup_s": t1 - t0, "status": r.status,
+            "inner_iters": r.inner_iters, "s_per_iter": (t2 - t1) / max(1, r.inner_iters),
+            "objective": r.objective, "cores": 1}
+
+
+def gpu_tts_118(P, torch, precision):
+    """The library's time to solution on the same 118-bus x 32 workload
+    (latency-bound: 48k KKT rows)."""
+    import synthgrid
+    lib = P.SCOPF(synthgrid.config_instance(1), precision=precision)
+    lib.ncl_solve()   # warm-up (graphs, caches)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = lib.ncl_solve()
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"seconds": dt, "status": r["call_status"], "inner_iters": r["inner_iters"],
+            "ms_per_iter": 1e3 * dt / max(1, r["inner_iters"]), "objective": r["objective"],
+            "factorizations": r["factorizations"]}
+
+
 def oracle_step_sample(n_steps: int = 3, idx: int = CONFIG_IDX):
     """The cpu_baseline leg: n_steps oracle Newton steps of the bounded
     sample; returns (seconds per full-size step extrapolated in blocks,
@@ -434,6 +472,9 @@ def run_ours(args):
                      "outer_iters": r["outer_iters"], "factorizations": r["factorizations"],
                      "fp64_fallbacks": r["fp64_fallbacks"], "max_violation": r["max_violation"],
                      "kkt_error": r["kkt_error"]}
+    if idx == CONFIG_IDX and args.tts != "none":
+        tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
+                             "fp64": gpu_tts_118(P, torch, P.PREC_FP64)}
     # ---- a mid-solve iterate: the state after a fixed number of IPM iterations
     lib.set_precision(P.PREC_MIXED)
     lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at,
@@ -566,6 +607,8 @@ def run_ours(args):
         cpu_s, cpu_desc, cores = oracle_step_sample(idx=idx)
         cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
                "sample": cpu_desc}
+        if idx == CONFIG_IDX:
+            cpu["tts_118bus_k32"] = oracle_tts_118()
     except Exception as exc:  # keep the GPU number even if the CPU sample fails
         cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                "sample": f"failed: {exc}"}

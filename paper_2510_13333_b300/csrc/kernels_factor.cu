@@ -247,21 +247,6 @@ __device__ __forceinline__ ChildInfo child_info(const DevFront &F, int q) {
     return c;
 }
 
-// 1 / d of a pivot, for a whole warp (all 32 lanes call it with the same d):
-// in FP64 one lane divides and the others receive the quotient by shuffle --
-// FP64 division is a sequence of double-precision instructions and the FP64
-// pipe is narrow, so 32 redundant divisions per pivot cost as much as the
-// pivot's updates.  A zero pivot is replaced by a tiny one (it is counted as
-// zero by the caller).
-template <typename T>
-__device__ __forceinline__ T pivot_inverse(T d) {
-    const T dd = d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d;
-    if (sizeof(T) == 4) return (T)1 / dd;
-    T v = (T)0;
-    if ((threadIdx.x & 31) == 0) v = (T)1 / dd;
-    return __shfl_sync(0xffffffffu, v, 0);
-}
-
 // Extend-add the children's update blocks into the front, then eliminate
 // its np pivot columns without pivoting: panel factorization (rank-1 updates
 // restricted to the np panel columns) followed by one pass of the trailing
@@ -300,7 +285,7 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
             else if (dd < -pivot_tol) n_neg++;
             else n_zero++;
         }
-        const T dinv = pivot_inverse<T>(d);
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
         for (int i = c + 1 + tid; i < f; i += GS) colc[i] *= dinv;
         gsync<GS>();
         for (int j = c + 1; j < np; j++) {
@@ -449,7 +434,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
             else if (dd < -pivot_tol) n_neg++;
             else n_zero++;
         }
-        const T dinv = pivot_inverse<T>(d);
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
         if (sizeof(T) == 8) {
             if (lane > c && lane < f) tile[lane][c] *= dinv;
             __syncwarp();
@@ -537,7 +522,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
             else if (dd < -pivot_tol) n_neg++;
             else n_zero++;
         }
-        const T dinv = pivot_inverse<T>(d);
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
         if (sizeof(T) == 8) {
             // FP64 runs at a fraction of the FP32 rate: lanes take rows j, j+1, ...
             // of each updated column, so no instruction carries the idle rows
@@ -750,7 +735,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
             else if (dd < -pivot_tol) n_neg++;
             else n_zero++;
         }
-        const T dinv = pivot_inverse<T>(d);
+        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
         for (int i = c + 1 + tid; i < f; i += kBT) colc[i] *= dinv;
         __syncthreads();
         for (int j = c + 1 + warp; j < np; j += nw) {
