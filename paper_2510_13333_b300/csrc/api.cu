@@ -246,8 +246,11 @@ int setup_device(scopf_handle *h) {
     F.scale = h->scale;
     {
         double *ov = nullptr;
-        TRY(alloc(h, HF.orig_nz.size(), &ov));
+        TRY(alloc(h, HF.orig_nz.size(), &ov));   // sized for FP64; FP32 uses half
         F.ovals = ov;
+        double *xsb = nullptr;
+        TRY(alloc(h, (size_t)M.n_kkt, &xsb));
+        F.xs = xsb;
         h->ovals = ov;
         F.n_orig = (int64_t)HF.orig_nz.size();
     }
@@ -823,7 +826,7 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
     h->timer.begin(PH_FRONT_INIT, s);
     launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, h->ruiz_mx, 3, s);
-    launch_orig_vals(h->df, h->ovals, s);
+    launch_orig_vals<T>(h->df, reinterpret_cast<T *>(h->ovals), s);
     h->timer.end(PH_FRONT_INIT, s);
     h->timer.begin(PH_FACTOR, s);
     launch_factor<T>(h->df, fr, h->fstat, h->opt.pivot_tol, h->opt.spin_limit, s);

@@ -180,7 +180,11 @@ struct DevFront {
     const int64_t *kkt_col;
     const double *kval;           // assembled K (set before each factorization)
     const double *scale;          // Ruiz scaling
-    const double *ovals;          // scaled original entries in task order (n_orig)
+    const void *ovals;            // scaled original entries in task order (n_orig), in the
+                                  // factor precision (float or double)
+    void *xs;                     // per KKT row: the scaled solution in the factor
+                                  // precision, written by the backward sweep and border
+                                  // solve, read by the fronts whose update rows hold it
     int64_t n_orig;
     // work items: item i is tasks [item_ptr[i], item_ptr[i+1]) in postorder
     // (a subtree of small fronts, or one front).  Factorization phases:
@@ -216,7 +220,8 @@ struct DevFront {
     const int32_t *nchild;        // child items per item
 };
 // ovals[p] = scale[i] K_ij scale[j] for the p-th original front entry
-void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s);
+template <typename T>
+void launch_orig_vals(const DevFront &F, T *ovals, cudaStream_t s);
 
 struct FactorStatus {             // device-side counters
     int n_pos, n_neg, n_zero, error, timeout_task;

@@ -255,13 +255,14 @@ __device__ __forceinline__ ChildInfo child_info(const DevFront &F, int q) {
 template <typename T, int GS>
 __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                 int tid, double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    const T ptol = (T)pivot_tol;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f;
     const int np = ti.np;
     // the front's own original entries (scaled), zeros elsewhere
     for (int e = tid; e < f * f; e += GS) Fr[e] = (T)0;
     gsync<GS>();
-    for (int q = ti.o0 + tid; q < ti.o1; q += GS) Fr[F.orig_off[q]] = (T)F.ovals[q];
+    for (int q = ti.o0 + tid; q < ti.o1; q += GS) Fr[F.orig_off[q]] = static_cast<const T *>(F.ovals)[q];
     gsync<GS>();
     for (int ci = ti.c0; ci < ti.c1; ci++) {
         const ChildInfo c = child_info(F, ci);
@@ -280,9 +281,9 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
         T *colc = Fr + (int64_t)c * f;
         const T d = colc[c];
         if (tid == 0) {
-            const double dd = (double)d;
-            if (dd > pivot_tol) n_pos++;
-            else if (dd < -pivot_tol) n_neg++;
+            // counted in the factor precision (no FP64 instructions in FP32 fronts)
+            if (d > ptol) n_pos++;
+            else if (d < -ptol) n_neg++;
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
@@ -392,6 +393,7 @@ template <typename T>
 __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                      int lane, T (*tile)[33], double pivot_tol, int &n_pos,
                                      int &n_neg, int &n_zero) {
+    const T ptol = (T)pivot_tol;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f;
     const int np = ti.np;
@@ -400,7 +402,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
     for (int q = ti.o0 + lane; q < ti.o1; q += 32) {
         const int off = F.orig_off[q];
         const int col = off / f, row = off - col * f;
-        tile[row][col] = (T)F.ovals[q];
+        tile[row][col] = static_cast<const T *>(F.ovals)[q];
     }
     __syncwarp();
     for (int ci = ti.c0; ci < ti.c1; ci++) {
@@ -429,9 +431,9 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
     for (int c = 0; c < np; c++) {
         const T d = tile[c][c];
         if (lane == 0) {
-            const double dd = (double)d;
-            if (dd > pivot_tol) n_pos++;
-            else if (dd < -pivot_tol) n_neg++;
+            // counted in the factor precision (no FP64 instructions in FP32 fronts)
+            if (d > ptol) n_pos++;
+            else if (d < -ptol) n_neg++;
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
@@ -471,6 +473,7 @@ template <typename T>
 __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts,
                                        const TaskInfo &ti, int lane, T (*M)[kMedF + 1],
                                        double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    const T ptol = (T)pivot_tol;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f, np = ti.np;
     const int i0 = lane, i1 = lane + 32;
@@ -482,7 +485,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
     for (int q = ti.o0 + lane; q < ti.o1; q += 32) {
         const int off = F.orig_off[q];
         const int col = off / f, row = off - col * f;
-        M[row][col] = (T)F.ovals[q];
+        M[row][col] = static_cast<const T *>(F.ovals)[q];
     }
     __syncwarp();
     for (int ci = ti.c0; ci < ti.c1; ci++) {
@@ -517,9 +520,9 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
     for (int c = 0; c < np; c++) {
         const T d = M[c][c];
         if (lane == 0) {
-            const double dd = (double)d;
-            if (dd > pivot_tol) n_pos++;
-            else if (dd < -pivot_tol) n_neg++;
+            // counted in the factor precision (no FP64 instructions in FP32 fronts)
+            if (d > ptol) n_pos++;
+            else if (d < -ptol) n_neg++;
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
@@ -668,6 +671,7 @@ __host__ __device__ constexpr size_t big_rel_offset(int big_panel, int big_np) {
 template <typename T>
 __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                     double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
+    const T ptol = (T)pivot_tol;
     extern __shared__ unsigned char big_smem[];
     T *P = reinterpret_cast<T *>(big_smem);   // P[c * f + i]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBT >> 5;
@@ -677,7 +681,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
     const int np = ti.np;
     for (int e = tid; e < f * f; e += kBT) Fr[e] = (T)0;
     __syncthreads();
-    for (int q = ti.o0 + tid; q < ti.o1; q += kBT) Fr[F.orig_off[q]] = (T)F.ovals[q];
+    for (int q = ti.o0 + tid; q < ti.o1; q += kBT) Fr[F.orig_off[q]] = static_cast<const T *>(F.ovals)[q];
     __syncthreads();
     // children's update blocks: the child->parent map is staged in shared
     // memory, and each warp pass takes two columns with up to kEA row chunks
@@ -730,9 +734,9 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
         T *colc = P + c * f;
         const T d = colc[c];
         if (tid == 0) {
-            const double dd = (double)d;
-            if (dd > pivot_tol) n_pos++;
-            else if (dd < -pivot_tol) n_neg++;
+            // counted in the factor precision (no FP64 instructions in FP32 fronts)
+            if (d > ptol) n_pos++;
+            else if (d < -ptol) n_neg++;
             else n_zero++;
         }
         const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
@@ -978,14 +982,31 @@ __global__ void __launch_bounds__(kDT) k_dense_ldlt(double *S, int n, FactorStat
                 Wj[c][r] = (ok && j0 + r < n) ? S[(int64_t)(k0 + c) * n + j0 + r] * A11[c][c] : 0.0;
             }
             __syncthreads();
-            const int tx = lane, ty = warp;   // 32 x 8
-            for (int r = ty; r < 32; r += 8) {
-                const int i = i0 + tx, j = j0 + r;
-                if (i >= n || j >= n || i < j) continue;
-                double acc = 0.0;
+            // U -= L21 W' on the FP64 tensor pipe: the 32 x 32 tile is sixteen
+            // 8 x 8 blocks, two per warp, each a chain of mma.m8n8k4 over the
+            // panel's (zero-padded) kDB columns.  Fragments (PTX ISA, .f64
+            // m8n8k4): A row = lane / 4, col = lane % 4; B row = lane % 4,
+            // col = lane / 4; D row = lane / 4, cols 2 (lane % 4) + {0, 1}.
+            const int g = lane >> 2, q = lane & 3;
+            const int bi = warp >> 1;
 #pragma unroll
-                for (int c = 0; c < kDB; c++) acc += Li[c][tx] * Wj[c][r];
-                S[(int64_t)j * n + i] -= acc;
+            for (int h = 0; h < 2; h++) {
+                const int bj = 2 * (warp & 1) + h;
+                double d0 = 0.0, d1 = 0.0;
+#pragma unroll
+                for (int kk = 0; kk < kDB; kk += 4) {
+                    const double a = Li[kk + q][8 * bi + g];
+                    const double b = Wj[kk + q][8 * bj + g];
+                    asm volatile(
+                        "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, "
+                        "{%0, %1};"
+                        : "+d"(d0), "+d"(d1)
+                        : "d"(a), "d"(b));
+                }
+                const int i = i0 + 8 * bi + g;
+                const int j = j0 + 8 * bj + 2 * q;
+                if (i < n && j < n && i >= j) S[(int64_t)j * n + i] -= d0;
+                if (i < n && j + 1 < n && i >= j + 1) S[(int64_t)(j + 1) * n + i] -= d1;
             }
         }
         if (!dense_grid_barrier(st, spin_limit)) break;
@@ -1260,6 +1281,7 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
             for (int k = 0; k < n; k++) acc += Sinv[(int64_t)k * n + j] * sm[k];
             const int64_t r = F.border_rows[j];
             x[r] = scale[r] * acc;
+            static_cast<T *>(F.xs)[r] = (T)acc;
         }
         return;
     }
@@ -1267,6 +1289,7 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
     for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
         x[r] = scale[r] * y[j];
+        static_cast<T *>(F.xs)[r] = (T)y[j];
     }
 }
 
@@ -1290,7 +1313,8 @@ template <typename T, int FB>
 __device__ __forceinline__ void bwd_small(const T *__restrict__ L, const T *__restrict__ v,
                                           const int64_t *__restrict__ rows,
                                           const double *__restrict__ scale,
-                                          double *__restrict__ x, int f, int np, int lane) {
+                                          double *__restrict__ x, T *__restrict__ xs, int f,
+                                          int np, int lane) {
     T Lc[FB];
 #pragma unroll
     for (int i = 0; i < FB; i++)
@@ -1301,7 +1325,7 @@ __device__ __forceinline__ void bwd_small(const T *__restrict__ L, const T *__re
     if (lane < np)
         z = v[lane];
     else if (lane < f)
-        z = (T)(x[r] / scale[r]);
+        z = xs[r];   // the scaled solution, written by the row's pivot owner
     T acc = (T)0;
 #pragma unroll
     for (int i = FB - 1; i >= 0; i--) {
@@ -1311,7 +1335,10 @@ __device__ __forceinline__ void bwd_small(const T *__restrict__ L, const T *__re
             acc += Lc[i] * zi;
         }
     }
-    if (lane < np) x[r] = scale[r] * (double)z;
+    if (lane < np) {
+        x[r] = scale[r] * (double)z;
+        xs[r] = z;
+    }
 }
 
 // Backward sweep of one (non-border) front: its update rows hold the final
@@ -1325,11 +1352,12 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
     const T *L = fronts + ti.front_off;
     T *v = vec + ti.vo;
     const int64_t *rows = F.rows + ti.vo;
+    T *xs = static_cast<T *>(F.xs);
     if (f <= 32) {
         if (f <= 16)
-            bwd_small<T, 16>(L, v, rows, scale, x, f, np, lane);
+            bwd_small<T, 16>(L, v, rows, scale, x, xs, f, np, lane);
         else
-            bwd_small<T, 32>(L, v, rows, scale, x, f, np, lane);
+            bwd_small<T, 32>(L, v, rows, scale, x, xs, f, np, lane);
         return;
     }
     // f > 32: stage [y (pivots); x (update rows)] in the warp's shared
@@ -1340,8 +1368,7 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
         if (i < np) {
             sv[i] = v[i];
         } else {
-            const int64_t r = rows[i];
-            sv[i] = (T)(x[r] / scale[r]);
+            sv[i] = xs[rows[i]];
         }
     }
     __syncwarp();
@@ -1400,6 +1427,7 @@ __device__ __forceinline__ void bwd_front(const DevFront &F, const T *__restrict
     for (int c = lane; c < np; c += 32) {
         const int64_t r = rows[c];
         x[r] = scale[r] * (double)sv[c];
+        xs[r] = sv[c];
     }
 }
 
@@ -1526,14 +1554,15 @@ __global__ void k_ruiz_finish(int64_t n, const double *__restrict__ s_in, double
 }
 
 // scaled original entries of every front, in task order
+template <typename T>
 __global__ void k_orig_vals(int64_t n_orig, const int64_t *__restrict__ nz,
                             const int32_t *__restrict__ row, const int64_t *__restrict__ col,
                             const double *__restrict__ scale, const double *__restrict__ kval,
-                            double *__restrict__ ovals) {
+                            T *__restrict__ ovals) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_orig) return;
     const int64_t q = nz[p];
-    ovals[p] = scale[row[q]] * kval[q] * scale[col[q]];
+    ovals[p] = (T)(scale[row[q]] * kval[q] * scale[col[q]]);
 }
 
 __global__ void k_fill(int64_t n, double v, double *x) {
@@ -1568,12 +1597,15 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     if (a != scale) cudaMemcpyAsync(scale, a, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
 }
 
-void launch_orig_vals(const DevFront &F, double *ovals, cudaStream_t s) {
+template <typename T>
+void launch_orig_vals(const DevFront &F, T *ovals, cudaStream_t s) {
     const int t = 256;
     if (F.n_orig > 0)
-        note_launch(), k_orig_vals<<<(int)((F.n_orig + t - 1) / t), t, 0, s>>>(F.n_orig, F.orig_nz, F.kkt_row,
-                                                               F.kkt_col, F.scale, F.kval, ovals);
+        note_launch(), k_orig_vals<T><<<(int)((F.n_orig + t - 1) / t), t, 0, s>>>(
+            F.n_orig, F.orig_nz, F.kkt_row, F.kkt_col, F.scale, F.kval, ovals);
 }
+template void launch_orig_vals<float>(const DevFront &, float *, cudaStream_t);
+template void launch_orig_vals<double>(const DevFront &, double *, cudaStream_t);
 
 void launch_queue_reset(const DevFront &F, QueueSeeds seeds, const int32_t *pend, cudaStream_t s) {
     const int t = 256;
