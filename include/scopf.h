@@ -357,6 +357,13 @@ int scopf_autotune(const scopf_network *net, const scopf_contingency *ctg, int32
                    scopf_options *opt, int32_t iterate_at, int32_t steps, int32_t capacity,
                    scopf_tune_entry *entries, int32_t *n_entries);
 
+/* The reciprocal the FP64 block factorization takes of its pivots (Newton's
+ * method from a single-precision seed, within one unit in the last place of
+ * 1/d), exposed so that it can be checked against the quotient: out[i] =
+ * 1 / d[i] for n device values (stream-ordered, no synchronisation).  Not a
+ * step of the paper's method. */
+int scopf_pivot_reciprocal(const double *d, double *out, int64_t n, void *stream);
+
 /* Full NCL solve (Section IV-A) from the flat start, or from warm (device
  * state, may be NULL).  The final iterate stays in the handle. */
 int ncl_solve(scopf_handle *h, const scopf_state *warm, scopf_result *res);

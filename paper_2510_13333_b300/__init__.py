@@ -165,6 +165,7 @@ def lib():
             "scopf_dense_ldlt_solve_noalloc": (c_i32, [P_dbl, c_i32, P_dbl, P_dbl, P_i32,
                                                        ctypes.c_void_p]),
             "scopf_peak_probe": (c_i32, [c_i32, c_i64, P_dbl, ctypes.c_void_p, P_dbl]),
+            "scopf_pivot_reciprocal": (c_i32, [P_dbl, P_dbl, c_i64, ctypes.c_void_p]),
             "scopf_autotune": (c_i32, [ctypes.POINTER(Network), ctypes.POINTER(Contingency),
                                        c_i32, ctypes.POINTER(Options), c_i32, c_i32, c_i32,
                                        ctypes.POINTER(TuneEntry), P_i32]),
@@ -244,6 +245,16 @@ def scopf_peak_probe(kind: int, iters: int = 1 << 14, repeats: int = 5):
             t = fl.value / (e0.elapsed_time(e1) / 1e3) / 1e12
             best = t if best is None else max(best, t)
     return best
+
+
+def scopf_pivot_reciprocal(d):
+    """The FP64 factorization's pivot reciprocal of every entry of d (torch
+    float64 CUDA tensor); returns a new tensor."""
+    import torch
+    out = torch.empty_like(d)
+    _check("scopf_pivot_reciprocal", lib().scopf_pivot_reciprocal(
+        _dp(d), _dp(out), d.numel(), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)))
+    return out
 
 
 def default_options(**kw) -> Options:

@@ -138,6 +138,8 @@ void launch_gmres_column(double *st, int m, int j, cudaStream_t s);
 void launch_gmres_solve(double *st, int m, int k, cudaStream_t s);
 // base[i] = kval[pos[i]];  kval[pos[i]] = base[i] + shift
 int sm_count();   // SMs of the current device
+// out[i] = the FP64 pivot reciprocal the factorization uses, of d[i]
+int launch_reciprocal(int64_t n, const double *d, double *out, cudaStream_t s);
 void launch_count_zero_diag(int64_t n, const int64_t *idx, const double *base, int *count,
                             cudaStream_t s);
 void launch_diag_gather(int64_t n, const int64_t *pos, const double *kval, double *base,

@@ -247,6 +247,47 @@ __device__ __forceinline__ ChildInfo child_info(const DevFront &F, int q) {
     return c;
 }
 
+// 1 / d in FP64 by Newton's method for the reciprocal, x <- x (2 - d x) in FMA
+// form, two steps from a single-precision seed: the hardware reciprocal of
+// d's leading 24 mantissa bits, with d's exponent handled in integer
+// arithmetic.  A 2^-23 seed becomes 2^-46 and then exact to rounding: the
+// result is within one unit in the last place of the quotient (tested against
+// 1.0 / d).  It costs four FP64 instructions, fewer than a full-precision
+// division; B300's FP64 pipe charges every warp instruction in full, and the
+// pivots' divisions were a large share of the FP64 factorization's
+// instructions.  Exponents outside single range (zero, subnormal, huge or
+// non-finite d) take the plain division.
+__device__ __forceinline__ double rcp_newton(double d) {
+    const int hi = __double2hiint(d), lo = __double2loint(d);
+    const int e = ((hi >> 20) & 0x7ff) - 1023;
+    if (e < -126 || e > 126) return 1.0 / d;
+    const unsigned m23 = ((unsigned)(hi & 0xfffff) << 3) | ((unsigned)lo >> 29);
+    const float y = __frcp_rn(__uint_as_float(0x3f800000u | m23));   // in (0.5, 1]
+    const unsigned fy = __float_as_uint(y);
+    const int ey = (int)((fy >> 23) & 0xff) - 127;
+    const unsigned my = fy & 0x7fffffu;
+    const int rhi = (int)((unsigned)hi & 0x80000000u) | ((ey - e + 1023) << 20) | (int)(my >> 3);
+    double r = __hiloint2double(rhi, (int)((my & 7u) << 29));
+    double t = fma(-d, r, 1.0);
+    r = fma(r, t, r);
+    t = fma(-d, r, 1.0);
+    return fma(r, t, r);
+}
+
+// the reciprocal of a pivot (a zero pivot is replaced by a tiny one; it is
+// counted as zero by the caller)
+template <typename T>
+__device__ __forceinline__ T pivot_reciprocal(T d) {
+    const T dd = d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d;
+    if constexpr (sizeof(T) == 4) return (T)1 / dd;
+    else return rcp_newton(dd);
+}
+
+__global__ void k_reciprocal(int64_t n, const double *__restrict__ d, double *__restrict__ out) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) out[i] = rcp_newton(d[i]);
+}
+
 // Extend-add the children's update blocks into the front, then eliminate
 // its np pivot columns without pivoting: panel factorization (rank-1 updates
 // restricted to the np panel columns) followed by one pass of the trailing
@@ -286,7 +327,7 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
             else if (d < -ptol) n_neg++;
             else n_zero++;
         }
-        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        const T dinv = pivot_reciprocal<T>(d);
         for (int i = c + 1 + tid; i < f; i += GS) colc[i] *= dinv;
         gsync<GS>();
         for (int j = c + 1; j < np; j++) {
@@ -436,7 +477,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
             else if (d < -ptol) n_neg++;
             else n_zero++;
         }
-        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        const T dinv = pivot_reciprocal<T>(d);
         if (sizeof(T) == 8) {
             if (lane > c && lane < f) tile[lane][c] *= dinv;
             __syncwarp();
@@ -525,7 +566,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
             else if (d < -ptol) n_neg++;
             else n_zero++;
         }
-        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        const T dinv = pivot_reciprocal<T>(d);
         if (sizeof(T) == 8) {
             // FP64 runs at a fraction of the FP32 rate: lanes take rows j, j+1, ...
             // of each updated column, so no instruction carries the idle rows
@@ -739,7 +780,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
             else if (d < -ptol) n_neg++;
             else n_zero++;
         }
-        const T dinv = (T)1 / (d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d);
+        const T dinv = pivot_reciprocal<T>(d);
         for (int i = c + 1 + tid; i < f; i += kBT) colc[i] *= dinv;
         __syncthreads();
         for (int j = c + 1 + warp; j < np; j += nw) {
@@ -1711,6 +1752,11 @@ void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_
     const int nb = F.n_border;
     if (nb == 0) return;
     note_launch(), k_schur_sum<T><<<(nb * nb + 255) / 256, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
+}
+
+int launch_reciprocal(int64_t n, const double *d, double *out, cudaStream_t s) {
+    if (n > 0) note_launch(), k_reciprocal<<<(int)((n + 255) / 256), 256, 0, s>>>(n, d, out);
+    return cudaGetLastError() == cudaSuccess ? 0 : -1;
 }
 
 void launch_dense_inverse(const double *S, int n, double *Sinv, cudaStream_t s) {

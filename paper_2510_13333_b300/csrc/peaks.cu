@@ -97,3 +97,9 @@ extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *
     if (flops) *flops = f;
     return SCOPF_OK;
 }
+
+extern "C" int scopf_pivot_reciprocal(const double *d, double *out, int64_t n, void *stream) {
+    if (n < 0 || (n > 0 && (!d || !out))) return SCOPF_ERR_INVALID_ARG;
+    return scopf::launch_reciprocal(n, d, out, (cudaStream_t)stream) == 0 ? SCOPF_OK
+                                                                          : SCOPF_ERR_CUDA;
+}
