@@ -274,6 +274,27 @@ __device__ __forceinline__ double rcp_newton(double d) {
     return fma(r, t, r);
 }
 
+// Inertia count of one pivot.  With a zero tolerance an FP64 pivot is
+// classified from its bit pattern (integer instructions: the FP64 pipe is the
+// scarce one); zero and NaN count as zero pivots.
+template <typename T>
+__device__ __forceinline__ void count_pivot(T d, T ptol, bool ptol_zero, int &n_pos, int &n_neg,
+                                            int &n_zero) {
+    if constexpr (sizeof(T) == 8) {
+        if (ptol_zero) {
+            const long long b = __double_as_longlong(d);
+            const long long a = b & 0x7fffffffffffffffLL;
+            if (a == 0 || a > 0x7ff0000000000000LL) n_zero++;
+            else if (b > 0) n_pos++;
+            else n_neg++;
+            return;
+        }
+    }
+    if (d > ptol) n_pos++;
+    else if (d < -ptol) n_neg++;
+    else n_zero++;
+}
+
 // the reciprocal of a pivot (a zero pivot is replaced by a tiny one; it is
 // counted as zero by the caller)
 template <typename T>
@@ -297,6 +318,7 @@ template <typename T, int GS>
 __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                 int tid, double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
     const T ptol = (T)pivot_tol;
+    const bool ptol_zero = pivot_tol == 0.0;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f;
     const int np = ti.np;
@@ -323,9 +345,7 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
         const T d = colc[c];
         if (tid == 0) {
             // counted in the factor precision (no FP64 instructions in FP32 fronts)
-            if (d > ptol) n_pos++;
-            else if (d < -ptol) n_neg++;
-            else n_zero++;
+            count_pivot<T>(d, ptol, ptol_zero, n_pos, n_neg, n_zero);
         }
         const T dinv = pivot_reciprocal<T>(d);
         for (int i = c + 1 + tid; i < f; i += GS) colc[i] *= dinv;
@@ -362,8 +382,8 @@ __device__ void eliminate_front(const DevFront &F, T *__restrict__ fronts, const
 // so every issued FP64 multiply-add updates an entry (the row-per-lane form
 // idles the lanes above each column's diagonal).  Column c holds l = L[., c]
 // (already divided by d) and row c of the unused upper triangle holds
-// l_j d for the panel columns (one multiply per column, not per entry); the
-// update is M[i][j] -= l_i (l_j d).
+// l_j d for the panel columns (column c before it was scaled); the update is
+// M[i][j] -= l_i (l_j d).
 template <typename T, int S>
 __device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, int c, int lane) {
     const int j0 = c + 1, ncol = np - j0, L0 = f - j0;
@@ -393,10 +413,13 @@ template <typename T, int S, int R>
 __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int lane) {
     const int m = f - np;
     if (np == 0 || m <= 0) return;
-    for (int c = 0; c < np; c++) {
-        const T d = tile[c][c];
-        for (int j = np + lane; j < f; j += 32) tile[c][j] = tile[j][c] * d;
-    }
+    // W = L D in the upper triangle: FP64 panels stored it at each pivot (the
+    // column before scaling), FP32 ones form it here
+    if (sizeof(T) == 4)
+        for (int c = 0; c < np; c++) {
+            const T d = tile[c][c];
+            for (int j = np + lane; j < f; j += 32) tile[c][j] = tile[j][c] * d;
+        }
     __syncwarp();
     for (int k = 0; 2 * k < m; k++) {
         const int a = np + k, la = m - k, b = f - 1 - k;
@@ -435,6 +458,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
                                      int lane, T (*tile)[33], double pivot_tol, int &n_pos,
                                      int &n_neg, int &n_zero) {
     const T ptol = (T)pivot_tol;
+    const bool ptol_zero = pivot_tol == 0.0;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f;
     const int np = ti.np;
@@ -473,15 +497,18 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         const T d = tile[c][c];
         if (lane == 0) {
             // counted in the factor precision (no FP64 instructions in FP32 fronts)
-            if (d > ptol) n_pos++;
-            else if (d < -ptol) n_neg++;
-            else n_zero++;
+            count_pivot<T>(d, ptol, ptol_zero, n_pos, n_neg, n_zero);
         }
         const T dinv = pivot_reciprocal<T>(d);
         if (sizeof(T) == 8) {
-            if (lane > c && lane < f) tile[lane][c] *= dinv;
-            __syncwarp();
-            if (lane > c && lane < np) tile[c][lane] = tile[lane][c] * d;
+            // column c before scaling is l d: kept in the unused upper
+            // triangle for the panel update and as W = L D for the trailing
+            // update (no multiply), then scaled to l
+            if (lane > c && lane < f) {
+                const T a = tile[lane][c];
+                tile[c][lane] = a;
+                tile[lane][c] = a * dinv;
+            }
             __syncwarp();
             panel_update_packed<T, 33>(tile, f, np, c, lane);
             __syncwarp();
@@ -515,6 +542,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
                                        const TaskInfo &ti, int lane, T (*M)[kMedF + 1],
                                        double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
     const T ptol = (T)pivot_tol;
+    const bool ptol_zero = pivot_tol == 0.0;
     T *Fr = fronts + ti.front_off;
     const int f = ti.f, np = ti.np;
     const int i0 = lane, i1 = lane + 32;
@@ -562,19 +590,20 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
         const T d = M[c][c];
         if (lane == 0) {
             // counted in the factor precision (no FP64 instructions in FP32 fronts)
-            if (d > ptol) n_pos++;
-            else if (d < -ptol) n_neg++;
-            else n_zero++;
+            count_pivot<T>(d, ptol, ptol_zero, n_pos, n_neg, n_zero);
         }
         const T dinv = pivot_reciprocal<T>(d);
         if (sizeof(T) == 8) {
             // FP64 runs at a fraction of the FP32 rate: lanes take rows j, j+1, ...
             // of each updated column, so no instruction carries the idle rows
             // above the diagonal (one or two chunks of 32 per column)
-            for (int i = c + 1 + lane; i < f; i += 32) M[i][c] *= dinv;
-            __syncwarp();
-            // l_j d once per panel column, kept in the unused upper triangle
-            for (int j = c + 1 + lane; j < np; j += 32) M[c][j] = M[j][c] * d;
+            // column c before scaling (l d) into the unused upper triangle:
+            // the panel update's l_j d and the trailing update's W = L D
+            for (int i = c + 1 + lane; i < f; i += 32) {
+                const T a = M[i][c];
+                M[c][i] = a;
+                M[i][c] = a * dinv;
+            }
             __syncwarp();
             for (int j = c + 1; j < np; j++) {   // panel columns only
                 const T lj = M[c][j];
@@ -713,6 +742,7 @@ template <typename T>
 __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, const TaskInfo &ti,
                                     double pivot_tol, int &n_pos, int &n_neg, int &n_zero) {
     const T ptol = (T)pivot_tol;
+    const bool ptol_zero = pivot_tol == 0.0;
     extern __shared__ unsigned char big_smem[];
     T *P = reinterpret_cast<T *>(big_smem);   // P[c * f + i]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = kBT >> 5;
@@ -776,9 +806,7 @@ __device__ void eliminate_front_big(const DevFront &F, T *__restrict__ fronts, c
         const T d = colc[c];
         if (tid == 0) {
             // counted in the factor precision (no FP64 instructions in FP32 fronts)
-            if (d > ptol) n_pos++;
-            else if (d < -ptol) n_neg++;
-            else n_zero++;
+            count_pivot<T>(d, ptol, ptol_zero, n_pos, n_neg, n_zero);
         }
         const T dinv = pivot_reciprocal<T>(d);
         for (int i = c + 1 + tid; i < f; i += kBT) colc[i] *= dinv;
