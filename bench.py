@@ -265,13 +265,17 @@ def gpu_tts_118(P, torch, precision):
     lib = P.SCOPF(synthgrid.config_instance(1), precision=precision)
     lib.ncl_solve()   # warm-up (graphs, caches)
     torch.cuda.synchronize()
+    n0 = P.scopf_launch_count()
     t0 = time.perf_counter()
     r = lib.ncl_solve()
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    launches = P.scopf_launch_count() - n0
     return {"seconds": dt, "status": r["call_status"], "inner_iters": r["inner_iters"],
             "ms_per_iter": 1e3 * dt / max(1, r["inner_iters"]), "objective": r["objective"],
-            "factorizations": r["factorizations"]}
+            "factorizations": r["factorizations"],
+            "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"]),
+            "launches_per_iter": launches / max(1, r["inner_iters"])}
 
 
 def oracle_step_sample(n_steps: int = 3, idx: int = CONFIG_IDX):
@@ -471,7 +475,8 @@ def run_ours(args):
                      "objective": r["objective"], "inner_iters": r["inner_iters"],
                      "outer_iters": r["outer_iters"], "factorizations": r["factorizations"],
                      "fp64_fallbacks": r["fp64_fallbacks"], "max_violation": r["max_violation"],
-                     "kkt_error": r["kkt_error"]}
+                     "kkt_error": r["kkt_error"], "feas_rt": r["feas_rt"],
+                     "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"])}
     if idx == CONFIG_IDX and args.tts != "none":
         tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
                              "fp64": gpu_tts_118(P, torch, P.PREC_FP64)}

@@ -180,6 +180,9 @@ typedef struct {
     double objective, kkt_error, feas_rt, max_violation, rho, mu;
     double time_total_s, time_newton_s;
     double delta_w_last;      /* last nonzero inertia-correction delta_w */
+    int64_t host_round_trips; /* stream synchronisations the host waited on
+                                 (reductions read back, inertia, refinement
+                                 cycles, line-search trials) during the solve */
 } scopf_result;
 
 void scopf_default_options(scopf_options *opt);

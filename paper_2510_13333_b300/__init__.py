@@ -93,7 +93,8 @@ class Result(ctypes.Structure):
                 ("factorizations", c_i32), ("refine_steps", c_i32), ("fp64_fallbacks", c_i32),
                 ("objective", c_dbl), ("kkt_error", c_dbl), ("feas_rt", c_dbl),
                 ("max_violation", c_dbl), ("rho", c_dbl), ("mu", c_dbl),
-                ("time_total_s", c_dbl), ("time_newton_s", c_dbl), ("delta_w_last", c_dbl)]
+                ("time_total_s", c_dbl), ("time_newton_s", c_dbl), ("delta_w_last", c_dbl),
+                ("host_round_trips", c_i64)]
 
 
 _LIB = None

@@ -573,7 +573,7 @@ int scopf_eval(scopf_handle *h, const double *w, double *obj, double *g, double 
     if (obj) {
         std::vector<double> p0(M.ng);
         CK(cudaMemcpyAsync(p0.data(), w + M.border0, sizeof(double) * M.ng, cudaMemcpyDeviceToHost, s));
-        CK(cudaStreamSynchronize(s));
+        CK(host_sync(h, s));
         double f = 0;
         for (int i = 0; i < M.ng; i++) {
             const double p = 100.0 * p0[i];
@@ -581,7 +581,7 @@ int scopf_eval(scopf_handle *h, const double *w, double *obj, double *g, double 
         }
         *obj = f / 1.0e4;
     }
-    CK(cudaStreamSynchronize(s));
+    CK(host_sync(h, s));
     CK(cudaGetLastError());
     return SCOPF_OK;
 }
@@ -592,7 +592,7 @@ int kkt_assemble(scopf_handle *h, const scopf_state *it, const double *lam_n, co
         return SCOPF_ERR_INVALID_ARG;
     int r = assemble_impl(h, it, lam_n, nu0_n, rho, mu, delta_w, rhs);
     if (r != SCOPF_OK) return r;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(host_sync(h, h->stream));
     h->timer.collect();
     return SCOPF_OK;
 }
@@ -605,7 +605,7 @@ int scopf_launch_count(int64_t *out) {
 
 int scopf_trace(scopf_handle *h, int32_t enable) {
     if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(host_sync(h, h->stream));
     h->kgraph_stale = true;   // the graphs captured the trace pointer
     if (h->trace) {
         cudaFree(h->trace);
@@ -629,7 +629,7 @@ int scopf_trace_read(scopf_handle *h, int32_t kind, uint64_t *out) {
     if (!h || h->host_only || !h->trace || kind < 0 || kind > 4 || !out)
         return SCOPF_ERR_INVALID_ARG;
     const size_t n = 4 * (size_t)h->HF.n_items;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(host_sync(h, h->stream));
     CK(cudaMemcpy(out, h->trace + (size_t)kind * n, sizeof(uint64_t) * n, cudaMemcpyDeviceToHost));
     return SCOPF_OK;
 }
@@ -659,7 +659,7 @@ int scopf_trace_items(scopf_handle *h, int32_t *n_items, int32_t *out) {
 
 int scopf_timing(scopf_handle *h, int32_t enable, double *ms_out, int32_t *calls_out) {
     if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
-    CK(cudaStreamSynchronize(h->stream));
+    CK(host_sync(h, h->stream));
     h->timer.collect();
     for (int i = 0; i < PhaseTimer::kPhases; i++) {
         if (ms_out) ms_out[i] = h->timer.ms[i];
@@ -729,7 +729,7 @@ static int copy_state(scopf_handle *h, const scopf_state *a, const scopf_state *
             CK(cudaMemcpyAsync(*pa[i], *pb[i], sizeof(double) * len[i], cudaMemcpyDeviceToDevice,
                                h->stream));
     }
-    CK(cudaStreamSynchronize(h->stream));
+    CK(host_sync(h, h->stream));
     return SCOPF_OK;
 }
 
@@ -761,7 +761,7 @@ double device_maxabs(scopf_handle *h, const double *x, int64_t n) {
     reduce_maxabs(x, n, h->red_out, h->red_scratch, h->stream);
     double v = 0;
     cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    cudaStreamSynchronize(h->stream);
+    host_sync(h, h->stream);
     return v;
 }
 
@@ -770,7 +770,7 @@ double device_sumabs(scopf_handle *h, const double *x, int64_t n) {
     reduce_sumabs(x, n, h->red_out, h->red_scratch, h->stream);
     double v = 0;
     cudaMemcpyAsync(&v, h->red_out, sizeof(double), cudaMemcpyDeviceToHost, h->stream);
-    cudaStreamSynchronize(h->stream);
+    host_sync(h, h->stream);
     return v;
 }
 
@@ -844,7 +844,7 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     h->timer.end(PH_SCHUR, s);
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
-    CK(cudaStreamSynchronize(s));
+    CK(host_sync(h, s));
     h->timer.collect();
     CK(cudaGetLastError());
     inertia[0] = fs.n_pos;
@@ -1014,7 +1014,7 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
         cudaMemcpyAsync(v, h->red_out, sizeof(v), cudaMemcpyDeviceToHost, s);
         cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s);
         if (G) cudaMemcpyAsync(&ctl, h->kctl, sizeof(ctl), cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        host_sync(h, s);
         bn = v[0];
         rn = v[1];
     };
@@ -1071,7 +1071,7 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
             launch_gmres_column(h->kst, m, j, s);
             double gj = 0;
             cudaMemcpyAsync(&gj, sc + 2, sizeof(double), cudaMemcpyDeviceToHost, s);
-            cudaStreamSynchronize(s);
+            host_sync(h, s);
             jend = j + 1;
             if (!(gj > target)) break;
         }

@@ -182,12 +182,18 @@ struct scopf_handle {
     int n_factor = 0, n_refine = 0;
     bool force_fp64 = false;      // sticky FP64 fallback inside a solve
     long long n_known_zero = 0;   // delta_w = 0 trials taken as failed without factoring
+    long long n_host_syncs = 0;   // stream synchronisations the host waited on
     unsigned long long *trace = nullptr;   // scheduler trace buffer (cudaMalloc'd)
     scopf::PhaseTimer timer;
     std::string last_error;
 };
 
 namespace scopf {
+// a host wait on the handle's stream (counted: the host round trips of a solve)
+inline cudaError_t host_sync(scopf_handle *h, cudaStream_t s) {
+    h->n_host_syncs++;
+    return cudaStreamSynchronize(s);
+}
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res,
                    bool resume = false);
 int block_multiplier_update(scopf_handle *h, double rho, double thr);

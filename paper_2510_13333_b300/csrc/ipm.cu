@@ -387,7 +387,7 @@ static bool zero_pivot_certain(scopf_handle *h) {
     launch_count_zero_diag(h->n_lead, h->lead_pdiag, h->pdiag_base, h->lead_zero, h->stream);
     int count = 0;
     cudaMemcpyAsync(&count, h->lead_zero, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
-    cudaStreamSynchronize(h->stream);
+    host_sync(h, h->stream);
     return count > 0;
 }
 
@@ -463,7 +463,7 @@ struct Ipm {
     // where each is combined in block order.
     void fetch(int k) {
         cudaMemcpyAsync(part.data(), dpart, sizeof(double) * kB * k, cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        host_sync(h, s);
     }
     double comb(int k, int slot, int op, int region = 0) {
         double a = op == 0 ? -INFINITY : (op == 1 ? INFINITY : 0.0);
@@ -542,7 +542,7 @@ struct Ipm {
         if (M.ng)
             cudaMemcpyAsync(p0h.data(), w + M.border0, sizeof(double) * M.ng,
                             cudaMemcpyDeviceToHost, s);
-        cudaStreamSynchronize(s);
+        host_sync(h, s);
     }
     // phi from the fetched p_g^0 (same formula as scopf_eval)
     double phi_host() const {
@@ -698,7 +698,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
         launch_constraints(h->dm, st.w, h->ev, st.r, s);
         cudaMemsetAsync(st.lam, 0, sizeof(double) * (m ? m : 1), s);
         launch_axpy(m, o.rho_init, st.r, st.lam, s);
-        cudaStreamSynchronize(s);
+        host_sync(h, s);
     }
     double mu = o.mu_init, eta = o.eta_init, omega = o.omega_init, dw_last = 0.0;
     if (resume) {
@@ -715,6 +715,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
     double E0 = INFINITY, feas = INFINITY;
     double t_newton = 0.0;
     const int fact0 = h->n_factor, ref0 = h->n_refine;
+    const long long syncs0 = h->n_host_syncs;
     for (outer = 1; outer <= o.max_outer; outer++) {
         const double om = std::fmax(omega, o.tol);
         // ------------------------------------------------------------ inner
@@ -834,7 +835,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
             note_launch(), k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
             std::swap(st, tr);
             inner++;
-            cudaStreamSynchronize(s);
+            host_sync(h, s);
             t_newton += tn.s();
             {
                 const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th, ph,
@@ -887,7 +888,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
         }
     }
     if (outer > o.max_outer) outer = o.max_outer;
-    cudaStreamSynchronize(s);
+    host_sync(h, s);
     h->rho = rho;
     h->mu_last = mu;
     h->dw_last = dw_last;
@@ -925,6 +926,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
     res->time_total_s = T.s();
     res->time_newton_s = t_newton;
     res->delta_w_last = dw_last;
+    res->host_round_trips = h->n_host_syncs - syncs0;
     return status == SCOPF_OK ? SCOPF_OK : status;
 }
 
@@ -975,7 +977,7 @@ extern "C" int scopf_newton_step(scopf_handle *h, const scopf_state *it, const d
     I.trial_eval(h->trial, rho, mu, tht, pht);
     const double ap = alpha[0], az = alpha[1];
     h->timer.end(PH_IPM, s);
-    cudaStreamSynchronize(s);
+    host_sync(h, s);
     h->timer.collect();
     if (out) {
         out[0] = ap;
