@@ -26,6 +26,7 @@
 // D K D (Ruiz scaling, D > 0 diagonal): the inertia is unchanged (Sylvester)
 // and FP32 fronts keep far more accuracy than on the raw barrier-scaled KKT.
 #include <algorithm>
+#include <climits>
 #include <cmath>
 
 #include "dense_ldlt.cuh"
@@ -1532,37 +1533,50 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
 }
 
 // ---- Ruiz equilibration: s_i <- s_i / sqrt(max_j |s_i K_ij s_j|) ---------
-// One Ruiz sweep, entry-parallel: thread t takes the kRE stored entries
+// Ruiz equilibration with power-of-two factors (s_i = 2^e_i), in integer
+// exponent arithmetic.  The FP64 version kept B300's FP64 pipe 78% busy for a
+// pass that only needs magnitudes; with powers of two the scaling is exact
+// (D K D adds no rounding) and a sweep is integer work plus the loads.
+// One sweep, entry-parallel: thread t takes the kRE stored entries
 // [kRE t, kRE t + kRE) (vector loads; the entries of a row are consecutive)
-// and forms v = |s_i a_ij s_j| for each, keeping a running maximum per run of
-// equal rows.  A run inside the chunk is the whole row: a plain store.  A run
-// that touches either end of the chunk may continue in a neighbouring one:
-// an atomic max on the bit pattern (v >= 0 orders like an unsigned integer).
-// mx must be zero on entry; k_ruiz_finish consumes and re-zeroes it.
+// and forms, for each nonzero a_ij, the exponent of |a_ij| s_j (that of a_ij's
+// leading bit plus e_j), keeping a running maximum per run of equal rows.  A
+// run inside the chunk is the whole row: a plain store.  A run that touches
+// either end of the chunk may continue in a neighbouring one: an atomic max.
+// Maxima are stored offset by kRuizBias so that 0 means "no entry"; mx must
+// be zero on entry and k_ruiz_finish re-zeroes it.
 constexpr int kRE = 8;
-__device__ __forceinline__ void ruiz_flush(unsigned long long *mx, int r, double m, bool edge) {
-    if (r < 0 || !(m == m)) return;
-    const unsigned long long b = (unsigned long long)__double_as_longlong(m);
+constexpr int kRuizBias = 8192;
+__device__ __forceinline__ void ruiz_flush(unsigned *mx, int r, int m, bool edge) {
+    if (r < 0 || m == INT_MIN) return;
+    const unsigned b = (unsigned)(m + kRuizBias);
     if (edge) atomicMax(&mx[r], b);
     else mx[r] = b;
+}
+
+// exponent of a normal FP64 value's leading bit, INT_MIN for zero, subnormal,
+// infinite or NaN values (read from the high word: integer instructions)
+__device__ __forceinline__ int exponent_of(int hi) {
+    const int f = (hi >> 20) & 0x7ff;
+    return (f == 0 || f == 0x7ff) ? INT_MIN : f - 1023;
 }
 
 __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t *__restrict__ row,
                                                       const int64_t *__restrict__ col,
                                                       const double *__restrict__ kval,
-                                                      const double *__restrict__ s_in,
-                                                      unsigned long long *__restrict__ mx) {
+                                                      const int *__restrict__ e,
+                                                      unsigned *__restrict__ mx) {
     const int64_t nthr = (int64_t)gridDim.x * blockDim.x;
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kRE < nnz; t += nthr) {
         const int64_t e0 = t * kRE;
         int rr[kRE];
         int64_t cc[kRE];
-        double vv[kRE];
+        int hh[kRE];
         int cnt = kRE;
         if (e0 + kRE <= nnz) {
             const int4 *r4 = reinterpret_cast<const int4 *>(row + e0);
             const longlong2 *c2 = reinterpret_cast<const longlong2 *>(col + e0);
-            const double2 *v2 = reinterpret_cast<const double2 *>(kval + e0);
+            const int4 *v4 = reinterpret_cast<const int4 *>(kval + e0);   // (lo, hi) pairs
 #pragma unroll
             for (int k = 0; k < kRE / 4; k++) {
                 const int4 a = __ldg(r4 + k);
@@ -1574,11 +1588,11 @@ __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t
 #pragma unroll
             for (int k = 0; k < kRE / 2; k++) {
                 const longlong2 a = __ldg(c2 + k);
-                const double2 b = __ldg(v2 + k);
+                const int4 b = __ldg(v4 + k);
                 cc[2 * k] = a.x;
                 cc[2 * k + 1] = a.y;
-                vv[2 * k] = b.x;
-                vv[2 * k + 1] = b.y;
+                hh[2 * k] = b.y;
+                hh[2 * k + 1] = b.w;
             }
         } else {
             cnt = (int)(nnz - e0);
@@ -1586,15 +1600,17 @@ __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t
             for (int k = 0; k < kRE; k++) {
                 rr[k] = k < cnt ? row[e0 + k] : -1;
                 cc[k] = k < cnt ? col[e0 + k] : 0;
-                vv[k] = k < cnt ? kval[e0 + k] : 0.0;
+                hh[k] = k < cnt ? __double2hiint(kval[e0 + k]) : 0;
             }
         }
-        double sj[kRE];
+        int v[kRE];
 #pragma unroll
-        for (int k = 0; k < kRE; k++) sj[k] = k < cnt ? s_in[cc[k]] : 0.0;
+        for (int k = 0; k < kRE; k++) {
+            const int x = k < cnt ? exponent_of(hh[k]) : INT_MIN;
+            v[k] = x == INT_MIN ? INT_MIN : x + e[cc[k]];
+        }
         int cur = rr[0];
-        double si = s_in[cur];
-        double m = fabs(si * vv[0] * sj[0]);
+        int m = v[0];
         bool at_start = true;
 #pragma unroll
         for (int k = 1; k < kRE; k++) {
@@ -1603,23 +1619,31 @@ __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t
                 ruiz_flush(mx, cur, m, at_start);
                 at_start = false;
                 cur = rr[k];
-                si = s_in[cur];
-                m = 0.0;
+                m = INT_MIN;
             }
-            m = fmax(m, fabs(si * vv[k] * sj[k]));
+            m = max(m, v[k]);
         }
         ruiz_flush(mx, cur, m, true);
     }
 }
 
-__global__ void k_ruiz_finish(int64_t n, const double *__restrict__ s_in, double *__restrict__ s_out,
-                              unsigned long long *__restrict__ mx) {
+// e_i <- e_i - floor(m_i / 2), m_i the exponent of max_j |s_i a_ij s_j|
+// (Ruiz: s_i <- s_i / sqrt(row max), rounded to a power of two)
+__global__ void k_ruiz_finish(int64_t n, int *__restrict__ e, unsigned *__restrict__ mx) {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const double m = __longlong_as_double((long long)mx[i]);
-    mx[i] = 0ull;
-    const double si = s_in[i];
-    s_out[i] = m > 0.0 ? si / sqrt(m) : si;
+    const unsigned b = mx[i];
+    mx[i] = 0u;
+    if (b) {
+        const int m = (int)b - kRuizBias + e[i];
+        e[i] -= m >> 1;
+    }
+}
+
+// scale_i = 2^e_i (built from the exponent bits)
+__global__ void k_ruiz_scale(int64_t n, const int *__restrict__ e, double *__restrict__ scale) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) scale[i] = __hiloint2double((e[i] + 1023) << 20, 0);
 }
 
 // scaled original entries of every front, in task order
@@ -1634,10 +1658,6 @@ __global__ void k_orig_vals(int64_t n_orig, const int64_t *__restrict__ nz,
     ovals[p] = (T)(scale[row[q]] * kval[q] * scale[col[q]]);
 }
 
-__global__ void k_fill(int64_t n, double v, double *x) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i < n) x[i] = v;
-}
 
 int warp_grid() { return sm_count() * (2048 / kWT); }
 
@@ -1652,18 +1672,16 @@ void launch_equilibrate(const DevModel &M, const double *kval, double *scale, do
     const int resident = sm_count() * (2048 / t);
     const int64_t chunks = (M.nnz_kkt + kRE - 1) / kRE;
     const int ge = (int)std::min<int64_t>((chunks + t - 1) / t, (int64_t)resident);
-    // start in the buffer that makes the last sweep land in `scale`
-    double *a = (iters & 1) ? tmp : scale, *b = (iters & 1) ? scale : tmp;
-    note_launch(), k_fill<<<g, t, 0, s>>>(n, 1.0, a);
+    // exponents in tmp (n int32), row maxima in mx (n uint32, zeros)
+    int *e = reinterpret_cast<int *>(tmp);
+    unsigned *m32 = reinterpret_cast<unsigned *>(mx);
+    cudaMemsetAsync(e, 0, sizeof(int) * (size_t)(n > 0 ? n : 1), s);
     for (int it = 0; it < iters; it++) {
         if (M.nnz_kkt)
-            note_launch(), k_ruiz_entries<<<ge, t, 0, s>>>(M.nnz_kkt, M.kkt_row, M.kkt_col, kval, a, mx);
-        note_launch(), k_ruiz_finish<<<g, t, 0, s>>>(n, a, b, mx);
-        double *c = a;
-        a = b;
-        b = c;
+            note_launch(), k_ruiz_entries<<<ge, t, 0, s>>>(M.nnz_kkt, M.kkt_row, M.kkt_col, kval, e, m32);
+        note_launch(), k_ruiz_finish<<<g, t, 0, s>>>(n, e, m32);
     }
-    if (a != scale) cudaMemcpyAsync(scale, a, sizeof(double) * n, cudaMemcpyDeviceToDevice, s);
+    note_launch(), k_ruiz_scale<<<g, t, 0, s>>>(n, e, scale);
 }
 
 template <typename T>
