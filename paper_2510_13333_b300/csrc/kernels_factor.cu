@@ -476,6 +476,28 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         const T *Fc = fronts + c.front_off + (int64_t)c.npc * c.fc + c.npc;
         const int fc = c.fc, nu = fc - c.npc;
         const int myrel = lane < nu ? F.rel[c.rel_off + lane] : 0;
+        if (sizeof(T) == 8 && nu <= 16) {
+            // FP64 and a short update block: the two half-warps take
+            // alternate columns (lane = 16 h + row), so each FP64 add
+            // instruction covers two columns (the pipe charges the whole
+            // warp per instruction).  A child's destinations are distinct.
+            const int h = lane >> 4, rw = lane & 15;
+            const int relr = __shfl_sync(0xffffffffu, myrel, rw);
+            T v[8];
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = 2 * k + h;
+                v[k] = (jj < nu && rw >= jj && rw < nu) ? Fc[(int64_t)jj * fc + rw] : (T)0;
+            }
+#pragma unroll
+            for (int k = 0; k < 8; k++) {
+                const int jj = 2 * k + h;
+                const int rj = __shfl_sync(0xffffffffu, myrel, jj);
+                if (jj < nu && rw >= jj && rw < nu) tile[relr][rj] += v[k];
+            }
+            __syncwarp();
+            continue;
+        }
         // sixteen independent column loads in flight per step (lane = row)
         for (int j0 = 0; j0 < nu; j0 += 16) {
             T v[16];
