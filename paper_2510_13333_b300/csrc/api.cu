@@ -799,6 +799,7 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
     }
     h->assembled = true;
     h->factored = false;
+    h->lead_zero_valid = false;
     h->last_delta_w = delta_w;
     h->assembled_delta_w = delta_w;
     h->last_rho = rho;

@@ -153,6 +153,8 @@ struct scopf_handle {
     int64_t n_lead = 0;
     const int64_t *lead_pdiag = nullptr;
     int *lead_zero = nullptr;                 // device count of those with a zero diagonal
+    int lead_zero_host = 0;                   // that count, read back with the IPM norms
+    bool lead_zero_valid = false;             // lead_zero_host describes the assembled K
     // iterate and NCL parameters owned by the handle
     scopf_state st{};
     double *lam_n = nullptr, *nu0_n = nullptr;

@@ -384,6 +384,7 @@ int ipm_partials() { return kB * kPartSlots; }
 // other values).  Only for a K assembled at delta_w = 0.
 static bool zero_pivot_certain(scopf_handle *h) {
     if (h->n_lead == 0 || h->assembled_delta_w != 0.0) return false;
+    if (h->lead_zero_valid) return h->lead_zero_host > 0;   // read with the norms
     launch_count_zero_diag(h->n_lead, h->lead_pdiag, h->pdiag_base, h->lead_zero, h->stream);
     int count = 0;
     cudaMemcpyAsync(&count, h->lead_zero, sizeof(int), cudaMemcpyDeviceToHost, h->stream);
@@ -488,7 +489,18 @@ struct Ipm {
         if (p)
             note_launch(), k_red_p<<<kB, kT, 0, s>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho,
                                                       dpart + kB * 12);
-        fetch(p ? 21 : 12);
+        // the zero-pivot test of reading IC-1 (zero_pivot_certain) for the K
+        // just assembled at delta_w = 0, in the same read-back
+        const int regions = p ? 21 : 12;
+        const bool zc = h->n_lead > 0 && h->assembled && h->assembled_delta_w == 0.0 &&
+                        o.known_zero_pivot;
+        int *zslot = reinterpret_cast<int *>(dpart + (size_t)kB * regions);
+        if (zc) launch_count_zero_diag(h->n_lead, h->lead_pdiag, h->pdiag_base, zslot, s);
+        fetch(regions + (zc ? 1 : 0));
+        if (zc) {
+            h->lead_zero_host = *reinterpret_cast<const int *>(part.data() + (size_t)kB * regions);
+            h->lead_zero_valid = true;
+        }
         double dw = comb(7, 0, 0);
         double cmin = std::fmin(comb(7, 1, 1), comb(7, 3, 1));
         double cmax = std::fmax(comb(7, 2, 0), comb(7, 4, 0));
@@ -835,8 +847,6 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
             note_launch(), k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
             std::swap(st, tr);
             inner++;
-            host_sync(h, s);
-            t_newton += tn.s();
             {
                 const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th, ph,
                                                 a, az, delta, (double)(h->n_factor - fact_before),
@@ -850,7 +860,8 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
                             E0, th, a, delta, tries, accepted ? "" : " R");
             r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, nullptr);
             if (r != SCOPF_OK) return r;
-            N = I.norms(st, rho);
+            N = I.norms(st, rho);   // waits for the step (and this assembly)
+            t_newton += tn.s();
         }
         feas = std::fmax(N.rmax, N.tmax);
         {
