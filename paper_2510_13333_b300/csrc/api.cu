@@ -261,7 +261,7 @@ int setup_device(scopf_handle *h) {
     h->vec = vv;
     TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->S));
     TRY(alloc(h, (size_t)M.nborder * M.nborder, &h->Sinv));
-    TRY(alloc(h, (size_t)M.nborder + 1, &h->border_work));
+    TRY(alloc(h, (size_t)M.nborder * 17 + 1, &h->border_work));   // y + 16 gather partials
     {
         const size_t nt = HF.n_items > 0 ? (size_t)HF.n_items : 1;
         F.n_items = HF.n_items;

@@ -1331,6 +1331,64 @@ __global__ void k_rhs_to_fronts(int64_t n, const int64_t *__restrict__ vpos,
 // Border right-hand side y = D b_border + sum_k (update vector of block k's
 // border front), then the dense border solve with S = L_S D_S L_S' by one
 // warp (column sweeps, warp-shuffle dot products).
+// Border right-hand side over the whole GPU: CTA (c, g) sums, for the 32
+// border rows of chunk c, the update vectors of the blocks k = g, g + kBG,
+// ... (block order) into part[g][j].  The combination over g happens in a
+// fixed order in the kernel that uses it, so the sum does not depend on
+// scheduling.
+constexpr int kBG = 16;     // block groups of the border gather
+template <typename T>
+__global__ void __launch_bounds__(256) k_border_gather(DevFront F, const T *__restrict__ vec, int n,
+                                                       double *__restrict__ part) {
+    __shared__ double red[8][33];
+    const int j = 32 * blockIdx.x + (threadIdx.x & 31), sub = threadIdx.x >> 5;
+    const int g = blockIdx.y;
+    double a = 0.0;
+    if (j < n)
+        for (int k = g + kBG * sub; k < F.n_blocks; k += kBG * 8)
+            a += (double)vec[F.border_vec_off[k] + j];
+    red[sub][threadIdx.x & 31] = a;
+    __syncthreads();
+    if (sub == 0 && j < n) {
+        double t = red[0][threadIdx.x];
+#pragma unroll
+        for (int q = 1; q < 8; q++) t += red[q][threadIdx.x];
+        part[(size_t)g * n + j] = t;
+    }
+}
+
+// y = D b_border + sum_g part[g] (fixed order, every CTA), then x = S^-1 y for
+// this CTA's 16 border rows: one warp per two rows, lanes over the columns
+// and a shuffle reduction (mixed precision: S^-1 formed from the FP64 factor)
+template <typename T>
+__global__ void __launch_bounds__(256) k_border_apply(DevFront F, const double *__restrict__ Sinv,
+                                                      int n, const double *__restrict__ b,
+                                                      const double *__restrict__ scale,
+                                                      const double *__restrict__ part,
+                                                      double *__restrict__ x) {
+    extern __shared__ double yb[];
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+        const int64_t r = F.border_rows[j];
+        double acc = scale[r] * b[r];
+        for (int g = 0; g < kBG; g++) acc += part[(size_t)g * n + j];
+        yb[j] = acc;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int jj = 0; jj < 2; jj++) {
+        const int j = 16 * blockIdx.x + 2 * warp + jj;
+        if (j >= n) break;
+        double acc = 0.0;
+        for (int k = lane; k < n; k += 32) acc += Sinv[(int64_t)k * n + j] * yb[k];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) {
+            const int64_t r = F.border_rows[j];
+            x[r] = scale[r] * acc;
+            static_cast<T *>(F.xs)[r] = (T)acc;
+        }
+    }
+}
+
 constexpr int kBS = 1024;   // threads of the border solve
 template <typename T>
 __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__restrict__ vec,
@@ -1340,43 +1398,16 @@ __global__ void __launch_bounds__(kBS) k_border_solve(DevFront F, const T *__res
                                                       const double *__restrict__ scale,
                                                       double *__restrict__ x,
                                                       double *__restrict__ y) {
-    extern __shared__ double sm[];          // partial sums, then the 32x32 diagonal blocks
     const int tid = threadIdx.x;
-    // y = D b_border + sum over blocks of the border update vectors:
-    // G groups of threads split the blocks, fixed combination order
-    const int G = kBS / n > 0 ? kBS / n : 1;
-    for (int t = tid; t < G * n; t += kBS) {
-        const int g = t / n, j = t - g * n;
-        double a0 = 0, a1 = 0;
-        int k = g;
-        for (; k + G < F.n_blocks; k += 2 * G) {
-            a0 += (double)vec[F.border_vec_off[k] + j];
-            a1 += (double)vec[F.border_vec_off[k + G] + j];
-        }
-        if (k < F.n_blocks) a0 += (double)vec[F.border_vec_off[k] + j];
-        sm[t] = a0 + a1;
-    }
-    __syncthreads();
+    // y = D b_border + sum_g part[g] (the gather's partials, fixed order)
+    const double *part = y + n;
     for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
         double acc = scale[r] * b[r];
-        for (int g = 0; g < G; g++) acc += sm[g * n + j];
+        for (int g = 0; g < kBG; g++) acc += part[(size_t)g * n + j];
         y[j] = acc;
     }
     __syncthreads();
-    if (Sinv) {
-        // S^-1 y with the explicit inverse (one independent dot per row)
-        for (int j = tid; j < n; j += kBS) sm[j] = y[j];
-        __syncthreads();
-        for (int j = tid; j < n; j += kBS) {
-            double acc = 0.0;
-            for (int k = 0; k < n; k++) acc += Sinv[(int64_t)k * n + j] * sm[k];
-            const int64_t r = F.border_rows[j];
-            x[r] = scale[r] * acc;
-            static_cast<T *>(F.xs)[r] = (T)acc;
-        }
-        return;
-    }
     block_ldlt_solve<kBS>(S, n, y);
     for (int j = tid; j < n; j += kBS) {
         const int64_t r = F.border_rows[j];
@@ -1862,10 +1893,16 @@ void launch_solve(const DevFront &F, const T *fronts, T *vec, const double *S, c
     note_launch(), k_rhs_to_fronts<T><<<(int)((F.n_rows + 255) / 256), 256, 0, s>>>(F.n_rows, F.vpos_of_row,
                                                                      scale, b, vec);
     note_launch(), k_solve_fwd<T><<<grid, kWT, sm, s>>>(F, fronts, vec, queue_a(F, F.n_items), st, spin_limit);
-    {
-        const int G = nS > 0 && kBS / nS > 0 ? kBS / nS : 1;
-        note_launch(), k_border_solve<T><<<1, kBS, sizeof(double) * (size_t)G * (nS > 0 ? nS : 1), s>>>(
-            F, vec, S, Sinv, nS, b, scale, x, border_work);
+    if (nS > 0) {
+        // border_work: y (nS), then the gather's partials (kBG x nS)
+        double *part = border_work + nS;
+        note_launch(), k_border_gather<T><<<dim3((nS + 31) / 32, kBG), 256, 0, s>>>(F, vec, nS, part);
+        if (Sinv)
+            note_launch(), k_border_apply<T><<<(nS + 15) / 16, 256, sizeof(double) * (size_t)nS, s>>>(
+                F, Sinv, nS, b, scale, part, x);
+        else
+            note_launch(), k_border_solve<T><<<1, kBS, 0, s>>>(F, vec, S, Sinv, nS, b, scale, x,
+                                                               border_work);
     }
     const int nb = F.n_items - F.n_blocks;   // every item but the border fronts
     if (nb > 0)
