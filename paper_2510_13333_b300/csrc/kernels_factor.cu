@@ -410,7 +410,7 @@ __device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, in
 // pairs (np + k with f - 1 - k, m + 1 entries together, m = f - np) and the
 // lanes take one entry each, so every multiply-add of the update is done by
 // an active lane: np multiply-adds per entry, no triangular idle lanes.
-template <typename T, int S, int R, int NT = 32>
+template <typename T, int S, int R>
 __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int lane) {
     const int m = f - np;
     if (np == 0 || m <= 0) return;
@@ -419,15 +419,15 @@ __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int
     if (sizeof(T) == 4)
         for (int c = 0; c < np; c++) {
             const T d = tile[c][c];
-            for (int j = np + lane; j < f; j += NT) tile[c][j] = tile[j][c] * d;
+            for (int j = np + lane; j < f; j += 32) tile[c][j] = tile[j][c] * d;
         }
-    gsync<NT>();
+    __syncwarp();
     for (int k = 0; 2 * k < m; k++) {
         const int a = np + k, la = m - k, b = f - 1 - k;
         const int lb = b > a ? k + 1 : 0;
 #pragma unroll
         for (int r = 0; r < R; r++) {
-            const int e = lane + NT * r;
+            const int e = lane + 32 * r;
             int i = -1, j = 0;
             if (e < la) {
                 i = a + e;
@@ -444,7 +444,7 @@ __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int
             }
         }
     }
-    gsync<NT>();
+    __syncwarp();
 }
 template <typename T>
 __device__ __forceinline__ void trailing_update_tile(T (*tile)[33], int f, int np, int lane) {
@@ -660,72 +660,6 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
     }
 }
 
-// FP64 medium front (32 < f <= 64) eliminated by two warps: thread t owns
-// row t.  The FP64 pipe charges each warp instruction in full, so the
-// instruction count is the one-warp version's; the gain is latency (two
-// warps per front, twice the warps per SM at the same shared memory).
-__device__ void eliminate_front_medium2(const DevFront &F, double *__restrict__ fronts,
-                                        const TaskInfo &ti, int tid,
-                                        double (*M)[kMedF + 1], double pivot_tol, int &n_pos,
-                                        int &n_neg, int &n_zero) {
-    const bool ptol_zero = pivot_tol == 0.0;
-    double *Fr = fronts + ti.front_off;
-    const int f = ti.f, np = ti.np;
-    for (int c = 0; c < kMedF; c++) M[tid][c] = 0.0;
-    __syncthreads();
-    for (int q = ti.o0 + tid; q < ti.o1; q += 64) {
-        const int off = F.orig_off[q];
-        const int col = off / f, row = off - col * f;
-        M[row][col] = static_cast<const double *>(F.ovals)[q];
-    }
-    __syncthreads();
-    for (int ci = ti.c0; ci < ti.c1; ci++) {
-        const ChildInfo c = child_info(F, ci);
-        const int fc = c.fc, nu = fc - c.npc;
-        const double *Fc = fronts + c.front_off + (int64_t)c.npc * fc + c.npc;
-        const int32_t *rel = F.rel + c.rel_off;
-        const int rr = tid < nu ? rel[tid] : 0;
-        for (int j0 = 0; j0 < nu; j0 += 8) {
-            double v[8];
-            int rj[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int jj = j0 + k;
-                v[k] = (jj < nu && tid < nu && tid >= jj) ? Fc[(int64_t)jj * fc + tid] : 0.0;
-                rj[k] = jj < nu ? rel[jj] : 0;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int jj = j0 + k;
-                if (jj < nu && tid < nu && tid >= jj) M[rr][rj[k]] += v[k];
-            }
-        }
-        __syncthreads();
-    }
-    for (int c = 0; c < np; c++) {
-        const double d = M[c][c];
-        if (tid == 0) count_pivot<double>(d, (double)pivot_tol, ptol_zero, n_pos, n_neg, n_zero);
-        const double dinv = pivot_reciprocal<double>(d);
-        // column c before scaling (l d) into the unused upper triangle: the
-        // panel update's l_j d and the trailing update's W = L D
-        if (tid > c && tid < f) {
-            const double a = M[tid][c];
-            M[c][tid] = a;
-            M[tid][c] = a * dinv;
-        }
-        __syncthreads();
-        for (int j = c + 1; j < np; j++) {   // panel columns only
-            const double lj = M[c][j];
-            const int i = j + tid;
-            if (i < f) M[i][j] -= M[i][c] * lj;
-        }
-        __syncthreads();
-    }
-    trailing_update<double, kMedF + 1, 1, 64>(M, f, np, tid);
-    for (int j = 0; j < f; j++)
-        if (tid < f) Fr[(int64_t)j * f + tid] = M[tid][j];
-}
-
 // Phase 1: tile-sized fronts, one warp per front (32 x 33 shared tile each).
 constexpr int kFT = 256;   // threads per CTA of the warp-per-front phases
 template <typename T>
@@ -769,59 +703,12 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 3)
 // front with its own 64 x 65 shared front.  FP64 fronts take 33 KB: one
 // warp per CTA lets six of them share an SM (four-warp CTAs fit only one).
 template <typename T>
-constexpr int med_threads() { return sizeof(T) == 4 ? kWT : 64; }
+constexpr int med_threads() { return sizeof(T) == 4 ? kWT : 32; }
 template <typename T>
 __global__ void __launch_bounds__(med_threads<T>())
     k_factor_med(DevFront F, T *__restrict__ fronts, FactorStatus *st, QueueView Q,
                  double pivot_tol, int spin_limit) {
     extern __shared__ __align__(16) unsigned char med_smem[];
-    if constexpr (sizeof(T) == 8) {
-        // FP64: one front per CTA of two warps (eliminate_front_medium2)
-        __shared__ int s_item;
-        double(*M2)[kMedF + 1] = reinterpret_cast<double(*)[kMedF + 1]>(med_smem);
-        const int tid = threadIdx.x;
-        int n_pos = 0, n_neg = 0, n_zero = 0;
-        if (tid == 0) s_item = -1;
-        __syncthreads();
-        while (true) {
-            const unsigned long long tc = F.trace ? dev_clock_ns() : 0;
-            if (tid == 0 && s_item < 0) {
-                int t;
-                do {
-                    t = claim_slot(Q, spin_limit);
-                } while (t == kSkip);
-                if (t == -2) {
-                    atomicExch(&st->error, 1);
-                    t = -1;
-                }
-                s_item = t;
-            }
-            __syncthreads();
-            const int item = s_item;
-            __syncthreads();
-            if (item < 0) break;
-            const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-            const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per item
-            if (ti.f <= kMedF)
-                eliminate_front_medium2(F, fronts, ti, tid, M2, pivot_tol, n_pos, n_neg, n_zero);
-            else   // not produced by the phase split; kept as a safe fallback
-                eliminate_front<T, 64>(F, fronts, ti, tid, pivot_tol, n_pos, n_neg, n_zero);
-            __syncthreads();   // orders every thread's writes before the release below
-            if (tid == 0) {
-                if (F.trace) trace_item(F, 3, item, tc, ts);
-                const int par = F.item_parent[item];
-                s_item = (par >= F.n_items_small && par < F.n_items_med && complete_child(Q, par))
-                             ? par : -1;
-            }
-            __syncthreads();
-        }
-        if (tid == 0) {
-            if (n_pos) atomicAdd(&st->n_pos, n_pos);
-            if (n_neg) atomicAdd(&st->n_neg, n_neg);
-            if (n_zero) atomicAdd(&st->n_zero, n_zero);
-        }
-        return;
-    }
     const int lane = threadIdx.x & 31;
     T (*M)[kMedF + 1] = reinterpret_cast<T (*)[kMedF + 1]>(med_smem) + kMedF * (threadIdx.x >> 5);
     int n_pos = 0, n_neg = 0, n_zero = 0;
@@ -1906,9 +1793,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
     launch_queue_reset(F, seeds, F.pend_factor, s);
     static int grids[kMaxDev][2][2] = {};   // [device][float, double][phase 1, 2]
     const size_t sm1 = sizeof(T) * (size_t)(kFT / 32) * 32 * 33;
-    // FP32: a 64 x 65 front per warp; FP64: one per CTA of two warps
-    constexpr int med_fronts = sizeof(T) == 8 ? 1 : med_threads<T>() / 32;
-    const size_t sm2 = sizeof(T) * (size_t)med_fronts * kMedF * (kMedF + 1);
+    const size_t sm2 = sizeof(T) * (size_t)(med_threads<T>() / 32) * kMedF * (kMedF + 1);
     const int dev = device_slot();
     int gtmp[2] = {0, 0};
     int *g = dev >= 0 ? grids[dev][sizeof(T) == 4 ? 0 : 1] : gtmp;
@@ -1930,7 +1815,7 @@ void launch_factor(const DevFront &F, T *fronts, FactorStatus *st, double pivot_
         note_launch(), k_factor<T><<<grid, kFT, sm1, s>>>(F, fronts, st, queue_a(F, n1), pivot_tol, spin_limit);
     }
     if (n2 > 0) {
-        const int wpc = med_fronts;
+        const int wpc = med_threads<T>() / 32;
         const int grid = std::min(g[1], (n2 + wpc - 1) / wpc);
         note_launch(), k_factor_med<T><<<grid, med_threads<T>(), sm2, s>>>(F, fronts, st, queue_b(F, n2), pivot_tol,
                                                spin_limit);
