@@ -52,8 +52,9 @@ FP64_PEAK_TFLOPS = 1.25
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
 # valid only for the sweep kernels' source it was taken with
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "12ef02fde60a2bf105f5fb9e0ea33ab600252724",
-                 "bytes_per_solve": 253.5e6 + 302.8e6}
+                 "sha1": "510fd13e140b74e9404714fcfa47060b39a3512a",
+                 # k_solve_fwd + k_border_gather + k_border_apply + k_solve_bwd (FP32)
+                 "bytes_per_solve": 254899200 + 212480 + 296704 + 315174912}
 
 
 def sweep_traffic():
