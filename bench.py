@@ -259,11 +259,12 @@ def oracle_tts_118():
             "objective": r.objective, "cores": 1}
 
 
-def gpu_tts_118(P, torch, precision):
+def gpu_tts_118(P, torch, precision, ipm_graph=1):
     """The library's time to solution on the same 118-bus x 32 workload
-    (latency-bound: 48k KKT rows)."""
+    (latency-bound: 48k KKT rows), with the device-resident iteration
+    (ipm_graph=1) or the host loop."""
     import synthgrid
-    lib = P.SCOPF(synthgrid.config_instance(1), precision=precision)
+    lib = P.SCOPF(synthgrid.config_instance(1), precision=precision, ipm_graph=ipm_graph)
     lib.ncl_solve()   # warm-up (graphs, caches)
     torch.cuda.synchronize()
     n0 = P.scopf_launch_count()
@@ -276,7 +277,8 @@ def gpu_tts_118(P, torch, precision):
             "ms_per_iter": 1e3 * dt / max(1, r["inner_iters"]), "objective": r["objective"],
             "factorizations": r["factorizations"],
             "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"]),
-            "launches_per_iter": launches / max(1, r["inner_iters"])}
+            "launches_per_iter": launches / max(1, r["inner_iters"]),
+            "graph_iters": r["graph_iters"]}
 
 
 def oracle_step_sample(n_steps: int = 3, idx: int = CONFIG_IDX):
@@ -439,7 +441,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     free0 = torch.cuda.mem_get_info()[0]
     t0 = time.perf_counter()
-    loop = {"device_loop": 0} if args.host_loop else {}
+    loop = {"device_loop": 0, "ipm_graph": 0} if args.host_loop else {}
     if args.workload == "condensed":
         loop["dual_first"] = 1
     tune = None
@@ -477,10 +479,13 @@ def run_ours(args):
                      "outer_iters": r["outer_iters"], "factorizations": r["factorizations"],
                      "fp64_fallbacks": r["fp64_fallbacks"], "max_violation": r["max_violation"],
                      "kkt_error": r["kkt_error"], "feas_rt": r["feas_rt"],
-                     "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"])}
+                     "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"]),
+                     "graph_iters": r["graph_iters"]}
     if idx == CONFIG_IDX and args.tts != "none":
         tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
-                             "fp64": gpu_tts_118(P, torch, P.PREC_FP64)}
+                             "fp64": gpu_tts_118(P, torch, P.PREC_FP64),
+                             "mixed_host_loop": gpu_tts_118(P, torch, P.PREC_MIXED, 0),
+                             "fp64_host_loop": gpu_tts_118(P, torch, P.PREC_FP64, 0)}
     # ---- a mid-solve iterate: the state after a fixed number of IPM iterations
     lib.set_precision(P.PREC_MIXED)
     lib2 = P.SCOPF(inst, precision=P.PREC_MIXED, max_inner=args.iterate_at,

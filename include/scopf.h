@@ -149,6 +149,18 @@ typedef struct {
                                  barrier error E_mu <= tol instead of E_0: the
                                  solution of the barrier problem at that mu, the
                                  smooth map scopf_adjoint differentiates */
+    int32_t ipm_graph;        /* 1: each interior-point iteration, after the host's
+                                 convergence test and barrier update, runs as two
+                                 CUDA-graph launches with one host read-back: the
+                                 inertia-correction trials, the refinement cycles
+                                 (with their Krylov steps) and the filter
+                                 line-search trials are WHILE nodes, the solve
+                                 after a successful inertia correction and the
+                                 elastic restoration IF nodes (Section IV-B; the
+                                 decisions are those of the host loop).  If the
+                                 graphs cannot be built the host loop runs (the
+                                 reason in scopf_last_error).  Needs
+                                 device_loop = 1.  0: host loop.  Default 1 */
 } scopf_options;
 
 /* Sizes of the handle's problem. */
@@ -183,6 +195,9 @@ typedef struct {
     int64_t host_round_trips; /* stream synchronisations the host waited on
                                  (reductions read back, inertia, refinement
                                  cycles, line-search trials) during the solve */
+    int32_t graph_iters;      /* interior-point iterations run as graph launches
+                                 (option ipm_graph) */
+    int32_t pad;
 } scopf_result;
 
 void scopf_default_options(scopf_options *opt);
@@ -194,6 +209,9 @@ int scopf_create(const scopf_network *net, const scopf_contingency *ctg, int32_t
                  const scopf_options *opt, scopf_handle **out);
 void scopf_destroy(scopf_handle *h);
 const char *scopf_strerror(int status);
+/* Text of the handle's last CUDA or internal error (owned by the handle,
+ * valid until its next call; "" when none). */
+const char *scopf_last_error(scopf_handle *h);
 
 int scopf_get_sizes(scopf_handle *h, scopf_sizes *out);
 /* Run the handle's kernels on this CUDA stream (cudaStream_t); NULL = legacy default. */

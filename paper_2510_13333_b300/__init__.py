@@ -62,7 +62,7 @@ _OPT_DOUBLES = ["tol", "mu_min", "mu_init", "kappa_eps", "kappa_mu", "theta_mu",
 _OPT_INTS = ["max_backtrack", "max_outer", "max_inner", "max_refine", "precision",
              "relax_max_nodes", "verbose", "spin_limit", "host_only", "cluster_max_tasks",
              "relax_max_front", "device_loop", "fp64_switch_refine", "fp64_switch_streak",
-             "known_zero_pivot", "dual_first", "fixed_mu"]
+             "known_zero_pivot", "dual_first", "fixed_mu", "ipm_graph"]
 
 
 class Options(ctypes.Structure):
@@ -94,7 +94,7 @@ class Result(ctypes.Structure):
                 ("objective", c_dbl), ("kkt_error", c_dbl), ("feas_rt", c_dbl),
                 ("max_violation", c_dbl), ("rho", c_dbl), ("mu", c_dbl),
                 ("time_total_s", c_dbl), ("time_newton_s", c_dbl), ("delta_w_last", c_dbl),
-                ("host_round_trips", c_i64)]
+                ("host_round_trips", c_i64), ("graph_iters", c_i32), ("pad", c_i32)]
 
 
 _LIB = None
@@ -130,6 +130,7 @@ def lib():
                                      ctypes.POINTER(Options), ctypes.POINTER(H)]),
             "scopf_destroy": (None, [H]),
             "scopf_strerror": (ctypes.c_char_p, [c_i32]),
+            "scopf_last_error": (ctypes.c_char_p, [H]),
             "scopf_get_sizes": (c_i32, [H, ctypes.POINTER(Sizes)]),
             "scopf_set_stream": (c_i32, [H, ctypes.c_void_p]),
             "scopf_set_precision": (c_i32, [H, c_i32]),
@@ -557,6 +558,10 @@ class SCOPF:
                      "delta_w", "factorizations", "refine_steps", "precision", "accepted",
                      "backtracks")
     HISTORY_OUTER = ("outer", "rho", "r_inf", "t_inf", "E0", "eta", "omega", "inner")
+
+    def last_error(self) -> str:
+        """Text of the handle's last CUDA or internal error ("" when none)."""
+        return lib().scopf_last_error(self.h).decode()
 
     def history(self, which: int = 0):
         """Iteration log of the last solve: (field names, numpy array with one

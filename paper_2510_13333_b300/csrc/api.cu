@@ -406,7 +406,10 @@ void scopf_default_options(scopf_options *o) {
     o->known_zero_pivot = 1;
     o->dual_first = 0;
     o->fixed_mu = 0;
+    o->ipm_graph = 1;
 }
+
+const char *scopf_last_error(scopf_handle *h) { return h ? h->last_error.c_str() : ""; }
 
 const char *scopf_strerror(int s) {
     switch (s) {
@@ -505,6 +508,7 @@ void scopf_destroy(scopf_handle *h) {
     if (!h) return;
     for (auto &g : h->kgraph)
         if (g.exec) cudaGraphExecDestroy(g.exec);
+    ipm_graphs_release(h);
     for (void *p : h->allocations) cudaFree(p);
     if (h->trace) cudaFree(h->trace);
     delete h;
@@ -607,6 +611,7 @@ int scopf_trace(scopf_handle *h, int32_t enable) {
     if (!h || h->host_only) return SCOPF_ERR_INVALID_ARG;
     CK(host_sync(h, h->stream));
     h->kgraph_stale = true;   // the graphs captured the trace pointer
+    h->ig_stale = true;
     if (h->trace) {
         cudaFree(h->trace);
         h->trace = nullptr;
@@ -774,11 +779,11 @@ double device_sumabs(scopf_handle *h, const double *x, int64_t n) {
     return v;
 }
 
-int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, const double *nu0_n,
-                  double rho, double mu, double delta_w, double *rhs) {
+// The model evaluation and KKT assembly at `it` (no right-hand side),
+// enqueued on h->stream; rho may be a device scalar
+void assemble_enqueue(scopf_handle *h, const scopf_state *it, DScalar rho, double delta_w) {
     cudaStream_t s = h->stream;
     const DevModel &d = h->dm;
-    h->timer.begin(PH_ASSEMBLE, s);
     launch_eval_elements(d, it->w, it->lam, it->yc, h->ev, 1, s);
     launch_constraints(d, it->w, h->ev, h->c, s);
     launch_gradient(d, it->w, h->g, s);
@@ -786,6 +791,14 @@ int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, c
     launch_assemble(d, h->ev, h->diag, h->kval, s);
     launch_diag_gather(h->n_pdiag, h->pdiag_pos, h->kval, h->pdiag_base, s);
     launch_dual_product(d, h->kval, h->g, it->lam, it->yc, h->gw, s);
+}
+
+int assemble_impl(scopf_handle *h, const scopf_state *it, const double *lam_n, const double *nu0_n,
+                  double rho, double mu, double delta_w, double *rhs) {
+    cudaStream_t s = h->stream;
+    const DevModel &d = h->dm;
+    h->timer.begin(PH_ASSEMBLE, s);
+    assemble_enqueue(h, it, rho, delta_w);
     if (rhs) {
         RhsArgs a{it->w, it->r, it->t, it->s, it->lam, it->yc, it->zs, h->gw, h->c, lam_n, nu0_n,
                   rho, mu};
@@ -820,11 +833,15 @@ int set_delta_w(scopf_handle *h, double delta_w) {
     return SCOPF_OK;
 }
 
+// The device work of one factorization of the assembled K (equilibration,
+// block fronts, Schur sum, dense border factor), enqueued on h->stream; the
+// inertia and status land in h->fstat.
 template <typename T>
-static int factor_t(scopf_handle *h, int inertia[3]) {
+cudaError_t factor_enqueue(scopf_handle *h) {
     cudaStream_t s = h->stream;
     T *fr = reinterpret_cast<T *>(h->fronts);
-    CK(cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s));
+    cudaError_t e = cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s);
+    if (e != cudaSuccess) return e;
     h->timer.begin(PH_FRONT_INIT, s);
     launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, h->ruiz_mx, 3, s);
     launch_orig_vals<T>(h->df, reinterpret_cast<T *>(h->ovals), s);
@@ -834,8 +851,9 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     h->timer.end(PH_FACTOR, s);
     h->timer.begin(PH_SCHUR, s);
     launch_schur_sum<T>(h->df, fr, h->S, s);
-    CK(launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s,
-                         h->opt.spin_limit));
+    e = launch_dense_ldlt(h->S, (int)h->M.nborder, h->fstat, h->opt.pivot_tol, s,
+                          h->opt.spin_limit);
+    if (e != cudaSuccess) return e;
     // FP32 block factors: the border block is applied through S^-1 (a mat-vec
     // per solve instead of two sequential triangular solves); the refinement
     // corrects its rounding like that of the block factors.  S^-1 is formed
@@ -843,6 +861,15 @@ static int factor_t(scopf_handle *h, int inertia[3]) {
     // the inertia correction never pay for it.
     h->sinv_stale = sizeof(T) == 4;
     h->timer.end(PH_SCHUR, s);
+    return cudaGetLastError();
+}
+template cudaError_t factor_enqueue<float>(scopf_handle *);
+template cudaError_t factor_enqueue<double>(scopf_handle *);
+
+template <typename T>
+static int factor_t(scopf_handle *h, int inertia[3]) {
+    cudaStream_t s = h->stream;
+    CK(factor_enqueue<T>(h));
     FactorStatus fs;
     CK(cudaMemcpyAsync(&fs, h->fstat, sizeof(fs), cudaMemcpyDeviceToHost, s));
     CK(host_sync(h, s));
@@ -867,12 +894,63 @@ int factor_impl(scopf_handle *h, int precision, int inertia[3]) {
 }
 
 template <typename T>
-static int solve_once(scopf_handle *h, const double *b, double *x) {
+int solve_once(scopf_handle *h, const double *b, double *x) {
     h->timer.begin(PH_SOLVE, h->stream);
     launch_solve<T>(h->df, reinterpret_cast<T *>(h->fronts), reinterpret_cast<T *>(h->vec), h->S,
                     sizeof(T) == 4 ? h->Sinv : nullptr, (int)h->M.nborder, h->scale, b, x,
                     h->border_work, h->fstat, h->opt.spin_limit, h->stream);
     h->timer.end(PH_SOLVE, h->stream);
+    return SCOPF_OK;
+}
+template int solve_once<float>(scopf_handle *, const double *, double *);
+template int solve_once<double>(scopf_handle *, const double *, double *);
+
+// One Krylov step of the refinement's FGMRES cycle (the body of a WHILE
+// node whose condition `loop` it sets), enqueued on h->stream -- a stream
+// that is capturing into the WHILE node's body graph.  Returns the kernels
+// it launched.
+template <typename T>
+long long enqueue_krylov_step(scopf_handle *h, cudaGraphConditionalHandle loop) {
+    const int64_t n = h->M.n_kkt;
+    constexpr int m = 16;
+    const GmresLayout GL = gmres_layout(m);
+    double *sc = h->kst + GL.sc;
+    double *vb = h->kry_buf, *zb = vb + n, *wb = zb + n;
+    cudaStream_t cs = h->stream;
+    const long long k0 = g_kernel_launches.load();
+    launch_kry_gather(n, h->kv, h->kctl, vb, cs);
+    solve_once<T>(h, vb, zb);
+    launch_kry_scatter(n, zb, h->kz, h->kctl, cs);
+    launch_spmv(h->dm, h->kval, zb, wb, cs);
+    for (double *coef : {h->kst + GL.c1, h->kst + GL.c2}) {   // classical Gram-Schmidt, twice
+        launch_kry_multi_dot(h->kv, n, h->kctl, wb, h->kpart, cs);
+        launch_kry_dot_finish(h->kpart, h->kctl, coef, cs);
+        launch_kry_axpy(wb, h->kv, n, h->kctl, false, coef, cs);
+    }
+    launch_multi_dot(wb, n, 1, wb, h->kpart, cs);
+    launch_dot_finish(h->kpart, 1, sc + 1, true, cs);
+    launch_kry_scale_out(n, sc + 1, wb, h->kv, h->kctl, cs);
+    launch_kry_column_next(h->kst, m, h->kctl, loop, cs);
+    return g_kernel_launches.load() - k0;
+}
+template long long enqueue_krylov_step<float>(scopf_handle *, cudaGraphConditionalHandle);
+template long long enqueue_krylov_step<double>(scopf_handle *, cudaGraphConditionalHandle);
+
+// FGMRES work buffers and the Krylov control block (allocated on first use)
+int krylov_buffers(scopf_handle *h) {
+    const int64_t n = h->M.n_kkt;
+    constexpr int m = 16;
+    const GmresLayout GL = gmres_layout(m);
+    if (!h->kv) {
+        TRY(alloc(h, (size_t)(m + 1) * n, &h->kv));
+        TRY(alloc(h, (size_t)m * n, &h->kz));
+        TRY(alloc(h, (size_t)kDotBlocks * kMaxKrylov, &h->kpart));
+        TRY(alloc(h, (size_t)GL.total, &h->kst));
+    }
+    if (!h->kctl) {
+        TRY(alloc(h, 1, &h->kctl));
+        TRY(alloc(h, (size_t)3 * n, &h->kry_buf));
+    }
     return SCOPF_OK;
 }
 
@@ -885,11 +963,6 @@ static int solve_once(scopf_handle *h, const double *b, double *x) {
 // formed in fixed buffers and copied out.
 template <typename T>
 static int build_krylov_graph(scopf_handle *h, scopf_handle::KrylovGraph &G) {
-    const int64_t n = h->M.n_kkt;
-    constexpr int m = 16;
-    const GmresLayout GL = gmres_layout(m);
-    double *sc = h->kst + GL.sc;
-    double *vb = h->kry_buf, *zb = vb + n, *wb = zb + n;
     cudaStream_t cs = nullptr;
     cudaGraph_t g = nullptr;
     auto fail = [&](cudaError_t e) {
@@ -921,21 +994,7 @@ static int build_krylov_graph(scopf_handle *h, scopf_handle::KrylovGraph &G) {
     const bool timing = h->timer.on;
     h->stream = cs;
     h->timer.on = false;
-    const long long k0 = g_kernel_launches.load();
-    launch_kry_gather(n, h->kv, h->kctl, vb, cs);
-    solve_once<T>(h, vb, zb);
-    launch_kry_scatter(n, zb, h->kz, h->kctl, cs);
-    launch_spmv(h->dm, h->kval, zb, wb, cs);
-    for (double *coef : {h->kst + GL.c1, h->kst + GL.c2}) {   // classical Gram-Schmidt, twice
-        launch_kry_multi_dot(h->kv, n, h->kctl, wb, h->kpart, cs);
-        launch_kry_dot_finish(h->kpart, h->kctl, coef, cs);
-        launch_kry_axpy(wb, h->kv, n, h->kctl, false, coef, cs);
-    }
-    launch_multi_dot(wb, n, 1, wb, h->kpart, cs);
-    launch_dot_finish(h->kpart, 1, sc + 1, true, cs);
-    launch_kry_scale_out(n, sc + 1, wb, h->kv, h->kctl, cs);
-    launch_kry_column_next(h->kst, m, h->kctl, loop, cs);
-    G.body_kernels = g_kernel_launches.load() - k0;
+    G.body_kernels = enqueue_krylov_step<T>(h, loop);
     g_kernel_launches -= G.body_kernels;   // counted when they run
     h->stream = keep;
     h->timer.on = timing;
@@ -974,20 +1033,11 @@ int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, doub
     }
     constexpr int m = 16;
     const GmresLayout GL = gmres_layout(m);
-    if (!h->kv) {
-        TRY(alloc(h, (size_t)(m + 1) * n, &h->kv));
-        TRY(alloc(h, (size_t)m * n, &h->kz));
-        TRY(alloc(h, (size_t)kDotBlocks * kMaxKrylov, &h->kpart));
-        TRY(alloc(h, (size_t)GL.total, &h->kst));
-    }
+    TRY(krylov_buffers(h));
     double *sc = h->kst + GL.sc;
     // device-resident Krylov loop (one graph per factor precision)
     scopf_handle::KrylovGraph *G = nullptr;
     if (h->opt.device_loop) {
-        if (!h->kctl) {
-            TRY(alloc(h, 1, &h->kctl));
-            TRY(alloc(h, (size_t)3 * n, &h->kry_buf));
-        }
         if (h->kgraph_stale) {
             for (auto &g : h->kgraph) {
                 if (g.exec) cudaGraphExecDestroy(g.exec);

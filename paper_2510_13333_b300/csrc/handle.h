@@ -136,6 +136,22 @@ struct scopf_handle {
         bool failed = false;
     } kgraph[2];
     bool kgraph_stale = false;   // a kernel argument captured in the graphs changed
+    // device-resident interior-point iteration (option ipm_graph): control
+    // block, filter entries, generator constant costs, and two graphs per
+    // iteration -- the direction (one per factor precision) and the step
+    scopf::IpmCtl *ipm_ctl = nullptr;
+    double *ipm_filter = nullptr;
+    double *gen_c0 = nullptr;
+    struct IpmGraphs {
+        cudaGraphExec_t dir[2] = {nullptr, nullptr};   // [mixed, FP64]
+        cudaGraphExec_t step = nullptr;
+        bool failed = false;
+        const double *key_st = nullptr, *key_trial = nullptr;   // iterate buffers captured
+        // kernels per launch of each part (the launch count)
+        long long k_dir_pre[2] = {}, k_ic[2] = {}, k_solve[2] = {}, k_ref[2] = {}, k_kry[2] = {};
+        long long k_step_pre = 0, k_step_if = 0, k_ls = 0, k_restore = 0;
+    } ig;
+    bool ig_stale = false;   // a kernel argument captured in the iteration graphs changed
     double *ovals = nullptr;                                // scaled front originals
     scopf::FactorStatus *fstat = nullptr;
     double *red_scratch = nullptr, *red_out = nullptr;
@@ -214,6 +230,17 @@ int set_delta_w(scopf_handle *h, double delta_w);
 int factor_inertia(scopf_handle *h, int precision, double dw_last, double &delta, int &tries);
 int solve_impl(scopf_handle *h, const double *b, double *x, int max_refine, double *rel,
                int *steps);
+// pieces of the factorization and the refinement, enqueued on h->stream
+// (also captured into the device-resident iteration's graphs)
+template <typename T>
+cudaError_t factor_enqueue(scopf_handle *h);
+template <typename T>
+int solve_once(scopf_handle *h, const double *b, double *x);
+template <typename T>
+long long enqueue_krylov_step(scopf_handle *h, cudaGraphConditionalHandle loop);
+int krylov_buffers(scopf_handle *h);
+void assemble_enqueue(scopf_handle *h, const scopf_state *it, DScalar rho, double delta_w);
+void ipm_graphs_release(scopf_handle *h);   // destroy the iteration graphs
 double device_maxabs(scopf_handle *h, const double *x, int64_t n);
 double device_sumabs(scopf_handle *h, const double *x, int64_t n);
 }  // namespace scopf

@@ -89,8 +89,9 @@ __global__ void k_red_w(Dev D, const double *w, const double *gw, const double *
 
 // m-part: [max|gr|, max|c-r|, sum|c-r|, sum|lam|, max|r|]
 __global__ void k_red_m(Dev D, const double *c, const double *r, const double *lam,
-                        const double *lam_n, double rho, double *part) {
+                        const double *lam_n, DScalar rho_, double *part) {
     __shared__ double sh[kT];
+    const double rho = rho_.get();
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < D.m;
          i += (int64_t)gridDim.x * blockDim.x) {
@@ -112,9 +113,10 @@ __global__ void k_red_m(Dev D, const double *c, const double *r, const double *l
 
 // p-part: [max|gt|, max|gs|, max|py|, sum|py|, min s zs, max s zs, sum|yc|, sum|zs|, max|t|]
 __global__ void k_red_p(Dev D, const double *w, const double *t, const double *s,
-                        const double *yc, const double *zs, const double *nu0_n, double rho,
+                        const double *yc, const double *zs, const double *nu0_n, DScalar rho_,
                         double *part) {
     __shared__ double sh[kT];
+    const double rho = rho_.get();
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = INFINITY, a5 = -INFINITY, a6 = 0, a7 = 0, a8 = 0;
     for (int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; q < D.p;
          q += (int64_t)gridDim.x * blockDim.x) {
@@ -146,9 +148,10 @@ __global__ void k_red_p(Dev D, const double *w, const double *t, const double *s
 // barrier objective pieces at a state: [sum ln(slacks of w), sum ln s, lam_n'r + rho/2 r'r,
 // nu0_n't + rho/2 t't, number of nonpositive slacks]
 __global__ void k_barrier(Dev D, const double *w, const double *r, const double *t,
-                          const double *s, const double *lam_n, const double *nu0_n, double rho,
+                          const double *s, const double *lam_n, const double *nu0_n, DScalar rho_,
                           double *part) {
     __shared__ double sh[kT];
+    const double rho = rho_.get();
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
     const int64_t tot = D.n + D.m + D.p;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
@@ -183,9 +186,10 @@ __global__ void k_barrier(Dev D, const double *w, const double *r, const double 
 // [g'dw, -mu sum dw/sl + mu sum dw/su, (lam_n + rho r)'dr, (nu0_n + rho t)'dt, -mu sum ds/s]
 __global__ void k_dirderiv(Dev D, const double *w, const double *g, const double *r,
                            const double *t, const double *s, const double *lam_n,
-                           const double *nu0_n, double rho, double mu, const double *dw,
+                           const double *nu0_n, DScalar rho_, DScalar mu_, const double *dw,
                            const double *dr, const double *dt, const double *ds, double *part) {
     __shared__ double sh[kT];
+    const double rho = rho_.get(), mu = mu_.get();
     double a0 = 0, a1 = 0, a2 = 0, a3 = 0, a4 = 0;
     const int64_t tot = D.n + D.m + D.p;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
@@ -216,9 +220,10 @@ __global__ void k_dirderiv(Dev D, const double *w, const double *g, const double
 // fraction to boundary: [alpha_primal, alpha_dual]
 __global__ void k_ftb(Dev D, const double *w, const double *s, const double *zl,
                       const double *zu, const double *zs, const double *dw, const double *ds,
-                      const double *dzl, const double *dzu, const double *dzs, double tau,
+                      const double *dzl, const double *dzu, const double *dzs, DScalar tau_,
                       double *part) {
     __shared__ double sh[kT];
+    const double tau = tau_.get();
     double ap = 1.0, az = 1.0;
     const int64_t tot = D.n + D.p;
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < tot;
@@ -261,12 +266,13 @@ __global__ void k_split(int64_t n_kkt, const int8_t *kind, const int64_t *index,
 __global__ void k_recover(Dev D, const double *w, const double *r, const double *t,
                           const double *s, const double *lam, const double *yc, const double *zl,
                           const double *zu, const double *zs, const double *lam_n,
-                          const double *nu0_n, double rho, double mu, const double *dw,
+                          const double *nu0_n, DScalar rho_, DScalar mu_, const double *dw,
                           const double *dlam, const double *dyc, double *dr, double *dt,
                           double *ds, double *dzl, double *dzu, double *dzs) {
     const int64_t tot = D.n + D.m + D.p;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tot) return;
+    const double rho = rho_.get(), mu = mu_.get();
     if (i < D.n) {
         const double l = D.wl[i], u = D.wu[i], x = w[i];
         dzl[i] = 0.0;
@@ -338,10 +344,11 @@ __global__ void k_ftb_finish(const double *part, int nblk, double *alpha) {
 
 // kappa_sigma safeguard of the bound multipliers (W&B 2006, eq. 16)
 __global__ void k_zsafe(Dev D, const double *w, const double *s, double *zl, double *zu,
-                        double *zs, double mu, double ks) {
+                        double *zs, DScalar mu_, double ks) {
     const int64_t tot = D.n + D.p;
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= tot) return;
+    const double mu = mu_.get();
     if (i < D.n) {
         const double l = D.wl[i], u = D.wu[i], x = w[i];
         if (l > -INFINITY) {
@@ -365,6 +372,81 @@ __global__ void k_reset_t(Dev D, const double *w, const double *s, double *t) {
 }
 
 inline int nb(int64_t n) { return (int)((n + kT - 1) / kT > 0 ? (n + kT - 1) / kT : 1); }
+
+// ---- fixed-order combination of per-CTA partials ------------------------
+// The host loop and the device-resident iteration combine the reductions'
+// partials in the same order, so both take the same decisions from the same
+// values: lane l of 32 folds entries l, l + 32, l + 64, ... in turn, then the
+// 32 lane values are folded pairwise (l with l + 16 for l < 16, then l with
+// l + 8, ..., l with l + 1).  Only additions, minima and maxima: no
+// contraction into FMA can change a result.
+enum { kOpMax = 0, kOpMin = 1, kOpSum = 2 };
+__host__ __device__ inline double comb_ident(int op) {
+    return op == kOpMax ? -INFINITY : (op == kOpMin ? INFINITY : 0.0);
+}
+__host__ __device__ inline double comb_op(double a, double b, int op) {
+    return op == kOpMax ? fmax(a, b) : (op == kOpMin ? fmin(a, b) : a + b);
+}
+// entries p[b * stride], b < count
+double comb32_host(const double *p, int count, int stride, int op) {
+    double v[32];
+    for (int l = 0; l < 32; l++) {
+        double a = comb_ident(op);
+        for (int b = l; b < count; b += 32) a = comb_op(a, p[(size_t)b * stride], op);
+        v[l] = a;
+    }
+    for (int off = 16; off > 0; off >>= 1)
+        for (int l = 0; l < off; l++) v[l] = comb_op(v[l], v[l + off], op);
+    return v[0];
+}
+// the same in one warp (all 32 lanes call it; every lane gets the result)
+__device__ double comb32_warp(const double *p, int count, int stride, int op) {
+    const int l = threadIdx.x & 31;
+    double a = comb_ident(op);
+    for (int b = l; b < count; b += 32) a = comb_op(a, p[(size_t)b * stride], op);
+    for (int off = 16; off > 0; off >>= 1) a = comb_op(a, __shfl_down_sync(0xffffffffu, a, off), op);
+    return __shfl_sync(0xffffffffu, a, 0);
+}
+
+// Generation cost phi(w) = sum_g [c2 (100 p_g)^2 + c1 (100 p_g) + c0] / 1e4
+// of eq. (scopf), per-generator terms folded in the order above.  Each term
+// is ((c2 pv) pv + c1 pv) + c0 with pv = 100 p_g, rounded operation by
+// operation on both sides.
+struct GenCost {
+    const double *c2, *c1, *c0;
+    int ng;
+};
+double phi_fixed_host(const double *p0, const double *c2, const double *c1, const double *c0,
+                      int ng) {
+    std::vector<double> t(ng > 0 ? ng : 1);
+    for (int i = 0; i < ng; i++) {
+        const double pv = 100.0 * p0[i];
+        t[i] = c2[i] * pv * pv + c1[i] * pv + c0[i];
+    }
+    return comb32_host(t.data(), ng, 1, kOpSum) / 1.0e4;
+}
+__device__ double phi_fixed_warp(const double *p0, const GenCost g) {
+    const int l = threadIdx.x & 31;
+    double a = 0.0;
+    for (int i = l; i < g.ng; i += 32) {
+        const double pv = __dmul_rn(100.0, p0[i]);
+        const double t = __dadd_rn(__dadd_rn(__dmul_rn(__dmul_rn(g.c2[i], pv), pv),
+                                             __dmul_rn(g.c1[i], pv)),
+                                   g.c0[i]);
+        a = a + t;
+    }
+    for (int off = 16; off > 0; off >>= 1) a = a + __shfl_down_sync(0xffffffffu, a, off);
+    return __ddiv_rn(__shfl_sync(0xffffffffu, a, 0), 1.0e4);
+}
+// barrier function phi + (lam_n'r + rho/2 r'r) + (nu0_n't + rho/2 t't)
+// - mu (sum ln slacks) from the 5-slot partials of k_barrier at `part`
+__device__ double barrier_fixed_warp(double phi, double mu, const double *part) {
+    const double bad = comb32_warp(part + 4, kB, 5, kOpSum);
+    const double l0 = comb32_warp(part + 0, kB, 5, kOpSum), l1 = comb32_warp(part + 1, kB, 5, kOpSum);
+    const double q2 = comb32_warp(part + 2, kB, 5, kOpSum), q3 = comb32_warp(part + 3, kB, 5, kOpSum);
+    if (bad > 0) return INFINITY;
+    return __dsub_rn(__dadd_rn(__dadd_rn(phi, q2), q3), __dmul_rn(mu, __dadd_rn(l0, l1)));
+}
 
 struct Timer {
     std::chrono::steady_clock::time_point t0 = std::chrono::steady_clock::now();
@@ -467,13 +549,7 @@ struct Ipm {
         host_sync(h, s);
     }
     double comb(int k, int slot, int op, int region = 0) {
-        double a = op == 0 ? -INFINITY : (op == 1 ? INFINITY : 0.0);
-        const double *pp = part.data() + (size_t)kB * region;
-        for (int b = 0; b < kB; b++) {
-            const double v = pp[(size_t)b * k + slot];
-            a = op == 0 ? std::fmax(a, v) : (op == 1 ? std::fmin(a, v) : a + v);
-        }
-        return a;
+        return comb32_host(part.data() + (size_t)kB * region + slot, kB, k, op);
     }
 
     // ---- residual norms (error measure E_mu, W&B 2006 eq. 5)
@@ -482,7 +558,6 @@ struct Ipm {
         bool has_comp;
     };
     Norms norms(const scopf_state &st, double rho) {
-        Norms N{};
         // regions: w (7 slots) at 0, constraint rows (5) at 7, pairs (9) at 12
         note_launch(), k_red_w<<<kB, kT, 0, s>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
         note_launch(), k_red_m<<<kB, kT, 0, s>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart + kB * 7);
@@ -501,6 +576,12 @@ struct Ipm {
             h->lead_zero_host = *reinterpret_cast<const int *>(part.data() + (size_t)kB * regions);
             h->lead_zero_valid = true;
         }
+        return combine_norms();
+    }
+    // the norms from fetched partials: w (7 slots) at region 0, constraint
+    // rows (5) at 7, pairs (9) at 12
+    Norms combine_norms() {
+        Norms N{};
         double dw = comb(7, 0, 0);
         double cmin = std::fmin(comb(7, 1, 1), comb(7, 3, 1));
         double cmax = std::fmax(comb(7, 2, 0), comb(7, 4, 0));
@@ -556,15 +637,11 @@ struct Ipm {
                             cudaMemcpyDeviceToHost, s);
         host_sync(h, s);
     }
-    // phi from the fetched p_g^0 (same formula as scopf_eval)
+    // phi from the fetched p_g^0 (the formula of scopf_eval, terms summed
+    // in the fixed order)
     double phi_host() const {
         const Model &M = h->M;
-        double f = 0;
-        for (int i = 0; i < M.ng; i++) {
-            const double pv = 100.0 * p0h[i];
-            f += M.c2[i] * pv * pv + M.c1[i] * pv + M.c0[i];
-        }
-        return f / 1.0e4;
+        return phi_fixed_host(p0h.data(), M.c2.data(), M.c1.data(), M.c0.data(), M.ng);
     }
     // barrier function from its partials (5 slots at `region`)
     double barrier_value(double phi, double mu, int region) {
@@ -650,6 +727,764 @@ struct Ipm {
     int streak = 0;
 };
 
+// ===========================================================================
+// Device-resident interior-point iteration (option ipm_graph).
+//
+// After the host has read the iteration's error measure and taken the
+// barrier update, one iteration is two CUDA-graph launches:
+//  * the direction graph (one per factor precision): right-hand side, then a
+//    WHILE node over the inertia-correction trials (shift of the primal
+//    diagonal, factorization, inertia test and next delta_w, W&B 2006 Alg. IC),
+//    then -- an IF node on its success -- the solve and the refinement: a
+//    WHILE node over FGMRES cycles whose Krylov steps are a nested WHILE node;
+//  * the step graph: an IF node on a usable direction holding the recovery
+//    of the eliminated directions, the fraction to the boundary, a WHILE node
+//    over the filter line-search trials (trial point, its theta and barrier
+//    function, the filter test and backtracking), an IF node for the elastic
+//    restoration, the bound-multiplier safeguard, and the model evaluation,
+//    KKT assembly and norm reductions at the new iterate.
+// The host reads the norms' partials and the control block once per
+// iteration.  The decisions are the host loop's, computed in the same
+// order from the same partials (the fixed-order combination above), so the
+// two loops take the same steps; the one difference is that the switching
+// condition's (-grad'd)^s_phi is evaluated with CUDA's pow (the host loop
+// uses the C library's; both within a few ulp).  A stalled FP32 refinement
+// is handed to the host, which redoes the direction in FP64 (as the host
+// loop does) and then launches the step graph.
+namespace {
+
+constexpr int kMaxIcTries = 200;   // safety bound only: delta_w > delta_w_max ends the loop first
+
+template <typename T>
+int dev_alloc(scopf_handle *h, size_t n, T **out) {
+    T *p = nullptr;
+    cudaError_t e = cudaMalloc(&p, sizeof(T) * (n ? n : 1));
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? SCOPF_ERR_OOM : SCOPF_ERR_CUDA;
+    }
+    cudaMemset(p, 0, sizeof(T) * (n ? n : 1));
+    h->allocations.push_back(p);
+    *out = p;
+    return SCOPF_OK;
+}
+
+__global__ void k_ctl_set(IpmCtl *c, double mu, double rho, double tau, double th, double tmin,
+                          double tmax, double pow_th, double dw_last, int clear_filter) {
+    c->mu = mu;
+    c->rho = rho;
+    c->tau = tau;
+    c->th = th;
+    c->theta_min = tmin;
+    c->theta_max = tmax;
+    c->pow_th = pow_th;
+    c->dw_last = dw_last;
+    if (clear_filter) c->filt_n = 0;
+}
+
+// the host redid the direction: the step graph may run
+__global__ void k_ctl_ok(IpmCtl *c) {
+    c->ok = 1;
+    c->stall = 0;
+    c->status = SCOPF_OK;
+}
+
+__global__ void k_cond_flag(cudaGraphConditionalHandle hc, const int *flag, int want) {
+    cudaGraphSetConditional(hc, *flag == want ? 1u : 0u);
+}
+
+// IC-1 / IC-3 start: delta_w = 0, unless its factorization must meet an
+// exactly zero pivot (counted into lead_zero), then the IC-3 value
+__global__ void k_ic_start(IpmCtl *c, scopf_options o, int have_lead) {
+    const double dw = c->dw_last;
+    const double ic3 = dw == 0.0 ? o.delta_w0 : fmax(o.delta_w_min, __dmul_rn(o.kappa_w_minus, dw));
+    c->ic3 = ic3;
+    c->delta = 0.0;
+    c->current = 0.0;   // the assembled K has delta_w = 0
+    c->known_zero = 0;
+    if (o.known_zero_pivot && have_lead && c->lead_zero > 0) {
+        c->delta = ic3;
+        c->known_zero = 1;
+    }
+    c->tries = 0;
+    c->status = SCOPF_OK;
+    c->ok = 0;
+    c->stall = 0;
+    c->dir_done = 0;
+    c->ref_it = 0;
+    c->ref_cycles = 0;
+    c->rel = 0.0;
+}
+
+// K(delta_w): primal diagonal = (assembled entry) + delta_w
+__global__ void k_diag_set_ctl(int64_t n, const int64_t *__restrict__ pos,
+                               const double *__restrict__ base, const IpmCtl *__restrict__ c,
+                               double *__restrict__ kval) {
+    const double d = c->delta;
+    if (d == c->current) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) kval[pos[i]] = base[i] + d;
+}
+
+// after a factorization: accept the inertia (n, m + p, 0) or take the next
+// delta_w (IC-3 value, then growth by kappa_w_plus or kappa_w_plus_bar)
+__global__ void k_ic_decide(IpmCtl *c, const FactorStatus *fs, scopf_options o, int64_t npos,
+                            int64_t nneg, cudaGraphConditionalHandle loop) {
+    c->current = c->delta;
+    c->tries++;
+    unsigned more = 0;
+    if (fs->error) {
+        c->status = SCOPF_ERR_TIMEOUT;
+    } else if (!(fs->n_pos == npos && fs->n_neg == nneg && fs->n_zero == 0)) {
+        const double d = c->delta == 0.0
+                             ? c->ic3
+                             : __dmul_rn(c->delta, c->dw_last > 0.0 ? o.kappa_w_plus : o.kappa_w_plus_bar);
+        c->delta = d;
+        if (d > o.delta_w_max || c->tries >= kMaxIcTries) c->status = SCOPF_ERR_WRONG_INERTIA;
+        else more = 1;
+    }
+    cudaGraphSetConditional(loop, more);
+}
+
+// residual check of the refinement: red = (|b|_inf, |b - K x|_inf)
+__global__ void k_ref_check(IpmCtl *c, const double *red, const KrylovCtl *kc, int first,
+                            double tol, int max_refine, cudaGraphConditionalHandle loop) {
+    const double bn = red[0], rn = red[1];
+    if (first) {
+        c->bden = bn > 0 ? bn : 1.0;
+        c->ref_it = 0;
+        c->ref_cycles = 0;
+    } else {
+        c->ref_it = kc->it;
+        c->ref_cycles++;
+    }
+    c->bnorm = bn;
+    const double r = rn / c->bden;
+    c->rel = r;
+    const bool more = r > tol && c->ref_it < max_refine && isfinite(r) &&
+                      c->ref_cycles <= max_refine;
+    cudaGraphSetConditional(loop, more ? 1u : 0u);
+}
+
+// a new FGMRES cycle's Krylov loop (its WHILE node runs at least one step)
+__global__ void k_kry_start_ctl(KrylovCtl *kc, const IpmCtl *c, int max_refine, double tol,
+                                cudaGraphConditionalHandle kry) {
+    kc->j = 0;
+    kc->it = c->ref_it;
+    kc->max_it = max_refine;
+    kc->jend = 0;
+    kc->target = __dmul_rn(__dmul_rn(tol, c->bnorm), 0.5);
+    cudaGraphSetConditional(kry, 1u);
+}
+
+// outcome of the direction: a stalled FP32 refinement goes to the host,
+// a stalled FP64 one is accepted
+__global__ void k_ref_end(IpmCtl *c, const FactorStatus *fs, double tol, int mixed) {
+    const double r = c->rel;
+    c->dir_done = 1;
+    if (fs->error) c->status = SCOPF_ERR_TIMEOUT;
+    else if (!isfinite(r)) c->status = SCOPF_ERR_NUMERICAL;
+    else if (r > tol && mixed) c->stall = 1;
+    else c->ok = 1;
+}
+
+// Line search start (W&B 2006 Section 2.3): fraction-to-boundary steps from
+// region 0 (2 slots), barrier function at the iterate from region 2 (5
+// slots), its directional derivative from region 7 (5 slots), alpha_min
+__global__ void k_ls_init(IpmCtl *c, const double *part, const double *p0, GenCost gc,
+                          scopf_options o, cudaGraphConditionalHandle loop) {
+    const double ap = fmin(1.0, comb32_warp(part, kB, 2, kOpMin));
+    const double az = fmin(1.0, comb32_warp(part + 1, kB, 2, kOpMin));
+    const double ph = barrier_fixed_warp(phi_fixed_warp(p0, gc), c->mu, part + kB * 2);
+    const double gd = comb32_warp(part + kB * 7, kB * 5, 1, kOpSum);
+    if (threadIdx.x != 0) return;
+    const double th = c->th;
+    double amin, pgd = 0.0;
+    if (gd < 0) {
+        pgd = pow(-gd, o.s_phi);
+        amin = __dmul_rn(o.gamma_alpha,
+                         fmin(o.gamma_theta, fmin(__ddiv_rn(__dmul_rn(o.gamma_phi, th), -gd),
+                                                  __ddiv_rn(__dmul_rn(o.delta_sw, c->pow_th), pgd))));
+    } else {
+        amin = __dmul_rn(o.gamma_alpha, o.gamma_theta);
+    }
+    c->ph = ph;
+    c->gd = gd;
+    c->amin = amin;
+    c->pow_gd = pgd;
+    c->alpha[0] = ap;
+    c->alpha[1] = az;
+    c->nback = 0;
+    c->accepted = 0;
+    c->ftype = 0;
+    c->trials = 0;
+    cudaGraphSetConditional(loop, 1u);
+}
+
+// One line-search trial's verdict from the trial point's partials: theta
+// from regions 0 (constraint rows, slot 2) and 5 (pairs, slot 3), barrier
+// function from region 14.  Filter acceptance, switching condition,
+// Armijo or sufficient decrease, backtracking by 1/2.
+__global__ void k_ls_decide(IpmCtl *c, const double *part, const double *p0, GenCost gc,
+                            double *filt, int filt_cap, scopf_options o, int has_p,
+                            cudaGraphConditionalHandle loop) {
+    const double tm = comb32_warp(part + 2, kB, 5, kOpSum);
+    const double tp = has_p ? comb32_warp(part + kB * 5 + 3, kB, 9, kOpSum) : 0.0;
+    const double tht = __dadd_rn(tm, tp);
+    const double pht = barrier_fixed_warp(phi_fixed_warp(p0, gc), c->mu, part + kB * 14);
+    const int lane = threadIdx.x & 31;
+    const int nf = c->filt_n;
+    bool in = false;
+    for (int i = lane; i < nf; i += 32) in = in || (tht >= filt[2 * i] && pht >= filt[2 * i + 1]);
+    in = __any_sync(0xffffffffu, in);
+    if (lane != 0) return;
+    const double a = c->alpha[0], th = c->th, ph = c->ph, gd = c->gd;
+    bool ok = false, ftype = false;
+    if (tht <= c->theta_max && !in) {
+        const bool sw = gd < 0 && __dmul_rn(a, c->pow_gd) > __dmul_rn(o.delta_sw, c->pow_th);
+        if (th <= c->theta_min && sw) {
+            ok = pht <= __dadd_rn(ph, __dmul_rn(__dmul_rn(o.eta_phi, a), gd));
+            ftype = ok;
+        } else {
+            ok = tht <= __dmul_rn(__dsub_rn(1.0, o.gamma_theta), th) ||
+                 pht <= __dsub_rn(ph, __dmul_rn(o.gamma_phi, th));
+        }
+    }
+    c->tht = tht;
+    c->pht = pht;
+    c->trials++;
+    unsigned more = 0;
+    if (ok) {
+        c->accepted = 1;
+        c->ftype = ftype;
+        if (!ftype && nf < filt_cap) {
+            filt[2 * nf] = __dmul_rn(__dsub_rn(1.0, o.gamma_theta), th);
+            filt[2 * nf + 1] = __dsub_rn(ph, __dmul_rn(o.gamma_phi, th));
+            c->filt_n = nf + 1;
+        }
+    } else {
+        c->nback++;
+        if (!(a < c->amin || c->nback >= o.max_backtrack) && c->trials <= o.max_backtrack + 1) {
+            c->alpha[0] = __dmul_rn(a, 0.5);
+            more = 1;
+        }
+    }
+    cudaGraphSetConditional(loop, more);
+}
+
+__global__ void k_filter_clear(IpmCtl *c) { c->filt_n = 0; }
+
+// st = trial, all nine iterate vectors
+__global__ void k_copy_all(StepSegs S) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= S.end[8]) return;
+    int k = 0;
+    while (i >= S.end[k]) k++;
+    const int64_t j = i - (k ? S.end[k - 1] : 0);
+    S.y[k][j] = S.x[k][j];
+}
+
+// ---- capture helpers
+// a conditional handle on the graph stream `s` is capturing into (its
+// default value is applied at every launch of the whole graph)
+cudaError_t cond_handle(cudaStream_t s, unsigned dflt, cudaGraphConditionalHandle *hc) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    return cudaGraphConditionalHandleCreate(hc, g, dflt, cudaGraphCondAssignDefault);
+}
+// a conditional node after what `s` has captured so far; later work on `s`
+// depends on it.  Its body graph is returned.
+cudaError_t cond_node(cudaStream_t s, cudaGraphConditionalNodeType type,
+                      cudaGraphConditionalHandle hc, cudaGraph_t *body) {
+    cudaStreamCaptureStatus cs;
+    cudaGraph_t g = nullptr;
+    const cudaGraphNode_t *deps = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, nullptr, &g, &deps, &ed, &nd);
+    if (e != cudaSuccess) return e;
+    if (cs != cudaStreamCaptureStatusActive) return cudaErrorStreamCaptureInvalidated;
+    cudaGraphNodeParams np{};
+    np.type = cudaGraphNodeTypeConditional;
+    np.conditional.handle = hc;
+    np.conditional.type = type;
+    np.conditional.size = 1;
+    cudaGraphNode_t node;
+    if ((e = cudaGraphAddNode(&node, g, deps, ed, nd, &np)) != cudaSuccess) return e;
+    *body = np.conditional.phGraph_out[0];
+    return cudaStreamUpdateCaptureDependencies(s, &node, nullptr, 1,
+                                               cudaStreamSetCaptureDependencies);
+}
+
+// Streams of the capture, one per nesting level; h->stream follows the
+// level being captured.
+struct Capture {
+    scopf_handle *h;
+    cudaStream_t s[4] = {};
+    cudaError_t e = cudaSuccess;
+    cudaStream_t keep;
+    bool timing;
+    explicit Capture(scopf_handle *hh) : h(hh), keep(hh->stream), timing(hh->timer.on) {
+        for (auto &x : s)
+            if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking);
+        h->timer.on = false;
+    }
+    void chk(cudaError_t x) {
+        if (e == cudaSuccess && x != cudaSuccess) e = x;
+    }
+    // start capturing level lv + 1 into `body`
+    void open(int lv, cudaGraph_t body) {
+        chk(cudaStreamBeginCaptureToGraph(s[lv + 1], body, nullptr, nullptr, 0,
+                                          cudaStreamCaptureModeRelaxed));
+        h->stream = s[lv + 1];
+    }
+    void close(int lv) {
+        cudaGraph_t g = nullptr;
+        chk(cudaStreamEndCapture(s[lv + 1], &g));
+        h->stream = s[lv];
+    }
+    ~Capture() {
+        for (int lv = 3; lv >= 0; lv--) {   // end any capture an error left open
+            cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+            if (s[lv] && cudaStreamIsCapturing(s[lv], &cs) == cudaSuccess &&
+                cs != cudaStreamCaptureStatusNone) {
+                cudaGraph_t g = nullptr;
+                cudaStreamEndCapture(s[lv], &g);
+                if (lv == 0 && g) cudaGraphDestroy(g);
+            }
+        }
+        for (auto &x : s)
+            if (x) cudaStreamDestroy(x);
+        cudaGetLastError();
+        h->stream = keep;
+        h->timer.on = timing;
+    }
+};
+
+GenCost gen_cost(scopf_handle *h) {
+    return GenCost{h->dm.c2, h->dm.c1, h->gen_c0, h->M.ng};
+}
+
+}  // namespace
+
+void ipm_graphs_release(scopf_handle *h) {
+    auto &G = h->ig;
+    for (auto &x : G.dir)
+        if (x) cudaGraphExecDestroy(x);
+    if (G.step) cudaGraphExecDestroy(G.step);
+    G.dir[0] = G.dir[1] = nullptr;
+    G.step = nullptr;
+}
+
+namespace {
+
+// The direction graph for factor precision T (see above).  cnt: kernels
+// per launch of its parts -- [0] always, [1] per inertia trial, [2] once
+// when the solve runs, [3] per refinement cycle, [4] per Krylov step.
+template <typename T>
+cudaError_t build_dir_graph(scopf_handle *h, cudaGraphExec_t *out, long long cnt[5]) {
+    const scopf_options &o = h->opt;
+    const Model &M = h->M;
+    const int64_t n = M.n_kkt;
+    constexpr int m = 16;
+    const GmresLayout GL = gmres_layout(m);
+    double *sc = h->kst + GL.sc;
+    IpmCtl *c = h->ipm_ctl;
+    const scopf_state &st = h->st;
+    auto now = []() { return g_kernel_launches.load(); };
+    const long long t0 = now();
+    for (int i = 0; i < 5; i++) cnt[i] = 0;
+    cudaGraph_t g = nullptr;
+    const bool sinv_stale = h->sinv_stale;   // capturing the factorization sets it
+    {
+        Capture C(h);
+        if (C.e != cudaSuccess) return C.e;
+        C.chk(cudaStreamBeginCapture(C.s[0], cudaStreamCaptureModeRelaxed));
+        h->stream = C.s[0];
+        cudaStream_t s0 = C.s[0];
+        {
+            RhsArgs a{st.w, st.r, st.t, st.s, st.lam, st.yc, st.zs, h->gw, h->c,
+                      h->lam_n, h->nu0_n, DScalar::at(&c->rho), DScalar::at(&c->mu)};
+            launch_rhs(h->dm, a, h->rhs, s0);
+        }
+        const bool lead = h->n_lead > 0 && o.known_zero_pivot;
+        if (lead) launch_count_zero_diag(h->n_lead, h->lead_pdiag, h->pdiag_base, &c->lead_zero, s0);
+        note_launch(), k_ic_start<<<1, 1, 0, s0>>>(c, o, lead ? 1 : 0);
+        cudaGraphConditionalHandle hic = 0, hok = 0, href = 0, hkry = 0;
+        cudaGraph_t body = nullptr;
+        // inertia correction: WHILE (default 1: at least one factorization)
+        C.chk(cond_handle(s0, 1, &hic));
+        if (C.e == cudaSuccess) C.chk(cond_node(s0, cudaGraphCondTypeWhile, hic, &body));
+        if (C.e == cudaSuccess) {
+            C.open(0, body);
+            const long long t1 = now();
+            if (h->n_pdiag)
+                note_launch(), k_diag_set_ctl<<<nb(h->n_pdiag), kT, 0, C.s[1]>>>(
+                    h->n_pdiag, h->pdiag_pos, h->pdiag_base, c, h->kval);
+            C.chk(factor_enqueue<T>(h));
+            note_launch(), k_ic_decide<<<1, 1, 0, C.s[1]>>>(c, h->fstat, o, M.n, M.m + M.p, hic);
+            cnt[1] = now() - t1;
+            C.close(0);
+        }
+        // solve and refinement: IF the inertia correction succeeded
+        C.chk(cond_handle(s0, 0, &hok));
+        note_launch(), k_cond_flag<<<1, 1, 0, s0>>>(hok, &c->status, SCOPF_OK);
+        if (C.e == cudaSuccess) C.chk(cond_node(s0, cudaGraphCondTypeIf, hok, &body));
+        if (C.e == cudaSuccess) {
+            C.open(0, body);
+            cudaStream_t s1 = C.s[1];
+            const long long t3 = now();
+            if (sizeof(T) == 4) launch_dense_inverse(h->S, (int)M.nborder, h->Sinv, s1);
+            C.chk(cudaMemcpyAsync(h->res, h->rhs, sizeof(double) * n, cudaMemcpyDeviceToDevice, s1));
+            solve_once<T>(h, h->res, h->sol);
+            launch_residual(h->dm, h->kval, h->sol, h->res, h->tmp_kkt, s1);
+            reduce_maxabs2(h->res, h->tmp_kkt, n, h->red_out, h->red_scratch, s1);
+            C.chk(cond_handle(s1, 0, &href));
+            note_launch(), k_ref_check<<<1, 1, 0, s1>>>(c, h->red_out, h->kctl, 1, o.refine_tol,
+                                                        o.max_refine, href);
+            // FGMRES cycles: WHILE the residual is above refine_tol
+            if (C.e == cudaSuccess) C.chk(cond_node(s1, cudaGraphCondTypeWhile, href, &body));
+            if (C.e == cudaSuccess) {
+                C.open(1, body);
+                cudaStream_t s2 = C.s[2];
+                const long long t4 = now();
+                launch_multi_dot(h->tmp_kkt, n, 1, h->tmp_kkt, h->kpart, s2);
+                launch_dot_finish(h->kpart, 1, sc + 0, true, s2);
+                launch_gmres_init(h->kst, m, s2);
+                launch_scale_inv(n, sc + 0, h->tmp_kkt, h->kv, s2);
+                C.chk(cond_handle(s2, 0, &hkry));
+                note_launch(), k_kry_start_ctl<<<1, 1, 0, s2>>>(h->kctl, c, o.max_refine,
+                                                                o.refine_tol, hkry);
+                // Krylov steps of the cycle: WHILE (set to 1 by the start kernel)
+                if (C.e == cudaSuccess) C.chk(cond_node(s2, cudaGraphCondTypeWhile, hkry, &body));
+                if (C.e == cudaSuccess) {
+                    C.open(2, body);
+                    cnt[4] = enqueue_krylov_step<T>(h, hkry);
+                    C.close(2);
+                }
+                launch_kry_solve(h->kst, m, h->kctl, s2);
+                launch_kry_axpy(h->sol, h->kz, n, h->kctl, true, h->kst + GL.c1, s2);
+                launch_residual(h->dm, h->kval, h->sol, h->res, h->tmp_kkt, s2);
+                reduce_maxabs2(h->res, h->tmp_kkt, n, h->red_out, h->red_scratch, s2);
+                note_launch(), k_ref_check<<<1, 1, 0, s2>>>(c, h->red_out, h->kctl, 0,
+                                                            o.refine_tol, o.max_refine, href);
+                cnt[3] = now() - t4 - cnt[4];
+                C.close(1);
+            }
+            note_launch(), k_ref_end<<<1, 1, 0, s1>>>(c, h->fstat, o.refine_tol, sizeof(T) == 4 ? 1 : 0);
+            cnt[2] = now() - t3 - cnt[3] - cnt[4];
+            C.close(0);
+        }
+        cnt[0] = now() - t0 - cnt[1] - cnt[2] - cnt[3] - cnt[4];
+        C.chk(cudaGetLastError());
+        if (C.e == cudaSuccess) C.chk(cudaStreamEndCapture(s0, &g));
+        if (C.e == cudaSuccess) C.chk(cudaGraphInstantiate(out, g, 0));
+        if (g) cudaGraphDestroy(g);
+        g_kernel_launches -= now() - t0;   // counted when they run
+        h->sinv_stale = sinv_stale;
+        if (C.e != cudaSuccess) return C.e;
+    }
+    return cudaSuccess;
+}
+
+// y = x + alpha d over the nine iterate vectors (alpha on the device)
+StepSegs step_segs(const scopf_state &out, const scopf_state &st, const scopf_state &d,
+                   const Model &M) {
+    StepSegs S;
+    const double *xs[9] = {st.w, st.r, st.lam, st.t, st.s, st.yc, st.zs, st.zl, st.zu};
+    const double *ds[9] = {d.w, d.r, d.lam, d.t, d.s, d.yc, d.zs, d.zl, d.zu};
+    double *ys[9] = {out.w, out.r, out.lam, out.t, out.s, out.yc, out.zs, out.zl, out.zu};
+    const int64_t len[9] = {M.n, M.m, M.m, M.p, M.p, M.p, M.p, M.n, M.n};
+    int64_t acc = 0;
+    for (int k = 0; k < 9; k++) {
+        S.x[k] = xs[k];
+        S.d[k] = ds[k];
+        S.y[k] = ys[k];
+        acc += len[k];
+        S.end[k] = acc;
+    }
+    S.dual_from = 6;
+    return S;
+}
+
+// The step graph (see above).  cnt: [0] always, [1] once when the direction
+// is usable, [2] per line-search trial, [3] for a restoration.
+cudaError_t build_step_graph(scopf_handle *h, cudaGraphExec_t *out, long long cnt[4]) {
+    const scopf_options &o = h->opt;
+    const Model &M = h->M;
+    const int64_t n = M.n, m = M.m, p = M.p;
+    IpmCtl *c = h->ipm_ctl;
+    const scopf_state &st = h->st, &d = h->dir, &tr = h->trial;
+    const Dev D{h->wl, h->wu, h->dm.comp1, h->dm.comp2, n, m, p};
+    double *dpart = h->ipm_part;
+    const DScalar rho = DScalar::at(&c->rho), mu = DScalar::at(&c->mu);
+    const GenCost gc = gen_cost(h);
+    const int filt_cap = o.max_inner + 2;
+    auto now = []() { return g_kernel_launches.load(); };
+    const long long t0 = now();
+    for (int i = 0; i < 4; i++) cnt[i] = 0;
+    cudaGraph_t g = nullptr;
+    Capture C(h);
+    if (C.e != cudaSuccess) return C.e;
+    C.chk(cudaStreamBeginCapture(C.s[0], cudaStreamCaptureModeRelaxed));
+    h->stream = C.s[0];
+    cudaStream_t s0 = C.s[0];
+    cudaGraphConditionalHandle hok = 0, hls = 0, hre = 0;
+    cudaGraph_t body = nullptr;
+    C.chk(cond_handle(s0, 0, &hok));
+    note_launch(), k_cond_flag<<<1, 1, 0, s0>>>(hok, &c->ok, 1);
+    if (C.e == cudaSuccess) C.chk(cond_node(s0, cudaGraphCondTypeIf, hok, &body));
+    if (C.e == cudaSuccess) {
+        C.open(0, body);
+        cudaStream_t s1 = C.s[1];
+        const long long t1 = now();
+        note_launch(), k_split<<<nb(M.n_kkt), kT, 0, s1>>>(M.n_kkt, h->dm.row_kind, h->dm.row_index,
+                                                           h->sol, d.w, d.lam, d.yc);
+        note_launch(), k_recover<<<nb(n + m + p), kT, 0, s1>>>(D, st.w, st.r, st.t, st.s, st.lam, st.yc,
+                                                                st.zl, st.zu, st.zs, h->lam_n, h->nu0_n,
+                                                                rho, mu, d.w, d.lam, d.yc, d.r, d.t,
+                                                                d.s, d.zl, d.zu, d.zs);
+        note_launch(), k_ftb<<<kB, kT, 0, s1>>>(D, st.w, st.s, st.zl, st.zu, st.zs, d.w, d.s, d.zl,
+                                                d.zu, d.zs, DScalar::at(&c->tau), dpart);
+        note_launch(), k_barrier<<<kB, kT, 0, s1>>>(D, st.w, st.r, st.t, st.s, h->lam_n, h->nu0_n,
+                                                    rho, dpart + kB * 2);
+        note_launch(), k_dirderiv<<<kB, kT, 0, s1>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n,
+                                                     h->nu0_n, rho, mu, d.w, d.r, d.t, d.s,
+                                                     dpart + kB * 7);
+        C.chk(cond_handle(s1, 0, &hls));
+        note_launch(), k_ls_init<<<1, 32, 0, s1>>>(c, dpart, st.w + M.border0, gc, o, hls);
+        // line-search trials: WHILE (set to 1 by the start kernel)
+        if (C.e == cudaSuccess) C.chk(cond_node(s1, cudaGraphCondTypeWhile, hls, &body));
+        if (C.e == cudaSuccess) {
+            C.open(1, body);
+            cudaStream_t s2 = C.s[2];
+            const long long t2 = now();
+            const StepSegs S = step_segs(tr, st, d, M);
+            if (S.end[8] > 0) note_launch(), k_step_all<<<nb(S.end[8]), kT, 0, s2>>>(S, 0.0, 0.0, c->alpha);
+            launch_eval_elements(h->dm, tr.w, tr.lam, tr.yc, h->ev, 0, s2);
+            launch_constraints(h->dm, tr.w, h->ev, h->c, s2);
+            note_launch(), k_red_m<<<kB, kT, 0, s2>>>(D, h->c, tr.r, tr.lam, h->lam_n, 1.0, dpart);
+            if (p)
+                note_launch(), k_red_p<<<kB, kT, 0, s2>>>(D, tr.w, tr.t, tr.s, tr.yc, tr.zs, h->nu0_n,
+                                                          1.0, dpart + kB * 5);
+            note_launch(), k_barrier<<<kB, kT, 0, s2>>>(D, tr.w, tr.r, tr.t, tr.s, h->lam_n, h->nu0_n,
+                                                        rho, dpart + kB * 14);
+            note_launch(), k_ls_decide<<<1, 32, 0, s2>>>(c, dpart, tr.w + M.border0, gc, h->ipm_filter,
+                                                         filt_cap, o, p > 0 ? 1 : 0, hls);
+            cnt[2] = now() - t2;
+            C.close(1);
+        }
+        // restoration: IF no trial was accepted
+        C.chk(cond_handle(s1, 0, &hre));
+        note_launch(), k_cond_flag<<<1, 1, 0, s1>>>(hre, &c->accepted, 0);
+        if (C.e == cudaSuccess) C.chk(cond_node(s1, cudaGraphCondTypeIf, hre, &body));
+        if (C.e == cudaSuccess) {
+            C.open(1, body);
+            cudaStream_t s2 = C.s[2];
+            const long long t2 = now();
+            const StepSegs S = step_segs(tr, st, d, M);
+            if (S.end[8] > 0) note_launch(), k_step_all<<<nb(S.end[8]), kT, 0, s2>>>(S, 0.0, 0.0, c->alpha);
+            launch_eval_elements(h->dm, tr.w, tr.lam, tr.yc, h->ev, 0, s2);
+            launch_constraints(h->dm, tr.w, h->ev, tr.r, s2);
+            if (p) note_launch(), k_reset_t<<<nb(p), kT, 0, s2>>>(D, tr.w, tr.s, tr.t);
+            note_launch(), k_filter_clear<<<1, 1, 0, s2>>>(c);
+            cnt[3] = now() - t2;
+            C.close(1);
+        }
+        note_launch(), k_zsafe<<<nb(n + p), kT, 0, s1>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu,
+                                                         o.kappa_sigma);
+        {
+            const StepSegs S = step_segs(st, tr, d, M);   // st = trial
+            if (S.end[8] > 0) note_launch(), k_copy_all<<<nb(S.end[8]), kT, 0, s1>>>(S);
+        }
+        // the next iterate's model, KKT (delta_w = 0) and norm partials
+        assemble_enqueue(h, &st, rho, 0.0);
+        note_launch(), k_red_w<<<kB, kT, 0, s1>>>(D, st.w, h->gw, st.zl, st.zu, dpart);
+        note_launch(), k_red_m<<<kB, kT, 0, s1>>>(D, h->c, st.r, st.lam, h->lam_n, rho, dpart + kB * 7);
+        if (p)
+            note_launch(), k_red_p<<<kB, kT, 0, s1>>>(D, st.w, st.t, st.s, st.yc, st.zs, h->nu0_n, rho,
+                                                      dpart + kB * 12);
+        cnt[1] = now() - t1 - cnt[2] - cnt[3];
+        C.close(0);
+    }
+    cnt[0] = now() - t0 - cnt[1] - cnt[2] - cnt[3];
+    C.chk(cudaGetLastError());
+    if (C.e == cudaSuccess) C.chk(cudaStreamEndCapture(s0, &g));
+    if (C.e == cudaSuccess) C.chk(cudaGraphInstantiate(out, g, 0));
+    if (g) cudaGraphDestroy(g);
+    g_kernel_launches -= now() - t0;
+    return C.e;
+}
+
+}  // namespace
+
+namespace {
+
+// Allocations and graphs of the device-resident iteration for factor
+// precision `prec`; G.failed (with last_error) when a graph could not be
+// built -- the host loop then runs.
+int ipm_graph_setup(scopf_handle *h, int prec) {
+    auto &G = h->ig;
+    if (G.failed) return SCOPF_OK;
+    const Model &M = h->M;
+    if (!h->ipm_ctl) {
+        int r = dev_alloc(h, 1, &h->ipm_ctl);
+        if (r == SCOPF_OK) r = dev_alloc(h, 2 * (size_t)(h->opt.max_inner + 2), &h->ipm_filter);
+        if (r == SCOPF_OK) r = dev_alloc(h, (size_t)M.ng, &h->gen_c0);
+        if (r != SCOPF_OK) return r;
+        if (M.ng && cudaMemcpy(h->gen_c0, M.c0.data(), sizeof(double) * M.ng,
+                               cudaMemcpyHostToDevice) != cudaSuccess)
+            return SCOPF_ERR_CUDA;
+    }
+    int r = krylov_buffers(h);
+    if (r != SCOPF_OK) return r;
+    if (h->ig_stale || G.key_st != h->st.w || G.key_trial != h->trial.w) {
+        ipm_graphs_release(h);   // built around other buffers
+        h->ig_stale = false;
+    }
+    G.key_st = h->st.w;
+    G.key_trial = h->trial.w;
+    const int pi = prec == SCOPF_PREC_MIXED ? 0 : 1;
+    cudaError_t e = cudaSuccess;
+    if (!G.dir[pi]) {
+        long long cnt[5];
+        e = pi == 0 ? build_dir_graph<float>(h, &G.dir[pi], cnt)
+                    : build_dir_graph<double>(h, &G.dir[pi], cnt);
+        if (e == cudaSuccess) {
+            G.k_dir_pre[pi] = cnt[0];
+            G.k_ic[pi] = cnt[1];
+            G.k_solve[pi] = cnt[2];
+            G.k_ref[pi] = cnt[3];
+            G.k_kry[pi] = cnt[4];
+        } else {
+            G.dir[pi] = nullptr;
+        }
+    }
+    if (e == cudaSuccess && !G.step) {
+        long long cnt[4];
+        e = build_step_graph(h, &G.step, cnt);
+        if (e == cudaSuccess) {
+            G.k_step_pre = cnt[0];
+            G.k_step_if = cnt[1];
+            G.k_ls = cnt[2];
+            G.k_restore = cnt[3];
+        } else {
+            G.step = nullptr;
+        }
+    }
+    if (e != cudaSuccess) {
+        h->last_error = std::string("interior-point iteration graph: ") + cudaGetErrorString(e);
+        G.failed = true;
+        ipm_graphs_release(h);
+    }
+    return SCOPF_OK;
+}
+
+// kernels the iteration's graph launches ran (the launch count)
+long long graph_kernels(const scopf_handle *h, int pi, const IpmCtl &c, bool step_ran) {
+    const auto &G = h->ig;
+    long long k = G.k_dir_pre[pi] + G.k_ic[pi] * c.tries;
+    if (c.dir_done) k += G.k_solve[pi] + G.k_ref[pi] * c.ref_cycles + G.k_kry[pi] * c.ref_it;
+    k += G.k_step_pre;
+    if (step_ran) k += G.k_step_if + G.k_ls * c.trials + (c.accepted ? 0 : G.k_restore);
+    return k;
+}
+
+}  // namespace
+
+// One device-resident iteration at (mu, rho): the direction and step graphs
+// and one read-back of the control block (into `out`) and of the new
+// iterate's norm partials (into I.part).  Returns the direction's error, if
+// any.
+static int graph_iteration(Ipm &I, int prec, double mu, double rho, double tau, double th,
+                           double theta_min, double theta_max, double dw_last, bool clear_filter,
+                           IpmCtl &out) {
+    scopf_handle *h = I.h;
+    const scopf_options &o = h->opt;
+    cudaStream_t s = h->stream;
+    auto &G = h->ig;
+    const int pi = prec == SCOPF_PREC_MIXED ? 0 : 1;
+    const int regions = I.p ? 21 : 12;
+    note_launch(), k_ctl_set<<<1, 1, 0, s>>>(h->ipm_ctl, mu, rho, tau, th, theta_min, theta_max,
+                                             std::pow(th, o.s_theta), dw_last, clear_filter ? 1 : 0);
+    cudaError_t e = cudaGraphLaunch(G.dir[pi], s);
+    if (e == cudaSuccess) e = cudaGraphLaunch(G.step, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(I.part.data(), I.dpart, sizeof(double) * kB * regions,
+                            cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(&out, h->ipm_ctl, sizeof(IpmCtl), cudaMemcpyDeviceToHost, s);
+    if (e == cudaSuccess) e = host_sync(h, s);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    if (e != cudaSuccess) {
+        h->last_error = cudaGetErrorString(e);
+        return SCOPF_ERR_CUDA;
+    }
+    g_kernel_launches += graph_kernels(h, pi, out, out.ok != 0);
+    h->n_factor += out.tries;
+    h->n_known_zero += out.known_zero;
+    h->factored_precision = prec;
+    h->last_delta_w = out.delta;
+    if (out.dir_done) {
+        h->n_refine += out.ref_it;
+        h->n_solve_calls++;
+    }
+    if (out.status != SCOPF_OK) {
+        if (out.status == SCOPF_ERR_TIMEOUT)
+            h->last_error = "dependency wait timed out in the factorization or a sweep";
+        return out.status;
+    }
+    if (out.stall) {
+        // FP32 factors no longer accurate enough: redo the direction with
+        // FP64 factors (host-driven, as in the host loop) and stay in FP64
+        I.force_fp64 = true;
+        I.fallbacks++;
+        int in[3];
+        int r = factor_impl(h, SCOPF_PREC_FP64, in);
+        if (r != SCOPF_OK) return r;
+        double rel = 0;
+        int steps = 0;
+        r = solve_impl(h, h->rhs, h->sol, o.max_refine, &rel, &steps);
+        if (r == SCOPF_ERR_REFINE_STALL) r = SCOPF_OK;
+        if (r != SCOPF_OK) return r;
+        note_launch(), k_ctl_ok<<<1, 1, 0, s>>>(h->ipm_ctl);
+        e = cudaGraphLaunch(G.step, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(I.part.data(), I.dpart, sizeof(double) * kB * regions,
+                                cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&out, h->ipm_ctl, sizeof(IpmCtl), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = host_sync(h, s);
+        if (e == cudaSuccess) e = cudaGetLastError();
+        if (e != cudaSuccess) {
+            h->last_error = cudaGetErrorString(e);
+            return SCOPF_ERR_CUDA;
+        }
+        g_kernel_launches += h->ig.k_step_pre + h->ig.k_step_if + h->ig.k_ls * out.trials +
+                             (out.accepted ? 0 : h->ig.k_restore);
+    } else if (!I.force_fp64 && o.fp64_switch_refine > 0 && prec == SCOPF_PREC_MIXED) {
+        // the cost switch of the host loop (Ipm::direction)
+        I.streak = out.ref_it >= o.fp64_switch_refine ? I.streak + 1 : 0;
+        if (I.streak >= std::max(1, o.fp64_switch_streak)) {
+            I.force_fp64 = true;
+            I.fallbacks++;
+        }
+    }
+    // the direction graph formed S^-1 of its factors; the step graph
+    // assembled K at the new iterate (delta_w = 0)
+    h->sinv_stale = false;
+    h->assembled = true;
+    h->factored = false;
+    h->lead_zero_valid = false;
+    h->last_delta_w = 0.0;
+    h->assembled_delta_w = 0.0;
+    h->last_rho = rho;
+    return SCOPF_OK;
+}
+
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, bool resume) {
     Timer T;
     const scopf_options &o = h->opt;
@@ -728,6 +1563,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
     double t_newton = 0.0;
     const int fact0 = h->n_factor, ref0 = h->n_refine;
     const long long syncs0 = h->n_host_syncs;
+    int graph_iters = 0;
     for (outer = 1; outer <= o.max_outer; outer++) {
         const double om = std::fmax(omega, o.tol);
         // ------------------------------------------------------------ inner
@@ -737,6 +1573,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
         const double th0 = N.theta;
         const double theta_max = 1e4 * std::fmax(1.0, th0), theta_min = 1e-4 * std::fmax(1.0, th0);
         std::vector<std::pair<double, double>> filt;
+        bool clear_filter = true;   // the device-resident iteration's filter starts empty
         int inner_status = SCOPF_OK;
         while (true) {
             E0 = I.error(N, o.fixed_mu ? mu : 0.0);   // fixed mu: the barrier error
@@ -749,9 +1586,48 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
             while (!o.fixed_mu && Emu <= o.kappa_eps * mu && mu > o.mu_min) {
                 mu = std::fmax(o.mu_min, std::fmin(o.kappa_mu * mu, std::pow(mu, o.theta_mu)));
                 filt.clear();
+                clear_filter = true;
                 Emu = I.error(N, mu);
             }
             const double tau = std::fmax(o.tau_min, 1.0 - mu);
+            const bool graph = o.ipm_graph && o.device_loop;
+            if (graph) {
+                const int prec = I.force_fp64 ? SCOPF_PREC_FP64 : h->precision;
+                r = ipm_graph_setup(h, prec);
+                if (r != SCOPF_OK) return r;
+            }
+            if (graph && !h->ig.failed) {
+                // the iteration as two graph launches and one read-back
+                Timer tn;
+                const int prec = I.force_fp64 ? SCOPF_PREC_FP64 : h->precision;
+                const int fact_before = h->n_factor, refine_before = h->n_refine;
+                const double E0_step = E0, th = N.theta;
+                IpmCtl c{};
+                r = graph_iteration(I, prec, mu, rho, tau, th, theta_min, theta_max, dw_last,
+                                    clear_filter, c);
+                clear_filter = false;
+                if (r != SCOPF_OK) {
+                    inner_status = r == SCOPF_ERR_WRONG_INERTIA ? SCOPF_ERR_NUMERICAL : r;
+                    break;
+                }
+                if (c.delta > 0.0) dw_last = c.delta;
+                inner++;
+                graph_iters++;
+                const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th,
+                                                c.ph, c.alpha[0], c.alpha[1], c.delta,
+                                                (double)(h->n_factor - fact_before),
+                                                (double)(h->n_refine - refine_before),
+                                                (double)h->factored_precision,
+                                                c.accepted ? 1.0 : 0.0, (double)c.nback};
+                h->hist_inner.insert(h->hist_inner.end(), rec, rec + kHistInner);
+                if (o.verbose)
+                    std::printf("  it %4d mu %.1e E0 %.2e th %.2e a %.2e dw %.1e tries %d%s (graph)\n",
+                                inner, mu, E0, th, c.alpha[0], c.delta, c.tries,
+                                c.accepted ? "" : " R");
+                N = I.combine_norms();
+                t_newton += tn.s();
+                continue;
+            }
             Timer tn;
             // right-hand side at the final mu (K at delta_w = 0 is assembled)
             {
@@ -786,16 +1662,11 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
             note_launch(), k_dirderiv<<<kB, kT, 0, s>>>(D, st.w, h->g, st.r, st.t, st.s, h->lam_n, h->nu0_n, rho,
                                          mu, d.w, d.r, d.t, d.s, I.dpart + kB * 7);
             I.fetch_p0(12, st.w);
-            double ap = 1.0, az = 1.0;
-            for (int b = 0; b < kB; b++) {
-                ap = std::fmin(ap, I.part[2 * b]);
-                az = std::fmin(az, I.part[2 * b + 1]);
-            }
+            const double ap = std::fmin(1.0, I.comb(2, 0, kOpMin));
+            const double az = std::fmin(1.0, I.comb(2, 1, kOpMin));
             const double th = N.theta;
             const double ph = I.barrier_value(I.phi_host(), mu, 2);
-            double gd = 0;
-            for (int b = 0; b < kB; b++)
-                for (int q = 0; q < 5; q++) gd += I.part[(size_t)kB * 7 + (size_t)b * 5 + q];
+            const double gd = comb32_host(I.part.data() + (size_t)kB * 7, kB * 5, 1, kOpSum);
             double amin;
             if (gd < 0)
                 amin = o.gamma_alpha * std::fmin(o.gamma_theta, std::fmin(o.gamma_phi * th / -gd,
@@ -938,6 +1809,7 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
     res->time_newton_s = t_newton;
     res->delta_w_last = dw_last;
     res->host_round_trips = h->n_host_syncs - syncs0;
+    res->graph_iters = graph_iters;
     return status == SCOPF_OK ? SCOPF_OK : status;
 }
 

@@ -13,6 +13,24 @@ extern std::atomic<long long> g_kernel_launches;
 inline void note_launch() { g_kernel_launches.fetch_add(1, std::memory_order_relaxed); }
 
 
+// A scalar kernel argument, given by value or -- for kernels replayed in a
+// CUDA graph whose scalars change between replays -- read from device
+// memory when the kernel runs (p != nullptr).
+struct DScalar {
+    double v = 0.0;
+    const double *p = nullptr;
+    DScalar() = default;
+    DScalar(double x) : v(x) {}
+    static DScalar at(const double *q) {
+        DScalar d;
+        d.p = q;
+        return d;
+    }
+#ifdef __CUDACC__
+    __device__ __forceinline__ double get() const { return p ? *p : v; }
+#endif
+};
+
 // ---------------------------------------------------------------- model
 struct DevModel {
     int64_t n, m, p, n_kkt, nnz;
@@ -52,7 +70,7 @@ void launch_constraints(const DevModel &M, const double *w, const double *ev, do
                         cudaStream_t s);
 void launch_gradient(const DevModel &M, const double *w, double *g, cudaStream_t s);
 void launch_diag_terms(const DevModel &M, const double *w, const double *zl, const double *zu,
-                       const double *sv, const double *zs, double rho, double delta_w,
+                       const double *sv, const double *zs, DScalar rho, DScalar delta_w,
                        double *diag, cudaStream_t s);
 void launch_assemble(const DevModel &M, const double *ev, const double *diag, double *kval,
                      cudaStream_t s);
@@ -61,7 +79,7 @@ void launch_dual_product(const DevModel &M, const double *kval, const double *g,
                          const double *lam, const double *yc, double *gw, cudaStream_t s);
 struct RhsArgs {
     const double *w, *r, *t, *sv, *lam, *yc, *zs, *gw, *c, *lam_n, *nu0_n;
-    double rho, mu;
+    DScalar rho, mu;
 };
 void launch_rhs(const DevModel &M, const RhsArgs &a, double *rhs, cudaStream_t s);
 // y = b - K x  (FP64); K from kval
@@ -109,6 +127,30 @@ struct KrylovCtl {
     double target;  // residual estimate at which the cycle stops
 };
 void launch_kry_start(KrylovCtl *c, int it, int max_it, double target, cudaStream_t s);
+
+// Control block of the device-resident interior-point iteration: the
+// scalars its kernels read at run time, the state of its inertia-correction,
+// refinement and line-search loops, and the outcome the host reads back.
+struct IpmCtl {
+    // set by the host before the iteration
+    double mu, rho, tau, th, theta_min, theta_max, pow_th, dw_last;
+    int clear_filter, pad0;
+    // inertia correction
+    double delta, current, ic3;
+    int tries, known_zero, lead_zero, pad1;
+    // refinement
+    double bnorm, bden, rel;
+    int ref_it, ref_cycles;
+    // line search
+    double alpha[2];   // primal and dual step of the current trial
+    double ph, gd, amin, pow_gd, tht, pht;
+    int nback, accepted, ftype, trials, filt_n, pad2;
+    // outcome
+    int status;        // SCOPF_OK or the error of the direction
+    int ok;            // the direction is usable: the step graph runs
+    int stall;         // mixed precision: the refinement stalled
+    int dir_done;      // the solve of the direction ran
+};
 void launch_kry_gather(int64_t n, const double *V, const KrylovCtl *c, double *out, cudaStream_t s);
 void launch_kry_scatter(int64_t n, const double *in, double *Z, const KrylovCtl *c, cudaStream_t s);
 void launch_kry_multi_dot(const double *V, int64_t n, const KrylovCtl *c, const double *w,

@@ -168,10 +168,11 @@ __global__ void k_diag(int64_t n_kkt, const int8_t *__restrict__ kind,
                        const int64_t *__restrict__ index, const double *__restrict__ wl,
                        const double *__restrict__ wu, const double *__restrict__ w,
                        const double *__restrict__ zl, const double *__restrict__ zu,
-                       const double *__restrict__ sv, const double *__restrict__ zs, double rho,
-                       double delta_w, double *__restrict__ diag) {
+                       const double *__restrict__ sv, const double *__restrict__ zs, DScalar rho_,
+                       DScalar delta_w_, double *__restrict__ diag) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_kkt) return;
+    const double rho = rho_.get(), delta_w = delta_w_.get();
     const int8_t k = kind[i];
     const int64_t j = index[i];
     double d;
@@ -262,22 +263,23 @@ __global__ void k_rhs(int64_t n_kkt, const int8_t *__restrict__ kind,
                       const int64_t *__restrict__ c2, RhsArgs a, double *__restrict__ rhs) {
     int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_kkt) return;
+    const double mu = a.mu.get(), rho = a.rho.get();
     const int8_t k = kind[i];
     const int64_t j = index[i];
     double v;
     if (k == 0) {
         double rw = a.gw[j];
         const double l = wl[j], u = wu[j], x = a.w[j];
-        if (l > -INFINITY) rw -= a.mu / (x - l);
-        if (u < INFINITY) rw += a.mu / (u - x);
+        if (l > -INFINITY) rw -= mu / (x - l);
+        if (u < INFINITY) rw += mu / (u - x);
         v = -rw;
     } else if (k == 1) {
-        v = -(a.c[j] - a.r[j]) - (a.lam_n[j] + a.rho * a.r[j] - a.lam[j]) / a.rho;
+        v = -(a.c[j] - a.r[j]) - (a.lam_n[j] + rho * a.r[j] - a.lam[j]) / rho;
     } else {
         const double s = a.sv[j];
         const double py = a.w[c1[j]] * a.w[c2[j]] - a.t[j] + s;
-        v = -py - (a.nu0_n[j] + a.rho * a.t[j] - a.yc[j]) / a.rho -
-            (a.mu / s - a.yc[j]) * s / a.zs[j];
+        v = -py - (a.nu0_n[j] + rho * a.t[j] - a.yc[j]) / rho -
+            (mu / s - a.yc[j]) * s / a.zs[j];
     }
     rhs[i] = v;
 }
@@ -770,7 +772,7 @@ void launch_gradient(const DevModel &M, const double *w, double *g, cudaStream_t
 }
 
 void launch_diag_terms(const DevModel &M, const double *w, const double *zl, const double *zu,
-                       const double *sv, const double *zs, double rho, double delta_w,
+                       const double *sv, const double *zs, DScalar rho, DScalar delta_w,
                        double *diag, cudaStream_t s) {
     note_launch(), k_diag<<<nblocks(M.n_kkt), kThreads, 0, s>>>(M.n_kkt, M.row_kind, M.row_index, M.wl, M.wu, w,
                                                  zl, zu, sv, zs, rho, delta_w, diag);

@@ -41,7 +41,8 @@ def test_refined_solve_identical(cuda, prec):
 def test_ncl_solve_identical(cuda):
     import paper_2510_13333_b300 as P
     inst = H.instance(1)
-    res = [P.SCOPF(inst, precision=P.PREC_MIXED, device_loop=loop).ncl_solve() for loop in (0, 1)]
+    res = [P.SCOPF(inst, precision=P.PREC_MIXED, device_loop=loop, ipm_graph=0).ncl_solve()
+           for loop in (0, 1)]
     a, b = res
     assert a["call_status"] == b["call_status"] == 0
     for k in ("objective", "inner_iters", "factorizations", "refine_steps", "fp64_fallbacks"):

@@ -1,0 +1,42 @@
+"""The device-resident interior-point iteration (option ipm_graph): after the
+host's convergence test and barrier update, an iteration is two CUDA-graph
+launches whose WHILE nodes run the inertia-correction trials, the refinement
+cycles and the line-search trials.  Its decisions are the host loop's, taken
+from the same partials combined in the same order, so it must take the very
+same steps as the host loop (Section IV-B; W&B 2006 inertia correction and
+filter line search), with one host read-back per iteration."""
+import numpy as np
+import pytest
+
+from tests import helpers as H
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("idx,prec", [(0, 0), (0, 1), (1, 0), (1, 1)])
+def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec):
+    import paper_2510_13333_b300 as P
+    inst = H.instance(idx)
+    host = P.SCOPF(inst, precision=prec, ipm_graph=0)
+    rh = host.ncl_solve()
+    assert rh["call_status"] == 0 and rh["graph_iters"] == 0
+    _, hh = host.history(0)
+    dev = P.SCOPF(inst, precision=prec, ipm_graph=1)
+    rd = dev.ncl_solve()
+    assert rd["call_status"] == 0, (rd, dev.last_error())
+    assert rd["graph_iters"] == rd["inner_iters"] > 0, dev.last_error()
+    _, hd = dev.history(0)
+    assert rd["inner_iters"] == rh["inner_iters"] and rd["outer_iters"] == rh["outer_iters"]
+    assert rd["factorizations"] == rh["factorizations"]
+    assert rd["refine_steps"] == rh["refine_steps"]
+    assert rd["fp64_fallbacks"] == rh["fp64_fallbacks"]
+    cols = P.SCOPF.HISTORY_INNER
+    for j, name in enumerate(cols):
+        np.testing.assert_array_equal(hd[:, j], hh[:, j], err_msg=name)
+    assert rd["objective"] == rh["objective"]
+    assert rd["max_violation"] == rh["max_violation"]
+    # one read-back per iteration; the outer loop's assembly and the final
+    # report add a few per outer iteration, an FP64 redo its own
+    bound = rd["inner_iters"] + 3 * rd["outer_iters"] + 8 + 12 * rd["fp64_fallbacks"]
+    assert rd["host_round_trips"] <= bound, (rd["host_round_trips"], bound)
+    assert rh["host_round_trips"] > 3 * rh["inner_iters"]
