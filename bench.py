@@ -50,18 +50,35 @@ FP64_PEAK_TFLOPS = 1.25
 
 # DRAM bytes (read + write) of one solve's forward and backward sweeps,
 # from the ncu capture summarized in profiles/solve_sweeps_syn500_k256.md,
-# valid only for the sweep kernels' source it was taken with
+# valid only for the sweep kernels' source it was taken with: the digest
+# covers the solve kernels' section of the source and the solve's launch
+# function
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "510fd13e140b74e9404714fcfa47060b39a3512a",
+                 "sha1": "358c906026a73b5f2170fa802748412d5477bbc7",
                  # k_solve_fwd + k_border_gather + k_border_apply + k_solve_bwd (FP32)
                  "bytes_per_solve": 254899200 + 212480 + 296704 + 315174912}
 
 
-def sweep_traffic():
+def sweep_source_digest(text: str):
+    """sha1 of the sweep kernels' source: from the solves section marker to
+    the first kernel after it that is not a solve kernel, plus the
+    launch_solve function."""
     import hashlib
     try:
-        with open(os.path.join(ROOT, SWEEP_TRAFFIC["source"]), "rb") as fh:
-            if hashlib.sha1(fh.read()).hexdigest() != SWEEP_TRAFFIC["sha1"]:
+        a = text.index("// ---------------------------------------------------------------- solves")
+        b = text.index("k_ruiz_entries(", a)
+        b = text.rindex("\n", a, b)
+        c = text.index("void launch_solve(")
+        d = text.index("#define INST(T)", c)
+    except ValueError:
+        return None
+    return hashlib.sha1((text[a:b] + text[c:d]).encode()).hexdigest()
+
+
+def sweep_traffic():
+    try:
+        with open(os.path.join(ROOT, SWEEP_TRAFFIC["source"])) as fh:
+            if sweep_source_digest(fh.read()) != SWEEP_TRAFFIC["sha1"]:
                 return None
     except OSError:
         return None

@@ -300,9 +300,13 @@ __device__ __forceinline__ void count_pivot(T d, T ptol, bool ptol_zero, int &n_
 // counted as zero by the caller)
 template <typename T>
 __device__ __forceinline__ T pivot_reciprocal(T d) {
-    const T dd = d == (T)0 ? (sizeof(T) == 4 ? (T)1e-30 : (T)1e-300) : d;
-    if constexpr (sizeof(T) == 4) return (T)1 / dd;
-    else return rcp_newton(dd);
+    if constexpr (sizeof(T) == 4) {
+        return 1.0f / (d == 0.0f ? 1e-30f : d);
+    } else {
+        // zero test on the bit pattern (an integer instruction)
+        const bool z = (__double_as_longlong(d) << 1) == 0;
+        return rcp_newton(z ? 1e-300 : d);
+    }
 }
 
 __global__ void k_reciprocal(int64_t n, const double *__restrict__ d, double *__restrict__ out) {
@@ -955,9 +959,15 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
 // One cooperative launch of G co-resident CTAs.  Per panel of kDB columns:
 //  A. every CTA loads the kDB x kDB diagonal block and factors it in shared
 //     memory (tiny; CTA 0 counts the inertia and writes it back), so no
-//     barrier is needed before
-//  B. the rows below are solved for their L entries, L21 = A21 L11^-T D^-1,
-//     one row per thread over the whole grid;
+//     barrier is needed before.  Column by column, the entries of the
+//     trailing triangle are updated by 120 threads at once (one entry each,
+//     one warp per SM sub-partition: on B300 an FP64 warp instruction holds
+//     the sub-partition's FP64 pipe for its full width whatever its active
+//     lanes, so the chain of pivots costs a few FP64 instructions each);
+//  B. the rows below are solved for W = L21 D = A21 L11^-T, two rows per
+//     warp (a half-warp per row, a lane per column: the forward substitution
+//     is one FMA per step across the lanes), spread over the grid's warps,
+//     and L21 = W D^-1 is stored;
 //  C. after a grid barrier, the trailing matrix takes the rank-kDB update
 //     A22 -= L21 D L21' in 32 x 32 tiles of its lower triangle, dealt to the
 //     CTAs; a second barrier ends the panel.
@@ -965,6 +975,7 @@ __global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ bo
 // st->error and every CTA then leaves without waiting again.
 constexpr int kDB = 16;     // panel width
 constexpr int kDT = 256;    // threads per CTA
+constexpr int kDTri = kDB * (kDB - 1) / 2;   // entries (r, j), 1 <= j <= r < kDB
 
 __device__ __forceinline__ bool dense_grid_barrier(FactorStatus *st, int spin_limit) {
     __syncthreads();
@@ -978,14 +989,12 @@ __device__ __forceinline__ bool dense_grid_barrier(FactorStatus *st, int spin_li
             st_release(reinterpret_cast<int *>(&st->bar_gen), g + 1);
         } else {
             int spins = 0;
-            unsigned ns = 32;
             while (ld_acquire(reinterpret_cast<const int *>(&st->bar_gen)) == g && *err == 0) {
                 if (++spins > spin_limit) {
                     atomicExch(&st->error, 3);
                     break;
                 }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
+                __nanosleep(32);
             }
         }
     }
@@ -999,6 +1008,16 @@ __global__ void __launch_bounds__(kDT) k_dense_ldlt(double *S, int n, FactorStat
     __shared__ double dinv[kDB];
     __shared__ double Li[kDB][33], Wj[kDB][33];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool ptol_zero = pivot_tol == 0.0;
+    // this thread's entry (er, ej), 1 <= ej <= er < kDB, of the diagonal
+    // block's trailing triangle (threads 0 .. kDTri - 1, row by row)
+    int er = 0, ej = 0;
+    if (tid < kDTri) {
+        int r = 0;
+        while ((r + 1) * (r + 2) / 2 <= tid) r++;
+        er = r + 1;
+        ej = tid - r * (r + 1) / 2 + 1;
+    }
     int s_pos = 0, s_neg = 0, s_zero = 0;
     for (int k0 = 0; k0 < n; k0 += kDB) {
         const int k1 = min(k0 + kDB, n), pw = k1 - k0;
@@ -1008,43 +1027,41 @@ __global__ void __launch_bounds__(kDT) k_dense_ldlt(double *S, int n, FactorStat
             A11[r][c] = (r < pw && c < pw && r >= c) ? S[(int64_t)(k0 + c) * n + k0 + r] : 0.0;
         }
         __syncthreads();
-        if (warp == 0) {
-            for (int c = 0; c < pw; c++) {
+        const bool act = tid < kDTri && er < pw;
+        for (int c = 0; c < pw; c++) {
+            if (tid < kDTri) {
                 const double d = A11[c][c];
-                if (lane == 0) {
-                    if (d > pivot_tol) s_pos++;
-                    else if (d < -pivot_tol) s_neg++;
-                    else s_zero++;
-                    dinv[c] = 1.0 / (d == 0.0 ? 1e-300 : d);
+                const double di = pivot_reciprocal<double>(d);
+                // u_r u_j / d_c with u the unscaled column (l d)
+                if (act && ej > c) A11[er][ej] -= A11[er][c] * (A11[ej][c] * di);
+                if (tid == 0) {
+                    dinv[c] = di;
+                    count_pivot<double>(d, pivot_tol, ptol_zero, s_pos, s_neg, s_zero);
                 }
-                __syncwarp();
-                const double di = dinv[c];
-                if (lane > c && lane < pw) A11[lane][c] *= di;
-                __syncwarp();
-                for (int j = c + 1; j < pw; j++) {
-                    const double ljd = A11[j][c] * d;
-                    if (lane >= j && lane < pw) A11[lane][j] -= A11[lane][c] * ljd;
-                }
-                __syncwarp();
             }
+            __syncthreads();
+        }
+        // the columns become L11 (unit lower)
+        if (act) {
+            const int c = ej - 1, r = er;   // every (r, c), 0 <= c < r < pw
+            A11[r][c] *= dinv[c];
         }
         __syncthreads();
-        // B: rows below the block, L21 = A21 L11^-T D^-1 (one row per thread)
-        for (int i = k1 + blockIdx.x * kDT + tid; i < n; i += gridDim.x * kDT) {
-            double w[kDB];
-#pragma unroll
-            for (int c = 0; c < kDB; c++) {
-                if (c < pw) {
-                    double v = S[(int64_t)(k0 + c) * n + i];
-#pragma unroll
-                    for (int c2 = 0; c2 < kDB; c2++)
-                        if (c2 < c) v -= w[c2] * A11[c][c2];
-                    w[c] = v;   // l_ic d_c
+        // B: rows below the block, W = A21 L11^-T by forward substitution
+        // (lane c of a half-warp holds w_c), then L21 = W D^-1
+        {
+            const int half = lane & 16, c = lane & 15;
+            const int nwarps = gridDim.x * (kDT / 32);
+            for (int gw = blockIdx.x * (kDT / 32) + warp; k1 + 2 * gw < n; gw += nwarps) {
+                const int i = k1 + 2 * gw + (half >> 4);
+                const bool ok = i < n && c < pw;
+                double x = ok ? S[(int64_t)(k0 + c) * n + i] : 0.0;
+                for (int c2 = 0; c2 + 1 < pw; c2++) {
+                    const double xc2 = __shfl_sync(0xffffffffu, x, half | c2);
+                    if (c > c2) x = fma(-xc2, A11[c][c2], x);
                 }
+                if (ok) S[(int64_t)(k0 + c) * n + i] = x * dinv[c];
             }
-#pragma unroll
-            for (int c = 0; c < kDB; c++)
-                if (c < pw) S[(int64_t)(k0 + c) * n + i] = w[c] * dinv[c];
         }
         // CTA 0 stores the factored diagonal block once no CTA can still be
         // loading it (after the barrier; the last block has no reader left)
