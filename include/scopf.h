@@ -348,7 +348,8 @@ int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, 
  * (a cudaStream_t or NULL) that keeps every SM busy with independent chains
  * of kind 0: FP32 FMA, 1: FP64 FMA, 2: FP64 tensor MMA (mma.sync m8n8k4),
  * 3: FP64 FMA on one lane per warp (flops of the active lanes only),
- * iters iterations each, and returns the launch's flop count in *flops (host,
+ * 4: FP64 FMA on even warps and FP64 tensor MMA on odd warps at once (equal
+ * flops per warp pair: whether the two share a pipe), iters iterations each, and returns the launch's flop count in *flops (host,
  * an FMA counted as 2).  out: device, at least 8 bytes, written only in a
  * case that never occurs (it keeps the chains from being optimised away).
  * The caller times the launch (CUDA events on the same stream).  Does not

@@ -223,7 +223,8 @@ def scopf_dense_ldlt_solve_noalloc(S, b, x=None):
     return x, tuple(int(v) for v in inert), st
 
 
-PEAK_KINDS = {0: "fp32_fma", 1: "fp64_fma", 2: "fp64_mma", 3: "fp64_fma_one_lane"}
+PEAK_KINDS = {0: "fp32_fma", 1: "fp64_fma", 2: "fp64_mma", 3: "fp64_fma_one_lane",
+              4: "fp64_fma_and_mma"}
 
 
 def scopf_peak_probe(kind: int, iters: int = 1 << 14, repeats: int = 5):

@@ -70,12 +70,48 @@ __global__ void __launch_bounds__(kPT) k_dmma_chains(int64_t iters, double *__re
     if (s == -1.2345) out[0] = s;
 }
 
+// Even warps run FP64 FMA chains (4 x iters steps), odd warps FP64 MMA
+// chains (iters steps): equal flops per warp pair, so the launch takes the
+// time of the slower half.  Whether the two FP64 paths share one pipe.
+__global__ void __launch_bounds__(kPT) k_fma_and_dmma(int64_t iters, double *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    double s = 0;
+    if ((threadIdx.x >> 5) & 1) {
+        const double a = 1e-3 * (lane + 1), b = 1e-3 * (32 - lane);
+        double d[kAcc][2];
+#pragma unroll
+        for (int j = 0; j < kAcc; j++) d[j][0] = d[j][1] = 0.0;
+        for (int64_t i = 0; i < iters; i++) {
+#pragma unroll
+            for (int j = 0; j < kAcc; j++)
+                asm volatile(
+                    "mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                    : "+d"(d[j][0]), "+d"(d[j][1])
+                    : "d"(a), "d"(b));
+        }
+#pragma unroll
+        for (int j = 0; j < kAcc; j++) s += d[j][0] + d[j][1];
+    } else {
+        double a[kChains];
+#pragma unroll
+        for (int j = 0; j < kChains; j++) a[j] = (double)(threadIdx.x + j) * 1e-3;
+        const double b = 0.999999, c = 1e-6;
+        for (int64_t i = 0; i < 4 * iters; i++) {
+#pragma unroll
+            for (int j = 0; j < kChains; j++) a[j] = fma(a[j], b, c);
+        }
+#pragma unroll
+        for (int j = 0; j < kChains; j++) s += a[j];
+    }
+    if (s == -1.2345) out[0] = s;
+}
+
 }  // namespace
 
 extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *stream,
                                 double *flops) {
     using namespace scopf;
-    if (!out || iters <= 0 || kind < 0 || kind > 3) return SCOPF_ERR_INVALID_ARG;
+    if (!out || iters <= 0 || kind < 0 || kind > 4) return SCOPF_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const int grid = sm_count() * (2048 / kPT);
     const double threads = (double)grid * kPT;
@@ -89,9 +125,13 @@ extern "C" int scopf_peak_probe(int32_t kind, int64_t iters, double *out, void *
     } else if (kind == 2) {
         note_launch(), k_dmma_chains<<<grid, kPT, 0, s>>>(iters, out);
         f = threads / 32.0 * kAcc * (8.0 * 8.0 * 4.0 * 2.0) * (double)iters;
-    } else {
+    } else if (kind == 3) {
         note_launch(), k_fma_chains_one_lane<<<grid, kPT, 0, s>>>(iters, out);
         f = threads / 32.0 * kChains * 2.0 * (double)iters;   // active lanes only
+    } else {
+        note_launch(), k_fma_and_dmma<<<grid, kPT, 0, s>>>(iters, out);
+        f = threads / 2.0 * kChains * 2.0 * 4.0 * (double)iters +
+            threads / 64.0 * kAcc * (8.0 * 8.0 * 4.0 * 2.0) * (double)iters;
     }
     if (cudaGetLastError() != cudaSuccess) return SCOPF_ERR_CUDA;
     if (flops) *flops = f;
