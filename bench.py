@@ -298,6 +298,20 @@ def gpu_tts_118(P, torch, precision, ipm_graph=1):
             "graph_iters": r["graph_iters"]}
 
 
+def host_cpu():
+    """The host's CPU model and logical core count (the oracle's machine)."""
+    model = None
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for ln in fh:
+                if ln.startswith("model name"):
+                    model = ln.split(":", 1)[1].strip()
+                    break
+    except OSError:
+        pass
+    return {"model": model, "nproc": os.cpu_count()}
+
+
 def oracle_step_sample(n_steps: int = 3, idx: int = CONFIG_IDX):
     """The cpu_baseline leg: n_steps oracle Newton steps of the bounded
     sample; returns (seconds per full-size step extrapolated in blocks,
@@ -338,7 +352,8 @@ def run_reference(args):
                        "sample_blocks": o.blocks, "full_blocks": o.full_blocks,
                        "setup_s": o.setup_s, "flush_l2": False},
             "cpu_baseline": {"value": value, "unit": "Newton steps/s", "cores": 1,
-                             "kind": "oracle", "sample": o.describe(args.steps, sec)},
+                             "kind": "oracle", "sample": o.describe(args.steps, sec),
+                             "host": host_cpu()},
             "e2e": {"value": value, "unit": "Newton steps/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -413,6 +428,12 @@ def phase_rooflines(sz, phases, solves, prec_bytes, peaks_live):
                       "frac_of_probe": ach / peaks_live[key] if peaks_live.get(key) else None,
                       "per_call": amount, "ms_per_call": per_call_s * 1e3, "calls": calls,
                       "work": what}
+            if k == "factor":
+                # the second roof of the small fronts: b nnz(L)
+                # written + 8 nnz(K) read
+                hb = prec_bytes * sz.nnz_L + 8 * sz.nnz_kkt
+                out[k]["hbm"] = {"bytes_per_call": hb, "achieved_gbs": hb / per_call_s / 1e9,
+                                 "peak_gbs": hbm, "frac": hb / per_call_s / 1e9 / hbm}
         else:
             ach = amount / per_call_s / 1e9
             out[k] = {"bound": "hbm", "achieved": ach, "unit": "GB/s", "peak": hbm,
@@ -498,6 +519,14 @@ def run_ours(args):
                      "kkt_error": r["kkt_error"], "feas_rt": r["feas_rt"],
                      "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"]),
                      "graph_iters": r["graph_iters"]}
+        # the metric's per-iteration rate: IPM iterations (each one Newton step
+        # with its inertia corrections, refinement and line search) per second,
+        # median over iterations 10..end, from the iteration log's wall times
+        names, hist = lib.history(0)
+        it_ms = hist[10:, list(names).index("ms")] if hist.shape[0] > 10 else hist[:, -1]
+        if it_ms.size:
+            tts[name]["iteration_ms_median_10_end"] = float(np.median(it_ms))
+            tts[name]["iterations_per_s_median_10_end"] = 1e3 / float(np.median(it_ms))
     if idx == CONFIG_IDX and args.tts != "none":
         tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
                              "fp64": gpu_tts_118(P, torch, P.PREC_FP64),
@@ -634,7 +663,7 @@ def run_ours(args):
     try:
         cpu_s, cpu_desc, cores = oracle_step_sample(idx=idx)
         cpu = {"value": 1.0 / cpu_s, "unit": "Newton steps/s", "cores": cores, "kind": "oracle",
-               "sample": cpu_desc}
+               "sample": cpu_desc, "host": host_cpu()}
         if idx == CONFIG_IDX:
             cpu["tts_118bus_k32"] = oracle_tts_118()
     except Exception as exc:  # keep the GPU number even if the CPU sample fails

@@ -432,14 +432,15 @@ int scopf_adjoint(scopf_handle *h, const double *seed_pg0, double seed_cost,
                   double *grad_Pd, double *grad_Qd, double *grad_c1);
 
 /* Iteration log of the handle's last ncl_solve (or scopf_screen).
- * which = 0: one record per interior-point iteration, 15 doubles: outer
+ * which = 0: one record per interior-point iteration, 16 doubles: outer
  *   iteration, inner iteration (cumulative), mu, rho, scaled KKT error E_0
  *   before the step, constraint violation theta and barrier objective phi at
  *   the iterate, accepted primal and dual step lengths, delta_w, number of
  *   factorizations (inertia corrections and FP64 fallback included),
  *   refinement steps, precision of the factors that produced the step
  *   (SCOPF_PREC_*), 1 if the filter accepted the step (0: elastic reset),
- *   backtracking steps.
+ *   backtracking steps, wall time of the iteration in ms (host clock, from
+ *   the right-hand side to the next iterate's norms read back).
  * which = 1: one record per NCL outer iteration, 8 doubles: outer iteration,
  *   rho, |r|_inf, |t|_inf, E_0, eta, omega, inner iterations so far.
  * *n_records and *record_len receive the log's size; out (host, capacity

@@ -557,7 +557,7 @@ class SCOPF:
 
     HISTORY_INNER = ("outer", "inner", "mu", "rho", "E0", "theta", "phi", "alpha_p", "alpha_d",
                      "delta_w", "factorizations", "refine_steps", "precision", "accepted",
-                     "backtracks")
+                     "backtracks", "ms")
     HISTORY_OUTER = ("outer", "rho", "r_inf", "t_inf", "E0", "eta", "omega", "inner")
 
     def last_error(self) -> str:

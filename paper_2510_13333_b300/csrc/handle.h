@@ -215,7 +215,7 @@ inline cudaError_t host_sync(scopf_handle *h, cudaStream_t s) {
 int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res,
                    bool resume = false);
 int block_multiplier_update(scopf_handle *h, double rho, double thr);
-constexpr int kHistInner = 15;   // fields of an inner-iteration record (scopf_history)
+constexpr int kHistInner = 16;   // fields of an inner-iteration record (scopf_history)
 constexpr int kHistOuter = 8;    // fields of an outer-iteration record
 void relaxed_bounds(const Model &M, double bound_relax, std::vector<double> &wl,
                     std::vector<double> &wu);

@@ -1613,19 +1613,21 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
                 if (c.delta > 0.0) dw_last = c.delta;
                 inner++;
                 graph_iters++;
+                N = I.combine_norms();
+                const double it_s = tn.s();
+                t_newton += it_s;
                 const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th,
                                                 c.ph, c.alpha[0], c.alpha[1], c.delta,
                                                 (double)(h->n_factor - fact_before),
                                                 (double)(h->n_refine - refine_before),
                                                 (double)h->factored_precision,
-                                                c.accepted ? 1.0 : 0.0, (double)c.nback};
+                                                c.accepted ? 1.0 : 0.0, (double)c.nback,
+                                                it_s * 1e3};
                 h->hist_inner.insert(h->hist_inner.end(), rec, rec + kHistInner);
                 if (o.verbose)
                     std::printf("  it %4d mu %.1e E0 %.2e th %.2e a %.2e dw %.1e tries %d%s (graph)\n",
                                 inner, mu, E0, th, c.alpha[0], c.delta, c.tries,
                                 c.accepted ? "" : " R");
-                N = I.combine_norms();
-                t_newton += tn.s();
                 continue;
             }
             Timer tn;
@@ -1718,21 +1720,22 @@ int ncl_solve_impl(scopf_handle *h, const scopf_state *warm, scopf_result *res, 
             note_launch(), k_zsafe<<<nb(n + p), kT, 0, s>>>(D, tr.w, tr.s, tr.zl, tr.zu, tr.zs, mu, o.kappa_sigma);
             std::swap(st, tr);
             inner++;
-            {
-                const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th, ph,
-                                                a, az, delta, (double)(h->n_factor - fact_before),
-                                                (double)(h->n_refine - refine_before),
-                                                (double)h->factored_precision, accepted ? 1.0 : 0.0,
-                                                (double)nback};
-                h->hist_inner.insert(h->hist_inner.end(), rec, rec + kHistInner);
-            }
             if (o.verbose)
                 std::printf("  it %4d mu %.1e E0 %.2e th %.2e a %.2e dw %.1e tries %d%s\n", inner, mu,
                             E0, th, a, delta, tries, accepted ? "" : " R");
             r = assemble_impl(h, &st, h->lam_n, h->nu0_n, rho, mu, 0.0, nullptr);
             if (r != SCOPF_OK) return r;
             N = I.norms(st, rho);   // waits for the step (and this assembly)
-            t_newton += tn.s();
+            const double it_s = tn.s();
+            t_newton += it_s;
+            {
+                const double rec[kHistInner] = {(double)outer, (double)inner, mu, rho, E0_step, th, ph,
+                                                a, az, delta, (double)(h->n_factor - fact_before),
+                                                (double)(h->n_refine - refine_before),
+                                                (double)h->factored_precision, accepted ? 1.0 : 0.0,
+                                                (double)nback, it_s * 1e3};
+                h->hist_inner.insert(h->hist_inner.end(), rec, rec + kHistInner);
+            }
         }
         feas = std::fmax(N.rmax, N.tmax);
         {

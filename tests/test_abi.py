@@ -98,7 +98,7 @@ def test_history_empty_before_a_solve():
     import paper_2510_13333_b300 as P
     h = P.SCOPF(H.instance(0), host_only=1)
     names, rows = h.history(0)
-    assert rows.shape == (0, 15) and len(names) == 15
+    assert rows.shape == (0, 16) and len(names) == 16
     names, rows = h.history(1)
     assert rows.shape == (0, 8) and len(names) == 8
 

@@ -32,7 +32,8 @@ def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec):
     assert rd["fp64_fallbacks"] == rh["fp64_fallbacks"]
     cols = P.SCOPF.HISTORY_INNER
     for j, name in enumerate(cols):
-        np.testing.assert_array_equal(hd[:, j], hh[:, j], err_msg=name)
+        if name != "ms":   # wall time of the iteration
+            np.testing.assert_array_equal(hd[:, j], hh[:, j], err_msg=name)
     assert rd["objective"] == rh["objective"]
     assert rd["max_violation"] == rh["max_violation"]
     # one read-back per iteration; the outer loop's assembly and the final
