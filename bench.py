@@ -400,7 +400,7 @@ def phase_work(sz, prec_bytes):
                   "every block's border front read once, S written (the n_c^3/3 dense factor "
                   "is negligible)"),
         "solve": (2 * b * nnzL + 16 * N, "B", "factor entries read by both sweeps, plus the "
-                  "right-hand side in and the solution out (SURVEY 8(d) a6)"),
+                  "right-hand side in and the solution out"),
         "residual": (16 * nnz + 24 * N, "B", "value + column per stored entry, x, b, r"),
     }
 
@@ -429,8 +429,8 @@ def phase_rooflines(sz, phases, solves, prec_bytes, peaks_live):
                       "per_call": amount, "ms_per_call": per_call_s * 1e3, "calls": calls,
                       "work": what}
             if k == "factor":
-                # the second roof of the small fronts: b nnz(L)
-                # written + 8 nnz(K) read
+                # the second roof, that of the small fronts' memory traffic:
+                # b nnz(L) written + 8 nnz(K) read
                 hb = prec_bytes * sz.nnz_L + 8 * sz.nnz_kkt
                 out[k]["hbm"] = {"bytes_per_call": hb, "achieved_gbs": hb / per_call_s / 1e9,
                                  "peak_gbs": hbm, "frac": hb / per_call_s / 1e9 / hbm}

@@ -13,15 +13,22 @@ from tests import helpers as H
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("idx,prec", [(0, 0), (0, 1), (1, 0), (1, 1)])
-def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec):
+@pytest.mark.parametrize("idx,prec,opts", [
+    (0, 0, {}), (0, 1, {}), (1, 0, {}), (1, 1, {}),
+    # the FP32 refinement stalls at the first step: the graph hands the step
+    # to the host, which redoes the direction in FP64 and launches the step graph
+    (0, 1, {"max_refine": 0}),
+    # the refinement-cost switch to FP64, taken from the graph's read-back
+    (0, 1, {"fp64_switch_refine": 1, "fp64_switch_streak": 1}),
+])
+def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec, opts):
     import paper_2510_13333_b300 as P
     inst = H.instance(idx)
-    host = P.SCOPF(inst, precision=prec, ipm_graph=0)
+    host = P.SCOPF(inst, precision=prec, ipm_graph=0, **opts)
     rh = host.ncl_solve()
     assert rh["call_status"] == 0 and rh["graph_iters"] == 0
     _, hh = host.history(0)
-    dev = P.SCOPF(inst, precision=prec, ipm_graph=1)
+    dev = P.SCOPF(inst, precision=prec, ipm_graph=1, **opts)
     rd = dev.ncl_solve()
     assert rd["call_status"] == 0, (rd, dev.last_error())
     assert rd["graph_iters"] == rd["inner_iters"] > 0, dev.last_error()
@@ -40,4 +47,7 @@ def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec):
     # report add a few per outer iteration, an FP64 redo its own
     bound = rd["inner_iters"] + 3 * rd["outer_iters"] + 8 + 12 * rd["fp64_fallbacks"]
     assert rd["host_round_trips"] <= bound, (rd["host_round_trips"], bound)
-    assert rh["host_round_trips"] > 3 * rh["inner_iters"]
+    if not opts:
+        assert rh["host_round_trips"] > 3 * rh["inner_iters"]
+    if "max_refine" in opts or "fp64_switch_refine" in opts:
+        assert rd["fp64_fallbacks"] == 1
