@@ -349,8 +349,9 @@ int scopf_dense_ldlt_solve_noalloc(const double *S, int32_t n, const double *b, 
  * of kind 0: FP32 FMA, 1: FP64 FMA, 2: FP64 tensor MMA (mma.sync m8n8k4),
  * 3: FP64 FMA on one lane per warp (flops of the active lanes only),
  * 4: FP64 FMA on even warps and FP64 tensor MMA on odd warps at once (equal
- * flops per warp pair: whether the two share a pipe), iters iterations each, and returns the launch's flop count in *flops (host,
- * an FMA counted as 2).  out: device, at least 8 bytes, written only in a
+ * flops per warp pair: whether the two share a pipe), iters iterations
+ * each, and returns the launch's flop count in *flops (host, an FMA counted
+ * as 2).  out: device, at least 8 bytes, written only in a
  * case that never occurs (it keeps the chains from being optimised away).
  * The caller times the launch (CUDA events on the same stream).  Does not
  * synchronise. */
@@ -366,12 +367,15 @@ typedef struct {
 /* Autotuner of the supernodal tile shapes (the paper leaves them to cuDSS
  * and has no counterpart of this call): chooses cluster_max_tasks (small
  * fronts per warp work item) and relax_max_nodes (nodes an only-child chain
- * merges into one supernode) for this instance.  A short NCL run (iterate_at interior-point iterations from
- * the flat start, options *opt) gives a common iterate; each candidate handle
- * times `steps` Newton steps (scopf_newton_step, after one untimed step)
- * from it with CUDA events.  Candidates: item sizes 4, 8, 16, 32 at the
- * given amalgamation limit, then limits 4, 8, 16 at the best item size.  On
- * return opt holds the fastest pair (every other field unchanged); entries
+ * merges into one supernode) for this instance.  A short NCL run
+ * (iterate_at interior-point iterations from the flat start, options *opt)
+ * gives a common iterate; each candidate handle times `steps` Newton steps
+ * (scopf_newton_step, after one untimed step) from it with CUDA events.
+ * Candidates: item sizes 4, 8, 16, 32 at the given amalgamation limit, then
+ * limits 4, 8, 16 at the best item size; a candidate replaces the best so
+ * far only when it is more than 2% faster (shapes within the timing noise
+ * keep the given ones, so the choice is repeatable).  On return opt holds
+ * the chosen pair (every other field unchanged); entries
  * (host, capacity, may be NULL) receive the candidates in the order tried,
  * *n_entries their number.  Creates and destroys one handle per candidate on
  * the current device (device memory of two handles at a time). */

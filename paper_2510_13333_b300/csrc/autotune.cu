@@ -23,6 +23,13 @@ struct Cand {
     int32_t cluster, relax;
 };
 
+// A candidate replaces the best so far only when its Newton step is faster
+// by more than this fraction: repeated timings of one shape differ by well
+// under 1%, and shapes within the noise would otherwise be picked at random
+// from run to run (each shape rounds the factors differently, so the
+// interior-point path would change with them).
+constexpr double kMargin = 0.02;
+
 // mean ms of `steps` Newton steps on h from the iterate of h0 (after one
 // untimed step)
 int time_steps(scopf_handle *h, scopf_handle *h0, int steps, double *ms) {
@@ -107,7 +114,7 @@ extern "C" int scopf_autotune(const scopf_network *net, const scopf_contingency 
         if (r != SCOPF_OK) break;
         double ms;
         r = run({cl, base.relax_max_nodes}, &ms);
-        if (r == SCOPF_OK && ms < best_ms) {
+        if (r == SCOPF_OK && ms < best_ms * (1.0 - kMargin)) {
             best_ms = ms;
             best = {cl, base.relax_max_nodes};
         }
@@ -116,7 +123,7 @@ extern "C" int scopf_autotune(const scopf_network *net, const scopf_contingency 
         if (r != SCOPF_OK) break;
         double ms;
         r = run({best.cluster, rx}, &ms);
-        if (r == SCOPF_OK && ms < best_ms) {
+        if (r == SCOPF_OK && ms < best_ms * (1.0 - kMargin)) {
             best_ms = ms;
             best = {best.cluster, rx};
         }

@@ -1,6 +1,8 @@
 """The supernode tile-shape autotuner (scopf_autotune) on the 118-bus x 32
-case: every candidate is timed, the fastest is written back, and a solve
-with the chosen shapes still meets the oracle's objective."""
+case: every candidate is timed, the chosen shape is written back and is
+within the 2% margin of the fastest (a shape replaces the best so far only
+when more than 2% faster), and a solve with the chosen shapes still meets the
+oracle's objective."""
 import numpy as np
 import pytest
 
@@ -21,7 +23,7 @@ def test_autotune_picks_fastest_and_solves(cuda):
     ms = np.array([c["ms_per_step"] for c in cands])
     assert np.all(ms > 0)
     chosen = [c for c in cands if c["chosen"]]
-    assert len(chosen) == 1 and chosen[0]["ms_per_step"] == ms.min()
+    assert len(chosen) == 1 and chosen[0]["ms_per_step"] <= ms.min() / 0.98 + 1e-12
     assert (opt.cluster_max_tasks, opt.relax_max_nodes) == (chosen[0]["cluster_max_tasks"],
                                                             chosen[0]["relax_max_nodes"])
     lib = P.SCOPF(inst, options=opt)
