@@ -298,6 +298,39 @@ int setup_device(scopf_handle *h) {
             F.child_rec = reinterpret_cast<const int4 *>(cr);
         }
         TRY(upload(h, HF.item_parent, &F.item_parent));
+        {
+            // the sweeps' item records (see DevFront::item_fwd)
+            const int ni = HF.n_items;
+            std::vector<int32_t> fw(12 * (size_t)(ni > 0 ? ni : 1), 0), bw(fw.size(), 0);
+            for (int i = 0; i < ni; i++) {
+                const int t0 = HF.item_ptr[i], t1 = HF.item_ptr[i + 1];
+                for (int k = 0; k < 2; k++) {
+                    const int t = k == 0 ? t0 : t1 - 1;
+                    int32_t *r = (k == 0 ? fw.data() : bw.data()) + 12 * (size_t)i;
+                    const int32_t *a = &HF.task_rec[8 * (size_t)t];
+                    const int32_t *nx = &HF.task_rec[8 * (size_t)(t + 1)];
+                    for (int w = 0; w < 5; w++) r[w] = a[w];
+                    r[5] = a[5];    // first child slot
+                    r[6] = nx[5];   // end child slot
+                    if (k == 0) {
+                        r[7] = t1;
+                        r[8] = t0;
+                        r[9] = HF.item_parent[i];
+                    } else {
+                        r[7] = t0;
+                        r[8] = t1;
+                        r[9] = HF.item_cont[i];
+                    }
+                    r[10] = a[6];   // original entries [o0, o1)
+                    r[11] = nx[6];
+                }
+            }
+            const int32_t *fwp = nullptr, *bwp = nullptr;
+            TRY(upload(h, fw, &fwp));
+            TRY(upload(h, bw, &bwp));
+            F.item_fwd = reinterpret_cast<const int4 *>(fwp);
+            F.item_bwd = reinterpret_cast<const int4 *>(bwp);
+        }
         TRY(upload(h, HF.item_child_ptr, &F.item_child_ptr));
         TRY(upload(h, HF.item_child, &F.item_child));
         TRY(upload(h, HF.item_cont, &F.item_cont));

@@ -252,6 +252,14 @@ struct DevFront {
     // scheduler trace (NULL = off): 4 kinds x n_items x 4 uint64
     unsigned long long *trace;
     const int32_t *item_ptr, *item_parent, *item_child_ptr, *item_child;
+    // per item, 3 int4 each: the record of the task a sweep starts the item
+    // with (the first for the forward sweep, the last for the backward one)
+    // together with the item's task range and successor, so that one load
+    // starts an item: front_off (2 words), vec_off (2), f | npiv << 16, first
+    // child slot, end child slot, then for the forward sweep t1, t0, parent
+    // item, and for the backward sweep t0, t1, the child item run next; then
+    // the task's original entries' range (2 words)
+    const int4 *item_fwd, *item_bwd;
     const int32_t *item_cont;     // backward sweep: child item run next by the same warp (-1 none)
     // ready queues of items (three per run: the factorization phases, or
     // the forward and backward sweeps)

@@ -218,6 +218,26 @@ struct TaskInfo {
 __device__ __forceinline__ int64_t join64(int lo, int hi) {
     return (int64_t)(((uint64_t)(uint32_t)hi << 32) | (uint32_t)lo);
 }
+// an item record of DevFront::item_fwd / item_bwd: the task record, and in
+// (e0, e1, e2) words 7, 8, 9
+__device__ __forceinline__ TaskInfo item_task(const int4 *rec, int item, int &e0, int &e1,
+                                              int &e2) {
+    const int4 a = rec[3 * item], b = rec[3 * item + 1], c = rec[3 * item + 2];
+    TaskInfo ti;
+    ti.front_off = join64(a.x, a.y);
+    ti.vo = join64(a.z, a.w);
+    ti.f = b.x & 0xffff;
+    ti.np = b.x >> 16;
+    ti.c0 = b.y;
+    ti.c1 = b.z;
+    ti.o0 = c.z;
+    ti.o1 = c.w;
+    ti.parent = -1;
+    e0 = b.w;
+    e1 = c.x;
+    e2 = c.y;
+    return ti;
+}
 __device__ __forceinline__ TaskInfo task_info(const DevFront &F, int t) {
     const int4 a = F.task_rec[2 * t], b = F.task_rec[2 * t + 1], n = F.task_rec[2 * t + 3];
     TaskInfo ti;
@@ -1320,8 +1340,8 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
         if (item < 0) item = warp_claim(Q, spin_limit, st, 2);
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
-        TaskInfo ti = task_info(F, t0);
+        int t0, t1, par;   // one record load starts the item
+        TaskInfo ti = item_task(F.item_fwd, item, t1, t0, par);
         for (int task = t0; task < t1; task++) {
             const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
             fwd_front<T>(F, fronts, vec, ti, lane, sv);
@@ -1329,7 +1349,6 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5)
             ti = nx;
         }
         if (F.trace && lane == 0) trace_item(F, 0, item, tc, ts);
-        const int par = F.item_parent[item];
         item = (par >= 0 && warp_complete_child(Q, par)) ? par : -1;
     }
 }
@@ -1587,8 +1606,9 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
         if (item < 0) item = warp_claim(Q, spin_limit, st, 3);
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
-        TaskInfo ti = task_info(F, t1 - 1);
+        int t0, t1, keep;   // one record load starts the item; keep: the child
+                            // with the longest path below, run next by this warp
+        TaskInfo ti = item_task(F.item_bwd, item, t0, t1, keep);
         for (int task = t1 - 1; task >= t0; task--) {
             const TaskInfo nx = task_info(F, task > t0 ? task - 1 : task);   // prefetch
             bwd_front<T>(F, fronts, vec, scale, x, ti, lane, sv);
@@ -1596,7 +1616,6 @@ __global__ void __launch_bounds__(kWT, sizeof(T) == 4 ? 8 : 5) k_solve_bwd(DevFr
             ti = nx;
         }
         if (F.trace && lane == 0) trace_item(F, 1, item, tc, ts);
-        const int keep = F.item_cont[item];   // the child with the longest path below
         push_children(Q, F, item, keep);
         item = keep;
     }
