@@ -700,8 +700,8 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 3)
         if (item < 0) item = warp_claim(Q, spin_limit, st, 1);
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-        const int t0 = F.item_ptr[item], t1 = F.item_ptr[item + 1];
-        TaskInfo ti = task_info(F, t0);
+        int t0, t1, par;   // one record load starts the item
+        TaskInfo ti = item_task(F.item_fwd, item, t1, t0, par);
         for (int task = t0; task < t1; task++) {
             const TaskInfo nx = task_info(F, task + 1 < t1 ? task + 1 : task);   // prefetch
             if (ti.f <= 32)
@@ -713,7 +713,6 @@ __global__ void __launch_bounds__(kFT, sizeof(T) == 4 ? 4 : 3)
             ti = nx;
         }
         if (F.trace && lane == 0) trace_item(F, 2, item, tc, ts);
-        const int par = F.item_parent[item];
         item = (par >= 0 && par < F.n_items_small && warp_complete_child(Q, par)) ? par : -1;
     }
     if (lane == 0) {
@@ -742,14 +741,14 @@ __global__ void __launch_bounds__(med_threads<T>())
         if (item < 0) item = warp_claim(Q, spin_limit, st, 1);
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-        const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per item
+        int t0, t1, par;   // one front per item
+        const TaskInfo ti = item_task(F.item_fwd, item, t1, t0, par);
         if (ti.f <= kMedF)
             eliminate_front_medium<T>(F, fronts, ti, lane, M, pivot_tol, n_pos, n_neg, n_zero);
         else   // not produced by the phase split; kept as a safe fallback
             eliminate_front<T, 32>(F, fronts, ti, lane, pivot_tol, n_pos, n_neg, n_zero);
         __syncwarp();
         if (F.trace && lane == 0) trace_item(F, 3, item, tc, ts);
-        const int par = F.item_parent[item];
         item = (par >= F.n_items_small && par < F.n_items_med && warp_complete_child(Q, par))
                    ? par : -1;
     }
@@ -933,7 +932,8 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
         __syncthreads();
         if (item < 0) break;
         const unsigned long long ts = F.trace ? dev_clock_ns() : 0;
-        const TaskInfo ti = task_info(F, F.item_ptr[item]);   // one front per large item
+        int t0, t1, par;   // one front per large item
+        const TaskInfo ti = item_task(F.item_fwd, item, t1, t0, par);
         if ((int64_t)ti.f * ti.np <= F.big_panel)
             eliminate_front_big<T>(F, fronts, ti, pivot_tol, n_pos, n_neg, n_zero);
         else
@@ -941,7 +941,6 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
         __syncthreads();   // orders every thread's writes before the release below
         if (threadIdx.x == 0) {
             if (F.trace) trace_item(F, 4, item, tc, ts);
-            const int par = F.item_parent[item];
             s_task = (par >= 0 && complete_child(Q, par)) ? par : -1;
         }
         __syncthreads();
