@@ -876,7 +876,17 @@ cudaError_t factor_enqueue(scopf_handle *h) {
     cudaError_t e = cudaMemsetAsync(h->fstat, 0, sizeof(FactorStatus), s);
     if (e != cudaSuccess) return e;
     h->timer.begin(PH_FRONT_INIT, s);
-    launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, h->ruiz_mx, 3, s);
+    // Ruiz equilibration with power-of-two scales.  Such a scaling is exact
+    // in floating point: the factors of D K D are D-scaled copies of those of
+    // K, rounding for rounding, so it changes no result except through the
+    // floating-point range and a nonzero pivot tolerance (compared with the
+    // scaled pivots).  FP64 fronts have range to spare and, with a zero
+    // tolerance, skip it (scale 1).  FP32 fronts take one sweep: it already
+    // bounds every scaled entry below 4 (|a_ij| is at most both its row's and
+    // its column's maximum), the guard against FP32 overflow the scaling is
+    // for.  A nonzero tolerance keeps the three sweeps it was defined with.
+    const int sweeps = h->opt.pivot_tol != 0.0 ? 3 : (sizeof(T) == 4 ? 1 : 0);
+    launch_equilibrate(h->dm, h->kval, h->scale, h->scale_tmp, h->ruiz_mx, sweeps, s);
     launch_orig_vals<T>(h->df, reinterpret_cast<T *>(h->ovals), s);
     h->timer.end(PH_FRONT_INIT, s);
     h->timer.begin(PH_FACTOR, s);
