@@ -117,7 +117,14 @@ int setup_device(scopf_handle *h) {
     TRY(upload(h, M.cf_idx, &d.cf_idx));
     TRY(upload(h, M.cf_coef, &d.cf_coef));
     TRY(upload(h, M.kkt_ptr, &d.kkt_ptr));
-    TRY(upload(h, M.kkt_col, &d.kkt_col));
+    {
+        if (M.n_kkt >= ((int64_t)1 << 31)) {
+            h->last_error = "the KKT system has 2^31 rows or more";
+            return SCOPF_ERR_INVALID_ARG;
+        }
+        const std::vector<int32_t> col32(M.kkt_col.begin(), M.kkt_col.end());
+        TRY(upload(h, col32, &d.kkt_col));
+    }
     TRY(upload(h, M.ctr_ptr, &d.ctr_ptr));
     {
         std::vector<int64_t> src(M.ctr.size());

@@ -43,7 +43,8 @@ struct DevModel {
     const double *c_const;
     const int64_t *cf_ptr, *cf_idx;
     const double *cf_coef;
-    const int64_t *kkt_ptr, *kkt_col, *ctr_ptr;
+    const int64_t *kkt_ptr, *ctr_ptr;
+    const int32_t *kkt_col;       // column of every stored entry (n_kkt < 2^31)
     const int32_t *kkt_row;       // row of every stored entry
     int64_t nnz_kkt;              // stored entries
     const int64_t *ctr_src;
@@ -221,7 +222,7 @@ struct DevFront {
     const int64_t *orig_nz;
     const int32_t *orig_off;
     const int32_t *kkt_row;       // row of every stored KKT entry
-    const int64_t *kkt_col;
+    const int32_t *kkt_col;
     const double *kval;           // assembled K (set before each factorization)
     const double *scale;          // Ruiz scaling
     const void *ovals;            // scaled original entries in task order (n_orig), in the

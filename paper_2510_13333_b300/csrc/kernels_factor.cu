@@ -1650,7 +1650,7 @@ __device__ __forceinline__ int exponent_of(int hi) {
 }
 
 __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t *__restrict__ row,
-                                                      const int64_t *__restrict__ col,
+                                                      const int32_t *__restrict__ col,
                                                       const double *__restrict__ kval,
                                                       const int *__restrict__ e,
                                                       unsigned *__restrict__ mx) {
@@ -1658,12 +1658,12 @@ __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t
     for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t * kRE < nnz; t += nthr) {
         const int64_t e0 = t * kRE;
         int rr[kRE];
-        int64_t cc[kRE];
+        int cc[kRE];
         int hh[kRE];
         int cnt = kRE;
         if (e0 + kRE <= nnz) {
             const int4 *r4 = reinterpret_cast<const int4 *>(row + e0);
-            const longlong2 *c2 = reinterpret_cast<const longlong2 *>(col + e0);
+            const int4 *c4 = reinterpret_cast<const int4 *>(col + e0);
             const int4 *v4 = reinterpret_cast<const int4 *>(kval + e0);   // (lo, hi) pairs
 #pragma unroll
             for (int k = 0; k < kRE / 4; k++) {
@@ -1672,13 +1672,15 @@ __global__ void __launch_bounds__(256) k_ruiz_entries(int64_t nnz, const int32_t
                 rr[4 * k + 1] = a.y;
                 rr[4 * k + 2] = a.z;
                 rr[4 * k + 3] = a.w;
+                const int4 c = __ldg(c4 + k);
+                cc[4 * k] = c.x;
+                cc[4 * k + 1] = c.y;
+                cc[4 * k + 2] = c.z;
+                cc[4 * k + 3] = c.w;
             }
 #pragma unroll
             for (int k = 0; k < kRE / 2; k++) {
-                const longlong2 a = __ldg(c2 + k);
                 const int4 b = __ldg(v4 + k);
-                cc[2 * k] = a.x;
-                cc[2 * k + 1] = a.y;
                 hh[2 * k] = b.y;
                 hh[2 * k + 1] = b.w;
             }
@@ -1737,7 +1739,7 @@ __global__ void k_ruiz_scale(int64_t n, const int *__restrict__ e, double *__res
 // scaled original entries of every front, in task order
 template <typename T>
 __global__ void k_orig_vals(int64_t n_orig, const int64_t *__restrict__ nz,
-                            const int32_t *__restrict__ row, const int64_t *__restrict__ col,
+                            const int32_t *__restrict__ row, const int32_t *__restrict__ col,
                             const double *__restrict__ scale, const double *__restrict__ kval,
                             T *__restrict__ ovals) {
     int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;

@@ -190,7 +190,7 @@ __global__ void k_diag(int64_t n_kkt, const int8_t *__restrict__ kind,
 }
 
 __global__ void k_assemble(int64_t nnz, const int32_t *__restrict__ row,
-                           const int64_t *__restrict__ col, const int64_t *__restrict__ cptr,
+                           const int32_t *__restrict__ col, const int64_t *__restrict__ cptr,
                            const int64_t *__restrict__ src, const double *__restrict__ coef,
                            const double *__restrict__ ev, const double *__restrict__ diag,
                            double *__restrict__ kval) {
@@ -206,7 +206,7 @@ __global__ void k_assemble(int64_t nnz, const int32_t *__restrict__ row,
     kval[j] = v;
 }
 
-__device__ __forceinline__ double dual_term(int64_t q, const int64_t *__restrict__ col,
+__device__ __forceinline__ double dual_term(int64_t q, const int32_t *__restrict__ col,
                                             const int8_t *__restrict__ kind,
                                             const int64_t *__restrict__ index,
                                             const double *__restrict__ kval,
@@ -220,7 +220,7 @@ __device__ __forceinline__ double dual_term(int64_t q, const int64_t *__restrict
 }
 
 __global__ void k_dual_product(int64_t n_kkt, const int64_t *__restrict__ ptr,
-                               const int64_t *__restrict__ col, const int8_t *__restrict__ kind,
+                               const int32_t *__restrict__ col, const int8_t *__restrict__ kind,
                                const int64_t *__restrict__ index, const double *__restrict__ kval,
                                const double *__restrict__ g, const double *__restrict__ lam,
                                const double *__restrict__ yc, double *__restrict__ gw,
@@ -236,7 +236,7 @@ __global__ void k_dual_product(int64_t n_kkt, const int64_t *__restrict__ ptr,
 // the same for the long rows, one warp per row
 __global__ void k_dual_product_long(int64_t n_long, const int64_t *__restrict__ rows,
                                     const int64_t *__restrict__ ptr,
-                                    const int64_t *__restrict__ col,
+                                    const int32_t *__restrict__ col,
                                     const int8_t *__restrict__ kind,
                                     const int64_t *__restrict__ index,
                                     const double *__restrict__ kval, const double *__restrict__ g,
@@ -286,7 +286,7 @@ __global__ void k_rhs(int64_t n_kkt, const int8_t *__restrict__ kind,
 
 // y = b - K x (b may be NULL: y = -K x ... used with sign = -1 for y = K x)
 __global__ void k_residual(int64_t n_kkt, const int64_t *__restrict__ ptr,
-                           const int64_t *__restrict__ col, const double *__restrict__ kval,
+                           const int32_t *__restrict__ col, const double *__restrict__ kval,
                            const double *__restrict__ x, const double *__restrict__ b,
                            double *__restrict__ y, const int8_t *__restrict__ is_long,
                            double sign) {
@@ -298,7 +298,7 @@ __global__ void k_residual(int64_t n_kkt, const int64_t *__restrict__ ptr,
 }
 
 __global__ void k_residual_long(int64_t n_long, const int64_t *__restrict__ rows,
-                                const int64_t *__restrict__ ptr, const int64_t *__restrict__ col,
+                                const int64_t *__restrict__ ptr, const int32_t *__restrict__ col,
                                 const double *__restrict__ kval, const double *__restrict__ x,
                                 const double *__restrict__ b, double *__restrict__ y,
                                 double sign) {
