@@ -952,26 +952,35 @@ __global__ void __launch_bounds__(kBT) k_factor_big(DevFront F, T *__restrict__ 
     }
 }
 
-// S = sum over blocks of the border fronts (lower triangle, fixed block order)
+// S = sum over blocks of the border fronts (lower triangle, fixed block
+// order): block k goes to partial sum k mod 8 (in increasing k), and the
+// eight partials are combined as ((p0 + p1) + (p2 + p3)) + ((p4 + p5) +
+// (p6 + p7)).  A CTA takes 32 entries: warp u forms partial u of all 32
+// (coalesced loads), warp 0 combines.
 template <typename T>
-__global__ void k_schur_sum(int n_blocks, int nb, const int64_t *__restrict__ boff,
-                            const T *__restrict__ fronts, double *__restrict__ S) {
-    const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= nb * nb) return;
-    const int j = idx / nb, i = idx - j * nb;
-    if (i < j) return;
-    // eight independent partial sums (fixed assignment k mod 8), combined in order
-    double a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
-    const int64_t off = (int64_t)j * nb + i;
-    int k = 0;
-    for (; k + 8 <= n_blocks; k += 8) {
-#pragma unroll
-        for (int u = 0; u < 8; u++) a[u] += (double)fronts[boff[k + u] + off];
+__global__ void __launch_bounds__(256) k_schur_sum(int n_blocks, int nb,
+                                                   const int64_t *__restrict__ boff,
+                                                   const T *__restrict__ fronts,
+                                                   double *__restrict__ S) {
+    __shared__ double part[8][32];
+    const int u = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int idx = blockIdx.x * 32 + lane;   // entry j * nb + i
+    const bool in = idx < nb * nb;
+    const int j = in ? idx / nb : 0, i = in ? idx - j * nb : 0;
+    const bool lower = in && i >= j;
+    double a = 0.0;
+    if (lower) {
+        const int64_t off = (int64_t)j * nb + i;
+        for (int k = u; k < n_blocks; k += 8) a += (double)fronts[boff[k] + off];
     }
-    for (int u = 0; k < n_blocks; k++, u++) a[u] += (double)fronts[boff[k] + off];
-    const double acc = ((a[0] + a[1]) + (a[2] + a[3])) + ((a[4] + a[5]) + (a[6] + a[7]));
-    S[(int64_t)j * nb + i] = acc;
-    S[(int64_t)i * nb + j] = acc;
+    part[u][lane] = a;
+    __syncthreads();
+    if (u == 0 && lower) {
+        const double acc = ((part[0][lane] + part[1][lane]) + (part[2][lane] + part[3][lane])) +
+                           ((part[4][lane] + part[5][lane]) + (part[6][lane] + part[7][lane]));
+        S[(int64_t)j * nb + i] = acc;
+        S[(int64_t)i * nb + j] = acc;
+    }
 }
 
 // ---- dense LDL^T of the border block (FP64, blocked right-looking) -------
@@ -1887,7 +1896,7 @@ template <typename T>
 void launch_schur_sum(const DevFront &F, const T *fronts, double *S, cudaStream_t s) {
     const int nb = F.n_border;
     if (nb == 0) return;
-    note_launch(), k_schur_sum<T><<<(nb * nb + 255) / 256, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
+    note_launch(), k_schur_sum<T><<<(nb * nb + 31) / 32, 256, 0, s>>>(F.n_blocks, nb, F.border_off, fronts, S);
 }
 
 int launch_reciprocal(int64_t n, const double *d, double *out, cudaStream_t s) {
