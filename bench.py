@@ -392,9 +392,12 @@ def phase_work(sz, prec_bytes):
         "assemble": (8 * sz.n_elem_values + 24 * sz.n_contrib + 16 * nnz + 48 * N, "B",
                      "element values written, (slot, coefficient, value) per contribution, "
                      "pointer + value per stored entry, iterate and right-hand-side vectors"),
-        "front_init": (3 * 20 * nnz + 24 * nnz, "B",
-                       "3 Ruiz sweeps over (value, column, row) per stored entry, then each "
-                       "front original's value, offset, scales and write"),
+        # power-of-two Ruiz scaling: one sweep for FP32 factors, none for FP64
+        # (exact either way; FP64 has the range without it)
+        "front_init": ((20 if b == 4 else 0) * nnz + 24 * nnz, "B",
+                       ("one Ruiz sweep over (value, column, row, column scale) per stored "
+                        "entry, then" if b == 4 else "unit scales, then") +
+                       " each front original's value, offset, scales and write"),
         "factor": (sz.factor_flops, "flop", "sum over pivots of (f-c-1)(f-c) on the fronts"),
         "schur": (nblk * nc * nc * b + 8 * nc * nc, "B",
                   "every block's border front read once, S written (the n_c^3/3 dense factor "
