@@ -54,9 +54,9 @@ FP64_PEAK_TFLOPS = 1.25
 # covers the solve kernels' section of the source and the solve's launch
 # function
 SWEEP_TRAFFIC = {"source": "paper_2510_13333_b300/csrc/kernels_factor.cu",
-                 "sha1": "358c906026a73b5f2170fa802748412d5477bbc7",
+                 "sha1": "a908fa075ea548fa73c0b54caca8a944e6f1a6ae",
                  # k_solve_fwd + k_border_gather + k_border_apply + k_solve_bwd (FP32)
-                 "bytes_per_solve": 254899200 + 212480 + 296704 + 315174912}
+                 "bytes_per_solve": 261414912 + 212736 + 296704 + 321260544}
 
 
 def sweep_source_digest(text: str):
