@@ -669,6 +669,14 @@ def run_ours(args):
                "sample": cpu_desc, "host": host_cpu()}
         if idx == CONFIG_IDX:
             cpu["tts_118bus_k32"] = oracle_tts_118()
+        if "fp64" in tts:
+            # the oracle's time to solution at this size, extrapolated (not run):
+            # its sampled seconds per Newton step times the IPM iterations of the
+            # GPU's FP64 solve (each iteration one Newton step and its trials)
+            cpu["tts_extrapolated"] = {
+                "seconds": cpu_s * tts["fp64"]["inner_iters"],
+                "basis": "oracle s per Newton step (sampled, extrapolated in blocks) x the "
+                         "GPU FP64 solve's IPM iterations; not a measured solve"}
     except Exception as exc:  # keep the GPU number even if the CPU sample fails
         cpu = {"value": None, "unit": "Newton steps/s", "cores": 1, "kind": "oracle",
                "sample": f"failed: {exc}"}
