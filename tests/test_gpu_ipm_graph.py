@@ -51,3 +51,23 @@ def test_graph_iteration_takes_the_host_loops_steps(cuda, idx, prec, opts):
         assert rh["host_round_trips"] > 3 * rh["inner_iters"]
     if "max_refine" in opts or "fp64_switch_refine" in opts:
         assert rd["fp64_fallbacks"] == 1
+
+
+def test_graph_iteration_full_size_fp64(cuda):
+    """The same at the 500-bus x 256-contingency size (FP64 factors): the
+    graph loop's 500-odd iterations take the host loop's steps."""
+    import paper_2510_13333_b300 as P
+    inst = H.instance(2)
+    rh = P.SCOPF(inst, precision=P.PREC_FP64, ipm_graph=0)
+    a = rh.ncl_solve()
+    rd = P.SCOPF(inst, precision=P.PREC_FP64, ipm_graph=1)
+    b = rd.ncl_solve()
+    assert a["call_status"] == 0 and b["call_status"] == 0, rd.last_error()
+    assert b["graph_iters"] == b["inner_iters"] == a["inner_iters"]
+    assert b["objective"] == a["objective"]
+    _, ha = rh.history(0)
+    _, hb = rd.history(0)
+    cols = P.SCOPF.HISTORY_INNER
+    for j, name in enumerate(cols):
+        if name != "ms":
+            np.testing.assert_array_equal(hb[:, j], ha[:, j], err_msg=name)
