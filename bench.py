@@ -895,6 +895,61 @@ def run_illcond(args):
                       "unit": "see rows", "data": "synthetic", "rows": rows}), flush=True)
 
 
+# tile shapes (cluster_max_tasks, relax_max_nodes) of the time-to-solution
+# spread.  The work-item size changes no arithmetic (children are summed in
+# a fixed order); the amalgamation limit changes the supernodes, and with
+# them the factors' rounding, a rounding-level perturbation of the path
+SPREAD_SHAPES = ((16, 8), (16, 1), (16, 2), (16, 3), (16, 4), (16, 6))
+
+
+def run_tts_spread(args):
+    """Time to solution at 500-bus x 256 in both precisions under the tile
+    shapes of SPREAD_SHAPES.  The shapes change no arithmetic of the
+    method, only the factors' rounding, which moves the interior-point path:
+    the spread over shapes is the path noise a single time-to-solution
+    comparison sits in."""
+    import numpy as np
+    import torch
+    import synthgrid
+    import paper_2510_13333_b300 as P
+
+    if int(os.environ.get("RANK", "0")) != 0:
+        return
+    torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    inst = synthgrid.config_instance(CONFIG_IDX)
+    rows = []
+    for cl, rx in SPREAD_SHAPES:
+        lib = P.SCOPF(inst, precision=P.PREC_MIXED, cluster_max_tasks=cl, relax_max_nodes=rx)
+        for name, prec in (("mixed", P.PREC_MIXED), ("fp64", P.PREC_FP64)):
+            lib.set_precision(prec)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r = lib.ncl_solve()
+            torch.cuda.synchronize()
+            rows.append({"cluster_max_tasks": cl, "relax_max_nodes": rx, "precision": name,
+                         "seconds": time.perf_counter() - t0, "status": r["call_status"],
+                         "inner_iters": r["inner_iters"], "objective": r["objective"],
+                         "fp64_fallbacks": r["fp64_fallbacks"],
+                         "max_violation": r["max_violation"]})
+            print(json.dumps(rows[-1]), file=sys.stderr, flush=True)
+        del lib
+    summary = {}
+    for name in ("mixed", "fp64"):
+        sec = np.array([r["seconds"] for r in rows if r["precision"] == name])
+        it = np.array([r["inner_iters"] for r in rows if r["precision"] == name])
+        summary[name] = {"seconds_median": float(np.median(sec)), "seconds_min": float(sec.min()),
+                         "seconds_max": float(sec.max()), "iters_median": float(np.median(it)),
+                         "iters_min": int(it.min()), "iters_max": int(it.max())}
+    ratio = [a["seconds"] / b["seconds"] for a, b in zip(rows[1::2], rows[0::2])]
+    summary["fp64_over_mixed_seconds_per_shape"] = ratio
+    summary["fp64_over_mixed_median_seconds"] = (summary["fp64"]["seconds_median"] /
+                                                 summary["mixed"]["seconds_median"])
+    print(json.dumps({"metric": "time to solution at 500-bus x 256 over tile shapes "
+                                "(rounding-level path perturbations)",
+                      "unit": "s", "data": "synthetic", "rows": rows, "summary": summary}),
+          flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -910,12 +965,14 @@ def main():
                     help="host-driven refinement loop (every kernel launched from the host, "
                          "for profilers that attribute launches to NVTX ranges)")
     ap.add_argument("--workload", default="newton",
-                    choices=["newton", "scale", "condensed", "screen", "illcond", "peaks"],
+                    choices=["newton", "scale", "condensed", "screen", "illcond", "peaks",
+                             "tts_spread"],
                     help="newton: the Newton step (default); scale: the same on the 2000-bus "
                          "x 128 scale-up workload, with its memory footprint; condensed: the "
                          "newton workload on the condensed primal variant; screen: batched "
                          "screening; illcond: NCL solves with narrowed reactive bands; peaks: "
-                         "the arithmetic probes")
+                         "the arithmetic probes; tts_spread: time to solution under six "
+                         "amalgamation limits (the path's rounding noise)")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
@@ -931,6 +988,10 @@ def main():
     if args.workload == "illcond":
         if args.impl != "reference":
             run_illcond(args)
+        return
+    if args.workload == "tts_spread":
+        if args.impl != "reference":
+            run_tts_spread(args)
         return
     if args.workload == "screen":
         if args.impl == "reference":
