@@ -129,3 +129,26 @@ def test_condensed_inertia_wrong_at_small_shift(cuda):
     expect = (int((ev > 0).sum()), int((ev < 0).sum()), 0)
     assert expect != (M.n, M.m + M.p, 0)
     assert lib.kkt_factor(0) == expect
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_equilibration_changes_no_result(cuda, prec):
+    """The factorization's Ruiz scales are powers of two, and scaling by a
+    power of two is exact in floating point: FP64 factors without scaling
+    (zero pivot tolerance) and FP32 factors after one sweep give bit for bit
+    the solve of the same factorization after the three sweeps a nonzero
+    pivot tolerance keeps (a tolerance below every pivot, so the inertia is
+    the same)."""
+    import paper_2510_13333_b300 as P
+    inst = H.instance(1)
+    out = []
+    for tol in (0.0, 1e-300):
+        M, S, st, prm, lib, dst, rhs, gen, K_or, rhs_or = _case(
+            inst, 5, rho=1e3, delta_w=0.5, precision=prec, pivot_tol=tol)
+        inertia = lib.kkt_factor()
+        x, rel, steps, status = lib.kkt_solve(rhs)
+        assert status == 0 and rel <= 1e-10
+        out.append((inertia, x.cpu().numpy(), steps))
+    (in0, x0, s0), (in1, x1, s1) = out
+    assert in0 == in1 and s0 == s1
+    assert np.array_equal(x0, x1)
