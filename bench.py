@@ -903,8 +903,9 @@ SPREAD_SHAPES = ((16, 8), (16, 1), (16, 2), (16, 3), (16, 4), (16, 6))
 
 
 def run_tts_spread(args):
-    """Time to solution at 500-bus x 256 in both precisions under the tile
-    shapes of SPREAD_SHAPES.  The shapes change no arithmetic of the
+    """Time to solution in both precisions under the tile shapes of
+    SPREAD_SHAPES, at 500-bus x 256 (or with --scale the 2000-bus x 128 case,
+    first four shapes).  The shapes change no arithmetic of the
     method, only the factors' rounding, which moves the interior-point path:
     the spread over shapes is the path noise a single time-to-solution
     comparison sits in."""
@@ -916,9 +917,10 @@ def run_tts_spread(args):
     if int(os.environ.get("RANK", "0")) != 0:
         return
     torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-    inst = synthgrid.config_instance(CONFIG_IDX)
+    idx = SCALE_IDX if args.scale else CONFIG_IDX
+    inst = synthgrid.config_instance(idx)
     rows = []
-    for cl, rx in SPREAD_SHAPES:
+    for cl, rx in SPREAD_SHAPES[:4] if args.scale else SPREAD_SHAPES:
         lib = P.SCOPF(inst, precision=P.PREC_MIXED, cluster_max_tasks=cl, relax_max_nodes=rx)
         for name, prec in (("mixed", P.PREC_MIXED), ("fp64", P.PREC_FP64)):
             lib.set_precision(prec)
@@ -944,8 +946,9 @@ def run_tts_spread(args):
     summary["fp64_over_mixed_seconds_per_shape"] = ratio
     summary["fp64_over_mixed_median_seconds"] = (summary["fp64"]["seconds_median"] /
                                                  summary["mixed"]["seconds_median"])
-    print(json.dumps({"metric": "time to solution at 500-bus x 256 over tile shapes "
-                                "(rounding-level path perturbations)",
+    print(json.dumps({"metric": "time to solution at " + ("2000-bus x 128" if args.scale else
+                                                          "500-bus x 256") +
+                                " over tile shapes (rounding-level path perturbations)",
                       "unit": "s", "data": "synthetic", "rows": rows, "summary": summary}),
           flush=True)
 
@@ -964,6 +967,8 @@ def main():
     ap.add_argument("--host-loop", action="store_true",
                     help="host-driven refinement loop (every kernel launched from the host, "
                          "for profilers that attribute launches to NVTX ranges)")
+    ap.add_argument("--scale", action="store_true",
+                    help="tts_spread on the 2000-bus x 128 case")
     ap.add_argument("--workload", default="newton",
                     choices=["newton", "scale", "condensed", "screen", "illcond", "peaks",
                              "tts_spread"],

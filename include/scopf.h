@@ -124,8 +124,8 @@ typedef struct {
                                  rest of the solve once fp64_switch_streak Newton
                                  steps in a row needed at least this many
                                  refinement steps (0 = only when refinement
-                                 stalls) */
-    int32_t fp64_switch_streak;
+                                 stalls).  Default 6 */
+    int32_t fp64_switch_streak;  /* default 5 */
     int32_t known_zero_pivot; /* 1: the inertia correction's first trial, delta_w = 0
                                  (IC-1 of Waechter & Biegler 2006), is taken as
                                  failed without factoring when the factorization

@@ -441,8 +441,8 @@ void scopf_default_options(scopf_options *o) {
     o->cluster_max_tasks = 16;
     o->relax_max_front = 0;
     o->device_loop = 1;
-    o->fp64_switch_refine = 0;
-    o->fp64_switch_streak = 3;
+    o->fp64_switch_refine = 6;
+    o->fp64_switch_streak = 5;
     o->known_zero_pivot = 1;
     o->dual_first = 0;
     o->fixed_mu = 0;
