@@ -524,12 +524,27 @@ def run_ours(args):
                      "graph_iters": r["graph_iters"]}
         # the metric's per-iteration rate: IPM iterations (each one Newton step
         # with its inertia corrections, refinement and line search) per second,
-        # median over iterations 10..end, from the iteration log's wall times
+        # mean over iterations 10..end, from the iteration log's wall times.  An
+        # iteration's time is set mostly by its number of factorizations (one,
+        # or more with inertia corrections), so the log is also split by that
+        # count and by the precision of the factors that made the step.
         names, hist = lib.history(0)
-        it_ms = hist[10:, list(names).index("ms")] if hist.shape[0] > 10 else hist[:, -1]
-        if it_ms.size:
-            tts[name]["iteration_ms_median_10_end"] = float(np.median(it_ms))
-            tts[name]["iterations_per_s_median_10_end"] = 1e3 / float(np.median(it_ms))
+        names = list(names)
+        h = hist[10:] if hist.shape[0] > 10 else hist
+        if h.shape[0]:
+            it_ms = h[:, names.index("ms")]
+            nf = h[:, names.index("factorizations")].astype(int)
+            pr = h[:, names.index("precision")].astype(int)
+            tts[name]["iteration_ms_mean_10_end"] = float(it_ms.mean())
+            tts[name]["iterations_per_s_mean_10_end"] = 1e3 / float(it_ms.mean())
+            tts[name]["iteration_ms_median_by_factorizations"] = {
+                str(k): {"iterations": int((nf == k).sum()),
+                         "ms_median": float(np.median(it_ms[nf == k]))}
+                for k in sorted(set(nf.tolist()))}
+            tts[name]["iteration_ms_mean_by_precision"] = {
+                lab: {"iterations": int((pr == v).sum()), "ms_mean": float(it_ms[pr == v].mean()),
+                      "refine_steps_mean": float(h[pr == v, names.index("refine_steps")].mean())}
+                for lab, v in (("fp32", P.PREC_MIXED), ("fp64", P.PREC_FP64)) if (pr == v).any()}
     if idx == CONFIG_IDX and args.tts != "none":
         tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
                              "fp64": gpu_tts_118(P, torch, P.PREC_FP64),
