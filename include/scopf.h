@@ -331,7 +331,7 @@ int scopf_dense_ldlt_solve(const double *S, int32_t n, const double *b, double *
  * Scratch is a static per-device array sized for n <= 768 (about 4.7 MB,
  * held by every GPU that loads the library until exit); n > 768 returns
  * SCOPF_ERR_INVALID_ARG.  The first call on a device looks up the array's
- * device address (cudaGetSymbolAddress); make it before any stream capture.
+ * device address (cudaGetSymbolAddress).
  * That address is cached per device ordinal for the life of the process: it
  * goes stale if the caller resets the device (cudaDeviceReset) and goes on
  * using the library.  Concurrent first calls from several host threads are

@@ -14,10 +14,9 @@
 // (about 4.7 MB for the maximum order 768).  Every GPU that loads this
 // library holds it until the process exits.  Its device address is looked
 // up once per device (cudaGetSymbolAddress, with that device current) by the
-// first call made on that device; make that first call before any stream
-// capture.  The address is cached per device ordinal for the life of the
-// process, so it goes stale if the caller resets the device
-// (cudaDeviceReset) and keeps using the library.  All calls on a device
+// first call made on that device.  The address is cached per device ordinal
+// for the life of the process, so it goes stale if the caller resets the
+// device (cudaDeviceReset) and keeps using the library.  All calls on a device
 // share the array and it keeps the last call's contents; each call
 // synchronises its stream before returning, so calls can only overlap on the
 // GPU when several host threads call at once (on different streams) --
