@@ -427,14 +427,28 @@ __device__ __forceinline__ void panel_update_packed(T (*M)[S], int f, int np, in
     }
 }
 
+// Column index u of entry e when the lower triangle of an m-column block is
+// numbered column by column (column u holds m - u entries and starts at
+// u m - u (u - 1) / 2): the root of the quadratic, then corrected in integer
+// arithmetic.  e < m (m + 1) / 2.
+__device__ __forceinline__ int packed_column(int e, int m) {
+    const float b = 2.0f * (float)m + 1.0f;
+    int u = (int)(0.5f * (b - sqrtf(fmaxf(b * b - 8.0f * (float)e, 0.0f))));
+    u = min(max(u, 0), m - 1);
+    while (u > 0 && u * m - u * (u - 1) / 2 > e) u--;
+    while (u + 1 < m && (u + 1) * m - (u + 1) * u / 2 <= e) u++;
+    return u;
+}
+
 // Trailing update U -= L21 D L21' of a front held in a shared tile with
 // row stride S (lower triangle; columns < np hold L, the diagonal D), for all
 // entries np <= j <= i < f.  W = L D is first written to the unused upper
-// triangle (W[c][j] at tile[c][j], c < np <= j); then columns are folded in
-// pairs (np + k with f - 1 - k, m + 1 entries together, m = f - np) and the
-// lanes take one entry each, so every multiply-add of the update is done by
-// an active lane: np multiply-adds per entry, no triangular idle lanes.
-template <typename T, int S, int R>
+// triangle (W[c][j] at tile[c][j], c < np <= j); then the m (m + 1) / 2
+// entries (m = f - np) are numbered column by column and dealt to the lanes
+// 32 at a time, one entry per lane: np multiply-adds per entry and no idle
+// lanes but in the last round (B300's FP64 pipe charges every warp
+// instruction in full, whatever its active lanes).
+template <typename T, int S>
 __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int lane) {
     const int m = f - np;
     if (np == 0 || m <= 0) return;
@@ -446,33 +460,59 @@ __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int
             for (int j = np + lane; j < f; j += 32) tile[c][j] = tile[j][c] * d;
         }
     __syncwarp();
-    for (int k = 0; 2 * k < m; k++) {
-        const int a = np + k, la = m - k, b = f - 1 - k;
-        const int lb = b > a ? k + 1 : 0;
-#pragma unroll
-        for (int r = 0; r < R; r++) {
-            const int e = lane + 32 * r;
-            int i = -1, j = 0;
-            if (e < la) {
-                i = a + e;
-                j = a;
-            } else if (e < la + lb) {
-                i = b + (e - la);
-                j = b;
-            }
-            if (i >= 0) {
-                T acc = (T)0;
+    const int total = m * (m + 1) / 2;
+    for (int e = lane; e < total; e += 32) {
+        const int u = packed_column(e, m);
+        const int j = np + u;
+        const int i = j + (e - (u * m - u * (u - 1) / 2));
+        T acc = (T)0;
 #pragma unroll 4
-                for (int c = 0; c < np; c++) acc += tile[i][c] * tile[c][j];
-                tile[i][j] -= acc;
-            }
-        }
+        for (int c = 0; c < np; c++) acc += tile[i][c] * tile[c][j];
+        tile[i][j] -= acc;
     }
     __syncwarp();
 }
-template <typename T>
-__device__ __forceinline__ void trailing_update_tile(T (*tile)[33], int f, int np, int lane) {
-    trailing_update<T, 33, 1>(tile, f, np, lane);
+
+// FP64 extend-add of one child's update block (nu x nu, lower triangle,
+// column stride fc) into a shared front with row stride S.  The entries are
+// numbered column by column and dealt to the lanes 32 at a time, so every
+// issued FP64 add updates an entry; four rounds' loads are in flight
+// together.  rel[i] of the child's update row i is held by lane i % 32 (r0
+// for i < 32, r1 for i >= 32: TWO = nu may exceed 32).  A child's
+// destinations are distinct, and the children are added one after another,
+// so every entry's sum keeps the child order.
+template <int S, bool TWO>
+__device__ __forceinline__ void extend_add_packed(double (*M)[S], const double *__restrict__ Fc,
+                                                  int fc, int nu, int r0, int r1, int lane) {
+    const int total = nu * (nu + 1) / 2;
+    for (int e0 = 0; e0 < total; e0 += 128) {
+        int di[4], dj[4];
+        double v[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            const int e = e0 + 32 * k + lane;
+            int i = 0, j = 0;
+            if (e < total) {
+                j = packed_column(e, nu);
+                i = j + (e - (j * nu - j * (j - 1) / 2));
+            }
+            di[k] = i;
+            dj[k] = j;
+            v[k] = e < total ? Fc[(int64_t)j * fc + i] : 0.0;
+        }
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            int ri = __shfl_sync(0xffffffffu, r0, di[k] & 31);
+            int rj = __shfl_sync(0xffffffffu, r0, dj[k] & 31);
+            if (TWO) {
+                const int ri1 = __shfl_sync(0xffffffffu, r1, di[k] & 31);
+                const int rj1 = __shfl_sync(0xffffffffu, r1, dj[k] & 31);
+                if (di[k] >= 32) ri = ri1;
+                if (dj[k] >= 32) rj = rj1;
+            }
+            if (e0 + 32 * k + lane < total) M[ri][rj] += v[k];
+        }
+    }
 }
 
 // A front with f <= 32 rows held in one warp's shared-memory tile (lane i
@@ -500,25 +540,10 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         const T *Fc = fronts + c.front_off + (int64_t)c.npc * c.fc + c.npc;
         const int fc = c.fc, nu = fc - c.npc;
         const int myrel = lane < nu ? F.rel[c.rel_off + lane] : 0;
-        if (sizeof(T) == 8 && nu <= 16) {
-            // FP64 and a short update block: the two half-warps take
-            // alternate columns (lane = 16 h + row), so each FP64 add
-            // instruction covers two columns (the pipe charges the whole
-            // warp per instruction).  A child's destinations are distinct.
-            const int h = lane >> 4, rw = lane & 15;
-            const int relr = __shfl_sync(0xffffffffu, myrel, rw);
-            T v[8];
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int jj = 2 * k + h;
-                v[k] = (jj < nu && rw >= jj && rw < nu) ? Fc[(int64_t)jj * fc + rw] : (T)0;
-            }
-#pragma unroll
-            for (int k = 0; k < 8; k++) {
-                const int jj = 2 * k + h;
-                const int rj = __shfl_sync(0xffffffffu, myrel, jj);
-                if (jj < nu && rw >= jj && rw < nu) tile[relr][rj] += v[k];
-            }
+        if constexpr (sizeof(T) == 8) {
+            // FP64: the update block's entries dealt to the lanes (the pipe
+            // charges the whole warp per instruction)
+            extend_add_packed<33, false>(tile, Fc, fc, nu, myrel, 0, lane);
             __syncwarp();
             continue;
         }
@@ -574,7 +599,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         }
         __syncwarp();
     }
-    trailing_update_tile<T>(tile, f, np, lane);
+    trailing_update<T, 33>(tile, f, np, lane);
     for (int j = 0; j < f; j++)
         if (lane < f) Fr[(int64_t)j * f + lane] = tile[lane][j];
 }
@@ -610,6 +635,12 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
         const T *Fc = fronts + c.front_off + (int64_t)c.npc * fc + c.npc;
         const int32_t *rel = F.rel + c.rel_off;
         const int r0 = lane < nu ? rel[lane] : 0, r1 = lane + 32 < nu ? rel[lane + 32] : 0;
+        if constexpr (sizeof(T) == 8) {
+            // FP64: the update block's entries dealt to the lanes
+            extend_add_packed<kMedF + 1, true>(M, Fc, fc, nu, r0, r1, lane);
+            __syncwarp();
+            continue;
+        }
         // kMB columns' loads in flight per step; column jj's map entry comes
         // from the lane holding it (a shuffle)
         constexpr int kMB = sizeof(T) == 4 ? 16 : 8;
@@ -652,10 +683,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
                 M[i][c] = a * dinv;
             }
             __syncwarp();
-            for (int j = c + 1; j < np; j++) {   // panel columns only
-                const T lj = M[c][j];
-                for (int i = j + lane; i < f; i += 32) M[i][j] -= M[i][c] * lj;
-            }
+            panel_update_packed<T, kMedF + 1>(M, f, np, c, lane);   // panel columns only
             __syncwarp();
             continue;
         }
@@ -676,7 +704,7 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
         }
         __syncwarp();
     }
-    trailing_update<T, kMedF + 1, 2>(M, f, np, lane);
+    trailing_update<T, kMedF + 1>(M, f, np, lane);
     for (int j = 0; j < f; j++) {
         T *colj = Fr + (int64_t)j * f;
         if (i0 < f) colj[i0] = M[i0][j];
