@@ -473,17 +473,18 @@ __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int
     __syncwarp();
 }
 
-// FP64 extend-add of one child's update block (nu x nu, lower triangle,
-// column stride fc) into a shared front with row stride S.  The entries are
-// numbered column by column and dealt to the lanes 32 at a time, so every
-// issued FP64 add updates an entry; four rounds' loads are in flight
-// together.  rel[i] of the child's update row i is held by lane i % 32 (r0
-// for i < 32, r1 for i >= 32: TWO = nu may exceed 32).  A child's
-// destinations are distinct, and the children are added one after another,
-// so every entry's sum keeps the child order.
-template <int S, bool TWO>
-__device__ __forceinline__ void extend_add_packed(double (*M)[S], const double *__restrict__ Fc,
-                                                  int fc, int nu, int r0, int r1, int lane) {
+// FP64 extend-add of one child's update block (nu <= 32 rows, lower
+// triangle, column stride fc) into a warp's 32-row shared tile.  The entries
+// are numbered column by column and dealt to the lanes 32 at a time, so
+// every issued FP64 add updates an entry; four rounds' loads are in flight
+// together.  rel[i] of the child's update row i is held by lane i.  A
+// child's destinations are distinct, and the children are added one after
+// another, so every entry's sum keeps the child order.  (The 64-row fronts
+// keep the column-by-column extend-add and panel update: with one warp per
+// CTA and few CTAs per SM they are latency-bound, and this index arithmetic
+// lengthens each round; measured, their FP64 kernel took 8% longer with it.)
+__device__ __forceinline__ void extend_add_packed(double (*M)[33], const double *__restrict__ Fc,
+                                                  int fc, int nu, int rel, int lane) {
     const int total = nu * (nu + 1) / 2;
     for (int e0 = 0; e0 < total; e0 += 128) {
         int di[4], dj[4];
@@ -502,14 +503,8 @@ __device__ __forceinline__ void extend_add_packed(double (*M)[S], const double *
         }
 #pragma unroll
         for (int k = 0; k < 4; k++) {
-            int ri = __shfl_sync(0xffffffffu, r0, di[k] & 31);
-            int rj = __shfl_sync(0xffffffffu, r0, dj[k] & 31);
-            if (TWO) {
-                const int ri1 = __shfl_sync(0xffffffffu, r1, di[k] & 31);
-                const int rj1 = __shfl_sync(0xffffffffu, r1, dj[k] & 31);
-                if (di[k] >= 32) ri = ri1;
-                if (dj[k] >= 32) rj = rj1;
-            }
+            const int ri = __shfl_sync(0xffffffffu, rel, di[k]);
+            const int rj = __shfl_sync(0xffffffffu, rel, dj[k]);
             if (e0 + 32 * k + lane < total) M[ri][rj] += v[k];
         }
     }
@@ -543,7 +538,7 @@ __device__ void eliminate_front_tile(const DevFront &F, T *__restrict__ fronts, 
         if constexpr (sizeof(T) == 8) {
             // FP64: the update block's entries dealt to the lanes (the pipe
             // charges the whole warp per instruction)
-            extend_add_packed<33, false>(tile, Fc, fc, nu, myrel, 0, lane);
+            extend_add_packed(tile, Fc, fc, nu, myrel, lane);
             __syncwarp();
             continue;
         }
@@ -635,12 +630,6 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
         const T *Fc = fronts + c.front_off + (int64_t)c.npc * fc + c.npc;
         const int32_t *rel = F.rel + c.rel_off;
         const int r0 = lane < nu ? rel[lane] : 0, r1 = lane + 32 < nu ? rel[lane + 32] : 0;
-        if constexpr (sizeof(T) == 8) {
-            // FP64: the update block's entries dealt to the lanes
-            extend_add_packed<kMedF + 1, true>(M, Fc, fc, nu, r0, r1, lane);
-            __syncwarp();
-            continue;
-        }
         // kMB columns' loads in flight per step; column jj's map entry comes
         // from the lane holding it (a shuffle)
         constexpr int kMB = sizeof(T) == 4 ? 16 : 8;
@@ -683,7 +672,10 @@ __device__ void eliminate_front_medium(const DevFront &F, T *__restrict__ fronts
                 M[i][c] = a * dinv;
             }
             __syncwarp();
-            panel_update_packed<T, kMedF + 1>(M, f, np, c, lane);   // panel columns only
+            for (int j = c + 1; j < np; j++) {   // panel columns only
+                const T lj = M[c][j];
+                for (int i = j + lane; i < f; i += 32) M[i][j] -= M[i][c] * lj;
+            }
             __syncwarp();
             continue;
         }
