@@ -482,7 +482,7 @@ __device__ __forceinline__ void trailing_update(T (*tile)[S], int f, int np, int
 // another, so every entry's sum keeps the child order.  (The 64-row fronts
 // keep the column-by-column extend-add and panel update: with one warp per
 // CTA and few CTAs per SM they are latency-bound, and this index arithmetic
-// lengthens each round; measured, their FP64 kernel took 8% longer with it.)
+// lengthens each round; measured, their FP64 kernel took 16% longer with it.)
 __device__ __forceinline__ void extend_add_packed(double (*M)[33], const double *__restrict__ Fc,
                                                   int fc, int nu, int rel, int lane) {
     const int total = nu * (nu + 1) / 2;
