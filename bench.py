@@ -362,6 +362,40 @@ def run_reference(args):
 PHASE_KEYS = ("factor", "solve", "assemble", "residual", "schur", "front_init", "ipm")
 
 
+def iteration_stats(names, hist, prec_fp32, prec_fp64, skip=10):
+    """The metric's per-iteration rate from the iteration log of one solve:
+    IPM iterations (each one Newton step with its inertia corrections,
+    refinement and line search) per second over iterations skip..end, from
+    the log's wall times; mean and median.  An iteration's time is set mostly
+    by its number of factorizations (one, or more with inertia corrections),
+    so the log is also split by that count and by the precision of the
+    factors that made the step.  The median falls in one of the modes (one
+    factorization or two, whichever holds just over half of the iterations)."""
+    import numpy as np
+    names = list(names)
+    h = hist[skip:] if hist.shape[0] > skip else hist
+    if not h.shape[0]:
+        return {}
+    it_ms = h[:, names.index("ms")]
+    nf = h[:, names.index("factorizations")].astype(int)
+    pr = h[:, names.index("precision")].astype(int)
+    rs = h[:, names.index("refine_steps")]
+    return {
+        "iteration_ms_mean_10_end": float(it_ms.mean()),
+        "iterations_per_s_mean_10_end": 1e3 / float(it_ms.mean()),
+        "iteration_ms_median_10_end": float(np.median(it_ms)),
+        "iterations_per_s_median_10_end": 1e3 / float(np.median(it_ms)),
+        "iteration_ms_median_by_factorizations": {
+            str(k): {"iterations": int((nf == k).sum()),
+                     "ms_median": float(np.median(it_ms[nf == k]))}
+            for k in sorted(set(nf.tolist()))},
+        "iteration_ms_mean_by_precision": {
+            lab: {"iterations": int((pr == v).sum()), "ms_mean": float(it_ms[pr == v].mean()),
+                  "refine_steps_mean": float(rs[pr == v].mean())}
+            for lab, v in (("fp32", prec_fp32), ("fp64", prec_fp64)) if (pr == v).any()},
+    }
+
+
 def dominant_phase(phases, solves):
     """The phase with the largest total time.  The phase timers see only the
     first block solve of each kkt solve (the refinement's solves run inside
@@ -522,33 +556,8 @@ def run_ours(args):
                      "kkt_error": r["kkt_error"], "feas_rt": r["feas_rt"],
                      "host_round_trips_per_iter": r["host_round_trips"] / max(1, r["inner_iters"]),
                      "graph_iters": r["graph_iters"]}
-        # the metric's per-iteration rate: IPM iterations (each one Newton step
-        # with its inertia corrections, refinement and line search) per second,
-        # mean over iterations 10..end, from the iteration log's wall times.  An
-        # iteration's time is set mostly by its number of factorizations (one,
-        # or more with inertia corrections), so the log is also split by that
-        # count and by the precision of the factors that made the step.
         names, hist = lib.history(0)
-        names = list(names)
-        h = hist[10:] if hist.shape[0] > 10 else hist
-        if h.shape[0]:
-            it_ms = h[:, names.index("ms")]
-            nf = h[:, names.index("factorizations")].astype(int)
-            pr = h[:, names.index("precision")].astype(int)
-            tts[name]["iteration_ms_mean_10_end"] = float(it_ms.mean())
-            tts[name]["iterations_per_s_mean_10_end"] = 1e3 / float(it_ms.mean())
-            # the median as well (it falls in one of the modes: one factorization
-            # or two, whichever holds just over half of the iterations)
-            tts[name]["iteration_ms_median_10_end"] = float(np.median(it_ms))
-            tts[name]["iterations_per_s_median_10_end"] = 1e3 / float(np.median(it_ms))
-            tts[name]["iteration_ms_median_by_factorizations"] = {
-                str(k): {"iterations": int((nf == k).sum()),
-                         "ms_median": float(np.median(it_ms[nf == k]))}
-                for k in sorted(set(nf.tolist()))}
-            tts[name]["iteration_ms_mean_by_precision"] = {
-                lab: {"iterations": int((pr == v).sum()), "ms_mean": float(it_ms[pr == v].mean()),
-                      "refine_steps_mean": float(h[pr == v, names.index("refine_steps")].mean())}
-                for lab, v in (("fp32", P.PREC_MIXED), ("fp64", P.PREC_FP64)) if (pr == v).any()}
+        tts[name].update(iteration_stats(names, hist, P.PREC_MIXED, P.PREC_FP64))
     if idx == CONFIG_IDX and args.tts != "none":
         tts["118bus_k32"] = {"mixed": gpu_tts_118(P, torch, P.PREC_MIXED),
                              "fp64": gpu_tts_118(P, torch, P.PREC_FP64),
